@@ -1,0 +1,294 @@
+"""TEST INFRASTRUCTURE -- the serial FP64 CPU oracle of the PP-WCNS-IS fractional
+algorithm (Wong, Angel & Kiris, arXiv 2208.04488).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+may import this package. It is independent of the CUDA library: it shares no
+source, header, constant table or helper with ``paper_2208_04488_gb300``, and
+the product path never calls it.
+
+The arithmetic lives in ``hrm_oracle.cpp`` (plain C++17, serial, FP64,
+``-O2 -ffp-contract=off``); this module only builds and loads it with ctypes.
+A second build (``-DOR_COUNT``) counts the floating-point operations the
+method performs, which the roofline figures use as algorithmic work.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hrm_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LOCK = threading.Lock()
+
+MAXN = 4
+
+
+def _lib_path(count: bool) -> str:
+    return os.path.join(_BUILD, "liboracle_count.so" if count else "liboracle.so")
+
+
+def build(force: bool = False) -> None:
+    """Compile both oracle shared libraries with gcc (seconds)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    for count in (False, True):
+        out = _lib_path(count)
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+            continue
+        cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", _SRC, "-o", out + ".tmp"]
+        if count:
+            cmd.insert(1, "-DOR_COUNT")
+        subprocess.run(cmd, check=True)
+        os.replace(out + ".tmp", out)
+
+
+class Fluid(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("D", ctypes.c_int32), ("liq", ctypes.c_int32),
+                ("pad", ctypes.c_int32),
+                ("gamma", ctypes.c_double * MAXN), ("pinf", ctypes.c_double * MAXN),
+                ("cv", ctypes.c_double * MAXN), ("q", ctypes.c_double * MAXN)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("limiters", ctypes.c_int32), ("blend", ctypes.c_int32),
+                ("relax_mode", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("integrator", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("pad1", ctypes.c_int32), ("pad2", ctypes.c_int32),
+                ("eps_ar", ctypes.c_double), ("eps_a", ctypes.c_double),
+                ("eps_rhoe", ctypes.c_double), ("hs_ar", ctypes.c_double),
+                ("hs_a", ctypes.c_double), ("hs_rc2", ctypes.c_double),
+                ("hs_rhoe", ctypes.c_double), ("weno_eps", ctypes.c_double),
+                ("Cs", ctypes.c_double), ("q_sensor", ctypes.c_double)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("n", ctypes.c_int64 * 3), ("dx", ctypes.c_double * 3),
+                ("bc", ctypes.c_int32 * 6)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_libs: dict = {}
+
+
+def lib(count: bool = False):
+    with _LOCK:
+        if count in _libs:
+            return _libs[count]
+        path = _lib_path(count)
+        if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+            build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        L.or_params_default.argtypes = [P(Params)]
+        L.or_prim_cell.argtypes = [P(Fluid), _DP, _DP, _DP]
+        L.or_cons_cell.argtypes = [P(Fluid), _DP, _DP, _DP]
+        L.or_weno_left.argtypes = [_DP, ctypes.c_double, _DP]
+        L.or_weno_left.restype = ctypes.c_double
+        L.or_hllc.argtypes = [P(Fluid), ctypes.c_int, _DP, _DP, _DP]
+        L.or_hllc.restype = ctypes.c_double
+        L.or_sensor.argtypes = [_DP]
+        L.or_sensor.restype = ctypes.c_double
+        L.or_face.argtypes = [P(Fluid), P(Params), ctypes.c_int, ctypes.c_double, _DP, _DP, _DP, _DP]
+        L.or_rhs.argtypes = [P(Fluid), P(Params), P(Grid), _DP, _DP, _DP]
+        L.or_relax_cell.argtypes = [P(Fluid), _DP, _DP]
+        L.or_relax.argtypes = [P(Fluid), P(Grid), _DP]
+        L.or_dt.argtypes = [P(Fluid), P(Grid), _DP, ctypes.c_double, _DP]
+        L.or_dt.restype = ctypes.c_double
+        L.or_lambdas.argtypes = [P(Fluid), P(Grid), _DP, ctypes.c_double, _DP]
+        L.or_step.argtypes = [P(Fluid), P(Params), P(Grid), _DP, ctypes.c_double, ctypes.c_int]
+        L.or_admissibility.argtypes = [P(Fluid), P(Grid), _DP, P(ctypes.c_int64)]
+        L.or_c4eq_cell.argtypes = [P(Fluid), _DP, _DP]
+        L.or_ic_from_prim.argtypes = [P(Fluid), ctypes.c_int64, _DP, _DP]
+        if count:
+            L.or_count_reset.argtypes = []
+            L.or_count_get.argtypes = [P(ctypes.c_ulonglong)]
+        _libs[count] = L
+        return L
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_DP)
+
+
+# ---------------------------------------------------------------- descriptions
+
+def make_fluid(gamma, pinf, cv, q=None, D=1, liq=None) -> Fluid:
+    n = len(gamma)
+    assert 1 <= n <= MAXN
+    f = Fluid()
+    f.N, f.D = n, D
+    if liq is None:
+        liq = next((k for k in range(n) if pinf[k] > 0), 0)
+    f.liq = liq
+    for k in range(n):
+        f.gamma[k] = gamma[k]
+        f.pinf[k] = pinf[k]
+        f.cv[k] = cv[k]
+        f.q[k] = 0.0 if q is None else q[k]
+    return f
+
+
+def make_params(**kw) -> Params:
+    p = Params()
+    lib().or_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def make_grid(n, dx, bc=None) -> Grid:
+    g = Grid()
+    g.D = len(n)
+    for d in range(3):
+        g.n[d] = n[d] if d < len(n) else 1
+        g.dx[d] = dx[d] if d < len(n) else 1.0
+    bc = bc or [0] * (2 * len(n))
+    for i in range(6):
+        g.bc[i] = bc[i] if i < len(bc) else 0
+    return g
+
+
+def fluid_dict(f: Fluid) -> dict:
+    return {"gamma": list(f.gamma)[:f.N], "pinf": list(f.pinf)[:f.N],
+            "cv": list(f.cv)[:f.N], "q": list(f.q)[:f.N], "D": f.D, "liq": f.liq}
+
+
+# ---------------------------------------------------------------- calls
+
+def prim_cell(f: Fluid, W):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    M = 2 * f.N + f.D
+    V = np.zeros(M)
+    out = np.zeros(4)
+    lib().or_prim_cell(ctypes.byref(f), _ptr(W), _ptr(V), _ptr(out))
+    return V, {"rho": out[0], "c": out[1], "rc2": out[2], "rhoe": out[3]}
+
+
+def cons_cell(f: Fluid, V):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    W = np.zeros_like(V)
+    out = np.zeros(3)
+    lib().or_cons_cell(ctypes.byref(f), _ptr(V), _ptr(W), _ptr(out))
+    return W, {"rho": out[0], "c": out[1], "E": out[2]}
+
+
+def weno_left(u, eps=1e-15):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    om = np.zeros(4)
+    v = lib().or_weno_left(_ptr(u), eps, _ptr(om))
+    return v, om
+
+
+def hllc(f: Fluid, dir_, VL, VR):
+    VL = np.ascontiguousarray(VL, dtype=np.float64)
+    VR = np.ascontiguousarray(VR, dtype=np.float64)
+    G = np.zeros_like(VL)
+    s = lib().or_hllc(ctypes.byref(f), dir_, _ptr(VL), _ptr(VR), _ptr(G))
+    return G, s
+
+
+def sensor(u6):
+    u6 = np.ascontiguousarray(u6, dtype=np.float64)
+    return lib().or_sensor(_ptr(u6))
+
+
+def face(f: Fluid, p: Params, dir_, lam, W6):
+    W6 = np.ascontiguousarray(W6, dtype=np.float64)
+    M = 2 * f.N + f.D
+    assert W6.shape == (6, M)
+    Gm = np.zeros(M)
+    Gp = np.zeros(M)
+    diag = np.zeros(8 * M + 8)
+    lib().or_face(ctypes.byref(f), ctypes.byref(p), dir_, lam, _ptr(W6), _ptr(Gm), _ptr(Gp), _ptr(diag))
+    names = ["VL_weno", "VR_weno", "VL", "VR", "Gt", "GH", "Ghcs"]
+    d = {nm: diag[i * M:(i + 1) * M].copy() for i, nm in enumerate(names)}
+    t = diag[7 * M:]
+    d.update(ut=t[0], uH=t[1], uhcs=t[2], sig=t[3], hsL=int(t[4]), hsR=int(t[5]), flux_flags=int(t[6]))
+    return Gm, Gp, d
+
+
+def rhs(f: Fluid, p: Params, g: Grid, W, lam):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    R = np.zeros_like(W)
+    lam = np.ascontiguousarray(np.resize(np.asarray(lam, dtype=np.float64), 3))
+    lib().or_rhs(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), _ptr(lam), _ptr(R))
+    return R
+
+
+def relax_cell(f: Fluid, W):
+    W = np.array(W, dtype=np.float64)
+    pT = np.zeros(2)
+    lib().or_relax_cell(ctypes.byref(f), _ptr(W), _ptr(pT))
+    return W, pT[0], pT[1]
+
+
+def relax(f: Fluid, g: Grid, W):
+    W = np.array(W, dtype=np.float64, order="C")
+    lib().or_relax(ctypes.byref(f), ctypes.byref(g), _ptr(W))
+    return W
+
+
+def dt(f: Fluid, g: Grid, W, cfl):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    tau = np.zeros(3)
+    d = lib().or_dt(ctypes.byref(f), ctypes.byref(g), _ptr(W), cfl, _ptr(tau))
+    return d, tau[:g.D].copy()
+
+
+def lambdas(f: Fluid, g: Grid, W, dt_):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    lam = np.zeros(3)
+    lib().or_lambdas(ctypes.byref(f), ctypes.byref(g), _ptr(W), dt_, _ptr(lam))
+    return lam
+
+
+def step(f: Fluid, p: Params, g: Grid, W, dt_, nsteps=1, count=False):
+    W = np.array(W, dtype=np.float64, order="C")
+    L = lib(count)
+    if count:
+        L.or_count_reset()
+    L.or_step(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), dt_, nsteps)
+    if count:
+        out = (ctypes.c_ulonglong * 5)()
+        L.or_count_get(out)
+        return W, {"add": out[0], "mul": out[1], "div": out[2], "sqrt": out[3], "tanh": out[4]}
+    return W
+
+
+def admissibility(f: Fluid, g: Grid, W):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    c = (ctypes.c_int64 * 4)()
+    lib().or_admissibility(ctypes.byref(f), ctypes.byref(g), _ptr(W), c)
+    return [int(x) for x in c]
+
+
+def c4eq_cell(f: Fluid, W):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    out = np.zeros(4 + MAXN)
+    lib().or_c4eq_cell(ctypes.byref(f), _ptr(W), _ptr(out))
+    return {"c4": out[0], "p": out[1], "T": out[2], "Gamma": out[3], "Psi": out[4:4 + f.N].copy()}
+
+
+def ic_from_prim(f: Fluid, prim):
+    """Conservative initial state W[M, ncells] from primitive planes
+    (alpha_1..alpha_{N-1}, u_d, p, T) in p-T equilibrium."""
+    prim = np.ascontiguousarray(prim, dtype=np.float64)
+    nc = prim.shape[1]
+    W = np.zeros((2 * f.N + f.D, nc))
+    lib().or_ic_from_prim(ctypes.byref(f), nc, _ptr(prim), _ptr(W))
+    return W
+
+
+def setup(problem):
+    """Oracle descriptions (fluid, grid) and the initial W of a problem from
+    paper_2208_04488_gb300.problems."""
+    f = make_fluid(problem.gamma, problem.pinf, problem.cv, problem.q, D=problem.D, liq=problem.liq)
+    g = make_grid(problem.n, problem.dx, problem.bc)
+    return f, g, ic_from_prim(f, problem.prim)

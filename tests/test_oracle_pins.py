@@ -1,0 +1,382 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows. None of them compares the oracle with
+itself or with the CUDA path: the expected values are the paper's printed
+numbers, closed forms, textbook results or invariants.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2208_04488_gb300 import problems as P
+from tests import exact_riemann as ER
+
+
+def _fluid(orc, fl, D=1):
+    gamma, pinf, cv, q = P._species(fl)
+    return orc.make_fluid(gamma, pinf, cv, q, D=D)
+
+
+def _W_from_prim(orc, f, prim_cols):
+    prim = np.asarray(prim_cols, dtype=np.float64)
+    if prim.ndim == 1:
+        prim = prim[:, None]
+    return orc.ic_from_prim(f, prim)
+
+
+# ---------------------------------------------------------------- initial-condition tables
+
+def test_ic_table_temporal_convergence(orc):
+    """Table exact_1D_convergence (Sec. 5.1): rho_1, rho_2 at 101325 Pa, 298 K."""
+    f = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR])
+    W = _W_from_prim(orc, f, [0.5, 0.0, 101325.0, 298.0])
+    assert W[0, 0] / 0.5 == pytest.approx(1022.7724412751677, rel=1e-15)
+    assert W[1, 0] / 0.5 == pytest.approx(1.1817862212832324, rel=1e-15)
+
+
+def test_ic_table_shock_tubes(orc):
+    """Tables IC_1D_gas_liquid_shock_tube_problem and IC_1D_extreme_... (Sec. 5.4, 5.5)."""
+    for extreme, ar2_left in ((False, 5.2511071660640894e-5), (True, 9.7235797802400965e-5)):
+        pr = P.shock_tube_1d_paper(n=100, extreme=extreme)
+        f, g, W = orc.setup(pr)
+        assert W[0, 0] == pytest.approx(9.9999998999999991e2, rel=1e-15)
+        assert W[1, 0] == pytest.approx(ar2_left, rel=2e-9)
+        assert W[0, -1] == pytest.approx(1.7538240816326533e-4, rel=1e-14)
+        assert W[1, -1] == pytest.approx(1.9999999799999998e1, rel=1e-15)
+    pr = P.shock_tube_1d_paper(n=100)
+    # temperatures quoted in the text (Sec. 5.4, Sec. 5.5)
+    assert pr.extra["TL"] == pytest.approx(661.89, abs=0.005)
+    assert pr.extra["TR"] == pytest.approx(17.378, abs=0.0005)
+    assert P.shock_tube_1d_paper(n=10, extreme=True).extra["TL"] == pytest.approx(357448, abs=0.5)
+
+
+def test_ic_table_three_species_and_cylinder(orc):
+    """Tables IC_1D_extreme_shock_interface_interaction (Sec. 5.6) and
+    IC_2D_shock_water_cylinder (Sec. 5.7), rows at 101325 Pa and 298 K."""
+    f3 = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR, P.PAPER_SF6])
+    # 0.15 <= x < 0.3: water with minor air and SF6
+    W = _W_from_prim(orc, f3, [1 - 2e-8, 1e-8, 0.0, 1.01325e5, 298.0])
+    assert W[0, 0] == pytest.approx(1.0227724208197188e3, rel=1e-14)
+    assert W[1, 0] == pytest.approx(1.1817862212832324e-8, rel=1e-14)
+    assert W[2, 0] == pytest.approx(5.6328080779493768e-8, rel=1e-14)
+    # x >= 0.3: air/SF6 mixture
+    W = _W_from_prim(orc, f3, [1e-8, 0.5 - 5e-9, 0.0, 1.01325e5, 298.0])
+    assert W[0, 0] == pytest.approx(1.0227724412751677e-5, rel=1e-14)
+    assert W[1, 0] == pytest.approx(0.59089310473268508, rel=1e-14)
+    assert W[2, 0] == pytest.approx(2.8164040108106478, rel=1e-14)
+    f2 = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR], D=2)
+    W = _W_from_prim(orc, f2, [1e-8, 0.0, 0.0, 1.01325e5, 298.0])  # pre-shock air
+    assert W[0, 0] == pytest.approx(1.0227724412751677e-5, rel=1e-14)
+    assert W[1, 0] == pytest.approx(1.1817862094653702, rel=1e-14)
+    W = _W_from_prim(orc, f2, [1 - 1e-8, 0.0, 0.0, 1.01325e5, 298.0])  # water cylinder
+    assert W[0, 0] == pytest.approx(1.0227724310474432e3, rel=1e-14)
+    assert W[1, 0] == pytest.approx(1.1817862212832324e-8, rel=1e-7)
+    # acoustic problem, x >= -0.5 (Table IC_1D_acoustic_wave_propagation_problem):
+    # its air column matches the fluid table at 101325 Pa, 298 K; its water
+    # column (684.46 = 0.5 x 1368.92) does not, so only the air entry is a pin.
+    f1 = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR])
+    W = _W_from_prim(orc, f1, [0.5, 0.0, 101325.0, 298.0])
+    assert W[1, 0] == pytest.approx(0.5908931106416162, rel=1e-14)
+
+
+def test_ic_table_material_interface(orc):
+    """Table IC_1D_material_interface_advection_no_temp_diff (App. A)."""
+    pr = P.material_interface_1d(n=100)
+    f, g, W = orc.setup(pr)
+    mid = 50
+    assert W[0, mid] == pytest.approx(1.0227724310474432e3, rel=1e-14)
+    assert W[1, mid] == pytest.approx(1.1817862272214237e-8, rel=1e-7)
+    assert W[0, 0] == pytest.approx(1.0227724412751677e-5, rel=1e-14)
+    assert W[1, 0] == pytest.approx(1.1817862094653702, rel=1e-14)
+    assert W[2, 0] / (W[0, 0] + W[1, 0]) == pytest.approx(100.0, rel=1e-14)
+
+
+# ---------------------------------------------------------------- sound speeds
+
+def test_sound_speeds_water_air(orc):
+    """Sec. 5.3: at alpha = 0.5 (101325 Pa, 298 K) the five-equation sound
+    speed is 913.05 m/s and the four-equation HRM one 19.897 m/s; the HRM
+    sound speed at alpha_1 = 1e-8 is c_ref = 346.46 m/s."""
+    f = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR])
+    W = _W_from_prim(orc, f, [0.5, 0.0, 101325.0, 298.0])[:, 0]
+    V, o = orc.prim_cell(f, W)
+    assert o["c"] == pytest.approx(913.05, abs=0.005)
+    c4 = orc.c4eq_cell(f, W)
+    assert c4["c4"] == pytest.approx(19.897, abs=0.0005)
+    assert c4["p"] == pytest.approx(101325.0, rel=1e-12)
+    assert c4["T"] == pytest.approx(298.0, rel=1e-12)
+    W = _W_from_prim(orc, f, [1e-8, 0.0, 101325.0, 298.0])[:, 0]
+    assert orc.c4eq_cell(f, W)["c4"] == pytest.approx(346.46, abs=0.005)
+
+
+def test_c4eq_matches_finite_differences(orc):
+    """Eq. 4_eqn_sos with Psi_k and Gamma from the implicit derivative of the
+    p* quadratic equals central finite differences of the relaxed pressure
+    p(alpha_k rho_k, e) (Sec. 3 definitions of Psi_k and Gamma)."""
+    f = _fluid(orc, [P.BENCH_WATER, P.BENCH_AIR, P.BENCH_HELIUM])
+    prim, _ = P.random_admissible_states(3, 1, 20, seed=7)
+    W = orc.ic_from_prim(f, prim)
+    for c in range(W.shape[1]):
+        w = W[:, c].copy()
+        res = orc.c4eq_cell(f, w)
+        rho = w[:3].sum()
+        e = (w[4] - 0.5 * w[3] ** 2 / rho) / rho  # specific internal energy (q = 0)
+
+        def p_of(ar, e_):
+            ww = w.copy()
+            ww[:3] = ar
+            r = ar.sum()
+            ww[3] = r * (w[3] / rho)
+            ww[4] = r * e_ + 0.5 * ww[3] ** 2 / r
+            return orc.relax_cell(f, ww)[1]
+
+        # central differences over a range of steps; the best one (truncation vs
+        # round-off) must agree to 1e-6
+        for k in range(3):
+            errs = []
+            for rel in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+                h = rel * min(w[k], rho)
+                ap, am = w[:3].copy(), w[:3].copy()
+                ap[k] += h
+                am[k] -= h
+                fd = (p_of(ap, e) - p_of(am, e)) / (2 * h)
+                errs.append(abs(fd / res["Psi"][k] - 1.0))
+            assert errs and min(errs) < 1e-6, (k, errs)
+        errs = []
+        for rel in (1e-3, 1e-4, 1e-5, 1e-6):
+            he = rel * e
+            fdG = (p_of(w[:3], e + he) - p_of(w[:3], e - he)) / (2 * he) / rho
+            errs.append(abs(fdG / res["Gamma"] - 1.0))
+        assert min(errs) < 1e-6
+
+
+# ---------------------------------------------------------------- WENO-IS (App. C)
+
+def test_weno_linear_and_quadratic_exact(orc):
+    """Linear and quadratic data have tau_5 = 0, so the weights are the linear
+    d_k and the scheme returns the 5-point interpolant: exact at x_{i+1/2}."""
+    x = np.arange(-2, 3, dtype=float)
+    for coef in ([0.0, 2.0, 1.5], [3.0, -1.0, 0.0], [1.0, 0.0, 0.0]):
+        u = coef[0] * x ** 2 + coef[1] * x + coef[2]
+        v, om = orc.weno_left(u)
+        exact = coef[0] * 0.25 + coef[1] * 0.5 + coef[2]
+        assert v == pytest.approx(exact, rel=1e-14, abs=1e-14)
+        np.testing.assert_allclose(om, [15 / 32, 5 / 32, 5 / 16, 1 / 16], rtol=1e-14)
+
+
+def test_weno_linear_weights_form_lagrange_interpolant(orc):
+    """sum_k d_k u^k equals the 5-point Lagrange interpolant at x_{i+1/2}
+    (weights computed here by solving the Vandermonde system)."""
+    nodes = np.arange(-2, 3, dtype=float)
+    A = np.vander(nodes, 5, increasing=True).T
+    lag = np.linalg.solve(A, 0.5 ** np.arange(5))
+    np.testing.assert_allclose(lag, np.array([3, -20, 90, 60, -5]) / 128.0, atol=1e-14)
+    u = np.array([1.0, 2.0, 4.0, 8.0, 16.0])
+    # a constant offset of u (tau_5 changes only through differences) keeps this exact
+    v_lin = float(lag @ u)
+    v, _ = orc.weno_left(u, eps=1e300)  # huge eps -> eta_k = d_k
+    assert v == pytest.approx(v_lin, rel=1e-14)
+
+
+def test_weno_fifth_order_on_smooth_data(orc):
+    """Interpolation error of sin(x + 0.3) at x_{i+1/2} decreases as h^5 (App. C)."""
+    errs = []
+    for h in (0.2, 0.1, 0.05, 0.025):
+        xs = np.arange(-2, 3) * h
+        u = np.sin(xs + 0.3)
+        v, _ = orc.weno_left(u)
+        errs.append(abs(v - math.sin(0.5 * h + 0.3)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert min(rates) > 4.6, (errs, rates)
+
+
+def test_weno_essentially_non_oscillatory_at_jump(orc):
+    """A jump between x_i and x_{i+1}: the left-biased value stays on the
+    smooth side (the stencils S1, S3 that avoid the jump carry the weight)."""
+    v, om = orc.weno_left([0.0, 0.0, 0.0, 1.0, 1.0])
+    assert abs(v) < 1e-12
+    assert om[1] + om[3] > 1 - 1e-12
+
+
+# ---------------------------------------------------------------- HLLC (Sec. 4.1.1)
+
+def _two_species_V(orc, f, a1, u, p, T, v=None):
+    cols = [a1, u] + ([v] if v is not None else []) + [p, T]
+    W = _W_from_prim(orc, f, cols)[:, 0]
+    V, o = orc.prim_cell(f, W)
+    return W, V, o
+
+
+def test_hllc_equal_states_give_physical_flux(orc):
+    f = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR], D=2)
+    W, V, o = _two_species_V(orc, f, 0.3, 55.0, 2.0e5, 310.0, v=-12.0)
+    for d in (0, 1):
+        G, s = orc.hllc(f, d, V, V)
+        un = V[2 + d]
+        p = V[4]
+        expect = np.array([W[0] * un, W[1] * un, W[2] * un, W[3] * un, (W[4] + p) * un,
+                           V[5] * un])
+        expect[2 + d] += p
+        np.testing.assert_allclose(G, expect, rtol=1e-13, atol=1e-9)
+        assert s == pytest.approx(un, rel=1e-13)
+
+
+def test_hllc_resolves_isolated_contact(orc):
+    """Equal p and u, different composition: HLLC is exact for a contact, so
+    s_* = u and the flux is the upwind (left) physical flux."""
+    f = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR])
+    WL, VL, _ = _two_species_V(orc, f, 1 - 1e-8, 40.0, 1e6, 300.0)
+    WR, VR, _ = _two_species_V(orc, f, 1e-8, 40.0, 1e6, 900.0)
+    G, s = orc.hllc(f, 0, VL, VR)
+    assert s == pytest.approx(40.0, rel=1e-12)
+    expect = np.array([WL[0] * 40, WL[1] * 40, WL[2] * 40 + 1e6, (WL[3] + 1e6) * 40, VL[4] * 40])
+    np.testing.assert_allclose(G, expect, rtol=1e-11)
+
+
+def test_hllc_mirror_states_zero_mass_flux(orc):
+    """Mirror-symmetric states (u_L = -u_R): s_* = 0 and no mass crosses."""
+    f = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR])
+    _, VL, _ = _two_species_V(orc, f, 0.4, 120.0, 3e5, 300.0)
+    VR = VL.copy()
+    VR[2] = -VL[2]
+    G, s = orc.hllc(f, 0, VL, VR)
+    assert abs(s) < 1e-10
+    assert abs(G[0]) < 1e-9 * abs(VL[0] * VL[2]) and abs(G[1]) < 1e-9 * abs(VL[1] * VL[2])
+    assert abs(G[3]) < 1e-6
+
+
+def test_first_order_update_quasi_positive(orc):
+    """Sec. 4.1.2: with CFL <= 0.5 the half-cell updates W_i -+ 2 lambda (G^HLLC -+ F_i)
+    of random admissible pairs stay in script-G (positive partial densities,
+    bounded volume fractions, positive rho e~)."""
+    f = _fluid(orc, [P.BENCH_WATER, P.BENCH_AIR, P.BENCH_HELIUM])
+    params = orc.make_params(scheme=1, limiters=0)
+    prim, _ = P.random_admissible_states(3, 1, 400, seed=11)
+    # make neighbours strongly different: shuffle pressures over 5 decades
+    W = orc.ic_from_prim(f, prim)
+    rng = np.random.default_rng(3)
+    bad = 0
+    for t in range(200):
+        i, j = rng.integers(0, W.shape[1], 2)
+        Wi, Wj = W[:, i], W[:, j]
+        Vi, oi = orc.prim_cell(f, Wi)
+        Vj, oj = orc.prim_cell(f, Wj)
+        lam = 0.5 / max(abs(Vi[3]) + oi["c"], abs(Vj[3]) + oj["c"])
+        W6 = np.stack([Wi, Wi, Wi, Wj, Wj, Wj])
+        Gm, Gp, dg = orc.face(f, params, 0, lam, W6)
+        for Wn, G, sgn in ((Wi, Gm, -1.0), (Wj, Gp, 1.0)):
+            Vn, _ = orc.prim_cell(f, Wn)
+            F = np.array([Wn[0] * Vn[3], Wn[1] * Vn[3], Wn[2] * Vn[3], Wn[3] * Vn[3] + Vn[4],
+                          (Wn[4] + Vn[4]) * Vn[3], 0.0, 0.0])
+            Wh = Wn + sgn * 2 * lam * (G - F)
+            al = np.array([Wh[5], Wh[6], 1 - Wh[5] - Wh[6]])
+            rhoe = Wh[4] - 0.5 * Wh[3] ** 2 / Wh[:3].sum()
+            if (Wh[:3] < 0).any() or (al < -1e-14).any() or (al > 1 + 1e-14).any() or rhoe <= 0:
+                bad += 1
+    assert bad == 0
+
+
+# ---------------------------------------------------------------- relaxation (Sec. 4.2)
+
+def _relax_checks(orc, f, W):
+    N = f.N
+    out, ps, Ts = orc.relax_cell(f, W)
+    # conserved: partial densities, momentum, energy unchanged bit for bit
+    np.testing.assert_array_equal(out[:N + f.D + 1], W[:N + f.D + 1])
+    al = np.append(out[N + f.D + 1:], 1.0 - out[N + f.D + 1:].sum())
+    assert (al >= 0).all() and (al <= 1).all()
+    # pressure and temperature equilibrium: every species at p*, T*
+    rho_k = out[:N] / al
+    for k in range(N - 1):
+        Tk = (ps + f.pinf[k]) / ((f.gamma[k] - 1.0) * rho_k[k] * f.cv[k])
+        assert Tk == pytest.approx(Ts, rel=1e-13)
+    # volume constraint (Eq. thermal_relax_constraint_1): sum_k alpha_k rho_k / rho_k(p*, T*) = 1,
+    # which also puts the derived species N at T*
+    rho_star = np.array([(ps + f.pinf[k]) / ((f.gamma[k] - 1.0) * f.cv[k] * Ts) for k in range(N)])
+    # (B_p and C_p cancel p_inf-sized terms when p* << p_inf, hence 1e-10)
+    assert np.sum(out[:N] / rho_star) == pytest.approx(1.0, abs=1e-10)
+    # the five-equation mixture pressure of the relaxed state equals p*
+    V, o = orc.prim_cell(f, out)
+    assert V[N + f.D] == pytest.approx(ps, rel=1e-9, abs=1e-9 * max(f.pinf))
+    # T* of Eq. T_relax_rho agrees with Eq. T_relax_e
+    rho = W[:N].sum()
+    Y = W[:N] / rho
+    cv = np.array(f.cv[:N])
+    cp = cv * np.array(f.gamma[:N])
+    l = f.liq
+    T_rho = 1.0 / rho / (Y[l] * (f.gamma[l] - 1) * cv[l] / (ps + f.pinf[l])
+                         + (np.dot(Y, cp) - np.dot(Y, cv) - Y[l] * (cp[l] - cv[l])) / ps)
+    assert T_rho == pytest.approx(Ts, rel=1e-9)
+    assert ps > 0 and Ts > 0
+    # idempotent
+    again, ps2, Ts2 = orc.relax_cell(f, out)
+    np.testing.assert_allclose(again, out, rtol=1e-12, atol=1e-20)
+    return out, ps, Ts
+
+
+def test_relaxation_equilibrium_and_conservation(orc):
+    f = _fluid(orc, [P.BENCH_WATER, P.BENCH_AIR, P.BENCH_HELIUM])
+    prim, _ = P.random_admissible_states(3, 2, 50, seed=5)
+    f.D = 2
+    W = orc.ic_from_prim(f, prim)
+    rng = np.random.default_rng(9)
+    for c in range(W.shape[1]):
+        w = W[:, c].copy()
+        # take it out of thermal equilibrium: move volume fraction, keep W conserved parts
+        w[6] = min(max(w[6] * rng.uniform(0.5, 1.5), 1e-9), 0.999)
+        w[7] = min(max(w[7] * rng.uniform(0.5, 1.5), 1e-9), 1.0 - w[6] - 1e-9)
+        _relax_checks(orc, f, w)
+
+
+def test_relaxation_keeps_equilibrium_states(orc):
+    """A state already in p-T equilibrium is a fixed point (Sec. 4.2)."""
+    f = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR, P.PAPER_SF6])
+    prim, _ = P.random_admissible_states(3, 1, 30, seed=2,
+                                         fluids=[P.PAPER_WATER, P.PAPER_AIR, P.PAPER_SF6])
+    W = orc.ic_from_prim(f, prim)
+    for c in range(W.shape[1]):
+        out, ps, Ts = orc.relax_cell(f, W[:, c])
+        assert ps == pytest.approx(prim[3, c], rel=1e-9)
+        assert Ts == pytest.approx(prim[4, c], rel=1e-9)
+        np.testing.assert_allclose(out[4:], W[4:, c], rtol=1e-9)
+
+
+def test_relaxation_ideal_gases_closed_form(orc):
+    """All ideal gases: C_p = 0 and p* = rho e~ (cbar_p - cbar_v)/cbar_v."""
+    f = _fluid(orc, [P.PAPER_AIR, P.BENCH_HELIUM])
+    W = np.array([0.7, 0.05, 30.0, 2.5e5, 0.3])
+    out, ps, Ts = orc.relax_cell(f, W)
+    rho = 0.75
+    Y = W[:2] / rho
+    cv = np.array(f.cv[:2])
+    cp = cv * np.array(f.gamma[:2])
+    rhoe = W[3] - 0.5 * W[2] ** 2 / rho
+    assert ps == pytest.approx(rhoe * (Y @ cp - Y @ cv) / (Y @ cv), rel=1e-14)
+
+
+# ---------------------------------------------------------------- shock sensor
+
+def test_sensor_constant_and_zero_denominator(orc):
+    assert orc.sensor(np.full(6, 3.0)) == 0.0
+    assert orc.sensor(np.zeros(6)) == 0.0  # zero denominator reads as 0
+    # linear data: the fourth-order second difference vanishes
+    assert orc.sensor(np.arange(6, dtype=float) + 10.0) == pytest.approx(0.0, abs=1e-16)
+
+
+# ---------------------------------------------------------------- time step (Sec. 4.1.2)
+
+def test_dt_closed_form(orc):
+    f = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR], D=2)
+    W = _W_from_prim(orc, f, [0.3, 20.0, -50.0, 1e5, 300.0])
+    _, o = orc.prim_cell(f, W[:, 0])
+    Wg = np.repeat(W, 12, axis=1)
+    g = orc.make_grid([4, 3], [0.1, 0.05])
+    dt, tau = orc.dt(f, g, Wg, 0.5)
+    t0 = (20 + o["c"]) / 0.1
+    t1 = (50 + o["c"]) / 0.05
+    assert dt == pytest.approx(0.5 / (t0 + t1), rel=1e-15)
+    lam = orc.lambdas(f, g, Wg, dt)
+    # lambda_d = CFL / (|u_d| + c)_max when dt is the CFL step
+    assert lam[0] == pytest.approx(0.5 / (20 + o["c"]), rel=1e-14)
+    assert lam[1] == pytest.approx(0.5 / (50 + o["c"]), rel=1e-14)
