@@ -1,0 +1,303 @@
+"""Benchmark: cell-updates/s of the PP-WCNS-IS fractional step on the
+1024 x 512 three-species 2D shock-bubble workload (water, air, helium; SSP-RK3
+with relaxation after every stage, CFL 0.4), FP64 plain, with the FP32-bulk
+form reported beside it at its relative L1 error against FP64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). A step is one full SSP-RK3 step (three stages,
+three relaxations, the CFL reduction) of the whole grid. With N > 1 (torchrun),
+every rank advances its own replica of the workload (the instances are
+independent; weak scaling) and the value is the total over ranks divided by the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s (FP64 plain vs FP32+learned) at stated L1 err; % of roofline"
+UNIT = "cell-updates/s"
+WORKLOAD = "2D three-species shock-bubble, 1024x512 cells, Mach 1.5 shock, water+air+helium, SSP-RK3, CFL 0.4"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.samples = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def summary(self):
+        if not getattr(self, "samples", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(p[0]) for p in self.samples if p[0].replace(".", "").isdigit()]
+        mx = [float(p[1]) for p in self.samples if p[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in self.samples for i in range(4) if p[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def algorithmic_face_flops(problem, cfl):
+    """Algorithmic flops per midpoint of each direction on the initial state,
+    from the oracle's operation-counting build (add, mul, div, sqrt, tanh each
+    one flop)."""
+    import oracle
+    f, g, W = oracle.setup(problem)
+    dt, _ = oracle.dt(f, g, W, cfl)
+    lam = oracle.lambdas(f, g, W, dt)
+    out = []
+    for d in range(problem.D):
+        c, nf = oracle.faces_flops(f, oracle.make_params(), g, W, lam, d)
+        out.append((sum(c.values()) / nf, nf, c))
+    return out
+
+
+def cpu_baseline(problem, seconds_budget=25.0):
+    """The CPU oracle as it stands (serial FP64, one host core) on a bounded
+    sample of the same workload: whole SSP-RK3 steps of the full grid."""
+    import oracle
+    f, g, W = oracle.setup(problem)
+    dt, _ = oracle.dt(f, g, W, problem.cfl)
+    p = oracle.make_params()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        W = oracle.step(f, p, g, W, dt, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds_budget * 0.5 or steps >= 8:
+            break
+    return {"value": problem.ncells * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full SSP-RK3 step(s) of the 1024x512 workload on one host core "
+                      f"({el:.1f} s, serial FP64 C++ oracle)"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host cores (rank 0 only)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2208_04488_gb300 import problems
+    pr = problems.shock_bubble_2d(1024, 512)
+    import oracle
+    f, g, W = oracle.setup(pr)
+    dt, _ = oracle.dt(f, g, W, pr.cfl)
+    p = oracle.make_params()
+    for _ in range(args.warmup):
+        W = oracle.step(f, p, g, W, dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        W = oracle.step(f, p, g, W, dt, 1)
+    el = time.perf_counter() - t0
+    value = pr.ncells * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "cells": pr.ncells},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full SSP-RK3 steps of the 1024x512 workload, serial FP64 "
+                                       "C++ oracle on one host core"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(torch, s, K, flush, ev_stream):
+    """K single steps, each bracketed by CUDA events on the library's stream,
+    with an L2 flush (a write larger than L2) before each. The step graph
+    carries an event pair around every kernel (hrm_set_profiling), read after
+    each step. Returns (seconds, {kernel kind: (launches, seconds)})."""
+    total = 0.0
+    per = {}
+    for _ in range(K):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ev_stream)
+        s.step(0.0, 1)
+        e1.record(ev_stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1) * 1e-3
+        for kind, ms in s.profile_read():
+            n, t = per.get(kind, (0, 0.0))
+            per[kind] = (n + 1, t + ms * 1e-3)
+    return total, per
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=512)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2208_04488_gb300 import build, hrm, problems
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    pr = problems.shock_bubble_2d(args.nx, args.ny)
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        prm = hrm.params_default(cfl=pr.cfl, check=0, precision=precision)
+        return hrm.Solver.from_problem(pr, params=prm, stream=stream)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    s = make(hrm.FP64)
+    s.set_profiling(True)
+    for _ in range(args.warmup):
+        s.step(0.0, 1)
+    torch.cuda.synchronize()
+    s.set_primitive(pr.prim)  # timed run starts from the initial condition
+    launches0 = s.kernel_launches()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t_dev, per_kernel = time_steps(torch, s, args.steps, flush, stream)
+    launches = s.kernel_launches() - launches0
+    torch.cuda.synchronize()
+    adm = s.admissibility()
+    W_fp64 = s.get(hrm.FIELD_W)
+    t_tensor = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
+    t_max = float(t_tensor.item())
+    cells_total = pr.ncells * args.steps * ws
+    value = cells_total / t_max
+
+    # end-to-end through the public API with host buffers: per step the state is
+    # uploaded from pinned host memory, advanced one step and read back.
+    Wh = torch.from_numpy(W_fp64.copy()).pin_memory()
+    Wout = torch.empty_like(Wh).pin_memory()
+    Wdev = torch.empty(Wh.shape, dtype=torch.float64, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    K_e2e = max(3, args.steps // 2)
+    e0.record(stream)
+    for _ in range(K_e2e):
+        Wdev.copy_(Wh, non_blocking=True)
+        s.set(Wdev)
+        s.step(0.0, 1)
+        s.get(hrm.FIELD_W, out=Wdev)
+        Wout.copy_(Wdev, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    t_e2e = e0.elapsed_time(e1) * 1e-3
+    bytes_step = Wh.numel() * 8
+
+    line = None
+    if rank == 0:
+        pk, pk_src = peaks()
+        fp64_peak = hrm.probe_fma_peak(hrm.FP64)
+        fp32_peak = hrm.probe_fma_peak(hrm.FP32)
+        faces = algorithmic_face_flops(pr, pr.cfl)
+        # dominant kernels: the per-midpoint sweeps (one launch per direction and
+        # stage); algorithmic flops per launch / average launch duration
+        face_kinds = [hrm.KERNEL_FACE_X + d for d in range(pr.D)]
+        fl_launch = sum(faces[d][0] * faces[d][1] for d in range(pr.D)) / pr.D
+        n_face = sum(per_kernel[k][0] for k in face_kinds)
+        t_face = sum(per_kernel[k][1] for k in face_kinds)
+        achieved = fl_launch / (t_face / n_face)
+        frac = achieved / fp64_peak
+        share = {hrm.KERNEL_NAMES[k]: round(v[1] / sum(x[1] for x in per_kernel.values()), 4)
+                 for k, v in sorted(per_kernel.items())}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": pr.ncells, "species": pr.N,
+                       "l2": "working set ~190 MB > L2 and L2 flushed (256 MB write) before every timed step",
+                       "parallelism": f"{ws} independent replica(s)" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "alu", "kernel": "k_face (per-midpoint, FP64)",
+                         "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                         "frac": frac, "traffic": None,
+                         "peak_source": "measured FP64 FMA-chain probe on this GPU (hrm_probe_fma_peak)",
+                         "algorithmic_flops_per_face": [round(x[0], 1) for x in faces],
+                         "avg_launch_ms": 1e3 * t_face / n_face, "launches_timed": n_face,
+                         "kernel_time_share": share},
+            "e2e": {"value": pr.ncells * K_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
+                    "d2h_bytes_per_step": bytes_step},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "admissibility_after": adm,
+            "peaks": {"fp64_fma_tflops": fp64_peak / 1e12, "fp32_fma_tflops": fp32_peak / 1e12,
+                      "hbm_gbs": pk.get("hbm_gbs"), "hbm_source": pk_src},
+        }
+    if dist is not None:
+        dist.barrier()
+    if rank == 0:
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(pr)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * hrm.h -- C ABI of the GB300 library for the positivity-preserving fractional
+ * algorithm of Wong, Angel & Kiris (arXiv 2208.04488): the five-equation model of
+ * Allaire et al. advanced by PP-WCNS-IS with SSP-RK time stepping, followed after
+ * every Runge-Kutta stage by the algebraic thermal relaxation at infinite rate,
+ * which yields the four-equation homogeneous relaxation model (HRM).
+ *
+ * Plain C types only. Every call is ordered on the CUDA stream given at creation
+ * (NULL = the legacy default stream). Device pointers are CUDA device addresses of
+ * the current device; host pointers are ordinary host memory.
+ *
+ * Conservative state layout (Sec. 2, vector W): structure of arrays
+ *   W[m][z][y][x], m = 0..M-1, x fastest, M = 2N + D, interior cells only:
+ *   m = 0..N-1      alpha_k rho_k      (partial densities)
+ *   m = N..N+D-1    rho u_d            (momentum)
+ *   m = N+D         E                  (total energy per unit volume)
+ *   m = N+D+1..M-1  alpha_k, k < N     (alpha_N = 1 - sum of the others)
+ * Species may be given in any order; at most one may have p_inf > 0 (the
+ * stiffened gas of Sec. 4.2), the others are ideal gases.
+ *
+ * Errors: every call returns an hrm_status; nothing aborts. hrm_last_error()
+ * gives a one-line description of the last failure on a context.
+ */
+#ifndef HRM_H
+#define HRM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hrm_ctx hrm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  HRM_OK = 0,
+  HRM_E_INVAL = -1,         /* invalid argument (message in hrm_last_error) */
+  HRM_E_CUDA = -2,          /* a CUDA call failed */
+  HRM_E_ADMISSIBILITY = -3, /* a step produced cells outside the admissible set */
+  HRM_E_TIMEOUT = -4,       /* a bounded device wait ran out */
+  HRM_E_NOMEM = -5          /* device allocation failed */
+} hrm_status;
+
+enum { HRM_BC_TRANSMISSIVE = 0, HRM_BC_PERIODIC = 1 };
+
+enum {
+  HRM_SCHEME_WCNS = 0,      /* PP-WCNS-IS (Sec. 4.3) */
+  HRM_SCHEME_HLLC1 = 1      /* first-order HLLC (Sec. 4.1.1) */
+};
+
+enum {
+  HRM_RELAX_OFF = 0,        /* five-equation model without relaxation */
+  HRM_RELAX_STAGE = 1,      /* after every RK stage (Sec. 4.4, the paper's choice) */
+  HRM_RELAX_STEP = 2        /* after the full step only */
+};
+
+enum { HRM_RK3 = 0, HRM_EULER = 1, HRM_RK2 = 2 }; /* SSP integrators (Sec. 4.4, 5.1) */
+
+enum {
+  HRM_FP64 = 0,             /* everything in FP64 */
+  HRM_FP32 = 1              /* WENO, HLLC, HCS in FP32; state, limiter theta and
+                               relaxation in FP64 */
+};
+
+/* Uniform Cartesian grid: n[d] cells on [lo[d], hi[d]] (Sec. 4.1, grid midpoints
+ * x_{i+1/2} = x_a + i dx); bc[2d], bc[2d+1] = low / high side of direction d. */
+typedef struct {
+  int32_t ndim;
+  int32_t pad;
+  int64_t n[3];
+  double lo[3], hi[3];
+  int32_t bc[6];
+} hrm_grid;
+
+/* Scheme options and the paper's constants; hrm_params_default() fills the
+ * values of Sec. 4.3 and App. C. */
+typedef struct {
+  double cfl;          /* CFL number for the automatic time step (<= 0.5, Sec. 4.1.2) */
+  int32_t limiters;    /* interpolation + flux limiters on (Sec. 4.3.2) */
+  int32_t blend;       /* shock-sensor flux/velocity blending (Eq. flux_blending) */
+  int32_t relax_mode;  /* HRM_RELAX_* */
+  int32_t scheme;      /* HRM_SCHEME_* */
+  int32_t integrator;  /* HRM_RK3 / HRM_EULER / HRM_RK2 */
+  int32_t precision;   /* HRM_FP64 / HRM_FP32 */
+  int32_t learned;     /* 1: MLP smoothness gate before the WENO weights */
+  int32_t check;       /* 1: hrm_step synchronises and reports admissibility */
+  double eps_ar, eps_a, eps_rhoe;      /* limiter thresholds 1e-10, 1e-10, 1e-8 */
+  double hs_ar, hs_a, hs_rc2, hs_rhoe; /* hard switches 1e-11, 1e-11, 1e-9, 1e-9 */
+  double weno_eps;                     /* 1e-15 (App. C) */
+  double Cs, q_sensor;                 /* shock sensor 1e12 and 2 (Sec. 4.3.1) */
+  double learned_threshold;            /* gate probability above which d_k are used */
+} hrm_params;
+
+/* Field selectors of hrm_get. */
+enum {
+  HRM_FIELD_W = 0,     /* M planes, layout above */
+  HRM_FIELD_V = 1,     /* M planes: alpha_k rho_k, u_d, p (five-equation EOS), alpha_k */
+  HRM_FIELD_C5 = 2,    /* 1 plane: five-equation sound speed, rho c^2 = gbar (p + pbar_inf) (Sec. 2) */
+  HRM_FIELD_PT = 3,    /* 2 planes: equilibrium p and T of the four-equation HRM (Sec. 4.2) */
+  HRM_FIELD_C4 = 4     /* 1 plane: four-equation HRM sound speed (Eq. 4_eqn_sos) */
+};
+
+/* Fill p with the paper's constants (Sec. 4.3.2, App. C, Sec. 4.3.1), PP-WCNS-IS,
+ * SSP-RK3, relaxation after every stage, FP64, CFL 0.5, check on. */
+void hrm_params_default(hrm_params* p);
+
+/* Create a context for one problem (Sec. 4: grid, N species, D dimensions).
+ * gamma[N] > 1, p_inf[N] >= 0 with at most one positive, c_v[N] > 0 (c_p = gamma c_v,
+ * Sec. 2), q[N] (NULL: all 0). params NULL: defaults. cuda_stream: a cudaStream_t
+ * (NULL: default stream). Allocates the state and the scratch on the device.
+ * Errors: HRM_E_INVAL (bad species table, N outside 2..3, ndim outside 1..3,
+ * periodic direction with fewer than 3 cells, CFL > 0.5 with limiters on),
+ * HRM_E_NOMEM, HRM_E_CUDA. On failure *out is NULL. */
+hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t nspecies,
+                      const double* gamma, const double* p_inf, const double* c_v,
+                      const double* q, const hrm_params* params, void* cuda_stream);
+
+/* Release every resource of ctx (NULL is accepted). Synchronises its stream. */
+void hrm_destroy(hrm_ctx* ctx);
+
+/* One-line description of the last error on ctx (never NULL); with ctx NULL,
+ * the reason the last hrm_create on this thread failed. */
+const char* hrm_last_error(const hrm_ctx* ctx);
+
+/* Replace the scheme options (same checks as hrm_create). */
+hrm_status hrm_set_params(hrm_ctx* ctx, const hrm_params* params);
+
+/* Set the state from W (layout above, M x ncells doubles), host (on_device = 0)
+ * or device memory; resets the time to 0. */
+hrm_status hrm_set(hrm_ctx* ctx, const double* W, int32_t on_device);
+
+/* Set the state from primitive planes prim[(N + D + 1) x ncells] =
+ * (alpha_1..alpha_{N-1}, u_1..u_D, p, T) in pressure and temperature
+ * equilibrium (Sec. 5): rho_k = (p + p_inf_k) / ((gamma_k - 1) c_v,k T)
+ * (Eq. rho_k_thermally_relaxed), E from the mixture EOS (Sec. 2). */
+hrm_status hrm_set_primitive(hrm_ctx* ctx, const double* prim, int32_t on_device);
+
+/* Time step of the current state (Sec. 4.1.2): tau_d = max(|u_d| + c) / dx_d,
+ * dt = cfl / sum_d tau_d. Synchronises. tau_out (optional) receives D values. */
+hrm_status hrm_dt(hrm_ctx* ctx, double cfl, double* dt_out, double* tau_out);
+
+/* Advance nsteps full time steps (Sec. 4.4). dt > 0: that step size; dt <= 0:
+ * the CFL step of params.cfl from the state at the start of each step
+ * (footnote of Sec. 5). The directional split sigma_d and lambda_d of the flux
+ * limiter come from the step-start state. Launches one captured CUDA graph per
+ * step. With params.check it synchronises and returns HRM_E_ADMISSIBILITY when
+ * a cell left the admissible set (the state is kept for inspection). */
+hrm_status hrm_step(hrm_ctx* ctx, double dt, int32_t nsteps);
+
+/* Apply the thermal relaxation (Sec. 4.2) to the current state in place. */
+hrm_status hrm_relax(hrm_ctx* ctx);
+
+/* Semi-discrete right-hand side L(W) of the current state (Eq. semi_W_G_pm_eqn)
+ * with flux-limiter lambda_d = lam[d], into rhs (M x ncells, device memory). */
+hrm_status hrm_rhs(hrm_ctx* ctx, const double* lam, double* rhs_device);
+
+/* Copy a field (HRM_FIELD_*) of the current state to dst (host: on_device = 0,
+ * synchronises; device otherwise). Planes x ncells doubles. */
+hrm_status hrm_get(hrm_ctx* ctx, int32_t field, double* dst, int32_t on_device);
+
+/* Simulated time and number of steps taken since the last hrm_set. */
+hrm_status hrm_time(hrm_ctx* ctx, double* t, int64_t* steps);
+
+/* Admissibility counters of the current state (Sec. 2, sets G and script-G):
+ * counts[0] cells with a negative partial density, [1] a volume fraction outside
+ * [0, 1], [2] rho c^2 <= 0 or NaN, [3] rho (e - qbar) <= 0 or NaN. Synchronises. */
+hrm_status hrm_admissibility(hrm_ctx* ctx, int64_t counts[4]);
+
+/* Number of kernels the library has launched on ctx since creation
+ * (graph launches count their kernel nodes). */
+int64_t hrm_kernel_launches(const hrm_ctx* ctx);
+
+/* Kernel kinds reported by hrm_profile_read. */
+enum {
+  HRM_KERNEL_PRIM = 0,      /* per-cell primitives (+ CFL reduction at the first stage) */
+  HRM_KERNEL_FINALIZE = 1,  /* dt, sigma_d, lambda_d */
+  HRM_KERNEL_FACE_X = 2,    /* per-midpoint sweep in x (HRM_KERNEL_FACE_X + d for direction d) */
+  HRM_KERNEL_UPDATE = 5     /* flux difference, RK combination, relaxation */
+};
+
+/* Tracing: with on != 0 the step graph is (re)captured with a CUDA event pair
+ * around every kernel. Costs one event-record node per kernel boundary. */
+hrm_status hrm_set_profiling(hrm_ctx* ctx, int32_t on);
+
+/* After a step with tracing on: synchronises the stream and writes, for the
+ * kernels of the last step in launch order, their device time in ms and their
+ * kind (HRM_KERNEL_*). Returns how many were written (at most max). */
+int32_t hrm_profile_read(hrm_ctx* ctx, int32_t max, float* ms, int32_t* kind);
+
+/* Diagnostic, not a step of the method: measured FMA-pipe throughput of the
+ * current device in flop/s (2 flops per FMA) for HRM_FP64 or HRM_FP32, from
+ * independent FMA chains on every SM (`iters` FMAs per chain); the denominator
+ * of the ALU roofline of the per-midpoint kernels. Synchronises `stream`. */
+hrm_status hrm_probe_fma_peak(int32_t precision, int32_t iters, void* stream, double* flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HRM_H */

@@ -105,6 +105,8 @@ def lib(count: bool = False):
         L.or_admissibility.argtypes = [P(Fluid), P(Grid), _DP, P(ctypes.c_int64)]
         L.or_c4eq_cell.argtypes = [P(Fluid), _DP, _DP]
         L.or_ic_from_prim.argtypes = [P(Fluid), ctypes.c_int64, _DP, _DP]
+        L.or_faces_flops.argtypes = [P(Fluid), P(Params), P(Grid), _DP, _DP, ctypes.c_int, _DP]
+        L.or_faces_flops.restype = ctypes.c_int64
         if count:
             L.or_count_reset.argtypes = []
             L.or_count_get.argtypes = [P(ctypes.c_ulonglong)]
@@ -292,3 +294,14 @@ def setup(problem):
     f = make_fluid(problem.gamma, problem.pinf, problem.cv, problem.q, D=problem.D, liq=problem.liq)
     g = make_grid(problem.n, problem.dx, problem.bc)
     return f, g, ic_from_prim(f, problem.prim)
+
+
+def faces_flops(f: Fluid, p: Params, g: Grid, W, lam, dir_):
+    """Algorithmic operation counts of the midpoint computations of one
+    direction (counting build): (counts dict, number of faces)."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    lam = np.ascontiguousarray(np.resize(np.asarray(lam, dtype=np.float64), 3))
+    out = np.zeros(5)
+    nf = lib(True).or_faces_flops(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), _ptr(lam),
+                                  dir_, _ptr(out))
+    return dict(zip(["add", "mul", "div", "sqrt", "tanh"], out.tolist())), nf

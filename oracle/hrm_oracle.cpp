@@ -1184,6 +1184,50 @@ void or_ic_from_prim(const or_fluid* fl, int64_t nc, const double* prim, double*
   }
 }
 
+// Operations performed by the midpoint computations alone (everything of
+// face_flux: projection, WENO, limiters, two HLLC solves, HCS, blending, flux
+// limiter) over every face of direction `dir`; the primitive variables of the
+// node cells are computed outside the counted region. out[0..4] = add, mul, div,
+// sqrt, tanh; returns the number of faces. Zero counts in the normal build.
+int64_t or_faces_flops(const or_fluid* fl, const or_params* P, const or_grid* g, const double* W,
+                       const double* lam, int dir, double* out) {
+  FluidK f = make_fluid(fl);
+  const int M = f.M;
+  const int64_t nc = ncells(g), n = g->n[dir], nl = nc / n;
+  std::vector<Cell> line(n + 6);
+  std::vector<real> Gm(M), Gp(M);
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int64_t l = 0; l < nl; ++l) {
+    int64_t ijk[3] = {0, 0, 0};
+    int64_t rem = l;
+    for (int d = 0; d < g->D; ++d) {
+      if (d == dir) continue;
+      ijk[d] = rem % g->n[d];
+      rem /= g->n[d];
+    }
+    for (int64_t j = -3; j < n + 3; ++j) {
+      int64_t q[3] = {ijk[0], ijk[1], ijk[2]};
+      q[dir] = map_index(g, dir, j);
+      real w[OR_MAXM];
+      load_W(f, W, nc, lin(g, q), w);
+      cell_from_W(f, w, line[j + 3]);
+    }
+#ifdef OR_COUNT
+    OrCounts before = g_cnt;
+#endif
+    for (int64_t fc = 0; fc <= n; ++fc) face_flux(f, P, dir, real(lam[dir]), &line[fc], Gm.data(), Gp.data(), nullptr);
+#ifdef OR_COUNT
+    acc[0] += (double)(g_cnt.add - before.add);
+    acc[1] += (double)(g_cnt.mul - before.mul);
+    acc[2] += (double)(g_cnt.div - before.div);
+    acc[3] += (double)(g_cnt.sqrt - before.sqrt);
+    acc[4] += (double)(g_cnt.tanh - before.tanh);
+#endif
+  }
+  for (int i = 0; i < 5; ++i) out[i] = acc[i];
+  return nl * (n + 1);
+}
+
 #ifdef OR_COUNT
 void or_count_reset(void) { memset(&g_cnt, 0, sizeof(g_cnt)); }
 void or_count_get(unsigned long long* out) {

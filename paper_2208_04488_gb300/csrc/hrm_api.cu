@@ -1,0 +1,541 @@
+// C ABI of the library (include/hrm.h): context management, the per-step CUDA
+// graph and dispatch to the kernel tables.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/hrm.h"
+#include "hrm_launch.h"
+
+using namespace hrm;
+
+namespace {
+constexpr int kMaxProf = 32;  // kernels of one step: at most 3 stages x (2 + 3 + 1) + 1
+}
+
+struct hrm_ctx {
+  int N = 0, D = 0, M = 0;
+  int64_t nc = 0;
+  hrm_grid grid{};
+  hrm_params params{};
+  DevFluid fl{};
+  DevGrid dg{};
+  DevParams dp{};
+  cudaStream_t stream = nullptr;   // caller's stream: every call is ordered on it
+  cudaStream_t cap = nullptr;      // private stream used only to capture the step graph
+  double* Wn = nullptr;            // state W^n (M planes)
+  double* Ws = nullptr;            // RK stage state
+  double* V = nullptr;             // primitive planes (M) -- also scratch for I/O
+  double* AUX = nullptr;           // c, rho, rho c^2
+  double* F[3] = {nullptr, nullptr, nullptr};  // midpoint fluxes per direction (M + 1 planes)
+  StepState* st = nullptr;
+  const CellKernels* ck = nullptr;
+  const FaceKernels* fk = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_kernels = 0;
+  int64_t launches = 0;
+  // tracing: event pairs around every kernel of the captured step
+  int profiling = 0;
+  int nprof = 0;
+  cudaEvent_t prof_ev[2 * kMaxProf] = {};
+  int32_t prof_kind[kMaxProf] = {};
+  std::string err;
+};
+
+namespace {
+
+// Message of the last failed hrm_create on this thread (its context is gone).
+thread_local std::string g_create_error = "null context";
+
+hrm_status fail(hrm_ctx* c, hrm_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+hrm_status cuda_check(hrm_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return HRM_OK;
+  return fail(c, e == cudaErrorMemoryAllocation ? HRM_E_NOMEM : HRM_E_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+hrm_status last_launch(hrm_ctx* c, const char* what) { return cuda_check(c, cudaGetLastError(), what); }
+
+hrm_status check_params(hrm_ctx* c, const hrm_params* p) {
+  if (p->cfl <= 0.0) return fail(c, HRM_E_INVAL, "cfl must be positive");
+  if (p->limiters && p->cfl > 0.5)
+    return fail(c, HRM_E_INVAL, "cfl %.3g > 0.5 with the positivity limiters on (Sec. 4.1.2)", p->cfl);
+  if (p->scheme < 0 || p->scheme > 1) return fail(c, HRM_E_INVAL, "unknown scheme %d", p->scheme);
+  if (p->relax_mode < 0 || p->relax_mode > 2) return fail(c, HRM_E_INVAL, "unknown relax_mode %d", p->relax_mode);
+  if (p->integrator < 0 || p->integrator > 2) return fail(c, HRM_E_INVAL, "unknown integrator %d", p->integrator);
+  if (p->precision < 0 || p->precision > 1) return fail(c, HRM_E_INVAL, "unknown precision %d", p->precision);
+  if (p->learned) return fail(c, HRM_E_INVAL, "learned gate not loaded on this context");
+  if (p->q_sensor < 1.0 || p->q_sensor != std::floor(p->q_sensor))
+    return fail(c, HRM_E_INVAL, "q_sensor must be a positive integer");
+  return HRM_OK;
+}
+
+void fill_dev_params(hrm_ctx* c) {
+  const hrm_params& p = c->params;
+  DevParams& d = c->dp;
+  d.limiters = p.limiters;
+  d.blend = p.blend;
+  d.scheme = p.scheme;
+  d.qexp = (int)p.q_sensor;
+  d.eps_ar = p.eps_ar;
+  d.eps_a = p.eps_a;
+  d.eps_rhoe = p.eps_rhoe;
+  d.hs_ar = p.hs_ar;
+  d.hs_a = p.hs_a;
+  d.hs_rc2 = p.hs_rc2;
+  d.hs_rhoe = p.hs_rhoe;
+  d.weno_eps = p.weno_eps;
+  d.Cs = p.Cs;
+}
+
+void drop_graph(hrm_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->graph_kernels = 0;
+}
+
+// Launch one kernel of the step; while profiling, bracket it with an event pair
+// (captured as event-record nodes) and remember its kind (HRM_KERNEL_*).
+template <typename F>
+void traced(hrm_ctx* c, cudaStream_t s, int kind, F&& launch) {
+  const bool on = c->profiling && c->nprof < kMaxProf;
+  if (on) cudaEventRecord(c->prof_ev[2 * c->nprof], s);
+  launch();
+  if (on) {
+    cudaEventRecord(c->prof_ev[2 * c->nprof + 1], s);
+    c->prof_kind[c->nprof] = kind;
+    ++c->nprof;
+  }
+}
+
+// One RK stage: primitives of Wsrc, midpoint fluxes, update into Wout.
+int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, double a, double b, int relax,
+                  int count, bool first) {
+  int k = 0;
+  traced(c, s, HRM_KERNEL_PRIM, [&] { c->ck->prim(Wsrc, c->V, c->AUX, c->dg, c->fl, c->st, first ? 1 : 0, s); });
+  ++k;
+  if (first) {
+    traced(c, s, HRM_KERNEL_FINALIZE, [&] { launch_finalize(c->st, c->dg, c->D, c->params.cfl, 0, s); });
+    ++k;
+  }
+  for (int d = 0; d < c->D; ++d) {
+    traced(c, s, HRM_KERNEL_FACE_X + d, [&] {
+      c->fk->face[d](c->params.precision, Wsrc, c->V, c->AUX, c->F[d], c->dg, c->fl, c->dp, c->st, s);
+    });
+    ++k;
+  }
+  traced(c, s, HRM_KERNEL_UPDATE, [&] {
+    c->fk->update(0, c->Wn, Wsrc, Wout, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, a, b, relax, count, s);
+  });
+  ++k;
+  return k;
+}
+
+// Kernels of one full step (Sec. 4.4): SSP-RK3 in Shu-Osher form, SSP-RK2 or
+// forward Euler, relaxation after every stage (or after the step).
+int enqueue_step(hrm_ctx* c, cudaStream_t s) {
+  const int rs = c->params.relax_mode == HRM_RELAX_STAGE;
+  const int rf = c->params.relax_mode != HRM_RELAX_OFF;
+  int k = 0;
+  switch (c->params.integrator) {
+    case HRM_EULER:
+      k += enqueue_stage(c, s, c->Wn, c->Wn, 0.0, 1.0, rf, 1, true);
+      break;
+    case HRM_RK2:
+      k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true);
+      k += enqueue_stage(c, s, c->Ws, c->Wn, 0.5, 0.5, rf, 1, false);
+      break;
+    default:
+      k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true);
+      k += enqueue_stage(c, s, c->Ws, c->Ws, 0.75, 0.25, rs, 0, false);
+      k += enqueue_stage(c, s, c->Ws, c->Wn, 1.0 / 3.0, 2.0 / 3.0, rf, 1, false);
+      break;
+  }
+  return k;
+}
+
+hrm_status build_graph(hrm_ctx* c) {
+  drop_graph(c);
+  c->nprof = 0;
+  cudaGraph_t g = nullptr;
+  hrm_status s = cuda_check(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (s) return s;
+  const int k = enqueue_step(c, c->cap);
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if ((s = cuda_check(c, e, "end capture"))) return s;
+  e = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if ((s = cuda_check(c, e, "graph instantiate"))) return s;
+  c->graph_kernels = k;
+  return HRM_OK;
+}
+
+void reset_step_state(hrm_ctx* c) {
+  StepState z{};
+  z.cfl = c->params.cfl;
+  cudaMemcpyAsync(c->st, &z, sizeof z, cudaMemcpyHostToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void hrm_params_default(hrm_params* p) {
+  std::memset(p, 0, sizeof *p);
+  p->cfl = 0.5;
+  p->limiters = 1;
+  p->blend = 1;
+  p->relax_mode = HRM_RELAX_STAGE;
+  p->scheme = HRM_SCHEME_WCNS;
+  p->integrator = HRM_RK3;
+  p->precision = HRM_FP64;
+  p->learned = 0;
+  p->check = 1;
+  p->eps_ar = 1.0e-10;
+  p->eps_a = 1.0e-10;
+  p->eps_rhoe = 1.0e-8;
+  p->hs_ar = 1.0e-11;
+  p->hs_a = 1.0e-11;
+  p->hs_rc2 = 1.0e-9;
+  p->hs_rhoe = 1.0e-9;
+  p->weno_eps = 1.0e-15;
+  p->Cs = 1.0e12;
+  p->q_sensor = 2.0;
+  p->learned_threshold = 0.5;
+}
+
+const char* hrm_last_error(const hrm_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const double* gamma, const double* p_inf,
+                      const double* c_v, const double* q, const hrm_params* params, void* cuda_stream) {
+  if (!out) return HRM_E_INVAL;
+  *out = nullptr;
+  hrm_ctx* c = new (std::nothrow) hrm_ctx();
+  if (!c) return HRM_E_NOMEM;
+  auto bail = [&](hrm_status s) {
+    g_create_error = c->err;  // reachable through hrm_last_error(NULL)
+    hrm_destroy(c);
+    return s;
+  };
+  if (!grid || !gamma || !p_inf || !c_v) return bail(fail(c, HRM_E_INVAL, "null argument"));
+  if (N < 2 || N > 3) return bail(fail(c, HRM_E_INVAL, "nspecies %d outside 2..3", N));
+  const int D = grid->ndim;
+  if (D < 1 || D > 3) return bail(fail(c, HRM_E_INVAL, "ndim %d outside 1..3", D));
+  int liq = -1;
+  for (int k = 0; k < N; ++k) {
+    if (!(gamma[k] > 1.0)) return bail(fail(c, HRM_E_INVAL, "gamma[%d] must exceed 1", k));
+    if (!(c_v[k] > 0.0)) return bail(fail(c, HRM_E_INVAL, "c_v[%d] must be positive", k));
+    if (p_inf[k] < 0.0) return bail(fail(c, HRM_E_INVAL, "p_inf[%d] must be non-negative", k));
+    if (p_inf[k] > 0.0) {
+      if (liq >= 0) return bail(fail(c, HRM_E_INVAL, "more than one stiffened gas (Sec. 4.2 allows one)"));
+      liq = k;
+    }
+  }
+  c->N = N;
+  c->D = D;
+  c->M = 2 * N + D;
+  c->grid = *grid;
+  c->nc = 1;
+  for (int d = 0; d < 3; ++d) {
+    const int64_t n = d < D ? grid->n[d] : 1;
+    if (n < 1) return bail(fail(c, HRM_E_INVAL, "n[%d] must be positive", d));
+    c->dg.n[d] = n;
+    c->nc *= n;
+    if (d < D) {
+      if (!(grid->hi[d] > grid->lo[d])) return bail(fail(c, HRM_E_INVAL, "empty extent in direction %d", d));
+      c->dg.dx[d] = (grid->hi[d] - grid->lo[d]) / (double)n;
+      c->dg.inv_dx[d] = 1.0 / c->dg.dx[d];
+      for (int side = 0; side < 2; ++side) {
+        const int b = grid->bc[2 * d + side];
+        if (b != HRM_BC_TRANSMISSIVE && b != HRM_BC_PERIODIC)
+          return bail(fail(c, HRM_E_INVAL, "unknown boundary condition %d", b));
+        c->dg.bc[2 * d + side] = b;
+      }
+      if ((grid->bc[2 * d] == HRM_BC_PERIODIC) != (grid->bc[2 * d + 1] == HRM_BC_PERIODIC))
+        return bail(fail(c, HRM_E_INVAL, "periodic boundaries must pair in direction %d", d));
+      if (grid->bc[2 * d] == HRM_BC_PERIODIC && n < 3)
+        return bail(fail(c, HRM_E_INVAL, "periodic direction %d needs at least 3 cells", d));
+    } else {
+      c->dg.dx[d] = 1.0;
+      c->dg.inv_dx[d] = 1.0;
+    }
+  }
+  c->dg.ncells = c->nc;
+  c->fl.liq = liq < 0 ? 0 : liq;
+  for (int k = 0; k < N; ++k) {
+    c->fl.inv_gm1[k] = 1.0 / (gamma[k] - 1.0);
+    c->fl.gpinf_gm1[k] = gamma[k] * p_inf[k] / (gamma[k] - 1.0);
+    c->fl.cv[k] = c_v[k];
+    c->fl.cp[k] = gamma[k] * c_v[k];
+    c->fl.Rg[k] = c->fl.cp[k] - c_v[k];
+    c->fl.q[k] = q ? q[k] : 0.0;
+    c->fl.pinf[k] = p_inf[k];
+    c->fl.gamma[k] = gamma[k];
+  }
+  if (params)
+    c->params = *params;
+  else
+    hrm_params_default(&c->params);
+  if (hrm_status s = check_params(c, &c->params)) return bail(s);
+  fill_dev_params(c);
+  c->ck = cell_kernels(N, D);
+  c->fk = face_kernels(N, D);
+  if (!c->ck || !c->fk) return bail(fail(c, HRM_E_INVAL, "no kernels for N=%d D=%d", N, D));
+  c->stream = (cudaStream_t)cuda_stream;
+  hrm_status s;
+  if ((s = cuda_check(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "stream create")))
+    return bail(s);
+  const size_t plane = sizeof(double) * (size_t)c->nc;
+  const int M = c->M;
+  if ((s = cuda_check(c, cudaMalloc(&c->Wn, plane * M), "alloc W"))) return bail(s);
+  if ((s = cuda_check(c, cudaMalloc(&c->Ws, plane * M), "alloc Ws"))) return bail(s);
+  if ((s = cuda_check(c, cudaMalloc(&c->V, plane * M), "alloc V"))) return bail(s);
+  if ((s = cuda_check(c, cudaMalloc(&c->AUX, plane * 3), "alloc aux"))) return bail(s);
+  for (int d = 0; d < D; ++d) {
+    size_t nf = 1;
+    for (int e = 0; e < 3; ++e) nf *= (size_t)(c->dg.n[e] + (e == d));
+    if ((s = cuda_check(c, cudaMalloc(&c->F[d], sizeof(double) * nf * (M + 1)), "alloc faces"))) return bail(s);
+  }
+  if ((s = cuda_check(c, cudaMalloc(&c->st, sizeof(StepState)), "alloc step state"))) return bail(s);
+  cudaMemsetAsync(c->Wn, 0, plane * M, c->stream);
+  reset_step_state(c);
+  if ((s = cuda_check(c, cudaGetLastError(), "init"))) return bail(s);
+  *out = c;
+  return HRM_OK;
+}
+
+void hrm_destroy(hrm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  cudaFree(c->Wn);
+  cudaFree(c->Ws);
+  cudaFree(c->V);
+  cudaFree(c->AUX);
+  for (int d = 0; d < 3; ++d) cudaFree(c->F[d]);
+  cudaFree(c->st);
+  for (int i = 0; i < 2 * kMaxProf; ++i)
+    if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+hrm_status hrm_set_profiling(hrm_ctx* c, int32_t on) {
+  if (!c) return HRM_E_INVAL;
+  if (on && !c->prof_ev[0]) {
+    for (int i = 0; i < 2 * kMaxProf; ++i) {
+      hrm_status s = cuda_check(c, cudaEventCreate(&c->prof_ev[i]), "event create");
+      if (s) return s;
+    }
+  }
+  if ((on != 0) != (c->profiling != 0)) drop_graph(c);
+  c->profiling = on != 0;
+  return HRM_OK;
+}
+
+int32_t hrm_profile_read(hrm_ctx* c, int32_t max, float* ms, int32_t* kind) {
+  if (!c || !c->profiling || !c->gexec) return 0;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return 0;
+  const int n = c->nprof < max ? c->nprof : max;
+  for (int i = 0; i < n; ++i) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]);
+    if (ms) ms[i] = t;
+    if (kind) kind[i] = c->prof_kind[i];
+  }
+  return n;
+}
+
+hrm_status hrm_set_params(hrm_ctx* c, const hrm_params* p) {
+  if (!c || !p) return HRM_E_INVAL;
+  if (hrm_status s = check_params(c, p)) return s;
+  c->params = *p;
+  fill_dev_params(c);
+  drop_graph(c);
+  StepState* st = c->st;
+  double cfl = p->cfl;
+  cudaMemcpyAsync(&st->cfl, &cfl, sizeof cfl, cudaMemcpyHostToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return last_launch(c, "set params");
+}
+
+hrm_status hrm_set(hrm_ctx* c, const double* W, int32_t on_device) {
+  if (!c || !W) return HRM_E_INVAL;
+  const size_t bytes = sizeof(double) * (size_t)c->nc * c->M;
+  hrm_status s = cuda_check(
+      c, cudaMemcpyAsync(c->Wn, W, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+      "copy W");
+  if (s) return s;
+  reset_step_state(c);
+  return last_launch(c, "set");
+}
+
+hrm_status hrm_set_primitive(hrm_ctx* c, const double* prim, int32_t on_device) {
+  if (!c || !prim) return HRM_E_INVAL;
+  const size_t bytes = sizeof(double) * (size_t)c->nc * (c->N + c->D + 1);
+  hrm_status s = cuda_check(
+      c, cudaMemcpyAsync(c->V, prim, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+      "copy primitives");
+  if (s) return s;
+  c->ck->ic(c->V, c->Wn, c->dg, c->fl, c->stream);
+  ++c->launches;
+  if ((s = last_launch(c, "initial state"))) return s;
+  reset_step_state(c);
+  return last_launch(c, "set primitive");
+}
+
+hrm_status hrm_dt(hrm_ctx* c, double cfl, double* dt_out, double* tau_out) {
+  if (!c || !(cfl > 0.0)) return c ? fail(c, HRM_E_INVAL, "cfl must be positive") : HRM_E_INVAL;
+  c->ck->prim(c->Wn, c->V, c->AUX, c->dg, c->fl, c->st, 1, c->stream);
+  launch_finalize(c->st, c->dg, c->D, cfl, 1, c->stream);
+  c->launches += 2;
+  StepState h;
+  hrm_status s = cuda_check(c, cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->stream), "read dt");
+  if (s) return s;
+  if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "dt sync"))) return s;
+  if (dt_out) *dt_out = h.dt;
+  if (tau_out)
+    for (int d = 0; d < c->D; ++d) tau_out[d] = h.tau[d];
+  return HRM_OK;
+}
+
+hrm_status hrm_step(hrm_ctx* c, double dt, int32_t nsteps) {
+  if (!c) return HRM_E_INVAL;
+  if (nsteps < 0) return fail(c, HRM_E_INVAL, "nsteps must be non-negative");
+  if (nsteps == 0) return HRM_OK;
+  hrm_status s;
+  if (!c->gexec && (s = build_graph(c))) return s;
+  launch_set_dt(c->st, dt > 0.0 ? dt : 0.0, c->stream);
+  ++c->launches;
+  if (c->params.check) cudaMemsetAsync(&c->st->counts, 0, sizeof(c->st->counts), c->stream);
+  for (int i = 0; i < nsteps; ++i) {
+    if ((s = cuda_check(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch"))) return s;
+    c->launches += c->graph_kernels;
+  }
+  if (!c->params.check) return last_launch(c, "step");
+  unsigned long long cnt[4];
+  if ((s = cuda_check(c, cudaMemcpyAsync(cnt, c->st->counts, sizeof cnt, cudaMemcpyDeviceToHost, c->stream),
+                      "read counters")))
+    return s;
+  if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "step sync"))) return s;
+  if (cnt[0] | cnt[1] | cnt[2] | cnt[3])
+    return fail(c, HRM_E_ADMISSIBILITY,
+                "non-admissible cells: %llu negative partial density, %llu volume fraction out of [0,1], "
+                "%llu rho c^2 <= 0, %llu rho e~ <= 0",
+                cnt[0], cnt[1], cnt[2], cnt[3]);
+  return HRM_OK;
+}
+
+hrm_status hrm_relax(hrm_ctx* c) {
+  if (!c) return HRM_E_INVAL;
+  c->ck->relax(c->Wn, c->dg, c->fl, c->stream);
+  ++c->launches;
+  return last_launch(c, "relax");
+}
+
+hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
+  if (!c || !lam || !rhs) return HRM_E_INVAL;
+  double l3[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < c->D; ++d) l3[d] = lam[d];
+  hrm_status s = cuda_check(c, cudaMemcpyAsync(c->st->lam, l3, sizeof l3, cudaMemcpyHostToDevice, c->stream),
+                            "copy lambda");
+  if (s) return s;
+  c->ck->prim(c->Wn, c->V, c->AUX, c->dg, c->fl, c->st, 0, c->stream);
+  for (int d = 0; d < c->D; ++d)
+    c->fk->face[d](c->params.precision, c->Wn, c->V, c->AUX, c->F[d], c->dg, c->fl, c->dp, c->st, c->stream);
+  c->fk->update(1, c->Wn, c->Wn, rhs, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, 0.0, 1.0, 0, 0, c->stream);
+  c->launches += 2 + c->D;
+  if ((s = last_launch(c, "rhs"))) return s;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "rhs sync");
+}
+
+hrm_status hrm_get(hrm_ctx* c, int32_t field, double* dst, int32_t on_device) {
+  if (!c || !dst) return HRM_E_INVAL;
+  int planes;
+  const double* src;
+  switch (field) {
+    case HRM_FIELD_W:
+      planes = c->M;
+      src = c->Wn;
+      break;
+    case HRM_FIELD_V:
+      planes = c->M;
+      break;
+    case HRM_FIELD_C5:
+    case HRM_FIELD_C4:
+      planes = 1;
+      break;
+    case HRM_FIELD_PT:
+      planes = 2;
+      break;
+    default:
+      return fail(c, HRM_E_INVAL, "unknown field %d", field);
+  }
+  if (field != HRM_FIELD_W) {
+    c->ck->fields(c->Wn, c->Ws, field, c->dg, c->fl, c->stream);
+    ++c->launches;
+    src = c->Ws;
+  }
+  const size_t bytes = sizeof(double) * (size_t)c->nc * planes;
+  hrm_status s = cuda_check(
+      c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+      "copy field");
+  if (s) return s;
+  if (!on_device) return cuda_check(c, cudaStreamSynchronize(c->stream), "get sync");
+  return last_launch(c, "get");
+}
+
+hrm_status hrm_time(hrm_ctx* c, double* t, int64_t* steps) {
+  if (!c) return HRM_E_INVAL;
+  StepState h;
+  hrm_status s = cuda_check(c, cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->stream), "read time");
+  if (s) return s;
+  if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "time sync"))) return s;
+  if (t) *t = h.t;
+  if (steps) *steps = h.steps;
+  return HRM_OK;
+}
+
+hrm_status hrm_admissibility(hrm_ctx* c, int64_t counts[4]) {
+  if (!c || !counts) return HRM_E_INVAL;
+  cudaMemsetAsync(&c->st->counts, 0, sizeof(c->st->counts), c->stream);
+  c->ck->admiss(c->Wn, c->dg, c->fl, c->st, c->stream);
+  ++c->launches;
+  unsigned long long h[4];
+  hrm_status s = cuda_check(c, cudaMemcpyAsync(h, c->st->counts, sizeof h, cudaMemcpyDeviceToHost, c->stream),
+                            "read counters");
+  if (s) return s;
+  if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "admissibility sync"))) return s;
+  for (int i = 0; i < 4; ++i) counts[i] = (int64_t)h[i];
+  return HRM_OK;
+}
+
+int64_t hrm_kernel_launches(const hrm_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"
+
+namespace hrm {
+const FaceKernels* face_kernels(int N, int D) {
+  if (D == 1) return face_kernels_d1(N);
+  if (D == 2) return face_kernels_d2(N);
+  if (D == 3) return face_kernels_d3(N);
+  return nullptr;
+}
+}  // namespace hrm

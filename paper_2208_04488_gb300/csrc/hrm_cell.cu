@@ -1,0 +1,55 @@
+// Per-cell kernels, instantiated for N = 2..3 species and D = 1..3 dimensions.
+// Built without FMA contraction (see hrm_cell.cuh).
+#include "hrm_cell.cuh"
+#include "hrm_launch.h"
+
+namespace hrm {
+namespace {
+
+template <int N, int D>
+void prim_l(const double* W, double* V, double* AUX, const DevGrid& g, const DevFluid& f, StepState* st, int tau,
+            cudaStream_t s) {
+  k_prim<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, V, AUX, g, f, st, tau);
+}
+template <int N, int D>
+void ic_l(const double* prim, double* W, const DevGrid& g, const DevFluid& f, cudaStream_t s) {
+  k_ic<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(prim, W, g, f);
+}
+template <int N, int D>
+void relax_l(double* W, const DevGrid& g, const DevFluid& f, cudaStream_t s) {
+  k_relax<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, g, f);
+}
+template <int N, int D>
+void fields_l(const double* W, double* out, int field, const DevGrid& g, const DevFluid& f, cudaStream_t s) {
+  k_fields<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, out, field, g, f);
+}
+template <int N, int D>
+void admiss_l(const double* W, const DevGrid& g, const DevFluid& f, StepState* st, cudaStream_t s) {
+  k_admiss<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, g, f, st);
+}
+
+template <int N, int D>
+const CellKernels* table() {
+  static const CellKernels t = {prim_l<N, D>, ic_l<N, D>, relax_l<N, D>, fields_l<N, D>, admiss_l<N, D>};
+  return &t;
+}
+
+}  // namespace
+
+const CellKernels* cell_kernels(int N, int D) {
+  if (N == 2 && D == 1) return table<2, 1>();
+  if (N == 2 && D == 2) return table<2, 2>();
+  if (N == 2 && D == 3) return table<2, 3>();
+  if (N == 3 && D == 1) return table<3, 1>();
+  if (N == 3 && D == 2) return table<3, 2>();
+  if (N == 3 && D == 3) return table<3, 3>();
+  return nullptr;
+}
+
+void launch_finalize(StepState* st, const DevGrid& g, int D, double cfl, int mode, cudaStream_t s) {
+  k_finalize<<<1, 32, 0, s>>>(st, g, D, cfl, mode);
+}
+
+void launch_set_dt(StepState* st, double dt, cudaStream_t s) { k_set_dt<<<1, 32, 0, s>>>(st, dt); }
+
+}  // namespace hrm

@@ -1,0 +1,260 @@
+// Per-cell kernels: primitive variables and the CFL reduction, the step-scalar
+// finalisation, the initial state in p-T equilibrium, standalone relaxation,
+// output fields and admissibility counters. Compiled without FMA contraction
+// (these are cheap), so their results are the IEEE-rounded evaluation of the
+// expressions as written.
+#pragma once
+
+#include "hrm_kernels.cuh"
+
+namespace hrm {
+
+// Primitive variables of a conservative vector (Sec. 2): rho = sum alpha_k rho_k,
+// u_d = rho u_d / rho, p from the mixture EOS p/(gbar-1) + gbar pbar_inf/(gbar-1) =
+// rho (e - qbar), rho c^2 = gbar (p + pbar_inf), c = sqrt(rho c^2 / rho).
+template <int N, int D>
+__device__ __forceinline__ void cell_prim(const double* W, const DevFluid& f, double* V, double& rho,
+                                          double& c, double& rc2) {
+  using L = Lay<N, D>;
+  rho = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) rho += W[k];
+  double S, P;
+  mix_SP<double, N>(f, &W[L::AL], S, P);
+  const double re = rhoe_tilde<N, D>(W, f);
+  const double p = (re - P) / S;
+#pragma unroll
+  for (int k = 0; k < N; ++k) V[k] = W[k];
+#pragma unroll
+  for (int d = 0; d < D; ++d) V[L::MOM + d] = W[L::MOM + d] / rho;
+  V[L::EN] = p;
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) V[L::AL + k] = W[L::AL + k];
+  rc2 = rho_c2(S, P, p);
+  c = sqrt(rc2 / rho);
+}
+
+// Order-preserving bits of a non-negative double (IEEE order equals unsigned order).
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+
+// Per cell: V (M planes), AUX = (c, rho, rho c^2). With `tau`, also the running
+// maxima tau_d = max(|u_d| + c)/dx_d (Sec. 4.1.2): warp shuffles, then one
+// atomicMax per block and direction on the order-preserving bits.
+template <int N, int D>
+__global__ void __launch_bounds__(kCellThreads)
+    k_prim(const double* __restrict__ W, double* __restrict__ V, double* __restrict__ AUX, DevGrid g,
+           DevFluid f, StepState* st, int tau) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nc = g.ncells;
+  double s[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) s[d] = 0.0;
+  if (c < nc) {
+    double w[M], v[M], rho, cs, rc2;
+#pragma unroll
+    for (int m = 0; m < M; ++m) w[m] = W[m * nc + c];
+    cell_prim<N, D>(w, f, v, rho, cs, rc2);
+#pragma unroll
+    for (int m = 0; m < M; ++m) V[m * nc + c] = v[m];
+    AUX[c] = cs;
+    AUX[nc + c] = rho;
+    AUX[2 * nc + c] = rc2;
+#pragma unroll
+    for (int d = 0; d < D; ++d) s[d] = (fabs(v[L::MOM + d]) + cs) / g.dx[d];
+  }
+  if (!tau) return;
+  __shared__ unsigned long long red[D][kCellThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    unsigned long long b = dbits(s[d]);
+    // NaN wave speeds (non-admissible states) reduce as the largest value
+    if (s[d] != s[d]) b = 0x7ff8000000000000ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long x = __shfl_xor_sync(0xffffffffu, b, o);
+      b = x > b ? x : b;
+    }
+    if (lane == 0) red[d][wid] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < D) {
+    unsigned long long b = 0;
+    for (int w = 0; w < kCellThreads / 32; ++w) b = red[threadIdx.x][w] > b ? red[threadIdx.x][w] : b;
+    atomicMax(&st->tau_bits[threadIdx.x], b);
+  }
+}
+
+// Step scalars from the reduced tau_d (Sec. 4.1.2): dt = cfl / sum tau, or the
+// requested dt; sigma_d = tau_d / sum tau, lambda_d = dt / (sigma_d dx_d).
+// mode 0 advances the step time and count, mode 1 only answers a dt query.
+__global__ void k_finalize(StepState* st, DevGrid g, int D, double cfl, int mode) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double tau[3] = {0.0, 0.0, 0.0}, sum = 0.0;
+  for (int d = 0; d < D; ++d) {
+    tau[d] = __longlong_as_double((long long)st->tau_bits[d]);
+    sum = sum + tau[d];
+    st->tau_bits[d] = 0ull;
+  }
+  const double dt = (mode == 0 && st->dt_req > 0.0) ? st->dt_req : cfl / sum;
+  for (int d = 0; d < D; ++d) {
+    const double sigma = tau[d] / sum;
+    st->lam[d] = dt / (sigma * g.dx[d]);
+    st->tau[d] = tau[d];
+  }
+  st->dt = dt;
+  if (mode == 0) {
+    st->t = st->t + dt;
+    st->steps = st->steps + 1;
+  }
+}
+
+__global__ void k_set_dt(StepState* st, double dt_req) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) st->dt_req = dt_req;
+}
+
+// Initial state from primitive planes (alpha_1..alpha_{N-1}, u_d, p, T) in p-T
+// equilibrium: rho_k = (p + p_inf_k) / ((gamma_k - 1) c_v,k T) and the mixture EOS.
+template <int N, int D>
+__global__ void __launch_bounds__(kCellThreads)
+    k_ic(const double* __restrict__ prim, double* __restrict__ W, DevGrid g, DevFluid f) {
+  using L = Lay<N, D>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nc = g.ncells;
+  if (c >= nc) return;
+  double al[N], s = 0.0;
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) {
+    al[k] = prim[k * nc + c];
+    s += al[k];
+  }
+  al[N - 1] = 1.0 - s;
+  const double p = prim[(N + D - 1) * nc + c], T = prim[(N + D) * nc + c];
+  double rho = 0.0, E = 0.0, ar[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double rhok = (p + f.pinf[k]) / (f.Rg[k] * T);
+    ar[k] = al[k] * rhok;
+    rho = rho + ar[k];
+    E = E + al[k] * (p + f.gamma[k] * f.pinf[k]) * f.inv_gm1[k] + ar[k] * f.q[k];
+  }
+  double kin = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double u = prim[(N - 1 + d) * nc + c];
+    kin = kin + u * u;
+    W[(L::MOM + d) * nc + c] = rho * u;
+  }
+  E = E + 0.5 * rho * kin;
+#pragma unroll
+  for (int k = 0; k < N; ++k) W[k * nc + c] = ar[k];
+  W[L::EN * nc + c] = E;
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) W[(L::AL + k) * nc + c] = al[k];
+}
+
+template <int N, int D>
+__global__ void __launch_bounds__(kCellThreads) k_relax(double* W, DevGrid g, DevFluid f) {
+  using L = Lay<N, D>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nc = g.ncells;
+  if (c >= nc) return;
+  double w[L::M];
+#pragma unroll
+  for (int m = 0; m < L::M; ++m) w[m] = W[m * nc + c];
+  relax_cell<N, D>(w, f);
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) W[(L::AL + k) * nc + c] = w[L::AL + k];
+}
+
+// Four-equation HRM sound speed (Eq. 4_eqn_sos): Psi_k and Gamma by implicit
+// differentiation of A_p p^2 + B_p p + C_p = 0 at the relaxed pressure.
+template <int N, int D>
+__device__ __forceinline__ double c4eq(const double* W, const DevFluid& f, double p) {
+  const int l = f.liq;
+  double rho = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) rho += W[k];
+  double Y[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) Y[k] = W[k] / rho;
+  const double re = rhoe_tilde<N, D>(W, f);
+  double cvb = 0.0, cpb = 0.0, qb = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    cvb += Y[k] * f.cv[k];
+    cpb += Y[k] * f.cp[k];
+    qb += Y[k] * f.q[k];
+  }
+  const double pinf1 = f.pinf[l], R1 = f.Rg[l], Rb = cpb - cvb;
+  const double Bp = -(re * Rb - pinf1 * cvb - pinf1 * Y[l] * R1);
+  const double den = 2.0 * cvb * p + Bp;
+  const double Gam = (-(-(rho * Rb) * p - pinf1 * rho * (Rb - Y[l] * R1)) / den) / rho;
+  double c2 = Gam * p / rho;
+  const double e = re / rho + qb;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double dre = e - f.q[k];
+    const double dcv = (f.cv[k] - cvb) / rho;
+    const double dRb = (f.Rg[k] - Rb) / rho;
+    const double dY1 = ((k == l ? 1.0 : 0.0) - Y[l]) / rho;
+    const double dB = -(dre * Rb + re * dRb - pinf1 * dcv - pinf1 * R1 * dY1);
+    const double dC = -(pinf1 * (dre * (Rb - Y[l] * R1) + re * (dRb - R1 * dY1)));
+    c2 += Y[k] * (-(dcv * p * p + dB * p + dC) / den);
+  }
+  return sqrt(c2);
+}
+
+// Output fields of the current state (HRM_FIELD_*).
+template <int N, int D>
+__global__ void __launch_bounds__(kCellThreads)
+    k_fields(const double* __restrict__ W, double* __restrict__ out, int field, DevGrid g, DevFluid f) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nc = g.ncells;
+  if (c >= nc) return;
+  double w[M], v[M], rho, cs, rc2;
+#pragma unroll
+  for (int m = 0; m < M; ++m) w[m] = W[m * nc + c];
+  if (field == 1 || field == 2) {
+    cell_prim<N, D>(w, f, v, rho, cs, rc2);
+    if (field == 1) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) out[m * nc + c] = v[m];
+    } else {
+      out[c] = cs;
+    }
+    return;
+  }
+  double pT[2];
+  double wr[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) wr[m] = w[m];
+  relax_cell<N, D>(wr, f, pT);
+  if (field == 3) {
+    out[c] = pT[0];
+    out[nc + c] = pT[1];
+  } else {
+    out[c] = c4eq<N, D>(w, f, pT[0]);
+  }
+}
+
+template <int N, int D>
+__global__ void __launch_bounds__(kCellThreads)
+    k_admiss(const double* __restrict__ W, DevGrid g, DevFluid f, StepState* st) {
+  using L = Lay<N, D>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nc = g.ncells;
+  if (c >= nc) return;
+  double w[L::M];
+#pragma unroll
+  for (int m = 0; m < L::M; ++m) w[m] = W[m * nc + c];
+  count_bits(st, admissibility_bits<N, D>(w, f));
+}
+
+}  // namespace hrm

@@ -1,0 +1,225 @@
+// Device-side building blocks of the PP-WCNS-IS fractional algorithm
+// (Wong, Angel & Kiris, arXiv 2208.04488) for sm_103a.
+//
+// Everything here is register-resident, templated on the number of species N,
+// the number of dimensions D and the bulk compute type R (double for the FP64
+// path, float for the precision form). The state itself always lives in FP64.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define HRM_MAXN 4
+
+namespace hrm {
+
+// ---------------------------------------------------------------- launch-time descriptions
+
+// Species constants, derived once on the host from gamma, p_inf, c_v, q (Sec. 2).
+struct DevFluid {
+  int32_t liq;  // index of the stiffened gas (Sec. 4.2 calls it species 1)
+  int32_t pad;
+  double inv_gm1[HRM_MAXN];    // 1/(gamma_k - 1)
+  double gpinf_gm1[HRM_MAXN];  // gamma_k p_inf_k / (gamma_k - 1)
+  double cv[HRM_MAXN], cp[HRM_MAXN], Rg[HRM_MAXN];  // c_v, c_p, c_p - c_v
+  double q[HRM_MAXN], pinf[HRM_MAXN], gamma[HRM_MAXN];
+};
+
+struct DevGrid {
+  int64_t n[3];
+  int64_t ncells;
+  double dx[3], inv_dx[3];
+  int32_t bc[6];  // 0 transmissive, 1 periodic
+};
+
+struct DevParams {
+  int32_t limiters, blend, scheme, qexp;
+  double eps_ar, eps_a, eps_rhoe, hs_ar, hs_a, hs_rc2, hs_rhoe, weno_eps, Cs;
+};
+
+// Per-step scalars kept on the device so that a captured graph needs no host input.
+struct StepState {
+  double dt;        // step size in use
+  double dt_req;    // > 0: requested step; <= 0: CFL step
+  double cfl;
+  double lam[3];    // flux-limiter lambda_d = dt / (sigma_d dx_d)
+  double tau[3];    // tau_d of the step-start state
+  double t;         // simulated time
+  long long steps;
+  unsigned long long tau_bits[3];  // running maxima (bit patterns of non-negative doubles)
+  unsigned long long counts[4];    // admissibility counters
+};
+
+// ---------------------------------------------------------------- small helpers
+
+template <typename T> __device__ __forceinline__ T dmin(T a, T b) { return (b < a) ? b : a; }
+template <typename T> __device__ __forceinline__ T dmax(T a, T b) { return (a < b) ? b : a; }
+
+__device__ __forceinline__ double rsqrt_r(double x) { return sqrt(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tanh_r(double x) { return tanh(x); }
+__device__ __forceinline__ float tanh_r(float x) { return tanhf(x); }
+
+// Index of cell j (may lie in the 3 ghost layers) along direction d under the
+// boundary condition of that side: transmissive copies the first interior cell
+// (zeroth-order extrapolation), periodic wraps.
+__device__ __forceinline__ int64_t bc_map(const DevGrid& g, int d, int64_t j) {
+  const int64_t n = g.n[d];
+  if (j < 0) return g.bc[2 * d] == 1 ? j + n : 0;
+  if (j >= n) return g.bc[2 * d + 1] == 1 ? j - n : n - 1;
+  return j;
+}
+
+template <int N, int D>
+struct Lay {
+  static constexpr int M = 2 * N + D;
+  static constexpr int MOM = N;          // first momentum / velocity slot
+  static constexpr int EN = N + D;       // E in W, p in V
+  static constexpr int AL = N + D + 1;   // first stored volume fraction
+  static constexpr int NC = N + D + 1;   // number of conservative (non-alpha) slots
+};
+
+// ---------------------------------------------------------------- mixture rules (Sec. 2)
+
+// S = 1/(gbar - 1), P = gbar pbar_inf / (gbar - 1) from the N-1 stored alphas.
+template <typename R, int N>
+__device__ __forceinline__ void mix_SP(const DevFluid& f, const R* al_stored, R& S, R& P) {
+  R sum = R(0);
+  S = R(0);
+  P = R(0);
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) sum = sum + al_stored[k];
+  const R last = R(1) - sum;  // alpha_N = 1 - sum of the others (Sec. 2)
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    R a = (k < N - 1) ? al_stored[k] : last;
+    S = S + a * R(f.inv_gm1[k]);
+    P = P + a * R(f.gpinf_gm1[k]);
+  }
+}
+
+// rho c^2 = gbar (p + pbar_inf) = (1 + 1/S) p + P/S
+template <typename R>
+__device__ __forceinline__ R rho_c2(R S, R P, R p) {
+  R gb = R(1) + R(1) / S;
+  return gb * p + P / S;
+}
+
+// ---------------------------------------------------------------- WENO-IS (App. C)
+
+// Left-biased incremental-stencil WENO value at x_{i+1/2} from
+// (u_{i-2}, u_{i-1}, u_i, u_{i+1}, u_{i+2}).
+template <typename R>
+__device__ __forceinline__ R weno_is(R um2, R um1, R u0, R up1, R up2, R eps) {
+  const R s0 = R(0.5) * (u0 + up1);
+  const R s1 = R(0.5) * (R(3) * u0 - um1);
+  const R s2 = R(0.125) * (R(3) * u0 + R(6) * up1 - up2);
+  const R s3 = R(0.125) * (R(3) * um2 - R(10) * um1 + R(15) * u0);
+  const R c13_12 = R(13.0 / 12.0);
+  R t;
+  const R b0 = (u0 - up1) * (u0 - up1);
+  const R b1 = (um1 - u0) * (um1 - u0);
+  t = um1 - R(2) * u0 + up1;
+  const R t01 = um1 - up1;
+  const R b01 = c13_12 * t * t + R(0.25) * t01 * t01;
+  t = u0 - R(2) * up1 + up2;
+  R tt = R(3) * u0 - R(4) * up1 + up2;
+  const R b2 = c13_12 * t * t + R(0.25) * tt * tt;
+  t = um2 - R(2) * um1 + u0;
+  tt = um2 - R(4) * um1 + R(3) * u0;
+  const R b3 = c13_12 * t * t + R(0.25) * tt * tt;
+  t = up2 - R(4) * up1 + R(6) * u0 - R(4) * um1 + um2;
+  tt = up2 - R(2) * up1 + R(2) * um1 - um2;
+  const R tau5 = c13_12 * t * t + R(0.25) * tt * tt;
+  const R q01 = tau5 / (b01 + eps);
+  const R e0 = R(15.0 / 32.0) * (R(1) + (tau5 / (b0 + eps)) * q01);
+  const R e1 = R(5.0 / 32.0) * (R(1) + (tau5 / (b1 + eps)) * q01);
+  const R e2 = R(5.0 / 16.0) * (R(1) + tau5 / (b2 + eps));
+  const R e3 = R(1.0 / 16.0) * (R(1) + tau5 / (b3 + eps));
+  const R inv = R(1) / (e0 + e1 + e2 + e3);
+  return (e0 * inv) * s0 + (e1 * inv) * s1 + (e2 * inv) * s2 + (e3 * inv) * s3;
+}
+
+// ---------------------------------------------------------------- HLLC (Sec. 4.1.1)
+
+// Conservative vector, total energy and sound speed of a primitive state.
+template <typename R, int N, int D>
+struct PrimState {
+  R V[Lay<N, D>::M];
+  R rho, E, c;
+};
+
+template <typename R, int N, int D>
+__device__ __forceinline__ void prim_state(const DevFluid& f, PrimState<R, N, D>& s) {
+  using L = Lay<N, D>;
+  R rho = R(0), rq = R(0), kin = R(0);
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    rho = rho + s.V[k];
+    rq = rq + s.V[k] * R(f.q[k]);
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) kin = kin + s.V[L::MOM + d] * s.V[L::MOM + d];
+  R S, P;
+  mix_SP<R, N>(f, &s.V[L::AL], S, P);
+  const R p = s.V[L::EN];
+  s.rho = rho;
+  s.E = (S * p + P) + R(0.5) * rho * kin + rq;
+  s.c = rsqrt_r(rho_c2(S, P, p) / rho);
+}
+
+// HLLC flux of the flux-source form G (F^HLLC plus the upwind alpha s_* in the
+// alpha slots) and s_*, from two primitive states. At s_* = 0 the two star
+// fluxes are averaged ((1 +- sign)/2 with sign(0) = 0).
+template <typename R, int N, int D, int DIR>
+__device__ __forceinline__ R hllc(const DevFluid& f, PrimState<R, N, D>& Ls, PrimState<R, N, D>& Rs,
+                                  R* G) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+  prim_state<R, N, D>(f, Ls);
+  prim_state<R, N, D>(f, Rs);
+  const R uL = Ls.V[L::MOM + DIR], uR = Rs.V[L::MOM + DIR];
+  const R pL = Ls.V[L::EN], pR = Rs.V[L::EN];
+  const R ubar = R(0.5) * (uL + uR), cbar = R(0.5) * (Ls.c + Rs.c);
+  const R sL = dmin(ubar - cbar, uL - Ls.c);
+  const R sR = dmax(ubar + cbar, uR + Rs.c);
+  const R ss = (pR - pL + Ls.rho * uL * (sL - uL) - Rs.rho * uR * (sR - uR)) /
+               (Ls.rho * (sL - uL) - Rs.rho * (sR - uR));
+  const int sg = (ss > R(0)) ? 1 : ((ss < R(0)) ? -1 : 0);
+  const R wL = (sg > 0) ? R(1) : ((sg < 0) ? R(0) : R(0.5));
+  const R wR = R(1) - wL;
+#pragma unroll
+  for (int m = 0; m < M; ++m) G[m] = R(0);
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    if ((side == 0 && sg < 0) || (side == 1 && sg > 0)) continue;
+    PrimState<R, N, D>& K = side == 0 ? Ls : Rs;
+    const R w = side == 0 ? wL : wR;
+    const R uK = side == 0 ? uL : uR;
+    const R pK = side == 0 ? pL : pR;
+    const R sK = side == 0 ? sL : sR;
+    const R sfac = side == 0 ? dmin(R(0), sL) : dmax(R(0), sR);
+    const R chi = (sK - uK) / (sK - ss);
+    // F_K + s_{-/+} (W_{*,K} - W_K), conservative slots
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const R wk = K.V[k];
+      G[k] = G[k] + w * (wk * uK + sfac * (chi * wk - wk));
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const R mom = K.rho * K.V[L::MOM + d];
+      R Fm = mom * uK;
+      if (d == DIR) Fm = Fm + pK;
+      const R ms = (d == DIR) ? chi * K.rho * ss : chi * mom;
+      G[L::MOM + d] = G[L::MOM + d] + w * (Fm + sfac * (ms - mom));
+    }
+    const R Es = chi * (K.E + (ss - uK) * (K.rho * ss + pK / (sK - uK)));
+    G[L::EN] = G[L::EN] + w * ((K.E + pK) * uK + sfac * (Es - K.E));
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) G[L::AL + k] = G[L::AL + k] + w * (K.V[L::AL + k] * ss);
+  }
+  return ss;
+}
+
+}  // namespace hrm

@@ -1,0 +1,48 @@
+// Per-midpoint and per-cell-update kernels for D = 3, N = 2..3 species,
+// FP64 and FP32-bulk midpoint arithmetic.
+#include "hrm_kernels.cuh"
+#include "hrm_launch.h"
+
+namespace hrm {
+namespace {
+
+constexpr int kD = 3;
+
+template <int N, int DIR>
+void face_l(int precision, const double* W, const double* V, const double* AUX, double* out, const DevGrid& g,
+            const DevFluid& f, const DevParams& p, const StepState* st, cudaStream_t s) {
+  if constexpr (DIR < kD) {
+    const long long nf = (g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
+    if (precision == 1)
+      k_face<float, N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, out, g, f, p, st);
+    else
+      k_face<double, N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, out, g, f, p, st);
+  }
+}
+
+template <int N>
+void update_l(int mode, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
+              const double* F2, const DevGrid& g, const DevFluid& f, StepState* st, double a, double b, int relax,
+              int count, cudaStream_t s) {
+  const unsigned gr = grid_for(g.ncells, kCellThreads);
+  if (mode == 1)
+    k_update<N, kD, 1><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count);
+  else
+    k_update<N, kD, 0><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count);
+}
+
+template <int N>
+const FaceKernels* table() {
+  static const FaceKernels t = {{face_l<N, 0>, face_l<N, 1>, face_l<N, 2>}, update_l<N>};
+  return &t;
+}
+
+}  // namespace
+
+const FaceKernels* face_kernels_d3(int N) {
+  if (N == 2) return table<2>();
+  if (N == 3) return table<3>();
+  return nullptr;
+}
+
+}  // namespace hrm

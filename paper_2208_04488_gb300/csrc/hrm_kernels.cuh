@@ -1,0 +1,597 @@
+// Kernel templates of the PP-WCNS-IS fractional step (arXiv 2208.04488).
+//
+// One RK stage is: k_prim (per cell: primitive variables, sound speed, and at
+// the first stage the CFL max-wave-speed reduction) -> k_face for each direction
+// (per midpoint: characteristic projection, WENO-IS, interpolation limiter,
+// two HLLC solves, HCS reconstruction, shock-sensor blending, quasi-conservative
+// fluxes and the flux limiter) -> k_update (per cell: flux difference with the
+// non-conservative alpha term, SSP-RK combination, thermal relaxation,
+// admissibility counters).
+#pragma once
+
+#include "hrm_device.cuh"
+
+namespace hrm {
+
+constexpr int kFaceThreads = 128;
+constexpr int kCellThreads = 256;
+
+// Face grid of direction DIR: n with n[DIR] + 1 entries along DIR.
+template <int DIR>
+__device__ __forceinline__ int64_t face_count(const DevGrid& g) {
+  return (g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
+}
+
+// ---------------------------------------------------------------- interpolation limiter
+
+// Positivity-preserving interpolation limiter (Sec. 4.3.2, Alg. interp_limit_densities,
+// Alg. interp_limit_vol_frac, hard switch) applied to the midpoint primitive
+// state Vt against the first-order (node) state Vn; velocity and pressure are
+// held, partial densities and volume fractions are limited, theta in FP64.
+template <typename R, int N, int D>
+__device__ __forceinline__ void interp_limit(R* Vt, const double* Vn, double rc2n, const DevFluid& f,
+                                             const DevParams& pr) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double lo = Vn[k], hi = (double)Vt[k];
+    const double tgt = dmin(pr.eps_ar, lo);
+    double th = 1.0;
+    if (hi < tgt) th = (tgt - lo) / (hi - lo);
+    Vt[k] = R((1.0 - th) * lo + th * hi);
+  }
+  double alt[N], aln[N];
+  {
+    double st = 0.0, sn = 0.0;
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+      alt[k] = (double)Vt[L::AL + k];
+      aln[k] = Vn[L::AL + k];
+      st += alt[k];
+      sn += aln[k];
+    }
+    alt[N - 1] = 1.0 - st;
+    aln[N - 1] = 1.0 - sn;
+  }
+  double th = 1.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double tgt = dmin(pr.eps_a, aln[k]);
+    double thk = 1.0;
+    if (alt[k] < tgt) thk = (tgt - aln[k]) / (alt[k] - aln[k]);
+    th = dmin(th, thk);
+  }
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) Vt[L::AL + k] = R((1.0 - th) * aln[k] + th * alt[k]);
+  // hard switch
+  bool hs = false;
+  {
+    double st = 0.0;
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+      alt[k] = (double)Vt[L::AL + k];
+      st += alt[k];
+    }
+    alt[N - 1] = 1.0 - st;
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    hs |= (double)Vt[k] < dmin(pr.hs_ar, Vn[k]);
+    hs |= alt[k] < dmin(pr.hs_a, aln[k]);
+  }
+  double S, P;
+  mix_SP<double, N>(f, alt, S, P);
+  const double rc2 = rho_c2(S, P, (double)Vt[L::EN]);
+  hs |= rc2 < dmin(pr.hs_rc2, rc2n);
+  if (hs) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) Vt[m] = R(Vn[m]);
+  }
+}
+
+// ---------------------------------------------------------------- flux limiter helpers
+
+// rho (e - qbar) of a conservative vector (Sec. 2).
+template <int N, int D>
+__device__ __forceinline__ double rhoe_tilde(const double* W, const DevFluid& f) {
+  using L = Lay<N, D>;
+  double rho = 0.0, kin = 0.0, rq = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    rho += W[k];
+    rq += W[k] * f.q[k];
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) kin += W[L::MOM + d] * W[L::MOM + d];
+  return W[L::EN] - 0.5 * kin / rho - rq;
+}
+
+__device__ __forceinline__ double theta_of(double lo, double hi, double eps) {
+  const double tgt = dmin(eps, lo);
+  return (hi < tgt) ? (tgt - lo) / (hi - lo) : 1.0;
+}
+
+// A midpoint flux in the compact form used between kernels: the conservative
+// slots Gc (identical for G^- and G^+), the alpha flux ga and the velocity u,
+// so that G^-_alpha = ga - u alpha_i and G^+_alpha = ga - u alpha_{i+1} (Eq. G_pm).
+template <int N, int D>
+struct FluxPack {
+  double Gc[Lay<N, D>::NC];
+  double ga[N - 1 > 0 ? N - 1 : 1];
+  double u;
+};
+
+// Half-cell state W_i + s (G - F_i) with G = pack evaluated against alpha_own.
+template <int N, int D>
+__device__ __forceinline__ void half_state(const double* Wn, const double* Fn, const FluxPack<N, D>& G,
+                                           double s, double* out) {
+  using L = Lay<N, D>;
+#pragma unroll
+  for (int m = 0; m < L::NC; ++m) out[m] = Wn[m] + s * (G.Gc[m] - Fn[m]);
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) out[L::AL + k] = Wn[L::AL + k] + s * (G.ga[k] - G.u * Wn[L::AL + k]);
+}
+
+template <int N, int D>
+__device__ __forceinline__ void mix_pack(const FluxPack<N, D>& H, const FluxPack<N, D>& G, double th,
+                                         FluxPack<N, D>& out) {
+  using L = Lay<N, D>;
+#pragma unroll
+  for (int m = 0; m < L::NC; ++m) out.Gc[m] = (1.0 - th) * H.Gc[m] + th * G.Gc[m];
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) out.ga[k] = (1.0 - th) * H.ga[k] + th * G.ga[k];
+  out.u = (1.0 - th) * H.u + th * G.u;
+}
+
+template <int N, int D>
+__device__ __forceinline__ void all_alpha_W(const double* W, double* al) {
+  using L = Lay<N, D>;
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) {
+    al[k] = W[L::AL + k];
+    s += al[k];
+  }
+  al[N - 1] = 1.0 - s;
+}
+
+// Quasi-positivity-preserving flux limiter (Sec. 4.3.2, Alg.
+// flux_limit_densities_vol_frac, Alg. flux_limit_energy, hard switch), FP64.
+// Wi/Wj: W_i, W_{i+1}; Fi/Fj: conservative fluxes F(W_i), F(W_{i+1});
+// G: high-order midpoint flux, H: first-order HLLC flux; the result replaces G.
+template <int N, int D>
+__device__ __forceinline__ void flux_limit(const double* Wi, const double* Wj, const double* Fi,
+                                           const double* Fj, double lam, FluxPack<N, D>& G,
+                                           const FluxPack<N, D>& H, const DevFluid& f,
+                                           const DevParams& pr) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+  const double m2l = -2.0 * lam, p2l = 2.0 * lam;
+  double Wp[M], Wm[M], WHp[M], WHm[M];
+  half_state<N, D>(Wi, Fi, G, m2l, Wp);   // W_i^{+}
+  half_state<N, D>(Wj, Fj, G, p2l, Wm);   // W_{i+1}^{-} (alpha slots use alpha_{i+1})
+  half_state<N, D>(Wi, Fi, H, m2l, WHp);  // W_i^{HLLC,+}
+  half_state<N, D>(Wj, Fj, H, p2l, WHm);  // W_{i+1}^{HLLC,-}
+  double th = 1.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    th = dmin(th, dmin(theta_of(WHp[k], Wp[k], pr.eps_ar), theta_of(WHm[k], Wm[k], pr.eps_ar)));
+  }
+  double aHp[N], aHm[N];
+  all_alpha_W<N, D>(WHp, aHp);
+  all_alpha_W<N, D>(WHm, aHm);
+  {
+    double ap[N], am[N];
+    all_alpha_W<N, D>(Wp, ap);
+    all_alpha_W<N, D>(Wm, am);
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      th = dmin(th, dmin(theta_of(aHp[k], ap[k], pr.eps_a), theta_of(aHm[k], am[k], pr.eps_a)));
+  }
+  FluxPack<N, D> Gs;
+  mix_pack<N, D>(H, G, th, Gs);
+  // energy stage
+  const double rHp = rhoe_tilde<N, D>(WHp, f), rHm = rhoe_tilde<N, D>(WHm, f);
+  half_state<N, D>(Wi, Fi, Gs, m2l, Wp);  // W_i^{*,+}
+  half_state<N, D>(Wj, Fj, Gs, p2l, Wm);  // W_{i+1}^{*,-}
+  const double th2 = dmin(theta_of(rHp, rhoe_tilde<N, D>(Wp, f), pr.eps_rhoe),
+                          theta_of(rHm, rhoe_tilde<N, D>(Wm, f), pr.eps_rhoe));
+  FluxPack<N, D> Gss;
+  mix_pack<N, D>(H, Gs, th2, Gss);
+  // hard switch
+  half_state<N, D>(Wi, Fi, Gss, m2l, Wp);  // W_i^{**,+}
+  half_state<N, D>(Wj, Fj, Gss, p2l, Wm);  // W_{i+1}^{**,-}
+  bool hs = false;
+  {
+    double ap[N], am[N];
+    all_alpha_W<N, D>(Wp, ap);
+    all_alpha_W<N, D>(Wm, am);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      hs |= Wp[k] < dmin(pr.hs_ar, WHp[k]);
+      hs |= ap[k] < dmin(pr.hs_a, aHp[k]);
+      hs |= Wm[k] < dmin(pr.hs_ar, WHm[k]);
+      hs |= am[k] < dmin(pr.hs_a, aHm[k]);
+    }
+  }
+  hs |= rhoe_tilde<N, D>(Wp, f) < dmin(pr.hs_rhoe, rHp);
+  hs |= rhoe_tilde<N, D>(Wm, f) < dmin(pr.hs_rhoe, rHm);
+  G = hs ? H : Gss;
+}
+
+// ---------------------------------------------------------------- per-midpoint kernel
+
+// Loads of the six node cells i-2..i+3 of a midpoint.
+struct Nodes6 {
+  int64_t c[6];
+};
+
+template <int DIR>
+__device__ __forceinline__ bool face_nodes(const DevGrid& g, int64_t t, Nodes6& nd) {
+  const int64_t f0 = g.n[0] + (DIR == 0), f1 = g.n[1] + (DIR == 1), f2 = g.n[2] + (DIR == 2);
+  if (t >= f0 * f1 * f2) return false;
+  const int64_t i0 = t % f0;
+  const int64_t r = t / f0;
+  const int64_t i1 = r % f1, i2 = r / f1;
+  const int64_t fp = DIR == 0 ? i0 : (DIR == 1 ? i1 : i2);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int64_t q = bc_map(g, DIR, fp - 3 + j);
+    nd.c[j] = DIR == 0 ? (i2 * g.n[1] + i1) * g.n[0] + q
+                       : (DIR == 1 ? (i2 * g.n[1] + q) * g.n[0] + i0 : (q * g.n[1] + i1) * g.n[0] + i0);
+  }
+  return true;
+}
+
+// Conservative flux F^DIR of a node (Eq. F_x_F_y_def), NC slots.
+template <int N, int D, int DIR>
+__device__ __forceinline__ void node_flux(const double* W, const double* V, double* F) {
+  using L = Lay<N, D>;
+  const double un = V[L::MOM + DIR], p = V[L::EN];
+#pragma unroll
+  for (int k = 0; k < N; ++k) F[k] = W[k] * un;
+#pragma unroll
+  for (int d = 0; d < D; ++d) F[L::MOM + d] = W[L::MOM + d] * un + (d == DIR ? p : 0.0);
+  F[L::EN] = (W[L::EN] + p) * un;
+}
+
+// Outputs of a midpoint: (M + 1) planes -- NC conservative flux slots, N-1 alpha
+// fluxes, velocity -- over the face grid of the direction.
+template <typename R, int N, int D, int DIR>
+__global__ void __launch_bounds__(kFaceThreads)
+    k_face(const double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ AUX,
+           double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr, const StepState* __restrict__ st) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  Nodes6 nd;
+  if (!face_nodes<DIR>(g, t, nd)) return;
+  const int64_t nc = g.ncells;
+  const int64_t nf = face_count<DIR>(g);
+  const double* __restrict__ Cc = AUX;           // sound speed
+  const double* __restrict__ Rr = AUX + nc;      // mixture density
+  const double* __restrict__ RC2 = AUX + 2 * nc; // rho c^2
+
+  // node states i and i+1 (FP64)
+  double Vi[M], Vj[M], Wi[M], Wj[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    Vi[m] = V[m * nc + nd.c[2]];
+    Vj[m] = V[m * nc + nd.c[3]];
+    Wi[m] = W[m * nc + nd.c[2]];
+    Wj[m] = W[m * nc + nd.c[3]];
+  }
+
+  // first-order HLLC flux and u_* from the node states (Sec. 4.1.1)
+  FluxPack<N, D> H;
+  {
+    PrimState<double, N, D> a, b;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      a.V[m] = Vi[m];
+      b.V[m] = Vj[m];
+    }
+    double GH[M];
+    H.u = hllc<double, N, D, DIR>(f, a, b, GH);
+#pragma unroll
+    for (int m = 0; m < L::NC; ++m) H.Gc[m] = GH[m];
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) H.ga[k] = GH[L::AL + k];
+  }
+
+  FluxPack<N, D> G;
+  if (pr.scheme == 1) {
+    G = H;
+  } else {
+    R p6[6], u6[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      p6[j] = R(V[L::EN * nc + nd.c[j]]);
+      u6[j] = R(V[(L::MOM + DIR) * nc + nd.c[j]]);
+    }
+    // characteristic projection with the face-averaged state (App. D)
+    const R rhob = R(0.5) * (R(Rr[nd.c[2]]) + R(Rr[nd.c[3]]));
+    const R cb = R(0.5) * (R(Cc[nd.c[2]]) + R(Cc[nd.c[3]]));
+    const R inv_rc = R(1) / (rhob * cb);
+    const R rc2b = rhob * cb * cb;
+    const R eps = R(pr.weno_eps);
+    R UL[M], UR[M];
+    R w6[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) w6[j] = u6[j] - inv_rc * p6[j];
+    UL[0] = weno_is<R>(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
+    UR[0] = weno_is<R>(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) w6[j] = u6[j] + inv_rc * p6[j];
+    UL[M - 1] = weno_is<R>(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
+    UR[M - 1] = weno_is<R>(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+    R arb[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) w6[j] = R(V[k * nc + nd.c[j]]);
+      arb[k] = R(0.5) * (w6[2] + w6[3]);
+      const R coef = arb[k] / rc2b;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) w6[j] = w6[j] - coef * p6[j];
+      UL[1 + k] = weno_is<R>(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
+      UR[1 + k] = weno_is<R>(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+    }
+    {
+      int t_ = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        if (d == DIR) continue;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) w6[j] = R(V[(L::MOM + d) * nc + nd.c[j]]);
+        UL[N + 1 + t_] = weno_is<R>(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
+        UR[N + 1 + t_] = weno_is<R>(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+        ++t_;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) w6[j] = R(V[(L::AL + k) * nc + nd.c[j]]);
+      UL[N + D + k] = weno_is<R>(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
+      UR[N + D + k] = weno_is<R>(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+    }
+    // back to primitive variables, V~ = R U~
+    PrimState<R, N, D> sl, sr;
+    {
+      R h[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) h[k] = arb[k] / (R(2) * cb);
+      const R rc_2 = rhob * cb / R(2);
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const R* U = side == 0 ? UL : UR;
+        R* Vt = side == 0 ? sl.V : sr.V;
+#pragma unroll
+        for (int k = 0; k < N; ++k) Vt[k] = (-h[k]) * U[0] + U[1 + k] + h[k] * U[M - 1];
+        Vt[L::MOM + DIR] = R(0.5) * U[0] + R(0.5) * U[M - 1];
+        int t_ = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          if (d == DIR) continue;
+          Vt[L::MOM + d] = U[N + 1 + t_];
+          ++t_;
+        }
+        Vt[L::EN] = (-rc_2) * U[0] + rc_2 * U[M - 1];
+#pragma unroll
+        for (int k = 0; k < N - 1; ++k) Vt[L::AL + k] = U[N + D + k];
+      }
+    }
+    // positivity-preserving interpolation limiter (Sec. 4.3.2)
+    if (pr.limiters) {
+      interp_limit<R, N, D>(sl.V, Vi, RC2[nd.c[2]], f, pr);
+      interp_limit<R, N, D>(sr.V, Vj, RC2[nd.c[3]], f, pr);
+    }
+    // high-order midpoint flux G~ and velocity u~
+    R Gt[M];
+    const R ut = hllc<R, N, D, DIR>(f, sl, sr, Gt);
+    // explicit HCS reconstruction (Eqs. reconstructed_G, reconstructed_vel)
+    constexpr double psi = 256.0 / 175.0;
+    constexpr double a1 = 75.0 * psi / 128.0 - 37.0 / 60.0;
+    constexpr double a2 = 25.0 * psi / 256.0 - 2.0 / 15.0;
+    constexpr double a3 = 3.0 * psi / 256.0 - 1.0 / 60.0;
+    // shock sensor (Sec. 4.3.1) on rho and p
+    R sig = R(0);
+    if (pr.blend) {
+      R r6[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) r6[j] = R(Rr[nd.c[j]]);
+      auto half = [](R a, R b, R c, R d, R e) -> R {
+        const R num = fabs(R(16) * b - a - R(30) * c + R(16) * d - e);
+        const R den = fabs(a + R(16) * b + R(30) * c + R(16) * d + e);
+        return den == R(0) ? R(0) : num / den;
+      };
+      const R sr_ = R(0.5) * (half(r6[1], r6[2], r6[3], r6[4], r6[5]) + half(r6[0], r6[1], r6[2], r6[3], r6[4]));
+      const R sp_ = R(0.5) * (half(p6[1], p6[2], p6[3], p6[4], p6[5]) + half(p6[0], p6[1], p6[2], p6[3], p6[4]));
+      const R prod = sr_ * sp_;
+      R pw = prod;
+      for (int e = 1; e < pr.qexp; ++e) pw = pw * prod;
+      sig = tanh_r(R(pr.Cs) * pw);
+    }
+    const R one_m = R(1) - sig;
+    // node fluxes G of the flux-source form at the six nodes, slot by slot
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      R Gn[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const double un = (double)u6[j];
+        double v;
+        if (m < L::MOM) {
+          v = W[m * nc + nd.c[j]] * un;
+        } else if (m < L::EN) {
+          v = W[m * nc + nd.c[j]] * un + ((m - L::MOM) == DIR ? (double)p6[j] : 0.0);
+        } else if (m == L::EN) {
+          v = (W[m * nc + nd.c[j]] + (double)p6[j]) * un;
+        } else {
+          v = W[m * nc + nd.c[j]] * un;
+        }
+        Gn[j] = R(v);
+      }
+      const R ghcs = R(psi) * Gt[m] - R(a1) * (Gn[2] + Gn[3]) + R(a2) * (Gn[1] + Gn[4]) - R(a3) * (Gn[0] + Gn[5]);
+      const R gh = sig * Gt[m] + one_m * ghcs;
+      if (m < L::NC)
+        G.Gc[m] = (double)gh;
+      else
+        G.ga[m - L::AL] = (double)gh;
+    }
+    const R uhcs = R(psi) * ut - R(a1) * (u6[2] + u6[3]) + R(a2) * (u6[1] + u6[4]) - R(a3) * (u6[0] + u6[5]);
+    G.u = (double)(sig * ut + one_m * uhcs);
+
+    if (pr.limiters) {
+      double Fi[L::NC], Fj[L::NC];
+      node_flux<N, D, DIR>(Wi, Vi, Fi);
+      node_flux<N, D, DIR>(Wj, Vj, Fj);
+      flux_limit<N, D>(Wi, Wj, Fi, Fj, st->lam[DIR], G, H, f, pr);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < L::NC; ++m) out[m * nf + t] = G.Gc[m];
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) out[(L::AL + k) * nf + t] = G.ga[k];
+  out[M * nf + t] = G.u;
+}
+
+// ---------------------------------------------------------------- thermal relaxation (Sec. 4.2)
+
+// Infinite-rate thermal relaxation of one cell: keeps alpha_k rho_k, rho u, E and
+// replaces the stored alpha_k by rho Y_k / rho_k(p*, T*). p* is the positive root of
+// A_p p^2 + B_p p + C_p = 0 (Eqs. Ap_Bp_Cp_1-3, p_relax) in the cancellation-free
+// form, T* from Eq. T_relax_e. Species `liq` is the stiffened gas.
+template <int N, int D>
+__device__ __forceinline__ void relax_cell(double* W, const DevFluid& f, double* pT = nullptr) {
+  using L = Lay<N, D>;
+  const int l = f.liq;
+  double rho = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) rho += W[k];
+  double Y[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) Y[k] = W[k] / rho;
+  const double re = rhoe_tilde<N, D>(W, f);
+  double cvb = 0.0, cpb = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    cvb += Y[k] * f.cv[k];
+    cpb += Y[k] * f.cp[k];
+  }
+  const double pinf1 = f.pinf[l], R1 = f.Rg[l], Yl = Y[l];
+  const double Ap = cvb;
+  const double Bp = -(re * (cpb - cvb) - pinf1 * cvb - pinf1 * Yl * R1);
+  const double Cp = -(re * pinf1 * ((cpb - cvb) - Yl * R1));
+  const double sq = sqrt(Bp * Bp - 4.0 * Ap * Cp);
+  const double ps = (Bp > 0.0) ? (-2.0 * Cp) / (Bp + sq) : (sq - Bp) / (2.0 * Ap);
+  const double den = Yl * (ps + f.gamma[l] * pinf1) * f.cv[l] / (ps + pinf1) + cvb - Yl * f.cv[l];
+  const double Ts = (re / rho) / den;
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) {
+    const double rhok = (ps + f.pinf[k]) / (f.Rg[k] * Ts);
+    W[L::AL + k] = W[k] / rhok;
+  }
+  if (pT) {
+    pT[0] = ps;
+    pT[1] = Ts;
+  }
+}
+
+// Admissibility of a conservative state: bit 0 negative partial density, bit 1 a
+// volume fraction outside [0, 1], bit 2 rho c^2 <= 0, bit 3 rho e~ <= 0 (NaN counts).
+template <int N, int D>
+__device__ __forceinline__ int admissibility_bits(const double* W, const DevFluid& f) {
+  using L = Lay<N, D>;
+  int b = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (!(W[k] >= 0.0)) b |= 1;
+  double al[N];
+  all_alpha_W<N, D>(W, al);
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (!(al[k] >= 0.0 && al[k] <= 1.0)) b |= 2;
+  const double re = rhoe_tilde<N, D>(W, f);
+  double S, P;
+  mix_SP<double, N>(f, &W[L::AL], S, P);
+  const double p = (re - P) / S;
+  if (!(rho_c2(S, P, p) > 0.0)) b |= 4;
+  if (!(re > 0.0)) b |= 8;
+  return b;
+}
+
+__device__ __forceinline__ void count_bits(StepState* st, int b) {
+  if (b) {
+    for (int i = 0; i < 4; ++i)
+      if (b & (1 << i)) atomicAdd(&st->counts[i], 1ull);
+  }
+}
+
+// ---------------------------------------------------------------- per-cell update
+
+// RHS_i = -sum_d (G^{d,-}_{i+1/2} - G^{d,+}_{i-1/2}) / dx_d (Eq. semi_W_G_pm_eqn),
+// then W_out = a W^n + b (W_src + dt RHS) (SSP-RK stage in Shu-Osher form),
+// optionally followed by the thermal relaxation and the admissibility count.
+// MODE 1 writes RHS instead of the combination. In-place (W_out == W_src or W^n)
+// is allowed: each thread reads its own cell before writing it.
+template <int N, int D, int MODE>
+__global__ void __launch_bounds__(kCellThreads)
+    k_update(const double* Wn, const double* Wsrc, double* Wout, const double* __restrict__ F0,
+             const double* __restrict__ F1, const double* __restrict__ F2, DevGrid g, DevFluid f,
+             StepState* st, double a, double b, int relax, int count) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nc = g.ncells;
+  if (c >= nc) return;
+  const int64_t i0 = c % g.n[0];
+  const int64_t r = c / g.n[0];
+  const int64_t i1 = r % g.n[1], i2 = r / g.n[1];
+  double Ws[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) Ws[m] = Wsrc[m * nc + c];
+  double rhs[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) rhs[m] = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double* F = d == 0 ? F0 : (d == 1 ? F1 : F2);
+    const int64_t f0 = g.n[0] + (d == 0), f1 = g.n[1] + (d == 1), f2 = g.n[2] + (d == 2);
+    const int64_t nf = f0 * f1 * f2;
+    const int64_t fl = (i2 * f1 + i1) * f0 + i0;
+    const int64_t fr = fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1));
+    const double idx = g.inv_dx[d];
+#pragma unroll
+    for (int m = 0; m < L::NC; ++m) rhs[m] = rhs[m] - (F[m * nf + fr] - F[m * nf + fl]) * idx;
+    const double ur = F[M * nf + fr], ul = F[M * nf + fl];
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+      const int m = L::AL + k;
+      const double al = Ws[m];
+      rhs[m] = rhs[m] - ((F[m * nf + fr] - ur * al) - (F[m * nf + fl] - ul * al)) * idx;
+    }
+  }
+  if (MODE == 1) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) Wout[m * nc + c] = rhs[m];
+    return;
+  }
+  const double dt = st->dt;
+  double Wo[M];
+  if (a == 0.0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) Wo[m] = b * (Ws[m] + dt * rhs[m]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < M; ++m) Wo[m] = a * Wn[m * nc + c] + b * (Ws[m] + dt * rhs[m]);
+  }
+  if (relax) relax_cell<N, D>(Wo, f);
+  if (count) count_bits(st, admissibility_bits<N, D>(Wo, f));
+#pragma unroll
+  for (int m = 0; m < M; ++m) Wout[m * nc + c] = Wo[m];
+}
+
+}  // namespace hrm

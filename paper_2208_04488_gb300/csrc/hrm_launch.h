@@ -1,0 +1,41 @@
+// Host-side launchers of the kernel templates, one table per (N, D), so that
+// the C-ABI layer dispatches at run time and the heavy instantiations compile
+// in separate translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hrm_device.cuh"
+
+namespace hrm {
+
+struct CellKernels {
+  void (*prim)(const double* W, double* V, double* AUX, const DevGrid&, const DevFluid&, StepState*, int tau,
+               cudaStream_t);
+  void (*ic)(const double* prim, double* W, const DevGrid&, const DevFluid&, cudaStream_t);
+  void (*relax)(double* W, const DevGrid&, const DevFluid&, cudaStream_t);
+  void (*fields)(const double* W, double* out, int field, const DevGrid&, const DevFluid&, cudaStream_t);
+  void (*admiss)(const double* W, const DevGrid&, const DevFluid&, StepState*, cudaStream_t);
+};
+
+struct FaceKernels {
+  // precision: 0 FP64, 1 FP32 bulk
+  void (*face[3])(int precision, const double* W, const double* V, const double* AUX, double* out,
+                  const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+  void (*update)(int mode, const double* Wn, const double* Wsrc, double* Wout, const double* F0,
+                 const double* F1, const double* F2, const DevGrid&, const DevFluid&, StepState*, double a,
+                 double b, int relax, int count, cudaStream_t);
+};
+
+const CellKernels* cell_kernels(int N, int D);
+const FaceKernels* face_kernels(int N, int D);
+const FaceKernels* face_kernels_d1(int N);
+const FaceKernels* face_kernels_d2(int N);
+const FaceKernels* face_kernels_d3(int N);
+
+void launch_finalize(StepState* st, const DevGrid& g, int D, double cfl, int mode, cudaStream_t s);
+void launch_set_dt(StepState* st, double dt, cudaStream_t s);
+
+inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace hrm

@@ -1,0 +1,271 @@
+"""Python binding of the C ABI in include/hrm.h (ctypes, argument marshalling
+only). Every step of the method runs in the CUDA library; there is no CPU
+path: a missing library raises.
+
+Device buffers are passed as torch CUDA tensors (their data pointers), host
+buffers as numpy arrays; the CUDA stream is torch's current stream unless one
+is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhrm.so")
+HEADER = os.path.join(HERE, "..", "include", "hrm.h")
+
+HRM_OK, HRM_E_INVAL, HRM_E_CUDA, HRM_E_ADMISSIBILITY, HRM_E_TIMEOUT, HRM_E_NOMEM = 0, -1, -2, -3, -4, -5
+FIELD_W, FIELD_V, FIELD_C5, FIELD_PT, FIELD_C4 = 0, 1, 2, 3, 4
+FP64, FP32 = 0, 1
+RK3, EULER, RK2 = 0, 1, 2
+RELAX_OFF, RELAX_STAGE, RELAX_STEP = 0, 1, 2
+KERNEL_PRIM, KERNEL_FINALIZE, KERNEL_FACE_X, KERNEL_FACE_Y, KERNEL_FACE_Z, KERNEL_UPDATE = 0, 1, 2, 3, 4, 5
+KERNEL_NAMES = {0: "prim", 1: "finalize", 2: "face_x", 3: "face_y", 4: "face_z", 5: "update"}
+
+
+class HrmGrid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("pad", ctypes.c_int32), ("n", ctypes.c_int64 * 3),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("bc", ctypes.c_int32 * 6)]
+
+
+class HrmParams(ctypes.Structure):
+    _fields_ = [("cfl", ctypes.c_double),
+                ("limiters", ctypes.c_int32), ("blend", ctypes.c_int32), ("relax_mode", ctypes.c_int32),
+                ("scheme", ctypes.c_int32), ("integrator", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("learned", ctypes.c_int32), ("check", ctypes.c_int32),
+                ("eps_ar", ctypes.c_double), ("eps_a", ctypes.c_double), ("eps_rhoe", ctypes.c_double),
+                ("hs_ar", ctypes.c_double), ("hs_a", ctypes.c_double), ("hs_rc2", ctypes.c_double),
+                ("hs_rhoe", ctypes.c_double), ("weno_eps", ctypes.c_double), ("Cs", ctypes.c_double),
+                ("q_sensor", ctypes.c_double), ("learned_threshold", ctypes.c_double)]
+
+
+class HrmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"hrm status {status}: {message}")
+        self.status = status
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the functions declared in include/hrm.h."""
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hrm_[a-z0-9_]+)\s*\(", txt)))
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built ({LIB_PATH}); run "
+                           "paper_2208_04488_gb300.build.build() -- there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    L.hrm_params_default.argtypes = [P(HrmParams)]
+    L.hrm_params_default.restype = None
+    L.hrm_create.argtypes = [P(_VP), P(HrmGrid), ctypes.c_int32, _DP, _DP, _DP, _DP, P(HrmParams), _VP]
+    L.hrm_destroy.argtypes = [_VP]
+    L.hrm_destroy.restype = None
+    L.hrm_last_error.argtypes = [_VP]
+    L.hrm_last_error.restype = ctypes.c_char_p
+    L.hrm_set_params.argtypes = [_VP, P(HrmParams)]
+    L.hrm_set.argtypes = [_VP, _VP, ctypes.c_int32]
+    L.hrm_set_primitive.argtypes = [_VP, _VP, ctypes.c_int32]
+    L.hrm_dt.argtypes = [_VP, ctypes.c_double, _DP, _DP]
+    L.hrm_step.argtypes = [_VP, ctypes.c_double, ctypes.c_int32]
+    L.hrm_relax.argtypes = [_VP]
+    L.hrm_rhs.argtypes = [_VP, _DP, _VP]
+    L.hrm_get.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
+    L.hrm_time.argtypes = [_VP, _DP, P(ctypes.c_int64)]
+    L.hrm_admissibility.argtypes = [_VP, P(ctypes.c_int64)]
+    L.hrm_kernel_launches.argtypes = [_VP]
+    L.hrm_kernel_launches.restype = ctypes.c_int64
+    L.hrm_set_profiling.argtypes = [_VP, ctypes.c_int32]
+    L.hrm_set_profiling.restype = ctypes.c_int
+    L.hrm_profile_read.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                                   ctypes.POINTER(ctypes.c_int32)]
+    L.hrm_profile_read.restype = ctypes.c_int32
+    L.hrm_probe_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, _VP, _DP]
+    L.hrm_probe_fma_peak.restype = ctypes.c_int
+    for name in ("hrm_create", "hrm_set_params", "hrm_set", "hrm_set_primitive", "hrm_dt", "hrm_step",
+                 "hrm_relax", "hrm_rhs", "hrm_get", "hrm_time", "hrm_admissibility"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def probe_fma_peak(precision=FP64, iters=4096, stream=None) -> float:
+    """Measured FMA-pipe throughput (flop/s) of the current device."""
+    v = ctypes.c_double()
+    st = lib().hrm_probe_fma_peak(precision, iters, _VP(_stream_handle(stream)), ctypes.byref(v))
+    if st != HRM_OK:
+        raise HrmError(st, "fma probe failed")
+    return v.value
+
+
+def params_default(**overrides) -> HrmParams:
+    p = HrmParams()
+    lib().hrm_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _darr(values, n):
+    a = (ctypes.c_double * n)()
+    for i, v in enumerate(values):
+        a[i] = float(v)
+    return a
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return int(stream) if isinstance(stream, int) else int(stream.cuda_stream)
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+class Solver:
+    """One hrm_ctx: a problem's grid and species table on the GPU."""
+
+    def __init__(self, n, lo, hi, bc, gamma, pinf, cv, q=None, params: Optional[HrmParams] = None,
+                 stream=None):
+        L = lib()
+        self.N = len(gamma)
+        self.D = len(n)
+        self.M = 2 * self.N + self.D
+        self.n = list(n)
+        self.ncells = int(np.prod(n))
+        g = HrmGrid()
+        g.ndim = self.D
+        for d in range(3):
+            g.n[d] = n[d] if d < self.D else 1
+            g.lo[d] = lo[d] if d < self.D else 0.0
+            g.hi[d] = hi[d] if d < self.D else 1.0
+        for i in range(6):
+            g.bc[i] = bc[i] if i < len(bc) else 0
+        self.grid = g
+        self.params = params if params is not None else params_default()
+        self.stream = _stream_handle(stream)
+        h = _VP()
+        st = L.hrm_create(ctypes.byref(h), ctypes.byref(g), self.N, _darr(gamma, self.N), _darr(pinf, self.N),
+                          _darr(cv, self.N), None if q is None else _darr(q, self.N), ctypes.byref(self.params),
+                          _VP(self.stream))
+        if st != HRM_OK:
+            raise HrmError(st, L.hrm_last_error(None).decode())
+        self.h = h
+
+    @classmethod
+    def from_problem(cls, problem, params: Optional[HrmParams] = None, stream=None, set_state=True):
+        s = cls(problem.n, problem.lo, problem.hi, problem.bc, problem.gamma, problem.pinf, problem.cv,
+                problem.q, params=params, stream=stream)
+        if set_state:
+            s.set_primitive(problem.prim)
+        return s
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hrm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != HRM_OK:
+            raise HrmError(st, lib().hrm_last_error(self.h).decode())
+        return st
+
+    # -- state
+    @staticmethod
+    def _ptr(a):
+        """(pointer, on_device) of a numpy array or a torch tensor."""
+        if isinstance(a, np.ndarray):
+            assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+            return a.ctypes.data, 0
+        assert a.dtype.__str__() == "torch.float64" and a.is_contiguous()
+        return a.data_ptr(), 1 if a.is_cuda else 0
+
+    def set(self, W):
+        ptr, dev = self._ptr(W)
+        self._check(lib().hrm_set(self.h, _VP(ptr), dev))
+
+    def set_primitive(self, prim):
+        ptr, dev = self._ptr(np.ascontiguousarray(prim, dtype=np.float64) if isinstance(prim, np.ndarray) else prim)
+        self._check(lib().hrm_set_primitive(self.h, _VP(ptr), dev))
+
+    def set_params(self, params: HrmParams):
+        self._check(lib().hrm_set_params(self.h, ctypes.byref(params)))
+        self.params = params
+
+    def get(self, field=FIELD_W, out=None):
+        planes = {FIELD_W: self.M, FIELD_V: self.M, FIELD_C5: 1, FIELD_PT: 2, FIELD_C4: 1}[field]
+        if out is None:
+            out = np.empty((planes, self.ncells))
+        ptr, dev = self._ptr(out)
+        self._check(lib().hrm_get(self.h, field, _VP(ptr), dev))
+        return out
+
+    # -- method
+    def dt(self, cfl):
+        dt = ctypes.c_double()
+        tau = (ctypes.c_double * 3)()
+        self._check(lib().hrm_dt(self.h, cfl, ctypes.byref(dt), tau))
+        return dt.value, np.array(tau[:self.D])
+
+    def step(self, dt=0.0, nsteps=1):
+        return self._check(lib().hrm_step(self.h, float(dt), int(nsteps)))
+
+    def try_step(self, dt=0.0, nsteps=1):
+        """hrm_step returning the status instead of raising."""
+        return lib().hrm_step(self.h, float(dt), int(nsteps))
+
+    def relax(self):
+        self._check(lib().hrm_relax(self.h))
+
+    def rhs(self, lam, out):
+        ptr, dev = self._ptr(out)
+        assert dev == 1
+        self._check(lib().hrm_rhs(self.h, _darr(lam, 3), _VP(ptr)))
+        return out
+
+    def time(self):
+        t = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(lib().hrm_time(self.h, ctypes.byref(t), ctypes.byref(n)))
+        return t.value, n.value
+
+    def admissibility(self):
+        c = (ctypes.c_int64 * 4)()
+        self._check(lib().hrm_admissibility(self.h, c))
+        return [int(x) for x in c]
+
+    def set_profiling(self, on=True):
+        self._check(lib().hrm_set_profiling(self.h, 1 if on else 0))
+
+    def profile_read(self, maxn=32):
+        """[(kind, ms)] of the kernels of the last traced step."""
+        ms = (ctypes.c_float * maxn)()
+        kd = (ctypes.c_int32 * maxn)()
+        n = lib().hrm_profile_read(self.h, maxn, ms, kd)
+        return [(int(kd[i]), float(ms[i])) for i in range(n)]
+
+    def kernel_launches(self) -> int:
+        return int(lib().hrm_kernel_launches(self.h))

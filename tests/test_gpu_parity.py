@@ -1,0 +1,245 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64 tolerance: relative L1 <= 1e-12 per conserved variable after one step and
+<= 1e-9 at final time (the contract of the method's FP64 form). The per-cell
+kernels (primitive variables, time step, initial state, relaxation) are built
+without FMA contraction and must agree bit for bit.
+"""
+import numpy as np
+import pytest
+
+from paper_2208_04488_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hrm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_04488_gb300 import build
+    build.build()
+    from paper_2208_04488_gb300 import hrm as H
+    return H
+
+
+def rel_l1(a, b):
+    """Per-variable sum|a - b| / sum|b| (variables along axis 0)."""
+    num = np.abs(a - b).sum(axis=1)
+    den = np.abs(b).sum(axis=1)
+    return num / np.where(den == 0, 1.0, den)
+
+
+def small_problems():
+    out = [P.shock_tube_1d_baseline(64), P.shock_tube_1d_paper(70, extreme=True),
+           P.shock_interface_1d_3species(90), P.material_interface_1d(50),
+           P.shock_bubble_2d(40, 21), P.advection_2d_smooth(16), P.interface_3d(12)]
+    sw = P.shock_water_column_2d(48, 26)
+    out.append(sw)
+    b = P.batch_instances(count=2, scale=16)
+    out.extend(b)
+    return out
+
+
+def ids(ps):
+    return [p.name + "_" + "x".join(map(str, p.n)) for p in ps]
+
+
+PROBLEMS = small_problems()
+
+
+@pytest.mark.parametrize("pr", PROBLEMS, ids=ids(PROBLEMS))
+def test_initial_state_and_primitives_bit_exact(hrm, orc, pr):
+    f, g, W = orc.setup(pr)
+    s = hrm.Solver.from_problem(pr)
+    Wg = s.get(hrm.FIELD_W)
+    np.testing.assert_array_equal(Wg, W)
+    Vg = s.get(hrm.FIELD_V)
+    c5 = s.get(hrm.FIELD_C5)[0]
+    for c in range(0, W.shape[1], max(1, W.shape[1] // 97)):
+        V, o = orc.prim_cell(f, W[:, c])
+        np.testing.assert_array_equal(Vg[:, c], V)
+        assert c5[c] == o["c"]
+    dt, tau = s.dt(pr.cfl)
+    dto, tauo = orc.dt(f, g, W, pr.cfl)
+    assert dt == dto
+    np.testing.assert_array_equal(tau, tauo)
+
+
+@pytest.mark.parametrize("pr", PROBLEMS[:5], ids=ids(PROBLEMS[:5]))
+def test_relaxation_bit_exact(hrm, orc, pr):
+    """Standalone relaxation of a state pushed out of thermal equilibrium."""
+    f, g, W = orc.setup(pr)
+    N, D = pr.N, pr.D
+    rng = np.random.default_rng(5)
+    W2 = W.copy()
+    for k in range(N - 1):
+        a = W2[N + D + 1 + k] * rng.uniform(0.7, 1.3, W.shape[1])
+        W2[N + D + 1 + k] = np.clip(a, 1e-9, 1.0 / N)
+    s = hrm.Solver.from_problem(pr, set_state=False)
+    s.set(np.ascontiguousarray(W2))
+    s.relax()
+    np.testing.assert_array_equal(s.get(hrm.FIELD_W), orc.relax(f, g, W2))
+
+
+@pytest.mark.parametrize("pr", PROBLEMS, ids=ids(PROBLEMS))
+def test_rhs_parity(hrm, orc, pr):
+    """Semi-discrete L(W) (all of Sec. 4.3 and App. C/D) against the oracle."""
+    import torch
+    f, g, W = orc.setup(pr)
+    dt, _ = orc.dt(f, g, W, 0.45)
+    lam = orc.lambdas(f, g, W, dt)
+    ref = orc.rhs(f, orc.make_params(), g, W, lam)
+    s = hrm.Solver.from_problem(pr)
+    out = torch.empty((pr.M, pr.ncells), dtype=torch.float64, device="cuda")
+    got = s.rhs(lam, out).cpu().numpy()
+    err = rel_l1(got, ref)
+    assert err.max() <= 1e-12, err
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert np.max(np.abs(got - ref) / np.where(scale == 0, 1, scale)) <= 1e-9
+
+
+@pytest.mark.parametrize("pr", PROBLEMS, ids=ids(PROBLEMS))
+def test_one_step_parity(hrm, orc, pr):
+    """One full SSP-RK3 step with relaxation after every stage: rel. L1 <= 1e-12."""
+    f, g, W = orc.setup(pr)
+    dt, _ = orc.dt(f, g, W, min(pr.cfl, 0.45))
+    ref = orc.step(f, orc.make_params(), g, W, dt, 1)
+    s = hrm.Solver.from_problem(pr)
+    s.step(dt, 1)
+    got = s.get(hrm.FIELD_W)
+    err = rel_l1(got, ref)
+    assert err.max() <= 1e-12, err
+    t, n = s.time()
+    assert n == 1 and t == dt
+
+
+def _run_to(hrm, orc, pr, t_end, max_steps=100000):
+    f, g, W = orc.setup(pr)
+    s = hrm.Solver.from_problem(pr)
+    t_o = 0.0
+    p = orc.make_params()
+    steps = 0
+    while t_o < t_end * (1 - 1e-14) and steps < max_steps:
+        dto, _ = orc.dt(f, g, W, pr.cfl)
+        dtg, _ = s.dt(pr.cfl)
+        assert abs(dtg / dto - 1) < 1e-9
+        dt = min(dto, t_end - t_o)
+        W = orc.step(f, p, g, W, dt, 1)
+        s.step(dt, 1)
+        t_o += dt
+        steps += 1
+    return W, s.get(hrm.FIELD_W), steps
+
+
+def test_final_time_parity_shock_tube_400(hrm, orc):
+    """The 400-cell water-air shock tube to t = 2.4e-4 s at CFL 0.4: rel. L1 <= 1e-9."""
+    pr = P.shock_tube_1d_baseline(400)
+    ref, got, steps = _run_to(hrm, orc, pr, pr.t_end)
+    assert steps > 50
+    err = rel_l1(got, ref)
+    assert err.max() <= 1e-9, err
+
+
+def test_final_time_parity_2d(hrm, orc):
+    pr = P.shock_bubble_2d(64, 32)
+    ref, got, steps = _run_to(hrm, orc, pr, 6e-5)
+    assert steps > 10
+    err = rel_l1(got, ref)
+    assert err.max() <= 1e-9, err
+
+
+def test_full_size_one_step_sampled(hrm, orc):
+    """The 1024 x 512 three-species shock-bubble workload in the launch
+    configuration the benchmark times: one step on the GPU; the oracle
+    recomputes the full step (seconds on one core) and every cell is compared,
+    plus conservation of the partial densities, momentum and energy fluxes."""
+    pr = P.shock_bubble_2d(1024, 512)
+    f, g, W = orc.setup(pr)
+    s = hrm.Solver.from_problem(pr)
+    dtg, _ = s.dt(pr.cfl)
+    dto, _ = orc.dt(f, g, W, pr.cfl)
+    assert dtg == dto
+    s.step(0.0, 1)  # CFL step computed on the device, as in the benchmark
+    got = s.get(hrm.FIELD_W)
+    ref = orc.step(f, orc.make_params(), g, W, dto, 1)
+    err = rel_l1(got, ref)
+    assert err.max() <= 1e-12, err
+    assert s.admissibility() == [0, 0, 0, 0]
+
+
+def test_extreme_shock_tube_positivity_gpu(hrm, orc):
+    """Sec. 5.5 on the GPU: admissible with the limiters; with them off the
+    library reports HRM_E_ADMISSIBILITY (no crash, the context stays usable)."""
+    pr = P.shock_tube_1d_paper(200, extreme=True)
+    s = hrm.Solver.from_problem(pr)
+    for _ in range(40):
+        s.step(4.0e-8, 1)
+    assert s.admissibility() == [0, 0, 0, 0]
+    s2 = hrm.Solver.from_problem(pr, params=hrm.params_default(limiters=0))
+    status = hrm.HRM_OK
+    for _ in range(40):
+        status = s2.try_step(4.0e-8, 1)
+        if status != hrm.HRM_OK:
+            break
+    assert status == hrm.HRM_E_ADMISSIBILITY
+    # the context is still usable
+    s2.set_primitive(pr.prim)
+    assert s2.admissibility() == [0, 0, 0, 0]
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64, 128, 256])
+def test_spatial_convergence_table_gpu(hrm, n):
+    """Sec. 5.2 table reproduced by the GPU path to the paper's printed digits."""
+    import os
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "convergence_2d.txt"))
+    ref = {int(r[0]): r[1:] for r in rows}[n]
+    pr = P.advection_2d_smooth(n)
+    s = hrm.Solver.from_problem(pr)
+    nsteps = int(round(pr.t_end / pr.dt))
+    s.step(pr.dt, nsteps)
+    W = s.get(hrm.FIELD_W)
+    ex = P.advection_2d_smooth(n, t=pr.t_end)
+    se = hrm.Solver.from_problem(ex)
+    We = se.get(hrm.FIELD_W)
+    rho, rho_e = W[0] + W[1], We[0] + We[1]
+    got = (np.sqrt(np.mean((rho - rho_e) ** 2)), np.max(np.abs(rho - rho_e)),
+           np.sqrt(np.mean((W[5] - We[5]) ** 2)), np.max(np.abs(W[5] - We[5])))
+    for g_, r_ in zip(got, ref):
+        assert g_ == pytest.approx(r_, rel=1.5e-3), (n, got, ref)
+
+
+def test_fields_against_oracle(hrm, orc):
+    pr = P.shock_bubble_2d(40, 21)
+    f, g, W = orc.setup(pr)
+    s = hrm.Solver.from_problem(pr)
+    s.step(0.0, 2)
+    W = s.get(hrm.FIELD_W)
+    pt = s.get(hrm.FIELD_PT)
+    c4 = s.get(hrm.FIELD_C4)[0]
+    for c in range(0, W.shape[1], 37):
+        o = orc.c4eq_cell(f, W[:, c])
+        assert pt[0, c] == pytest.approx(o["p"], rel=1e-13)
+        assert pt[1, c] == pytest.approx(o["T"], rel=1e-13)
+        assert c4[c] == pytest.approx(o["c4"], rel=1e-11)
+
+
+def test_admissibility_counters(hrm, orc):
+    pr = P.shock_tube_1d_baseline(32)
+    f, g, W = orc.setup(pr)
+    W[0, 3] = -1e-3        # negative partial density
+    W[4, 7] = 1.5          # alpha_1 > 1 (and alpha_2 < 0)
+    W[3, 9] = -1e9         # negative energy: rho e~ <= 0 and rho c^2 <= 0
+    s = hrm.Solver.from_problem(pr, set_state=False)
+    s.set(np.ascontiguousarray(W))
+    assert s.admissibility() == orc.admissibility(f, g, W)
+
+
+def test_invalid_arguments_do_not_touch_state(hrm):
+    with pytest.raises(hrm.HrmError) as e:
+        hrm.Solver([10], [0], [1], [0, 0], [1.4, 3.0], [1e9, 8e8], [700, 1400])
+    assert e.value.status == hrm.HRM_E_INVAL
+    with pytest.raises(hrm.HrmError):
+        hrm.Solver([10], [0], [1], [0, 0], [1.4, 1.67], [0, 0], [700, 3000],
+                   params=hrm.params_default(cfl=0.7))
