@@ -1,8 +1,9 @@
 """Build the in-tree CUDA library ``_build/libhrm.so`` for sm_103a with nvcc.
 
-Each translation unit compiles in parallel; the per-cell unit is built without
-FMA contraction (its primitive variables and time step are then the IEEE
-evaluation of the expressions as written), the per-midpoint units with it.
+Each translation unit compiles in parallel. The per-cell unit and the FP64
+per-midpoint units are built without FMA contraction, so the FP64 path
+evaluates every expression in the order written with IEEE rounding; the FP32
+units keep contraction.
 """
 from __future__ import annotations
 
@@ -19,9 +20,12 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 UNITS = {
     "hrm_cell.cu": ["--fmad=false"],
-    "hrm_face_d1.cu": [],
-    "hrm_face_d2.cu": [],
-    "hrm_face_d3.cu": [],
+    "hrm_face64_d1.cu": ["--fmad=false"],
+    "hrm_face64_d2.cu": ["--fmad=false"],
+    "hrm_face64_d3.cu": ["--fmad=false"],
+    "hrm_face32_d1.cu": [],
+    "hrm_face32_d2.cu": [],
+    "hrm_face32_d3.cu": [],
     "hrm_api.cu": [],
     "hrm_probe.cu": [],
 }

@@ -32,7 +32,7 @@ struct hrm_ctx {
   double* Ws = nullptr;            // RK stage state
   double* V = nullptr;             // primitive planes (M) -- also scratch for I/O
   double* AUX = nullptr;           // c, rho, rho c^2
-  double* F[3] = {nullptr, nullptr, nullptr};  // midpoint fluxes per direction (M + 1 planes)
+  double* F[3] = {nullptr, nullptr, nullptr};  // midpoint fluxes per direction (M + N - 1 planes)
   StepState* st = nullptr;
   const CellKernels* ck = nullptr;
   const FaceKernels* fk = nullptr;
@@ -115,10 +115,11 @@ void drop_graph(hrm_ctx* c) {
 template <typename F>
 void traced(hrm_ctx* c, cudaStream_t s, int kind, F&& launch) {
   const bool on = c->profiling && c->nprof < kMaxProf;
-  if (on) cudaEventRecord(c->prof_ev[2 * c->nprof], s);
+  // external event-record nodes: recorded each time the graph runs
+  if (on) cudaEventRecordWithFlags(c->prof_ev[2 * c->nprof], s, cudaEventRecordExternal);
   launch();
   if (on) {
-    cudaEventRecord(c->prof_ev[2 * c->nprof + 1], s);
+    cudaEventRecordWithFlags(c->prof_ev[2 * c->nprof + 1], s, cudaEventRecordExternal);
     c->prof_kind[c->nprof] = kind;
     ++c->nprof;
   }
@@ -311,7 +312,7 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
   for (int d = 0; d < D; ++d) {
     size_t nf = 1;
     for (int e = 0; e < 3; ++e) nf *= (size_t)(c->dg.n[e] + (e == d));
-    if ((s = cuda_check(c, cudaMalloc(&c->F[d], sizeof(double) * nf * (M + 1)), "alloc faces"))) return bail(s);
+    if ((s = cuda_check(c, cudaMalloc(&c->F[d], sizeof(double) * nf * (M + N - 1)), "alloc faces"))) return bail(s);
   }
   if ((s = cuda_check(c, cudaMalloc(&c->st, sizeof(StepState)), "alloc step state"))) return bail(s);
   cudaMemsetAsync(c->Wn, 0, plane * M, c->stream);
@@ -356,7 +357,10 @@ int32_t hrm_profile_read(hrm_ctx* c, int32_t max, float* ms, int32_t* kind) {
   const int n = c->nprof < max ? c->nprof : max;
   for (int i = 0; i < n; ++i) {
     float t = 0.f;
-    cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]);
+    if (cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) != cudaSuccess) {
+      cudaGetLastError();  // leave no sticky error for the next call
+      return 0;
+    }
     if (ms) ms[i] = t;
     if (kind) kind[i] = c->prof_kind[i];
   }

@@ -136,8 +136,8 @@ __device__ __forceinline__ R weno_is(R um2, R um1, R u0, R up1, R up2, R eps) {
   const R e1 = R(5.0 / 32.0) * (R(1) + (tau5 / (b1 + eps)) * q01);
   const R e2 = R(5.0 / 16.0) * (R(1) + tau5 / (b2 + eps));
   const R e3 = R(1.0 / 16.0) * (R(1) + tau5 / (b3 + eps));
-  const R inv = R(1) / (e0 + e1 + e2 + e3);
-  return (e0 * inv) * s0 + (e1 * inv) * s1 + (e2 * inv) * s2 + (e3 * inv) * s3;
+  const R es = e0 + e1 + e2 + e3;
+  return (e0 / es) * s0 + (e1 / es) * s1 + (e2 / es) * s2 + (e3 / es) * s3;
 }
 
 // ---------------------------------------------------------------- HLLC (Sec. 4.1.1)
@@ -211,7 +211,7 @@ __device__ __forceinline__ R hllc(const DevFluid& f, PrimState<R, N, D>& Ls, Pri
       const R mom = K.rho * K.V[L::MOM + d];
       R Fm = mom * uK;
       if (d == DIR) Fm = Fm + pK;
-      const R ms = (d == DIR) ? chi * K.rho * ss : chi * mom;
+      const R ms = (d == DIR) ? chi * K.rho * ss : chi * K.rho * K.V[L::MOM + d];
       G[L::MOM + d] = G[L::MOM + d] + w * (Fm + sfac * (ms - mom));
     }
     const R Es = chi * (K.E + (ss - uK) * (K.rho * ss + pK / (sK - uK)));

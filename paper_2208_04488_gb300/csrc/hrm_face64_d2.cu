@@ -1,22 +1,24 @@
-// Per-midpoint and per-cell-update kernels for D = 1, N = 2..3 species,
-// FP64 and FP32-bulk midpoint arithmetic.
+// FP64 per-midpoint and per-cell-update kernels for D = 2, N = 2..3 species.
+// Built without FMA contraction: the FP64 path evaluates the method's
+// expressions in the same order and rounding as written, operation by operation.
 #include "hrm_kernels.cuh"
 #include "hrm_launch.h"
 
 namespace hrm {
 namespace {
 
-constexpr int kD = 1;
+constexpr int kD = 2;
 
 template <int N, int DIR>
 void face_l(int precision, const double* W, const double* V, const double* AUX, double* out, const DevGrid& g,
             const DevFluid& f, const DevParams& p, const StepState* st, cudaStream_t s) {
   if constexpr (DIR < kD) {
+    if (precision == 1) {
+      face32_d2(N, DIR, W, V, AUX, out, g, f, p, st, s);
+      return;
+    }
     const long long nf = (g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
-    if (precision == 1)
-      k_face<float, N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, out, g, f, p, st);
-    else
-      k_face<double, N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, out, g, f, p, st);
+    k_face<double, N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, out, g, f, p, st);
   }
 }
 
@@ -39,7 +41,7 @@ const FaceKernels* table() {
 
 }  // namespace
 
-const FaceKernels* face_kernels_d1(int N) {
+const FaceKernels* face_kernels_d2(int N) {
   if (N == 2) return table<2>();
   if (N == 3) return table<3>();
   return nullptr;

@@ -112,25 +112,25 @@ __device__ __forceinline__ double theta_of(double lo, double hi, double eps) {
   return (hi < tgt) ? (tgt - lo) / (hi - lo) : 1.0;
 }
 
-// A midpoint flux in the compact form used between kernels: the conservative
-// slots Gc (identical for G^- and G^+), the alpha flux ga and the velocity u,
-// so that G^-_alpha = ga - u alpha_i and G^+_alpha = ga - u alpha_{i+1} (Eq. G_pm).
+// A midpoint flux G^-_{i+1/2} / G^+_{i+1/2} (Eq. G_pm): the conservative slots Gc
+// are shared, the alpha slots differ (gm uses alpha_i, gp uses alpha_{i+1}).
 template <int N, int D>
 struct FluxPack {
   double Gc[Lay<N, D>::NC];
-  double ga[N - 1 > 0 ? N - 1 : 1];
-  double u;
+  double gm[N - 1 > 0 ? N - 1 : 1];
+  double gp[N - 1 > 0 ? N - 1 : 1];
 };
 
-// Half-cell state W_i + s (G - F_i) with G = pack evaluated against alpha_own.
+// Half-cell state W_n + s (G - F_n): with minus = true the alpha slots of G^-
+// (cell i side), otherwise those of G^+ (cell i+1 side); F has zero alpha slots.
 template <int N, int D>
 __device__ __forceinline__ void half_state(const double* Wn, const double* Fn, const FluxPack<N, D>& G,
-                                           double s, double* out) {
+                                           double s, bool minus, double* out) {
   using L = Lay<N, D>;
 #pragma unroll
   for (int m = 0; m < L::NC; ++m) out[m] = Wn[m] + s * (G.Gc[m] - Fn[m]);
 #pragma unroll
-  for (int k = 0; k < N - 1; ++k) out[L::AL + k] = Wn[L::AL + k] + s * (G.ga[k] - G.u * Wn[L::AL + k]);
+  for (int k = 0; k < N - 1; ++k) out[L::AL + k] = Wn[L::AL + k] + s * (minus ? G.gm[k] : G.gp[k]);
 }
 
 template <int N, int D>
@@ -140,8 +140,10 @@ __device__ __forceinline__ void mix_pack(const FluxPack<N, D>& H, const FluxPack
 #pragma unroll
   for (int m = 0; m < L::NC; ++m) out.Gc[m] = (1.0 - th) * H.Gc[m] + th * G.Gc[m];
 #pragma unroll
-  for (int k = 0; k < N - 1; ++k) out.ga[k] = (1.0 - th) * H.ga[k] + th * G.ga[k];
-  out.u = (1.0 - th) * H.u + th * G.u;
+  for (int k = 0; k < N - 1; ++k) {
+    out.gp[k] = (1.0 - th) * H.gp[k] + th * G.gp[k];
+    out.gm[k] = (1.0 - th) * H.gm[k] + th * G.gm[k];
+  }
 }
 
 template <int N, int D>
@@ -169,10 +171,10 @@ __device__ __forceinline__ void flux_limit(const double* Wi, const double* Wj, c
   constexpr int M = L::M;
   const double m2l = -2.0 * lam, p2l = 2.0 * lam;
   double Wp[M], Wm[M], WHp[M], WHm[M];
-  half_state<N, D>(Wi, Fi, G, m2l, Wp);   // W_i^{+}
-  half_state<N, D>(Wj, Fj, G, p2l, Wm);   // W_{i+1}^{-} (alpha slots use alpha_{i+1})
-  half_state<N, D>(Wi, Fi, H, m2l, WHp);  // W_i^{HLLC,+}
-  half_state<N, D>(Wj, Fj, H, p2l, WHm);  // W_{i+1}^{HLLC,-}
+  half_state<N, D>(Wi, Fi, G, m2l, true, Wp);    // W_i^{+}
+  half_state<N, D>(Wj, Fj, G, p2l, false, Wm);   // W_{i+1}^{-}
+  half_state<N, D>(Wi, Fi, H, m2l, true, WHp);   // W_i^{HLLC,+}
+  half_state<N, D>(Wj, Fj, H, p2l, false, WHm);  // W_{i+1}^{HLLC,-}
   double th = 1.0;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
@@ -193,15 +195,15 @@ __device__ __forceinline__ void flux_limit(const double* Wi, const double* Wj, c
   mix_pack<N, D>(H, G, th, Gs);
   // energy stage
   const double rHp = rhoe_tilde<N, D>(WHp, f), rHm = rhoe_tilde<N, D>(WHm, f);
-  half_state<N, D>(Wi, Fi, Gs, m2l, Wp);  // W_i^{*,+}
-  half_state<N, D>(Wj, Fj, Gs, p2l, Wm);  // W_{i+1}^{*,-}
+  half_state<N, D>(Wi, Fi, Gs, m2l, true, Wp);   // W_i^{*,+}
+  half_state<N, D>(Wj, Fj, Gs, p2l, false, Wm);  // W_{i+1}^{*,-}
   const double th2 = dmin(theta_of(rHp, rhoe_tilde<N, D>(Wp, f), pr.eps_rhoe),
                           theta_of(rHm, rhoe_tilde<N, D>(Wm, f), pr.eps_rhoe));
   FluxPack<N, D> Gss;
   mix_pack<N, D>(H, Gs, th2, Gss);
   // hard switch
-  half_state<N, D>(Wi, Fi, Gss, m2l, Wp);  // W_i^{**,+}
-  half_state<N, D>(Wj, Fj, Gss, p2l, Wm);  // W_{i+1}^{**,-}
+  half_state<N, D>(Wi, Fi, Gss, m2l, true, Wp);   // W_i^{**,+}
+  half_state<N, D>(Wj, Fj, Gss, p2l, false, Wm);  // W_{i+1}^{**,-}
   bool hs = false;
   {
     double ap[N], am[N];
@@ -256,8 +258,9 @@ __device__ __forceinline__ void node_flux(const double* W, const double* V, doub
   F[L::EN] = (W[L::EN] + p) * un;
 }
 
-// Outputs of a midpoint: (M + 1) planes -- NC conservative flux slots, N-1 alpha
-// fluxes, velocity -- over the face grid of the direction.
+// Outputs of a midpoint: M + N - 1 planes over the face grid of the direction --
+// the NC conservative flux slots, the N-1 alpha slots of G^-_{i+1/2} (planes
+// AL..M-1) and the N-1 alpha slots of G^+_{i+1/2} (planes M..M+N-2).
 template <typename R, int N, int D, int DIR>
 __global__ void __launch_bounds__(kFaceThreads)
     k_face(const double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ AUX,
@@ -293,11 +296,14 @@ __global__ void __launch_bounds__(kFaceThreads)
       b.V[m] = Vj[m];
     }
     double GH[M];
-    H.u = hllc<double, N, D, DIR>(f, a, b, GH);
+    const double uH = hllc<double, N, D, DIR>(f, a, b, GH);
 #pragma unroll
     for (int m = 0; m < L::NC; ++m) H.Gc[m] = GH[m];
 #pragma unroll
-    for (int k = 0; k < N - 1; ++k) H.ga[k] = GH[L::AL + k];
+    for (int k = 0; k < N - 1; ++k) {
+      H.gm[k] = GH[L::AL + k] - uH * Vi[L::AL + k];
+      H.gp[k] = GH[L::AL + k] - uH * Vj[L::AL + k];
+    }
   }
 
   FluxPack<N, D> G;
@@ -415,6 +421,8 @@ __global__ void __launch_bounds__(kFaceThreads)
       sig = tanh_r(R(pr.Cs) * pw);
     }
     const R one_m = R(1) - sig;
+    const R uhcs = R(psi) * ut - R(a1) * (u6[2] + u6[3]) + R(a2) * (u6[1] + u6[4]) - R(a3) * (u6[0] + u6[5]);
+    const double uhat = (double)(sig * ut + one_m * uhcs);
     // node fluxes G of the flux-source form at the six nodes, slot by slot
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -435,14 +443,15 @@ __global__ void __launch_bounds__(kFaceThreads)
         Gn[j] = R(v);
       }
       const R ghcs = R(psi) * Gt[m] - R(a1) * (Gn[2] + Gn[3]) + R(a2) * (Gn[1] + Gn[4]) - R(a3) * (Gn[0] + Gn[5]);
-      const R gh = sig * Gt[m] + one_m * ghcs;
-      if (m < L::NC)
-        G.Gc[m] = (double)gh;
-      else
-        G.ga[m - L::AL] = (double)gh;
+      const double gh = (double)(sig * Gt[m] + one_m * ghcs);
+      if (m < L::NC) {
+        G.Gc[m] = gh;
+      } else {
+        // quasi-conservative alpha slots (Eq. G_pm, high-order form)
+        G.gm[m - L::AL] = gh - uhat * Vi[m];
+        G.gp[m - L::AL] = gh - uhat * Vj[m];
+      }
     }
-    const R uhcs = R(psi) * ut - R(a1) * (u6[2] + u6[3]) + R(a2) * (u6[1] + u6[4]) - R(a3) * (u6[0] + u6[5]);
-    G.u = (double)(sig * ut + one_m * uhcs);
 
     if (pr.limiters) {
       double Fi[L::NC], Fj[L::NC];
@@ -454,8 +463,10 @@ __global__ void __launch_bounds__(kFaceThreads)
 #pragma unroll
   for (int m = 0; m < L::NC; ++m) out[m * nf + t] = G.Gc[m];
 #pragma unroll
-  for (int k = 0; k < N - 1; ++k) out[(L::AL + k) * nf + t] = G.ga[k];
-  out[M * nf + t] = G.u;
+  for (int k = 0; k < N - 1; ++k) {
+    out[(L::AL + k) * nf + t] = G.gm[k];
+    out[(M + k) * nf + t] = G.gp[k];
+  }
 }
 
 // ---------------------------------------------------------------- thermal relaxation (Sec. 4.2)
@@ -553,6 +564,7 @@ __global__ void __launch_bounds__(kCellThreads)
   double Ws[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) Ws[m] = Wsrc[m * nc + c];
+  (void)Ws;
   double rhs[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) rhs[m] = 0.0;
@@ -563,15 +575,15 @@ __global__ void __launch_bounds__(kCellThreads)
     const int64_t nf = f0 * f1 * f2;
     const int64_t fl = (i2 * f1 + i1) * f0 + i0;
     const int64_t fr = fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1));
-    const double idx = g.inv_dx[d];
+    const double dx = g.dx[d];
+    // G^-_{i+1/2} - G^+_{i-1/2}: the alpha slots of the right face use alpha_i
+    // (planes AL..), those of the left face alpha_i as its right neighbour (planes M..)
 #pragma unroll
-    for (int m = 0; m < L::NC; ++m) rhs[m] = rhs[m] - (F[m * nf + fr] - F[m * nf + fl]) * idx;
-    const double ur = F[M * nf + fr], ul = F[M * nf + fl];
+    for (int m = 0; m < L::NC; ++m) rhs[m] = rhs[m] - (F[m * nf + fr] - F[m * nf + fl]) / dx;
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) {
       const int m = L::AL + k;
-      const double al = Ws[m];
-      rhs[m] = rhs[m] - ((F[m * nf + fr] - ur * al) - (F[m * nf + fl] - ul * al)) * idx;
+      rhs[m] = rhs[m] - (F[m * nf + fr] - F[(M + k) * nf + fl]) / dx;
     }
   }
   if (MODE == 1) {

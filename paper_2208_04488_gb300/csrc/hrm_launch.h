@@ -33,6 +33,14 @@ const FaceKernels* face_kernels_d1(int N);
 const FaceKernels* face_kernels_d2(int N);
 const FaceKernels* face_kernels_d3(int N);
 
+// FP32-bulk midpoint kernels, compiled in their own units (with FMA contraction).
+void face32_d1(int N, int dir, const double* W, const double* V, const double* AUX, double* out, const DevGrid&,
+               const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+void face32_d2(int N, int dir, const double* W, const double* V, const double* AUX, double* out, const DevGrid&,
+               const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+void face32_d3(int N, int dir, const double* W, const double* V, const double* AUX, double* out, const DevGrid&,
+               const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+
 void launch_finalize(StepState* st, const DevGrid& g, int D, double cfl, int mode, cudaStream_t s);
 void launch_set_dt(StepState* st, double dt, cudaStream_t s);
 
