@@ -105,6 +105,8 @@ def lib(count: bool = False):
         L.or_admissibility.argtypes = [P(Fluid), P(Grid), _DP, P(ctypes.c_int64)]
         L.or_c4eq_cell.argtypes = [P(Fluid), _DP, _DP]
         L.or_ic_from_prim.argtypes = [P(Fluid), ctypes.c_int64, _DP, _DP]
+        L.or_tanh.argtypes = [ctypes.c_double]
+        L.or_tanh.restype = ctypes.c_double
         L.or_faces_flops.argtypes = [P(Fluid), P(Params), P(Grid), _DP, _DP, ctypes.c_int, _DP]
         L.or_faces_flops.restype = ctypes.c_int64
         if count:
@@ -305,3 +307,8 @@ def faces_flops(f: Fluid, p: Params, g: Grid, W, lam, dir_):
     nf = lib(True).or_faces_flops(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), _ptr(lam),
                                   dir_, _ptr(out))
     return dict(zip(["add", "mul", "div", "sqrt", "tanh"], out.tolist())), nf
+
+
+def tanh(x: float) -> float:
+    """The oracle's explicit tanh (Cody-Waite reduction and Taylor series)."""
+    return lib().or_tanh(float(x))

@@ -33,6 +33,43 @@
 #include <cstring>
 #include <vector>
 
+// tanh of the shock sensor (Sec. 4.3.1), evaluated explicitly so that its
+// rounding does not depend on a math library: tanh|x| = m / (m + 2) with
+// m = expm1(2|x|); expm1 by its Taylor series for arguments below 0.5, else
+// exp by Cody-Waite argument reduction (exp(y) = 2^k exp(r), y = k ln2 + r,
+// |r| <= ln2 / 2, ln2 split into a 32-bit head and a tail) and its Taylor
+// series; tanh|x| = 1 above 22, where 1 - tanh is below half an ulp.
+static double tanh_explicit(double x) {
+  static const double kLn2 = 0.6931471805599453;
+  static const double kLn2Hi = 0.6931471803691238;     // 32 significant bits of ln 2
+  static const double kLn2Lo = 1.9082149292705877e-10;  // ln 2 - kLn2Hi
+  static const double kInv[19] = {0.0,       1.0,        1.0 / 2.0,  1.0 / 3.0,  1.0 / 4.0,
+                                  1.0 / 5.0, 1.0 / 6.0,  1.0 / 7.0,  1.0 / 8.0,  1.0 / 9.0,
+                                  1.0 / 10.0, 1.0 / 11.0, 1.0 / 12.0, 1.0 / 13.0, 1.0 / 14.0,
+                                  1.0 / 15.0, 1.0 / 16.0, 1.0 / 17.0, 1.0 / 18.0};
+  const double ax = std::fabs(x);
+  double t;
+  if (ax > 22.0) {
+    t = 1.0;
+  } else {
+    const double y = 2.0 * ax;
+    double m;
+    if (y < 0.5) {
+      double s = 1.0;
+      for (int k = 18; k >= 2; --k) s = 1.0 + (y * kInv[k]) * s;  // expm1(y) / y
+      m = y * s;
+    } else {
+      const double k = std::nearbyint(y / kLn2);
+      const double r = (y - k * kLn2Hi) - k * kLn2Lo;
+      double s = 1.0;
+      for (int j = 17; j >= 1; --j) s = 1.0 + (r * kInv[j]) * s;  // exp(r)
+      m = std::ldexp(s, (int)k) - 1.0;
+    }
+    t = m / (m + 2.0);
+  }
+  return x < 0.0 ? -t : t;
+}
+
 #ifdef OR_COUNT
 struct OrCounts { unsigned long long add, mul, div, sqrt, tanh; };
 static OrCounts g_cnt = {0, 0, 0, 0, 0};
@@ -53,13 +90,13 @@ static inline bool operator>=(real a, real b) { return a.v >= b.v; }
 static inline bool operator==(real a, real b) { return a.v == b.v; }
 static inline bool operator!=(real a, real b) { return a.v != b.v; }
 static inline real rsqrt_(real a) { g_cnt.sqrt++; return real(std::sqrt(a.v)); }
-static inline real rtanh_(real a) { g_cnt.tanh++; return real(std::tanh(a.v)); }
+static inline real rtanh_(real a) { g_cnt.tanh++; return real(tanh_explicit(a.v)); }
 static inline real rabs_(real a) { return real(std::fabs(a.v)); }
 static inline double val(real a) { return a.v; }
 #else
 typedef double real;
 static inline real rsqrt_(real a) { return std::sqrt(a); }
-static inline real rtanh_(real a) { return std::tanh(a); }
+static inline real rtanh_(real a) { return tanh_explicit(a); }
 static inline real rabs_(real a) { return std::fabs(a); }
 static inline double val(real a) { return a; }
 #endif
@@ -1227,6 +1264,8 @@ int64_t or_faces_flops(const or_fluid* fl, const or_params* P, const or_grid* g,
   for (int i = 0; i < 5; ++i) out[i] = acc[i];
   return nl * (n + 1);
 }
+
+double or_tanh(double x) { return tanh_explicit(x); }
 
 #ifdef OR_COUNT
 void or_count_reset(void) { memset(&g_cnt, 0, sizeof(g_cnt)); }

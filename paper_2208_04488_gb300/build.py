@@ -17,7 +17,9 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhrm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# host code: no FP contraction either (species constants are derived on the host)
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "--expt-relaxed-constexpr"]
 UNITS = {
     "hrm_cell.cu": ["--fmad=false"],
     "hrm_face64_d1.cu": ["--fmad=false"],

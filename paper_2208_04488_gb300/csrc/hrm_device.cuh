@@ -57,7 +57,38 @@ template <typename T> __device__ __forceinline__ T dmax(T a, T b) { return (a < 
 
 __device__ __forceinline__ double rsqrt_r(double x) { return sqrt(x); }
 __device__ __forceinline__ float rsqrt_r(float x) { return sqrtf(x); }
-__device__ __forceinline__ double tanh_r(double x) { return tanh(x); }
+// tanh|x| = m / (m + 2), m = expm1(2|x|): Taylor series of expm1 below 0.5, else
+// exp(y) = 2^k exp(r) with Cody-Waite reduction (y = k ln2 + r, ln2 split into
+// a 32-bit head and its tail) and the Taylor series of exp(r); 1 above 22.
+// Built without contraction, every rounding is fixed by the expression order.
+__device__ __forceinline__ double tanh_r(double x) {
+  constexpr double kLn2 = 0.6931471805599453;
+  constexpr double kLn2Hi = 0.6931471803691238;
+  constexpr double kLn2Lo = 1.9082149292705877e-10;
+  const double ax = fabs(x);
+  double t;
+  if (ax > 22.0) {
+    t = 1.0;
+  } else {
+    const double y = 2.0 * ax;
+    double m;
+    if (y < 0.5) {
+      double s = 1.0;
+#pragma unroll
+      for (int k = 18; k >= 2; --k) s = 1.0 + (y * (1.0 / (double)k)) * s;
+      m = y * s;
+    } else {
+      const double k = rint(y / kLn2);
+      const double r = (y - k * kLn2Hi) - k * kLn2Lo;
+      double s = 1.0;
+#pragma unroll
+      for (int j = 17; j >= 1; --j) s = 1.0 + (r * (1.0 / (double)j)) * s;
+      m = ldexp(s, (int)k) - 1.0;
+    }
+    t = m / (m + 2.0);
+  }
+  return x < 0.0 ? -t : t;
+}
 __device__ __forceinline__ float tanh_r(float x) { return tanhf(x); }
 
 // Index of cell j (may lie in the 3 ghost layers) along direction d under the

@@ -1,0 +1,65 @@
+"""Command-line runner: advance one of the built-in workloads on the GPU.
+
+    python -m paper_2208_04488_gb300.run --workload shock_bubble --nx 1024 --ny 512 \
+        --steps 10 [--precision fp64|fp32] [--dt 0]
+
+Prints the wall time per step (CUDA events), the simulated time and the
+admissibility counters. Used for profiling captures of single kernels.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+WORKLOADS = ("shock_bubble", "shock_tube", "interface_3d", "water_column", "advection_2d")
+
+
+def make_problem(name, nx, ny, nz):
+    from paper_2208_04488_gb300 import problems as P
+    if name == "shock_bubble":
+        return P.shock_bubble_2d(nx, ny)
+    if name == "shock_tube":
+        return P.shock_tube_1d_baseline(nx)
+    if name == "interface_3d":
+        return P.interface_3d(nx)
+    if name == "water_column":
+        return P.shock_water_column_2d(nx, ny)
+    if name == "advection_2d":
+        return P.advection_2d_smooth(nx)
+    raise ValueError(name)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="shock_bubble", choices=WORKLOADS)
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=512)
+    ap.add_argument("--nz", type=int, default=0)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--dt", type=float, default=0.0, help="0: CFL step of the workload")
+    a = ap.parse_args(argv)
+    import torch
+    from paper_2208_04488_gb300 import build, hrm
+    build.build()
+    pr = make_problem(a.workload, a.nx, a.ny, a.nz)
+    prec = hrm.FP64 if a.precision == "fp64" else hrm.FP32
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, precision=prec, check=0))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.step(a.dt, a.steps)
+    e1.record()
+    e1.synchronize()
+    t, n = s.time()
+    out = {"workload": pr.name, "cells": pr.ncells, "steps": n, "t": t,
+           "ms_per_step": e0.elapsed_time(e1) / max(a.steps, 1), "admissibility": s.admissibility()}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -157,7 +157,7 @@ def test_full_size_one_step_sampled(hrm, orc):
     plus conservation of the partial densities, momentum and energy fluxes."""
     pr = P.shock_bubble_2d(1024, 512)
     f, g, W = orc.setup(pr)
-    s = hrm.Solver.from_problem(pr)
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, check=0))
     dtg, _ = s.dt(pr.cfl)
     dto, _ = orc.dt(f, g, W, pr.cfl)
     assert dtg == dto

@@ -380,3 +380,17 @@ def test_dt_closed_form(orc):
     # lambda_d = CFL / (|u_d| + c)_max when dt is the CFL step
     assert lam[0] == pytest.approx(0.5 / (20 + o["c"]), rel=1e-14)
     assert lam[1] == pytest.approx(0.5 / (50 + o["c"]), rel=1e-14)
+
+
+def test_explicit_tanh_matches_the_function(orc):
+    """The sensor's tanh (Sec. 4.3.1) is evaluated explicitly (Cody-Waite
+    reduction and Taylor series); it must be tanh to within a few ulps over the
+    whole range, including the odd symmetry and the saturated tails."""
+    import math
+    xs = np.concatenate([np.linspace(-40, 40, 8001), np.logspace(-300, 1.6, 2000)])
+    for x in xs:
+        for v in (x, -x):
+            t = orc.tanh(v)
+            ref = math.tanh(v)
+            assert abs(t - ref) <= 4 * np.spacing(abs(ref)) + 1e-300, (v, t, ref)
+            assert orc.tanh(-v) == -t
