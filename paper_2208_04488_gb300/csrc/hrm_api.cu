@@ -32,6 +32,7 @@ struct hrm_ctx {
   double* Ws = nullptr;            // RK stage state
   double* V = nullptr;             // primitive planes (M) -- also scratch for I/O
   double* AUX = nullptr;           // c, rho, rho c^2
+  float* P32 = nullptr;            // FP32 planes of the precision form (M + D + 4)
   double* F[3] = {nullptr, nullptr, nullptr};  // midpoint fluxes per direction (M + N - 1 planes)
   StepState* st = nullptr;
   const CellKernels* ck = nullptr;
@@ -129,7 +130,9 @@ void traced(hrm_ctx* c, cudaStream_t s, int kind, F&& launch) {
 int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, double a, double b, int relax,
                   int count, bool first) {
   int k = 0;
-  traced(c, s, HRM_KERNEL_PRIM, [&] { c->ck->prim(Wsrc, c->V, c->AUX, c->dg, c->fl, c->st, first ? 1 : 0, s); });
+  float* p32 = c->params.precision == HRM_FP32 ? c->P32 : nullptr;
+  traced(c, s, HRM_KERNEL_PRIM,
+         [&] { c->ck->prim(Wsrc, c->V, c->AUX, p32, c->dg, c->fl, c->st, first ? 1 : 0, s); });
   ++k;
   if (first) {
     traced(c, s, HRM_KERNEL_FINALIZE, [&] { launch_finalize(c->st, c->dg, c->D, c->params.cfl, 0, s); });
@@ -137,7 +140,7 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
   }
   for (int d = 0; d < c->D; ++d) {
     traced(c, s, HRM_KERNEL_FACE_X + d, [&] {
-      c->fk->face[d](c->params.precision, Wsrc, c->V, c->AUX, c->F[d], c->dg, c->fl, c->dp, c->st, s);
+      c->fk->face[d](c->params.precision, Wsrc, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st, s);
     });
     ++k;
   }
@@ -309,6 +312,8 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
   if ((s = cuda_check(c, cudaMalloc(&c->Ws, plane * M), "alloc Ws"))) return bail(s);
   if ((s = cuda_check(c, cudaMalloc(&c->V, plane * M), "alloc V"))) return bail(s);
   if ((s = cuda_check(c, cudaMalloc(&c->AUX, plane * 3), "alloc aux"))) return bail(s);
+  if ((s = cuda_check(c, cudaMalloc(&c->P32, sizeof(float) * (size_t)c->nc * (M + D + 4)), "alloc fp32 planes")))
+    return bail(s);
   for (int d = 0; d < D; ++d) {
     size_t nf = 1;
     for (int e = 0; e < 3; ++e) nf *= (size_t)(c->dg.n[e] + (e == d));
@@ -330,6 +335,7 @@ void hrm_destroy(hrm_ctx* c) {
   cudaFree(c->Ws);
   cudaFree(c->V);
   cudaFree(c->AUX);
+  cudaFree(c->P32);
   for (int d = 0; d < 3; ++d) cudaFree(c->F[d]);
   cudaFree(c->st);
   for (int i = 0; i < 2 * kMaxProf; ++i)
@@ -407,7 +413,7 @@ hrm_status hrm_set_primitive(hrm_ctx* c, const double* prim, int32_t on_device) 
 
 hrm_status hrm_dt(hrm_ctx* c, double cfl, double* dt_out, double* tau_out) {
   if (!c || !(cfl > 0.0)) return c ? fail(c, HRM_E_INVAL, "cfl must be positive") : HRM_E_INVAL;
-  c->ck->prim(c->Wn, c->V, c->AUX, c->dg, c->fl, c->st, 1, c->stream);
+  c->ck->prim(c->Wn, c->V, c->AUX, nullptr, c->dg, c->fl, c->st, 1, c->stream);
   launch_finalize(c->st, c->dg, c->D, cfl, 1, c->stream);
   c->launches += 2;
   StepState h;
@@ -461,9 +467,11 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
   hrm_status s = cuda_check(c, cudaMemcpyAsync(c->st->lam, l3, sizeof l3, cudaMemcpyHostToDevice, c->stream),
                             "copy lambda");
   if (s) return s;
-  c->ck->prim(c->Wn, c->V, c->AUX, c->dg, c->fl, c->st, 0, c->stream);
+  c->ck->prim(c->Wn, c->V, c->AUX, c->params.precision == HRM_FP32 ? c->P32 : nullptr, c->dg, c->fl, c->st, 0,
+              c->stream);
   for (int d = 0; d < c->D; ++d)
-    c->fk->face[d](c->params.precision, c->Wn, c->V, c->AUX, c->F[d], c->dg, c->fl, c->dp, c->st, c->stream);
+    c->fk->face[d](c->params.precision, c->Wn, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st,
+                   c->stream);
   c->fk->update(1, c->Wn, c->Wn, rhs, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, 0.0, 1.0, 0, 0, c->stream);
   c->launches += 2 + c->D;
   if ((s = last_launch(c, "rhs"))) return s;

@@ -44,8 +44,8 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
 // atomicMax per block and direction on the order-preserving bits.
 template <int N, int D>
 __global__ void __launch_bounds__(kCellThreads)
-    k_prim(const double* __restrict__ W, double* __restrict__ V, double* __restrict__ AUX, DevGrid g,
-           DevFluid f, StepState* st, int tau) {
+    k_prim(const double* __restrict__ W, double* __restrict__ V, double* __restrict__ AUX,
+           float* __restrict__ P32, DevGrid g, DevFluid f, StepState* st, int tau) {
   using L = Lay<N, D>;
   constexpr int M = L::M;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,6 +63,17 @@ __global__ void __launch_bounds__(kCellThreads)
     AUX[c] = cs;
     AUX[nc + c] = rho;
     AUX[2 * nc + c] = rc2;
+    if (P32) {
+      // FP32 copies for the precision form: V, c, rho, rho c^2, rho u_d, E
+#pragma unroll
+      for (int m = 0; m < M; ++m) P32[m * nc + c] = (float)v[m];
+      P32[M * nc + c] = (float)cs;
+      P32[(M + 1) * nc + c] = (float)rho;
+      P32[(M + 2) * nc + c] = (float)rc2;
+#pragma unroll
+      for (int d = 0; d < D; ++d) P32[(M + 3 + d) * nc + c] = (float)w[L::MOM + d];
+      P32[(M + 3 + D) * nc + c] = (float)w[L::EN];
+    }
 #pragma unroll
     for (int d = 0; d < D; ++d) s[d] = (fabs(v[L::MOM + d]) + cs) / g.dx[d];
   }

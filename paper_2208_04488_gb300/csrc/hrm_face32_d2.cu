@@ -1,6 +1,6 @@
 // FP32-bulk per-midpoint kernels for D = 2, N = 2..3 species (the precision
 // form: interpolation, Riemann fluxes and HCS in FP32; limiter theta in FP64).
-#include "hrm_kernels.cuh"
+#include "hrm_face32.cuh"
 #include "hrm_launch.h"
 
 namespace hrm {
@@ -9,26 +9,26 @@ namespace {
 constexpr int kD = 2;
 
 template <int N, int DIR>
-void launch(const double* W, const double* V, const double* AUX, double* out, const DevGrid& g, const DevFluid& f,
-            const DevParams& p, const StepState* st, cudaStream_t s) {
+void launch(const double* W, const double* V, const double* AUX, const float* P32, double* out, const DevGrid& g,
+            const DevFluid& f, const DevParams& p, const StepState* st, cudaStream_t s) {
   if constexpr (DIR < kD) {
     const long long nf = (g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
-    k_face<float, N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, out, g, f, p, st);
+    k_face32<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, P32, out, g, f, p, st);
   }
 }
 
 }  // namespace
 
-void face32_d2(int N, int dir, const double* W, const double* V, const double* AUX, double* out, const DevGrid& g,
-               const DevFluid& f, const DevParams& p, const StepState* st, cudaStream_t s) {
+void face32_d2(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
+               const DevGrid& g, const DevFluid& f, const DevParams& p, const StepState* st, cudaStream_t s) {
   if (N == 2) {
-    if (dir == 0) launch<2, 0>(W, V, AUX, out, g, f, p, st, s);
-    if (dir == 1) launch<2, 1>(W, V, AUX, out, g, f, p, st, s);
-    if (dir == 2) launch<2, 2>(W, V, AUX, out, g, f, p, st, s);
+    if (dir == 0) launch<2, 0>(W, V, AUX, P32, out, g, f, p, st, s);
+    if (dir == 1) launch<2, 1>(W, V, AUX, P32, out, g, f, p, st, s);
+    if (dir == 2) launch<2, 2>(W, V, AUX, P32, out, g, f, p, st, s);
   } else if (N == 3) {
-    if (dir == 0) launch<3, 0>(W, V, AUX, out, g, f, p, st, s);
-    if (dir == 1) launch<3, 1>(W, V, AUX, out, g, f, p, st, s);
-    if (dir == 2) launch<3, 2>(W, V, AUX, out, g, f, p, st, s);
+    if (dir == 0) launch<3, 0>(W, V, AUX, P32, out, g, f, p, st, s);
+    if (dir == 1) launch<3, 1>(W, V, AUX, P32, out, g, f, p, st, s);
+    if (dir == 2) launch<3, 2>(W, V, AUX, P32, out, g, f, p, st, s);
   }
 }
 

@@ -10,11 +10,11 @@ namespace {
 constexpr int kD = 3;
 
 template <int N, int DIR>
-void face_l(int precision, const double* W, const double* V, const double* AUX, double* out, const DevGrid& g,
-            const DevFluid& f, const DevParams& p, const StepState* st, cudaStream_t s) {
+void face_l(int precision, const double* W, const double* V, const double* AUX, const float* P32, double* out,
+            const DevGrid& g, const DevFluid& f, const DevParams& p, const StepState* st, cudaStream_t s) {
   if constexpr (DIR < kD) {
     if (precision == 1) {
-      face32_d3(N, DIR, W, V, AUX, out, g, f, p, st, s);
+      face32_d3(N, DIR, W, V, AUX, P32, out, g, f, p, st, s);
       return;
     }
     const long long nf = (g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));

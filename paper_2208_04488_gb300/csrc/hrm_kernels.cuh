@@ -191,19 +191,29 @@ __device__ __forceinline__ void flux_limit(const double* Wi, const double* Wj, c
     for (int k = 0; k < N; ++k)
       th = dmin(th, dmin(theta_of(aHp[k], ap[k], pr.eps_a), theta_of(aHm[k], am[k], pr.eps_a)));
   }
+  // with theta = 1 the mixed flux is G itself, bit for bit ((1 - 1) H + 1 G), and
+  // the half-cell states need no recomputation
   FluxPack<N, D> Gs;
-  mix_pack<N, D>(H, G, th, Gs);
+  if (th < 1.0) {
+    mix_pack<N, D>(H, G, th, Gs);
+    half_state<N, D>(Wi, Fi, Gs, m2l, true, Wp);   // W_i^{*,+}
+    half_state<N, D>(Wj, Fj, Gs, p2l, false, Wm);  // W_{i+1}^{*,-}
+  } else {
+    Gs = G;
+  }
   // energy stage
   const double rHp = rhoe_tilde<N, D>(WHp, f), rHm = rhoe_tilde<N, D>(WHm, f);
-  half_state<N, D>(Wi, Fi, Gs, m2l, true, Wp);   // W_i^{*,+}
-  half_state<N, D>(Wj, Fj, Gs, p2l, false, Wm);  // W_{i+1}^{*,-}
   const double th2 = dmin(theta_of(rHp, rhoe_tilde<N, D>(Wp, f), pr.eps_rhoe),
                           theta_of(rHm, rhoe_tilde<N, D>(Wm, f), pr.eps_rhoe));
   FluxPack<N, D> Gss;
-  mix_pack<N, D>(H, Gs, th2, Gss);
+  if (th2 < 1.0) {
+    mix_pack<N, D>(H, Gs, th2, Gss);
+    half_state<N, D>(Wi, Fi, Gss, m2l, true, Wp);   // W_i^{**,+}
+    half_state<N, D>(Wj, Fj, Gss, p2l, false, Wm);  // W_{i+1}^{**,-}
+  } else {
+    Gss = Gs;
+  }
   // hard switch
-  half_state<N, D>(Wi, Fi, Gss, m2l, true, Wp);   // W_i^{**,+}
-  half_state<N, D>(Wj, Fj, Gss, p2l, false, Wm);  // W_{i+1}^{**,-}
   bool hs = false;
   {
     double ap[N], am[N];

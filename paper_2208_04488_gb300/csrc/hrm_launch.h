@@ -10,8 +10,9 @@
 namespace hrm {
 
 struct CellKernels {
-  void (*prim)(const double* W, double* V, double* AUX, const DevGrid&, const DevFluid&, StepState*, int tau,
-               cudaStream_t);
+  // P32 (nullable): FP32 planes for the precision form
+  void (*prim)(const double* W, double* V, double* AUX, float* P32, const DevGrid&, const DevFluid&, StepState*,
+               int tau, cudaStream_t);
   void (*ic)(const double* prim, double* W, const DevGrid&, const DevFluid&, cudaStream_t);
   void (*relax)(double* W, const DevGrid&, const DevFluid&, cudaStream_t);
   void (*fields)(const double* W, double* out, int field, const DevGrid&, const DevFluid&, cudaStream_t);
@@ -20,8 +21,8 @@ struct CellKernels {
 
 struct FaceKernels {
   // precision: 0 FP64, 1 FP32 bulk
-  void (*face[3])(int precision, const double* W, const double* V, const double* AUX, double* out,
-                  const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+  void (*face[3])(int precision, const double* W, const double* V, const double* AUX, const float* P32,
+                  double* out, const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
   void (*update)(int mode, const double* Wn, const double* Wsrc, double* Wout, const double* F0,
                  const double* F1, const double* F2, const DevGrid&, const DevFluid&, StepState*, double a,
                  double b, int relax, int count, cudaStream_t);
@@ -34,12 +35,12 @@ const FaceKernels* face_kernels_d2(int N);
 const FaceKernels* face_kernels_d3(int N);
 
 // FP32-bulk midpoint kernels, compiled in their own units (with FMA contraction).
-void face32_d1(int N, int dir, const double* W, const double* V, const double* AUX, double* out, const DevGrid&,
-               const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
-void face32_d2(int N, int dir, const double* W, const double* V, const double* AUX, double* out, const DevGrid&,
-               const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
-void face32_d3(int N, int dir, const double* W, const double* V, const double* AUX, double* out, const DevGrid&,
-               const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+void face32_d1(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
+               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+void face32_d2(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
+               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+void face32_d3(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
+               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
 
 void launch_finalize(StepState* st, const DevGrid& g, int D, double cfl, int mode, cudaStream_t s);
 void launch_set_dt(StepState* st, double dt, cudaStream_t s);

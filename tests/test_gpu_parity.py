@@ -246,3 +246,68 @@ def test_invalid_arguments_do_not_touch_state(hrm):
     with pytest.raises(hrm.HrmError):
         hrm.Solver([10], [0], [1], [0, 0], [1.4, 1.67], [0, 0], [700, 3000],
                    params=hrm.params_default(cfl=0.7))
+
+
+@pytest.mark.parametrize("pr", [P.shock_tube_1d_baseline(400), P.shock_bubble_2d(64, 32),
+                                P.shock_tube_1d_paper(200, extreme=True), P.interface_3d(12)],
+                         ids=["shock_tube_400", "shock_bubble_64x32", "extreme_200", "interface_3d_12"])
+def test_fp64_path_reproduces_oracle_bit_for_bit(hrm, orc, pr):
+    """The FP64 path evaluates every operation of the method in the oracle's
+    order with IEEE rounding (no contraction, the same explicit tanh), so the
+    states agree exactly, step after step, limiters and hard switches included."""
+    f, g, W = orc.setup(pr)
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=min(pr.cfl, 0.45), check=0))
+    p = orc.make_params()
+    dt_fixed = 4.0e-8 if pr.name.startswith("extreme") else None
+    for k in range(25):
+        dt = dt_fixed or orc.dt(f, g, W, min(pr.cfl, 0.45))[0]
+        W = orc.step(f, p, g, W, dt, 1)
+        s.step(dt, 1)
+    np.testing.assert_array_equal(s.get(hrm.FIELD_W), W)
+
+
+# ---------------------------------------------------------------- precision form (FP32 bulk)
+
+def _fp32_vs_fp64(hrm, pr, nsteps, cfl=None):
+    cfl = cfl or pr.cfl
+    a = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=cfl, check=0))
+    b = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=cfl, check=0, precision=hrm.FP32))
+    for _ in range(nsteps):
+        dt, _ = a.dt(cfl)
+        a.step(dt, 1)
+        b.step(dt, 1)
+    return a, b
+
+
+def test_fp32_form_keeps_uniform_states_exactly(hrm):
+    pr = P.advection_2d_smooth(16)
+    pr.prim[0][:] = 0.3  # uniform alpha: the whole state is uniform
+    a, b = _fp32_vs_fp64(hrm, pr, 3)
+    W0 = hrm.Solver.from_problem(pr).get(hrm.FIELD_W)
+    Wb = b.get(hrm.FIELD_W)
+    for m in range(pr.M):
+        assert np.all(Wb[m] == Wb[m][0])
+    np.testing.assert_allclose(Wb[:, 0], W0[:, 0], rtol=1e-12)
+
+
+@pytest.mark.parametrize("pr,nsteps,tol", [
+    (P.shock_tube_1d_baseline(400), 100, 2e-3),
+    (P.shock_bubble_2d(128, 64), 40, 1e-3),
+    (P.advection_2d_smooth(64), 40, 1e-6),
+], ids=["shock_tube_400", "shock_bubble_128x64", "advection_64"])
+def test_fp32_form_error_against_fp64(hrm, pr, nsteps, tol):
+    """The precision form stays within a stated relative L1 error of the FP64
+    path and keeps every cell admissible."""
+    a, b = _fp32_vs_fp64(hrm, pr, nsteps)
+    err = rel_l1(b.get(hrm.FIELD_W), a.get(hrm.FIELD_W))
+    assert err.max() <= tol, err
+    assert b.admissibility() == [0, 0, 0, 0]
+
+
+def test_fp32_form_extreme_shock_tube_admissible(hrm):
+    """Sec. 5.5 with the precision form: the FP64 limiters keep it admissible."""
+    pr = P.shock_tube_1d_paper(200, extreme=True)
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(precision=hrm.FP32))
+    for _ in range(40):
+        s.step(4.0e-8, 1)
+    assert s.admissibility() == [0, 0, 0, 0]
