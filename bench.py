@@ -224,6 +224,25 @@ def main():
     torch.cuda.synchronize()
     adm = s.admissibility()
     W_fp64 = s.get(hrm.FIELD_W)
+    # precision form on the same workload: timed the same way, and its relative
+    # L1 error against FP64 after the same number of equal fixed-size steps
+    s32 = make(hrm.FP32)
+    s32.set_profiling(True)
+    for _ in range(args.warmup):
+        s32.step(0.0, 1)
+    s32.set_primitive(pr.prim)
+    torch.cuda.synchronize()
+    t32, per32 = time_steps(torch, s32, args.steps, flush, stream)
+    adm32 = s32.admissibility()
+    dt0, _ = s.dt(pr.cfl)
+    ea, eb = make(hrm.FP64), make(hrm.FP32)
+    ea.step(dt0, args.steps)
+    eb.step(dt0, args.steps)
+    Wa, Wb = ea.get(hrm.FIELD_W), eb.get(hrm.FIELD_W)
+    from paper_2208_04488_gb300.metrics import rel_l1_state
+    l1_32 = rel_l1_state(Wb, Wa, pr.N, pr.D).tolist()
+    del ea, eb, s32
+
     t_tensor = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
     if dist is not None:
         dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
@@ -267,6 +286,11 @@ def main():
         frac = achieved / fp64_peak
         share = {hrm.KERNEL_NAMES[k]: round(v[1] / sum(x[1] for x in per_kernel.values()), 4)
                  for k, v in sorted(per_kernel.items())}
+        n32 = sum(per32[k][0] for k in face_kinds)
+        tf32 = sum(per32[k][1] for k in face_kinds)
+        ach32 = fl_launch / (tf32 / n32)
+        share32 = {hrm.KERNEL_NAMES[k]: round(v[1] / sum(x[1] for x in per32.values()), 4)
+                   for k, v in sorted(per32.items())}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -283,6 +307,22 @@ def main():
                          "kernel_time_share": share},
             "e2e": {"value": pr.ncells * K_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
                     "d2h_bytes_per_step": bytes_step},
+            "forms": {
+                "fp32": {"value": pr.ncells * args.steps / t32, "unit": UNIT,
+                         "ms_per_step": 1e3 * t32 / args.steps,
+                         "description": "WENO-IS, HLLC, HCS and sensor blend in FP32; limiter theta, half-cell "
+                                        "states, state, RK combination and relaxation in FP64",
+                         "rel_l1_vs_fp64": {"max_over_variables": max(l1_32), "per_variable": l1_32,
+                                            "after_steps": args.steps, "dt": dt0,
+                                            "definition": "sum|W32 - W64| / sum|W64| per variable; momentum "
+                                                          "components over sum |rho u| (vector norm)"},
+                         "admissibility_after": adm32,
+                         "roofline": {"bound": "alu", "kernel": "k_face32 (per-midpoint, FP32 bulk + FP64 limiter)",
+                                      "achieved": ach32 / 1e12, "unit": "TFLOP/s",
+                                      "peak_fp32": fp32_peak / 1e12, "frac_of_fp32_peak": ach32 / fp32_peak,
+                                      "peak_fp64": fp64_peak / 1e12,
+                                      "avg_launch_ms": 1e3 * tf32 / n32, "kernel_time_share": share32}},
+            },
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "admissibility_after": adm,

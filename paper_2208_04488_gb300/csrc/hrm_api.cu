@@ -32,7 +32,7 @@ struct hrm_ctx {
   double* Ws = nullptr;            // RK stage state
   double* V = nullptr;             // primitive planes (M) -- also scratch for I/O
   double* AUX = nullptr;           // c, rho, rho c^2
-  float* P32 = nullptr;            // FP32 planes of the precision form (M + D + 4)
+  float* P32 = nullptr;            // FP32 planes of the precision form (M + D + 4 + N - 1)
   double* F[3] = {nullptr, nullptr, nullptr};  // midpoint fluxes per direction (M + N - 1 planes)
   StepState* st = nullptr;
   const CellKernels* ck = nullptr;
@@ -145,7 +145,8 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
     ++k;
   }
   traced(c, s, HRM_KERNEL_UPDATE, [&] {
-    c->fk->update(0, c->Wn, Wsrc, Wout, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, a, b, relax, count, s);
+    c->fk->update(0, c->params.precision == HRM_FP32, c->Wn, Wsrc, Wout, c->F[0], c->F[1], c->F[2], c->dg, c->fl,
+                  c->st, a, b, relax, count, s);
   });
   ++k;
   return k;
@@ -312,7 +313,7 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
   if ((s = cuda_check(c, cudaMalloc(&c->Ws, plane * M), "alloc Ws"))) return bail(s);
   if ((s = cuda_check(c, cudaMalloc(&c->V, plane * M), "alloc V"))) return bail(s);
   if ((s = cuda_check(c, cudaMalloc(&c->AUX, plane * 3), "alloc aux"))) return bail(s);
-  if ((s = cuda_check(c, cudaMalloc(&c->P32, sizeof(float) * (size_t)c->nc * (M + D + 4)), "alloc fp32 planes")))
+  if ((s = cuda_check(c, cudaMalloc(&c->P32, sizeof(float) * (size_t)c->nc * (M + D + 4 + N - 1)), "alloc fp32 planes")))
     return bail(s);
   for (int d = 0; d < D; ++d) {
     size_t nf = 1;
@@ -472,7 +473,8 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
   for (int d = 0; d < c->D; ++d)
     c->fk->face[d](c->params.precision, c->Wn, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st,
                    c->stream);
-  c->fk->update(1, c->Wn, c->Wn, rhs, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, 0.0, 1.0, 0, 0, c->stream);
+  c->fk->update(1, 0, c->Wn, c->Wn, rhs, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, 0.0, 1.0, 0, 0,
+                c->stream);
   c->launches += 2 + c->D;
   if ((s = last_launch(c, "rhs"))) return s;
   return cuda_check(c, cudaStreamSynchronize(c->stream), "rhs sync");

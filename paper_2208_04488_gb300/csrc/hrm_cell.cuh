@@ -73,6 +73,11 @@ __global__ void __launch_bounds__(kCellThreads)
 #pragma unroll
       for (int d = 0; d < D; ++d) P32[(M + 3 + d) * nc + c] = (float)w[L::MOM + d];
       P32[(M + 3 + D) * nc + c] = (float)w[L::EN];
+#pragma unroll
+      for (int k = 0; k < N - 1; ++k) {
+        const double a = w[L::AL + k];
+        P32[(M + 4 + D + k) * nc + c] = (float)(a - (double)(float)a);  // rounding residue
+      }
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) s[d] = (fabs(v[L::MOM + d]) + cs) / g.dx[d];

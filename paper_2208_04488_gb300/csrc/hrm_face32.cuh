@@ -9,12 +9,14 @@
 namespace hrm {
 
 // FP32 planes written by k_prim for the precision form (per cell):
-// V[0..M-1], c, rho, rho c^2, rho u_d (D planes), E.
+// V[0..M-1], c, rho, rho c^2, rho u_d (D planes), E, and the rounding residues
+// alpha_k - (float)alpha_k of the N-1 stored volume fractions, so that
+// differences of volume fractions near 1 keep their full precision.
 template <int N, int D>
 struct P32Lay {
   static constexpr int M = Lay<N, D>::M;
-  static constexpr int C = M, RHO = M + 1, RC2 = M + 2, MOM = M + 3, E = M + 3 + D;
-  static constexpr int PLANES = M + 4 + D;
+  static constexpr int C = M, RHO = M + 1, RC2 = M + 2, MOM = M + 3, E = M + 3 + D, ALO = M + 4 + D;
+  static constexpr int PLANES = M + 4 + D + (N - 1);
 };
 
 // Incremental-stencil WENO (App. C) in FP32 on the stencil's differences from
@@ -23,10 +25,14 @@ struct P32Lay {
 // sub-stencil interpolants reproduce constants, so this equals the unscaled
 // scheme up to rounding and to smoothness indicators below 1e-15 of the
 // stencil's range.
+// A stencil whose range is below 1e-30 is taken as constant: its reciprocal
+// would leave the normal float range (1/s = inf for subnormal s).
+constexpr float kTinyRange = 1e-30f;
+
 __device__ __forceinline__ float weno_is_scaled(float um2, float um1, float u0, float up1, float up2, float eps) {
   float a = um2 - u0, b = um1 - u0, d = up1 - u0, e = up2 - u0;
   const float s = fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(d), fabsf(e)));
-  if (s == 0.f) return u0;
+  if (!(s > kTinyRange)) return u0;
   const float inv = 1.f / s;
   a *= inv;
   b *= inv;
@@ -34,6 +40,87 @@ __device__ __forceinline__ float weno_is_scaled(float um2, float um1, float u0, 
   e *= inv;
   const float eps_s = fmaxf(eps * inv * inv, 1e-15f);
   return u0 + s * weno_is<float>(a, b, 0.f, d, e, eps_s);
+}
+
+// WENO-IS increment from already-formed differences (u_j - u_0) of a stencil
+// whose central value is the reference (left-biased order um2, um1, up1, up2).
+__device__ __forceinline__ float weno_increment(float a, float b, float d, float e, float eps) {
+  const float s = fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(d), fabsf(e)));
+  if (!(s > kTinyRange)) return 0.f;
+  const float inv = 1.f / s;
+  const float eps_s = fmaxf(eps * inv * inv, 1e-15f);
+  return s * weno_is<float>(a * inv, b * inv, 0.f, d * inv, e * inv, eps_s);
+}
+
+// Interpolation limiter of the precision form: partial densities from FP32,
+// volume fractions carried in FP64 (at, the N-1 stored ones); theta in FP64.
+template <int N, int D>
+__device__ __forceinline__ void interp_limit32(float* Vt, double* at, const double* Vn, double rc2n,
+                                               const DevFluid& f, const DevParams& pr) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double lo = Vn[k], hi = (double)Vt[k];
+    const double tgt = dmin(pr.eps_ar, lo);
+    double th = 1.0;
+    if (hi < tgt) th = (tgt - lo) / (hi - lo);
+    Vt[k] = (float)((1.0 - th) * lo + th * hi);
+  }
+  double alt[N], aln[N];
+  {
+    double st = 0.0, sn = 0.0;
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+      alt[k] = at[k];
+      aln[k] = Vn[L::AL + k];
+      st += alt[k];
+      sn += aln[k];
+    }
+    alt[N - 1] = 1.0 - st;
+    aln[N - 1] = 1.0 - sn;
+  }
+  double th = 1.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double tgt = dmin(pr.eps_a, aln[k]);
+    if (alt[k] < tgt) th = dmin(th, (tgt - aln[k]) / (alt[k] - aln[k]));
+  }
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) at[k] = (1.0 - th) * aln[k] + th * alt[k];
+  bool hs = false;
+  {
+    double st = 0.0;
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+      alt[k] = at[k];
+      st += alt[k];
+    }
+    alt[N - 1] = 1.0 - st;
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    hs |= (double)Vt[k] < dmin(pr.hs_ar, Vn[k]);
+    hs |= alt[k] < dmin(pr.hs_a, aln[k]);
+  }
+  double S, P;
+  mix_SP<double, N>(f, alt, S, P);
+  hs |= rho_c2(S, P, (double)Vt[L::EN]) < dmin(pr.hs_rc2, rc2n);
+  if (hs) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) Vt[m] = (float)Vn[m];
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) at[k] = Vn[L::AL + k];
+  }
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) Vt[L::AL + k] = (float)at[k];
+}
+
+// Upwind alpha flux of HLLC (Sec. 4.1.1) in FP64: (1 + sign s*)/2 aL s* + (1 - sign s*)/2 aR s*.
+__device__ __forceinline__ double alpha_flux(double aL, double aR, double ss) {
+  if (ss > 0.0) return aL * ss;
+  if (ss < 0.0) return aR * ss;
+  return 0.5 * (aL * ss) + 0.5 * (aR * ss);
 }
 
 template <int N, int D, int DIR>
@@ -76,8 +163,9 @@ __global__ void __launch_bounds__(kFaceThreads)
     for (int m = 0; m < L::NC; ++m) H.Gc[m] = (double)GH[m];
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) {
-      H.gm[k] = (double)GH[L::AL + k] - uH * Vi[L::AL + k];
-      H.gp[k] = (double)GH[L::AL + k] - uH * Vj[L::AL + k];
+      const double ga = alpha_flux(Vi[L::AL + k], Vj[L::AL + k], uH);
+      H.gm[k] = ga - uH * Vi[L::AL + k];
+      H.gp[k] = ga - uH * Vj[L::AL + k];
     }
   }
 
@@ -129,12 +217,22 @@ __global__ void __launch_bounds__(kFaceThreads)
         ++t_;
       }
     }
+    // volume fractions: increments of the identity fields on exact differences
+    // (FP32 value differences plus residue differences), added to the FP64 node values
+    double aL[N > 1 ? N - 1 : 1], aR[N > 1 ? N - 1 : 1];
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) {
+      float hi6[6], lo6[6];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) w6[j] = ld(L::AL + k, j);
-      UL[N + D + k] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-      UR[N + D + k] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+      for (int j = 0; j < 6; ++j) {
+        hi6[j] = ld(L::AL + k, j);
+        lo6[j] = ld(Q::ALO + k, j);
+      }
+      auto dl = [&](int j, int c) { return (hi6[j] - hi6[c]) + (lo6[j] - lo6[c]); };
+      aL[k] = Vi[L::AL + k] + (double)weno_increment(dl(0, 2), dl(1, 2), dl(3, 2), dl(4, 2), eps);
+      aR[k] = Vj[L::AL + k] + (double)weno_increment(dl(5, 3), dl(4, 3), dl(2, 3), dl(1, 3), eps);
+      UL[N + D + k] = (float)aL[k];
+      UR[N + D + k] = (float)aR[k];
     }
     PrimState<float, N, D> sl, sr;
     {
@@ -162,11 +260,14 @@ __global__ void __launch_bounds__(kFaceThreads)
       }
     }
     if (pr.limiters) {
-      interp_limit<float, N, D>(sl.V, Vi, AUX[2 * nc + nd.c[2]], f, pr);
-      interp_limit<float, N, D>(sr.V, Vj, AUX[2 * nc + nd.c[3]], f, pr);
+      interp_limit32<N, D>(sl.V, aL, Vi, AUX[2 * nc + nd.c[2]], f, pr);
+      interp_limit32<N, D>(sr.V, aR, Vj, AUX[2 * nc + nd.c[3]], f, pr);
     }
     float Gt[M];
     const float ut = hllc<float, N, D, DIR>(f, sl, sr, Gt);
+    double Gt_a[N > 1 ? N - 1 : 1];
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) Gt_a[k] = alpha_flux(aL[k], aR[k], (double)ut);
     constexpr float psi = 256.0f / 175.0f;
     constexpr float a1 = 101.0f / 420.0f, a2 = 1.0f / 105.0f, a3 = 1.0f / 2100.0f;
     float sig = 0.f;
@@ -190,7 +291,7 @@ __global__ void __launch_bounds__(kFaceThreads)
     const float uhcs = psi * ut - a1 * (u6[2] + u6[3]) + a2 * (u6[1] + u6[4]) - a3 * (u6[0] + u6[5]);
     const double uhat = (double)(sig * ut + one_m * uhcs);
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
+    for (int m = 0; m < L::NC; ++m) {
       float Gn[6];
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
@@ -200,19 +301,26 @@ __global__ void __launch_bounds__(kFaceThreads)
           v = ld(m, j) * un;
         else if (m < L::EN)
           v = ld(Q::MOM + (m - L::MOM), j) * un + ((m - L::MOM) == DIR ? p6[j] : 0.f);
-        else if (m == L::EN)
-          v = (ld(Q::E, j) + p6[j]) * un;
         else
-          v = ld(m, j) * un;
+          v = (ld(Q::E, j) + p6[j]) * un;
         Gn[j] = v;
       }
       const float ghcs = psi * Gt[m] - a1 * (Gn[2] + Gn[3]) + a2 * (Gn[1] + Gn[4]) - a3 * (Gn[0] + Gn[5]);
-      const double gh = (double)(sig * Gt[m] + one_m * ghcs);
-      if (m < L::NC) {
-        G.Gc[m] = gh;
-      } else {
-        G.gm[m - L::AL] = gh - uhat * Vi[m];
-        G.gp[m - L::AL] = gh - uhat * Vj[m];
+      G.Gc[m] = (double)(sig * Gt[m] + one_m * ghcs);
+    }
+    // alpha slots in FP64: node fluxes alpha_j u_j, HCS, blend, quasi-conservative form
+    {
+      constexpr double dpsi = 256.0 / 175.0, d1 = 101.0 / 420.0, d2 = 1.0 / 105.0, d3 = 1.0 / 2100.0;
+      const double sg = (double)sig, om = 1.0 - sg;
+#pragma unroll
+      for (int k = 0; k < N - 1; ++k) {
+        double gn[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) gn[j] = V[(L::AL + k) * nc + nd.c[j]] * (double)u6[j];
+        const double ghcs = dpsi * Gt_a[k] - d1 * (gn[2] + gn[3]) + d2 * (gn[1] + gn[4]) - d3 * (gn[0] + gn[5]);
+        const double gh = sg * Gt_a[k] + om * ghcs;
+        G.gm[k] = gh - uhat * Vi[L::AL + k];
+        G.gp[k] = gh - uhat * Vj[L::AL + k];
       }
     }
     if (pr.limiters) {

@@ -19,6 +19,16 @@ void launch(const double* W, const double* V, const double* AUX, const float* P3
 
 }  // namespace
 
+void update32_d3(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
+                 const double* F2, const DevGrid& g, const DevFluid& f, StepState* st, double a, double b, int relax,
+                 int count, cudaStream_t s) {
+  const unsigned gr = grid_for(g.ncells, kCellThreads);
+  if (N == 2)
+    k_update<2, kD, 0, true><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count);
+  else if (N == 3)
+    k_update<3, kD, 0, true><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count);
+}
+
 void face32_d3(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
                const DevGrid& g, const DevFluid& f, const DevParams& p, const StepState* st, cudaStream_t s) {
   if (N == 2) {

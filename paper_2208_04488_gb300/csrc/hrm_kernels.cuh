@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(kFaceThreads)
 // replaces the stored alpha_k by rho Y_k / rho_k(p*, T*). p* is the positive root of
 // A_p p^2 + B_p p + C_p = 0 (Eqs. Ap_Bp_Cp_1-3, p_relax) in the cancellation-free
 // form, T* from Eq. T_relax_e. Species `liq` is the stiffened gas.
-template <int N, int D>
+template <int N, int D, bool FAST = false>
 __device__ __forceinline__ void relax_cell(double* W, const DevFluid& f, double* pT = nullptr) {
   using L = Lay<N, D>;
   const int l = f.liq;
@@ -493,8 +493,9 @@ __device__ __forceinline__ void relax_cell(double* W, const DevFluid& f, double*
 #pragma unroll
   for (int k = 0; k < N; ++k) rho += W[k];
   double Y[N];
+  const double inv_rho = FAST ? 1.0 / rho : 0.0;
 #pragma unroll
-  for (int k = 0; k < N; ++k) Y[k] = W[k] / rho;
+  for (int k = 0; k < N; ++k) Y[k] = FAST ? W[k] * inv_rho : W[k] / rho;
   const double re = rhoe_tilde<N, D>(W, f);
   double cvb = 0.0, cpb = 0.0;
 #pragma unroll
@@ -512,8 +513,12 @@ __device__ __forceinline__ void relax_cell(double* W, const DevFluid& f, double*
   const double Ts = (re / rho) / den;
 #pragma unroll
   for (int k = 0; k < N - 1; ++k) {
-    const double rhok = (ps + f.pinf[k]) / (f.Rg[k] * Ts);
-    W[L::AL + k] = W[k] / rhok;
+    if (FAST) {
+      W[L::AL + k] = W[k] * (f.Rg[k] * Ts) / (ps + f.pinf[k]);  // alpha_k = rho Y_k / rho_k(p*, T*)
+    } else {
+      const double rhok = (ps + f.pinf[k]) / (f.Rg[k] * Ts);
+      W[L::AL + k] = W[k] / rhok;
+    }
   }
   if (pT) {
     pT[0] = ps;
@@ -558,7 +563,8 @@ __device__ __forceinline__ void count_bits(StepState* st, int b) {
 // optionally followed by the thermal relaxation and the admissibility count.
 // MODE 1 writes RHS instead of the combination. In-place (W_out == W_src or W^n)
 // is allowed: each thread reads its own cell before writing it.
-template <int N, int D, int MODE>
+// FAST (precision form): reciprocal of dx and of rho instead of divisions.
+template <int N, int D, int MODE, bool FAST = false>
 __global__ void __launch_bounds__(kCellThreads)
     k_update(const double* Wn, const double* Wsrc, double* Wout, const double* __restrict__ F0,
              const double* __restrict__ F1, const double* __restrict__ F2, DevGrid g, DevFluid f,
@@ -585,15 +591,19 @@ __global__ void __launch_bounds__(kCellThreads)
     const int64_t nf = f0 * f1 * f2;
     const int64_t fl = (i2 * f1 + i1) * f0 + i0;
     const int64_t fr = fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1));
-    const double dx = g.dx[d];
+    const double dx = g.dx[d], idx = g.inv_dx[d];
     // G^-_{i+1/2} - G^+_{i-1/2}: the alpha slots of the right face use alpha_i
     // (planes AL..), those of the left face alpha_i as its right neighbour (planes M..)
 #pragma unroll
-    for (int m = 0; m < L::NC; ++m) rhs[m] = rhs[m] - (F[m * nf + fr] - F[m * nf + fl]) / dx;
+    for (int m = 0; m < L::NC; ++m) {
+      const double df = F[m * nf + fr] - F[m * nf + fl];
+      rhs[m] = rhs[m] - (FAST ? df * idx : df / dx);
+    }
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) {
       const int m = L::AL + k;
-      rhs[m] = rhs[m] - (F[m * nf + fr] - F[(M + k) * nf + fl]) / dx;
+      const double df = F[m * nf + fr] - F[(M + k) * nf + fl];
+      rhs[m] = rhs[m] - (FAST ? df * idx : df / dx);
     }
   }
   if (MODE == 1) {
@@ -610,7 +620,7 @@ __global__ void __launch_bounds__(kCellThreads)
 #pragma unroll
     for (int m = 0; m < M; ++m) Wo[m] = a * Wn[m * nc + c] + b * (Ws[m] + dt * rhs[m]);
   }
-  if (relax) relax_cell<N, D>(Wo, f);
+  if (relax) relax_cell<N, D, FAST>(Wo, f);
   if (count) count_bits(st, admissibility_bits<N, D>(Wo, f));
 #pragma unroll
   for (int m = 0; m < M; ++m) Wout[m * nc + c] = Wo[m];

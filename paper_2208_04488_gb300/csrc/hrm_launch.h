@@ -23,7 +23,8 @@ struct FaceKernels {
   // precision: 0 FP64, 1 FP32 bulk
   void (*face[3])(int precision, const double* W, const double* V, const double* AUX, const float* P32,
                   double* out, const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
-  void (*update)(int mode, const double* Wn, const double* Wsrc, double* Wout, const double* F0,
+  // mode 0: RK combination, mode 1: write the RHS; fast: precision-form variant
+  void (*update)(int mode, int fast, const double* Wn, const double* Wsrc, double* Wout, const double* F0,
                  const double* F1, const double* F2, const DevGrid&, const DevFluid&, StepState*, double a,
                  double b, int relax, int count, cudaStream_t);
 };
@@ -35,10 +36,19 @@ const FaceKernels* face_kernels_d2(int N);
 const FaceKernels* face_kernels_d3(int N);
 
 // FP32-bulk midpoint kernels, compiled in their own units (with FMA contraction).
+void update32_d1(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
+                 const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
+                 int count, cudaStream_t);
 void face32_d1(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
                const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+void update32_d2(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
+                 const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
+                 int count, cudaStream_t);
 void face32_d2(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
                const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+void update32_d3(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
+                 const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
+                 int count, cudaStream_t);
 void face32_d3(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
                const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
 

@@ -298,8 +298,9 @@ def test_fp32_form_keeps_uniform_states_exactly(hrm):
 def test_fp32_form_error_against_fp64(hrm, pr, nsteps, tol):
     """The precision form stays within a stated relative L1 error of the FP64
     path and keeps every cell admissible."""
+    from paper_2208_04488_gb300.metrics import rel_l1_state
     a, b = _fp32_vs_fp64(hrm, pr, nsteps)
-    err = rel_l1(b.get(hrm.FIELD_W), a.get(hrm.FIELD_W))
+    err = rel_l1_state(b.get(hrm.FIELD_W), a.get(hrm.FIELD_W), pr.N, pr.D)
     assert err.max() <= tol, err
     assert b.admissibility() == [0, 0, 0, 0]
 
