@@ -193,6 +193,33 @@ int32_t hrm_profile_read(hrm_ctx* ctx, int32_t max, float* ms, int32_t* kind);
  * of the ALU roofline of the per-midpoint kernels. Synchronises `stream`. */
 hrm_status hrm_probe_fma_peak(int32_t precision, int32_t iters, void* stream, double* flops_per_s);
 
+/* Allocation-free time step. The paper has no counterpart: this entry point
+ * exists for callers that may not allocate device memory -- an application
+ * whose device memory is already owned by its own pool (for example a caching
+ * allocator holding the free memory, or a fixed memory budget per solver), or
+ * code that runs where cudaMalloc is not allowed (for example while a stream is
+ * being captured into a CUDA graph). It computes what hrm_dt computes (tau_d =
+ * max(|u_d| + c)/dx_d, dt = cfl / sum tau_d, Sec. 4.1.2) for a state the caller
+ * owns, without a context and without calling cudaMalloc, cudaFree or any
+ * allocating library routine.
+ *   W_device: the state, layout above, nspecies (2..3), ndim (1..3), n[ndim],
+ *             dx[ndim], species table as for hrm_create (q may be NULL);
+ *   out_device: 1 + ndim doubles of device memory, receives dt then tau_d.
+ * Work is enqueued on `stream` (NULL: default stream); the call does not
+ * synchronise. Its only scratch is a file-scope device array of 1.5 MiB (one
+ * partial maximum per 2048 cells and direction) that every GPU which loads the
+ * library holds until the process exits; grids above 65536 x 2048 =
+ * 134,217,728 cells are rejected with HRM_E_INVAL (hrm_last_error(NULL) says
+ * why). Every call overwrites the part of the array it reads, so nothing has to
+ * be cleared, but calls that overlap on the GPU (other streams, other threads)
+ * share the array and race. The first call on a device looks up the array's
+ * device address for that device (cudaGetSymbolAddress, once per device); make
+ * that first call before any stream capture. */
+hrm_status hrm_dt_noalloc(int32_t nspecies, int32_t ndim, const int64_t* n, const double* dx,
+                          const double* gamma, const double* p_inf, const double* c_v,
+                          const double* q, const double* W_device, double cfl,
+                          double* out_device, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,7 @@ UNITS = {
     "hrm_face32_d3.cu": [],
     "hrm_api.cu": [],
     "hrm_probe.cu": [],
+    "hrm_noalloc.cu": ["--fmad=false"],
 }
 
 

@@ -546,6 +546,8 @@ int64_t hrm_kernel_launches(const hrm_ctx* c) { return c ? c->launches : 0; }
 }  // extern "C"
 
 namespace hrm {
+void set_thread_error(const char* msg) { g_create_error = msg; }
+
 const FaceKernels* face_kernels(int N, int D) {
   if (D == 1) return face_kernels_d1(N);
   if (D == 2) return face_kernels_d2(N);

@@ -4,6 +4,35 @@
 #include "hrm_launch.h"
 
 namespace hrm {
+
+// Step scalars from the reduced tau_d (Sec. 4.1.2): dt = cfl / sum tau, or the
+// requested dt; sigma_d = tau_d / sum tau, lambda_d = dt / (sigma_d dx_d).
+// mode 0 advances the step time and count, mode 1 only answers a dt query.
+__global__ void k_finalize(StepState* st, DevGrid g, int D, double cfl, int mode) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double tau[3] = {0.0, 0.0, 0.0}, sum = 0.0;
+  for (int d = 0; d < D; ++d) {
+    tau[d] = __longlong_as_double((long long)st->tau_bits[d]);
+    sum = sum + tau[d];
+    st->tau_bits[d] = 0ull;
+  }
+  const double dt = (mode == 0 && st->dt_req > 0.0) ? st->dt_req : cfl / sum;
+  for (int d = 0; d < D; ++d) {
+    const double sigma = tau[d] / sum;
+    st->lam[d] = dt / (sigma * g.dx[d]);
+    st->tau[d] = tau[d];
+  }
+  st->dt = dt;
+  if (mode == 0) {
+    st->t = st->t + dt;
+    st->steps = st->steps + 1;
+  }
+}
+
+__global__ void k_set_dt(StepState* st, double dt_req) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) st->dt_req = dt_req;
+}
+
 namespace {
 
 template <int N, int D>

@@ -96,6 +96,9 @@ def lib():
     L.hrm_profile_read.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(ctypes.c_int32)]
     L.hrm_profile_read.restype = ctypes.c_int32
+    L.hrm_dt_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), _DP, _DP, _DP,
+                                 _DP, _DP, _VP, ctypes.c_double, _VP, _VP]
+    L.hrm_dt_noalloc.restype = ctypes.c_int
     L.hrm_probe_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, _VP, _DP]
     L.hrm_probe_fma_peak.restype = ctypes.c_int
     for name in ("hrm_create", "hrm_set_params", "hrm_set", "hrm_set_primitive", "hrm_dt", "hrm_step",
