@@ -27,6 +27,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM traffic per launch of the dominant kernels, dram__bytes_read.sum + dram__bytes_write.sum from one
+# ncu --set full capture on this workload (profiles/k_face_fp64_shock_bubble_1024x512.md and
+# profiles/k_face32_shock_bubble_1024x512.md); to be re-taken whenever those kernels change.
+TRAFFIC_BYTES = {"k_face_fp64": 98.45e6, "k_face32": 124.0e6}
 METRIC = "cell-updates/s (FP64 plain vs FP32+learned) at stated L1 err; % of roofline"
 UNIT = "cell-updates/s"
 WORKLOAD = "2D three-species shock-bubble, 1024x512 cells, Mach 1.5 shock, water+air+helium, SSP-RK3, CFL 0.4"
@@ -300,7 +304,8 @@ def main():
                        "parallelism": f"{ws} independent replica(s)" if ws > 1 else "single GPU"},
             "roofline": {"bound": "alu", "kernel": "k_face (per-midpoint, FP64)",
                          "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                         "frac": frac, "traffic": None,
+                         "frac": frac, "traffic": TRAFFIC_BYTES["k_face_fp64"],
+                         "traffic_unit": "bytes per launch (ncu capture, y sweep)",
                          "peak_source": "measured FP64 FMA-chain probe on this GPU (hrm_probe_fma_peak)",
                          "algorithmic_flops_per_face": [round(x[0], 1) for x in faces],
                          "avg_launch_ms": 1e3 * t_face / n_face, "launches_timed": n_face,
@@ -321,7 +326,8 @@ def main():
                                       "achieved": ach32 / 1e12, "unit": "TFLOP/s",
                                       "peak_fp32": fp32_peak / 1e12, "frac_of_fp32_peak": ach32 / fp32_peak,
                                       "peak_fp64": fp64_peak / 1e12,
-                                      "avg_launch_ms": 1e3 * tf32 / n32, "kernel_time_share": share32}},
+                                      "avg_launch_ms": 1e3 * tf32 / n32, "kernel_time_share": share32,
+                                      "traffic": TRAFFIC_BYTES["k_face32"]}},
             },
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
