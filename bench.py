@@ -179,6 +179,44 @@ def time_steps(torch, s, K, flush, ev_stream):
     return total, per
 
 
+def measure_batched(torch, hrm, problems, stream, flush, args):
+    """64 seeded 2D instances (128x128 .. 1024x512, 2-3 species, Mach 1.2-3)
+    advanced together: autotuned launch shape (FP32 precision form), then
+    total-cells-weighted cell-updates/s of both precision forms."""
+    ps = problems.batch_instances(64, seed=4242)
+    out = {"instances": len(ps), "total_cells": int(sum(p.ncells for p in ps)),
+           "species": sorted({p.N for p in ps}), "scaling": "n/a (one GPU)"}
+    shape = None
+    for name, prec in (("fp32", hrm.FP32), ("fp64", hrm.FP64)):
+        b = hrm.BatchSolver(ps, params=hrm.params_default(cfl=0.4, check=0, precision=prec), stream=stream)
+        if shape is None:
+            t0 = time.perf_counter()
+            shape = b.tune(1)
+            out["tuned_shape"] = shape
+            out["tune_seconds"] = time.perf_counter() - t0
+        else:
+            b.set_launch(shape["face_threads"], shape["face_tile"], shape["cell_tile"], shape["blocks_per_sm"])
+        K = max(3, args.steps // (4 if prec == hrm.FP64 else 1))
+        b.step(1)
+        torch.cuda.synchronize()
+        l0 = b.kernel_launches()
+        total = 0.0
+        for _ in range(K):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(1)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1) * 1e-3
+        out[name] = {"value": out["total_cells"] * K / total, "unit": UNIT, "ms_per_step": 1e3 * total / K,
+                     "steps": K, "launches_per_step": (b.kernel_launches() - l0) / K,
+                     "admissibility_after": b.admissibility()}
+        del b
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,6 +224,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
     args = ap.parse_args()
@@ -246,6 +285,9 @@ def main():
     from paper_2208_04488_gb300.metrics import rel_l1_state
     l1_32 = rel_l1_state(Wb, Wa, pr.N, pr.D).tolist()
     del ea, eb, s32
+
+    # batched form: the 64 seeded uneven instances, one persistent launch per phase
+    batched = measure_batched(torch, hrm, problems, stream, flush, args) if rank == 0 and not args.no_batch else None
 
     t_tensor = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
     if dist is not None:
@@ -329,6 +371,7 @@ def main():
                                       "avg_launch_ms": 1e3 * tf32 / n32, "kernel_time_share": share32,
                                       "traffic": TRAFFIC_BYTES["k_face32"]}},
             },
+            "batched": batched,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "admissibility_after": adm,

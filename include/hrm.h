@@ -193,6 +193,59 @@ int32_t hrm_profile_read(hrm_ctx* ctx, int32_t max, float* ms, int32_t* kind);
  * of the ALU roofline of the per-midpoint kernels. Synchronises `stream`. */
 hrm_status hrm_probe_fma_peak(int32_t precision, int32_t iters, void* stream, double* flops_per_s);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent 2D problems of uneven size (each its own grid
+ * and species table, N = 2 or 3) advanced together. Each phase of a step (cell
+ * primitives and CFL maxima, step scalars, midpoint sweeps per direction,
+ * update with relaxation) is ONE persistent launch over a table of work items
+ * (instance, range of cells or faces) covering every instance, and one step is
+ * one captured CUDA graph. Every instance keeps its own CFL time step (params.cfl,
+ * Sec. 4.1.2) and simulated time. The per-element arithmetic is that of the
+ * single-problem path: with HRM_FP64 every instance reproduces an hrm_ctx of the
+ * same problem bit for bit. Only PP-WCNS-IS with SSP-RK3 is offered.
+ * ------------------------------------------------------------------------- */
+typedef struct hrm_batch hrm_batch; /* opaque, owned by the library */
+
+typedef struct {
+  hrm_grid grid;       /* ndim must be 2 */
+  int32_t nspecies;    /* 2 or 3 */
+  int32_t pad;
+  double gamma[4], p_inf[4], c_v[4], q[4];
+} hrm_instance;
+
+/* Create a batch of ninst instances (device memory for every state and scratch).
+ * Errors as hrm_create; on failure *out is NULL and hrm_batch_last_error(NULL)
+ * explains. */
+hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* inst,
+                            const hrm_params* params, void* cuda_stream);
+void hrm_batch_destroy(hrm_batch* b);
+const char* hrm_batch_last_error(const hrm_batch* b);
+/* Initial state of instance i from primitive planes (as hrm_set_primitive). */
+hrm_status hrm_batch_set_primitive(hrm_batch* b, int32_t i, const double* prim, int32_t on_device);
+/* State of instance i from W (as hrm_set). */
+hrm_status hrm_batch_set(hrm_batch* b, int32_t i, const double* W, int32_t on_device);
+/* Copy the state W of instance i (host: synchronises). */
+hrm_status hrm_batch_get(hrm_batch* b, int32_t i, double* dst, int32_t on_device);
+/* nsteps CFL steps of every instance: one graph launch per step. With
+ * params.check, synchronises and returns HRM_E_ADMISSIBILITY if any cell of any
+ * instance left the admissible set. */
+hrm_status hrm_batch_step(hrm_batch* b, int32_t nsteps);
+hrm_status hrm_batch_time(hrm_batch* b, int32_t i, double* t, int64_t* steps);
+/* Admissibility counters summed over the instances (as hrm_admissibility). */
+hrm_status hrm_batch_admissibility(hrm_batch* b, int64_t counts[4]);
+/* Launch shape of the persistent kernels: threads per block of the midpoint
+ * sweeps (64, 128 or 256), faces per work item (>= face_threads), cells per work
+ * item (>= 256), persistent blocks per SM (1..32). */
+hrm_status hrm_batch_set_launch(hrm_batch* b, int32_t face_threads, int32_t face_tile, int32_t cell_tile,
+                                int32_t blocks_per_sm);
+/* Autotuner: times steps_per_trial steps of the batch itself for each candidate
+ * launch shape (threads {64,128,256} x faces per item {1,8,64} x threads x blocks
+ * per SM {1,2,4,8}), restores the states after every trial, keeps the fastest and
+ * writes it to best[4] (face_threads, face_tile, cell_tile, blocks_per_sm). */
+hrm_status hrm_batch_tune(hrm_batch* b, int32_t steps_per_trial, int32_t* best);
+int64_t hrm_batch_kernel_launches(const hrm_batch* b);
+int64_t hrm_batch_total_cells(const hrm_batch* b);
+
 /* Allocation-free time step. The paper has no counterpart: this entry point
  * exists for callers that may not allocate device memory -- an application
  * whose device memory is already owned by its own pool (for example a caching

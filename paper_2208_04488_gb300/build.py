@@ -31,6 +31,9 @@ UNITS = {
     "hrm_api.cu": [],
     "hrm_probe.cu": [],
     "hrm_noalloc.cu": ["--fmad=false"],
+    "hrm_batch64_d2.cu": ["--fmad=false"],
+    "hrm_batch32_d2.cu": [],
+    "hrm_batch_api.cu": [],
 }
 
 

@@ -1,0 +1,135 @@
+// Batched form: many independent problems of uneven size advanced together,
+// one persistent launch per phase for all of them. Blocks loop over a table of
+// work items (instance, element range); every item lies inside one instance,
+// so the per-element bodies are exactly those of the single-instance kernels
+// and a batched instance reproduces its own context bit for bit.
+#pragma once
+
+#include "hrm_cell.cuh"
+#include "hrm_face32.cuh"
+
+namespace hrm {
+
+// Device-side description of one instance.
+struct BatchInst {
+  DevGrid g;
+  DevFluid f;
+  int32_t N;
+  int32_t pad;
+  double* Wn;
+  double* Ws;
+  double* V;
+  double* AUX;
+  double* F[3];
+  float* P32;
+  StepState* st;
+};
+
+// A contiguous range [begin, end) of cells or faces of one instance.
+struct WorkItem {
+  int32_t inst;
+  int32_t pad;
+  int64_t begin;
+  int64_t end;
+};
+
+constexpr int kBatchMaxThreads = 256;
+
+__device__ __forceinline__ const double* pick(const BatchInst& I, int sel) { return sel == 0 ? I.Wn : I.Ws; }
+__device__ __forceinline__ double* pick_mut(const BatchInst& I, int sel) { return sel == 0 ? I.Wn : I.Ws; }
+
+// Primitives of every cell of every instance (+ per-instance CFL maxima).
+template <int D>
+__global__ void __launch_bounds__(kBatchMaxThreads)
+    k_batch_prim(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
+                 int fp32, int tau) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const WorkItem w = items[it];
+    const BatchInst& I = insts[w.inst];
+    double s[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) s[d] = 0.0;
+    const double* W = pick(I, src);
+    float* P32 = fp32 ? I.P32 : nullptr;
+    for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
+      double sc[D];
+      if (I.N == 2)
+        prim_body<2, D>(c, W, I.V, I.AUX, P32, I.g, I.f, sc);
+      else
+        prim_body<3, D>(c, W, I.V, I.AUX, P32, I.g, I.f, sc);
+#pragma unroll
+      for (int d = 0; d < D; ++d) s[d] = (sc[d] != sc[d]) ? sc[d] : (sc[d] > s[d] ? sc[d] : s[d]);
+    }
+    if (tau) block_tau_max<D>(s, I.st->tau_bits);
+  }
+}
+
+// Midpoints of direction DIR of every instance; FP64 (bit-exact) or precision form.
+template <int D, int DIR, bool FP32>
+__global__ void __launch_bounds__(kBatchMaxThreads)
+    k_batch_face(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
+                 DevParams pr) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const WorkItem w = items[it];
+    const BatchInst& I = insts[w.inst];
+    const double* W = pick(I, src);
+    const double lam = I.st->lam[DIR];
+    for (int64_t t = w.begin + threadIdx.x; t < w.end; t += blockDim.x) {
+      Nodes6 nd;
+      if (!face_nodes<DIR>(I.g, t, nd)) continue;
+      if constexpr (FP32) {
+        if (I.N == 2)
+          face32_body<2, D, DIR>(t, nd, W, I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr, lam);
+        else
+          face32_body<3, D, DIR>(t, nd, W, I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr, lam);
+      } else {
+        if (I.N == 2)
+          face_body<double, 2, D, DIR>(t, nd, W, I.V, I.AUX, I.F[DIR], I.g, I.f, pr, lam);
+        else
+          face_body<double, 3, D, DIR>(t, nd, W, I.V, I.AUX, I.F[DIR], I.g, I.f, pr, lam);
+      }
+    }
+  }
+}
+
+// Flux difference, SSP-RK combination and relaxation of every cell of every instance.
+template <int D, bool FAST>
+__global__ void __launch_bounds__(kBatchMaxThreads)
+    k_batch_update(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
+                   int dst, double a, double b, int relax, int count) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const WorkItem w = items[it];
+    const BatchInst& I = insts[w.inst];
+    const double* Wsrc = pick(I, src);
+    double* Wout = pick_mut(I, dst);
+    const double dt = I.st->dt;
+    for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
+      if (I.N == 2)
+        update_body<2, D, 0, FAST>(c, I.Wn, Wsrc, Wout, I.F[0], I.F[1], I.F[2], I.g, I.f, I.st, dt, a, b, relax,
+                                   count);
+      else
+        update_body<3, D, 0, FAST>(c, I.Wn, Wsrc, Wout, I.F[0], I.F[1], I.F[2], I.g, I.f, I.st, dt, a, b, relax,
+                                   count);
+    }
+  }
+}
+
+// Host launchers (instantiated for D = 2 in hrm_batch64_d2.cu / hrm_batch32_d2.cu).
+struct BatchLaunch {
+  int grid;      // persistent blocks
+  int threads;   // threads per block
+};
+
+void batch_prim_d2(const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int fp32, int tau,
+                   cudaStream_t);
+void batch_finalize(const BatchInst*, int ninst, int D, double cfl, cudaStream_t);
+void batch_face64_d2(int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
+                     const DevParams&, cudaStream_t);
+void batch_face32_d2(int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
+                     const DevParams&, cudaStream_t);
+void batch_update64_d2(const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst, double a,
+                       double b, int relax, int count, cudaStream_t);
+void batch_update32_d2(const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst, double a,
+                       double b, int relax, int count, cudaStream_t);
+
+}  // namespace hrm

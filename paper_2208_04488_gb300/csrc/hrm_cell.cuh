@@ -42,18 +42,15 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
 // Per cell: V (M planes), AUX = (c, rho, rho c^2). With `tau`, also the running
 // maxima tau_d = max(|u_d| + c)/dx_d (Sec. 4.1.2): warp shuffles, then one
 // atomicMax per block and direction on the order-preserving bits.
+// One cell c < ncells: primitives, AUX, optional FP32 planes; s[d] = (|u_d| + c)/dx_d.
 template <int N, int D>
-__global__ void __launch_bounds__(kCellThreads)
-    k_prim(const double* __restrict__ W, double* __restrict__ V, double* __restrict__ AUX,
-           float* __restrict__ P32, DevGrid g, DevFluid f, StepState* st, int tau) {
+__device__ __forceinline__ void prim_body(int64_t c, const double* __restrict__ W, double* __restrict__ V,
+                                          double* __restrict__ AUX, float* __restrict__ P32, const DevGrid& g,
+                                          const DevFluid& f, double* s) {
   using L = Lay<N, D>;
   constexpr int M = L::M;
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nc = g.ncells;
-  double s[D];
-#pragma unroll
-  for (int d = 0; d < D; ++d) s[d] = 0.0;
-  if (c < nc) {
+  {
     double w[M], v[M], rho, cs, rc2;
 #pragma unroll
     for (int m = 0; m < M; ++m) w[m] = W[m * nc + c];
@@ -82,7 +79,12 @@ __global__ void __launch_bounds__(kCellThreads)
 #pragma unroll
     for (int d = 0; d < D; ++d) s[d] = (fabs(v[L::MOM + d]) + cs) / g.dx[d];
   }
-  if (!tau) return;
+}
+
+// Block-level max of s[d] over the threads of the block, then one atomicMax per
+// direction on the order-preserving bits (NaN reduces as the largest value).
+template <int D>
+__device__ __forceinline__ void block_tau_max(const double* s, unsigned long long* tau_bits) {
   __shared__ unsigned long long red[D][kCellThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -100,9 +102,23 @@ __global__ void __launch_bounds__(kCellThreads)
   __syncthreads();
   if (threadIdx.x < D) {
     unsigned long long b = 0;
-    for (int w = 0; w < kCellThreads / 32; ++w) b = red[threadIdx.x][w] > b ? red[threadIdx.x][w] : b;
-    atomicMax(&st->tau_bits[threadIdx.x], b);
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) b = red[threadIdx.x][w] > b ? red[threadIdx.x][w] : b;
+    atomicMax(&tau_bits[threadIdx.x], b);
   }
+  __syncthreads();  // red is reused by the next call in a persistent loop
+}
+
+template <int N, int D>
+__global__ void __launch_bounds__(kCellThreads)
+    k_prim(const double* __restrict__ W, double* __restrict__ V, double* __restrict__ AUX,
+           float* __restrict__ P32, DevGrid g, DevFluid f, StepState* st, int tau) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double s[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) s[d] = 0.0;
+  if (c < g.ncells) prim_body<N, D>(c, W, V, AUX, P32, g, f, s);
+  if (!tau) return;
+  block_tau_max<D>(s, st->tau_bits);
 }
 
 // Initial state from primitive planes (alpha_1..alpha_{N-1}, u_d, p, T) in p-T

@@ -124,16 +124,13 @@ __device__ __forceinline__ double alpha_flux(double aL, double aR, double ss) {
 }
 
 template <int N, int D, int DIR>
-__global__ void __launch_bounds__(kFaceThreads)
-    k_face32(const double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ AUX,
-             const float* __restrict__ P32, double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr,
-             const StepState* __restrict__ st) {
+__device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const double* __restrict__ W,
+                                            const double* __restrict__ V, const double* __restrict__ AUX,
+                                            const float* __restrict__ P32, double* __restrict__ out,
+                                            const DevGrid& g, const DevFluid& f, const DevParams& pr, double lam) {
   using L = Lay<N, D>;
   using Q = P32Lay<N, D>;
   constexpr int M = L::M;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  Nodes6 nd;
-  if (!face_nodes<DIR>(g, t, nd)) return;
   const int64_t nc = g.ncells;
   const int64_t nf = face_count<DIR>(g);
   auto ld = [&](int plane, int j) -> float { return P32[(int64_t)plane * nc + nd.c[j]]; };
@@ -327,7 +324,7 @@ __global__ void __launch_bounds__(kFaceThreads)
       double Fi[L::NC], Fj[L::NC];
       node_flux<N, D, DIR>(Wi, Vi, Fi);
       node_flux<N, D, DIR>(Wj, Vj, Fj);
-      flux_limit<N, D>(Wi, Wj, Fi, Fj, st->lam[DIR], G, H, f, pr);
+      flux_limit<N, D>(Wi, Wj, Fi, Fj, lam, G, H, f, pr);
     }
   }
 #pragma unroll
@@ -337,6 +334,17 @@ __global__ void __launch_bounds__(kFaceThreads)
     out[(L::AL + k) * nf + t] = G.gm[k];
     out[(M + k) * nf + t] = G.gp[k];
   }
+}
+
+template <int N, int D, int DIR>
+__global__ void __launch_bounds__(kFaceThreads)
+    k_face32(const double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ AUX,
+             const float* __restrict__ P32, double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr,
+             const StepState* __restrict__ st) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  Nodes6 nd;
+  if (!face_nodes<DIR>(g, t, nd)) return;
+  face32_body<N, D, DIR>(t, nd, W, V, AUX, P32, out, g, f, pr, st->lam[DIR]);
 }
 
 }  // namespace hrm

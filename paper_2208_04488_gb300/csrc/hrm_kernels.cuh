@@ -271,15 +271,14 @@ __device__ __forceinline__ void node_flux(const double* W, const double* V, doub
 // Outputs of a midpoint: M + N - 1 planes over the face grid of the direction --
 // the NC conservative flux slots, the N-1 alpha slots of G^-_{i+1/2} (planes
 // AL..M-1) and the N-1 alpha slots of G^+_{i+1/2} (planes M..M+N-2).
+// One midpoint t of direction DIR (t inside the face grid); lam = lambda_DIR.
 template <typename R, int N, int D, int DIR>
-__global__ void __launch_bounds__(kFaceThreads)
-    k_face(const double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ AUX,
-           double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr, const StepState* __restrict__ st) {
+__device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const double* __restrict__ W,
+                                          const double* __restrict__ V, const double* __restrict__ AUX,
+                                          double* __restrict__ out, const DevGrid& g, const DevFluid& f,
+                                          const DevParams& pr, double lam) {
   using L = Lay<N, D>;
   constexpr int M = L::M;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  Nodes6 nd;
-  if (!face_nodes<DIR>(g, t, nd)) return;
   const int64_t nc = g.ncells;
   const int64_t nf = face_count<DIR>(g);
   const double* __restrict__ Cc = AUX;           // sound speed
@@ -467,7 +466,7 @@ __global__ void __launch_bounds__(kFaceThreads)
       double Fi[L::NC], Fj[L::NC];
       node_flux<N, D, DIR>(Wi, Vi, Fi);
       node_flux<N, D, DIR>(Wj, Vj, Fj);
-      flux_limit<N, D>(Wi, Wj, Fi, Fj, st->lam[DIR], G, H, f, pr);
+      flux_limit<N, D>(Wi, Wj, Fi, Fj, lam, G, H, f, pr);
     }
   }
 #pragma unroll
@@ -477,6 +476,16 @@ __global__ void __launch_bounds__(kFaceThreads)
     out[(L::AL + k) * nf + t] = G.gm[k];
     out[(M + k) * nf + t] = G.gp[k];
   }
+}
+
+template <typename R, int N, int D, int DIR>
+__global__ void __launch_bounds__(kFaceThreads)
+    k_face(const double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ AUX,
+           double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr, const StepState* __restrict__ st) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  Nodes6 nd;
+  if (!face_nodes<DIR>(g, t, nd)) return;
+  face_body<R, N, D, DIR>(t, nd, W, V, AUX, out, g, f, pr, st->lam[DIR]);
 }
 
 // ---------------------------------------------------------------- thermal relaxation (Sec. 4.2)
@@ -564,16 +573,15 @@ __device__ __forceinline__ void count_bits(StepState* st, int b) {
 // MODE 1 writes RHS instead of the combination. In-place (W_out == W_src or W^n)
 // is allowed: each thread reads its own cell before writing it.
 // FAST (precision form): reciprocal of dx and of rho instead of divisions.
+// One cell c < ncells.
 template <int N, int D, int MODE, bool FAST = false>
-__global__ void __launch_bounds__(kCellThreads)
-    k_update(const double* Wn, const double* Wsrc, double* Wout, const double* __restrict__ F0,
-             const double* __restrict__ F1, const double* __restrict__ F2, DevGrid g, DevFluid f,
-             StepState* st, double a, double b, int relax, int count) {
+__device__ __forceinline__ void update_body(int64_t c, const double* Wn, const double* Wsrc, double* Wout,
+                                            const double* __restrict__ F0, const double* __restrict__ F1,
+                                            const double* __restrict__ F2, const DevGrid& g, const DevFluid& f,
+                                            StepState* st, double dt, double a, double b, int relax, int count) {
   using L = Lay<N, D>;
   constexpr int M = L::M;
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nc = g.ncells;
-  if (c >= nc) return;
   const int64_t i0 = c % g.n[0];
   const int64_t r = c / g.n[0];
   const int64_t i1 = r % g.n[1], i2 = r / g.n[1];
@@ -611,7 +619,6 @@ __global__ void __launch_bounds__(kCellThreads)
     for (int m = 0; m < M; ++m) Wout[m * nc + c] = rhs[m];
     return;
   }
-  const double dt = st->dt;
   double Wo[M];
   if (a == 0.0) {
 #pragma unroll
@@ -624,6 +631,17 @@ __global__ void __launch_bounds__(kCellThreads)
   if (count) count_bits(st, admissibility_bits<N, D>(Wo, f));
 #pragma unroll
   for (int m = 0; m < M; ++m) Wout[m * nc + c] = Wo[m];
+}
+
+template <int N, int D, int MODE, bool FAST = false>
+__global__ void __launch_bounds__(kCellThreads)
+    k_update(const double* Wn, const double* Wsrc, double* Wout, const double* __restrict__ F0,
+             const double* __restrict__ F1, const double* __restrict__ F2, DevGrid g, DevFluid f,
+             StepState* st, double a, double b, int relax, int count) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncells) return;
+  update_body<N, D, MODE, FAST>(c, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, MODE == 1 ? 0.0 : st->dt, a, b, relax,
+                                count);
 }
 
 }  // namespace hrm

@@ -44,6 +44,12 @@ class HrmParams(ctypes.Structure):
                 ("q_sensor", ctypes.c_double), ("learned_threshold", ctypes.c_double)]
 
 
+class HrmInstance(ctypes.Structure):
+    _fields_ = [("grid", HrmGrid), ("nspecies", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("gamma", ctypes.c_double * 4), ("p_inf", ctypes.c_double * 4), ("c_v", ctypes.c_double * 4),
+                ("q", ctypes.c_double * 4)]
+
+
 class HrmError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"hrm status {status}: {message}")
@@ -99,6 +105,27 @@ def lib():
     L.hrm_dt_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), _DP, _DP, _DP,
                                  _DP, _DP, _VP, ctypes.c_double, _VP, _VP]
     L.hrm_dt_noalloc.restype = ctypes.c_int
+    L.hrm_batch_create.argtypes = [P(_VP), ctypes.c_int32, P(HrmInstance), P(HrmParams), _VP]
+    L.hrm_batch_destroy.argtypes = [_VP]
+    L.hrm_batch_destroy.restype = None
+    L.hrm_batch_last_error.argtypes = [_VP]
+    L.hrm_batch_last_error.restype = ctypes.c_char_p
+    L.hrm_batch_set_primitive.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
+    L.hrm_batch_set.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
+    L.hrm_batch_get.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
+    L.hrm_batch_step.argtypes = [_VP, ctypes.c_int32]
+    L.hrm_batch_time.argtypes = [_VP, ctypes.c_int32, _DP, P(ctypes.c_int64)]
+    L.hrm_batch_admissibility.argtypes = [_VP, P(ctypes.c_int64)]
+    L.hrm_batch_set_launch.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    L.hrm_batch_tune.argtypes = [_VP, ctypes.c_int32, P(ctypes.c_int32)]
+    L.hrm_batch_kernel_launches.argtypes = [_VP]
+    L.hrm_batch_kernel_launches.restype = ctypes.c_int64
+    L.hrm_batch_total_cells.argtypes = [_VP]
+    L.hrm_batch_total_cells.restype = ctypes.c_int64
+    for name in ("hrm_batch_create", "hrm_batch_set_primitive", "hrm_batch_set", "hrm_batch_get",
+                 "hrm_batch_step", "hrm_batch_time", "hrm_batch_admissibility", "hrm_batch_set_launch",
+                 "hrm_batch_tune"):
+        getattr(L, name).restype = ctypes.c_int
     L.hrm_probe_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, _VP, _DP]
     L.hrm_probe_fma_peak.restype = ctypes.c_int
     for name in ("hrm_create", "hrm_set_params", "hrm_set", "hrm_set_primitive", "hrm_dt", "hrm_step",
@@ -272,3 +299,86 @@ class Solver:
 
     def kernel_launches(self) -> int:
         return int(lib().hrm_kernel_launches(self.h))
+
+
+class BatchSolver:
+    """One hrm_batch: many 2D problems (paper_2208_04488_gb300.problems.Problem)
+    advanced together."""
+
+    def __init__(self, problems, params: Optional[HrmParams] = None, stream=None, set_state=True):
+        L = lib()
+        self.problems = list(problems)
+        arr = (HrmInstance * len(self.problems))()
+        for i, pr in enumerate(self.problems):
+            it = arr[i]
+            it.grid.ndim = pr.D
+            for d in range(3):
+                it.grid.n[d] = pr.n[d] if d < pr.D else 1
+                it.grid.lo[d] = pr.lo[d] if d < pr.D else 0.0
+                it.grid.hi[d] = pr.hi[d] if d < pr.D else 1.0
+            for j in range(6):
+                it.grid.bc[j] = pr.bc[j] if j < len(pr.bc) else 0
+            it.nspecies = pr.N
+            for k in range(pr.N):
+                it.gamma[k], it.p_inf[k], it.c_v[k], it.q[k] = pr.gamma[k], pr.pinf[k], pr.cv[k], pr.q[k]
+        self.params = params if params is not None else params_default()
+        self.stream = _stream_handle(stream)
+        h = _VP()
+        st = L.hrm_batch_create(ctypes.byref(h), len(self.problems), arr, ctypes.byref(self.params),
+                                _VP(self.stream))
+        if st != HRM_OK:
+            raise HrmError(st, L.hrm_batch_last_error(None).decode())
+        self.h = h
+        if set_state:
+            for i, pr in enumerate(self.problems):
+                self._check(L.hrm_batch_set_primitive(self.h, i, _VP(np.ascontiguousarray(pr.prim).ctypes.data), 0))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hrm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != HRM_OK:
+            raise HrmError(st, lib().hrm_batch_last_error(self.h).decode())
+        return st
+
+    def step(self, nsteps=1):
+        return self._check(lib().hrm_batch_step(self.h, int(nsteps)))
+
+    def get(self, i):
+        pr = self.problems[i]
+        out = np.empty((pr.M, pr.ncells))
+        self._check(lib().hrm_batch_get(self.h, i, _VP(out.ctypes.data), 0))
+        return out
+
+    def time(self, i):
+        t = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(lib().hrm_batch_time(self.h, i, ctypes.byref(t), ctypes.byref(n)))
+        return t.value, n.value
+
+    def admissibility(self):
+        c = (ctypes.c_int64 * 4)()
+        self._check(lib().hrm_batch_admissibility(self.h, c))
+        return [int(x) for x in c]
+
+    def set_launch(self, face_threads, face_tile, cell_tile, blocks_per_sm):
+        self._check(lib().hrm_batch_set_launch(self.h, face_threads, face_tile, cell_tile, blocks_per_sm))
+
+    def tune(self, steps_per_trial=1):
+        best = (ctypes.c_int32 * 4)()
+        self._check(lib().hrm_batch_tune(self.h, steps_per_trial, best))
+        return dict(zip(["face_threads", "face_tile", "cell_tile", "blocks_per_sm"], list(best)))
+
+    def kernel_launches(self) -> int:
+        return int(lib().hrm_batch_kernel_launches(self.h))
+
+    def total_cells(self) -> int:
+        return int(lib().hrm_batch_total_cells(self.h))
