@@ -90,12 +90,20 @@ def lib(count: bool = False):
         L.or_cons_cell.argtypes = [P(Fluid), _DP, _DP, _DP]
         L.or_weno_left.argtypes = [_DP, ctypes.c_double, _DP]
         L.or_weno_left.restype = ctypes.c_double
+        L.or_weno_lin.argtypes = [_DP]
+        L.or_weno_lin.restype = ctypes.c_double
         L.or_hllc.argtypes = [P(Fluid), ctypes.c_int, _DP, _DP, _DP]
         L.or_hllc.restype = ctypes.c_double
         L.or_sensor.argtypes = [_DP]
         L.or_sensor.restype = ctypes.c_double
         L.or_face.argtypes = [P(Fluid), P(Params), ctypes.c_int, ctypes.c_double, _DP, _DP, _DP, _DP]
         L.or_rhs.argtypes = [P(Fluid), P(Params), P(Grid), _DP, _DP, _DP]
+        _U8 = ctypes.POINTER(ctypes.c_uint8)
+        L.or_rhs_gated.argtypes = [P(Fluid), P(Params), P(Grid), _DP, _DP, _U8, _U8, _U8, _DP]
+        L.or_step_gated.argtypes = [P(Fluid), P(Params), P(Grid), _DP, ctypes.c_double, ctypes.c_int,
+                                    _U8, _U8, _U8]
+        L.or_stencil_sample.argtypes = [P(Fluid), P(Params), P(Grid), _DP, ctypes.c_int, ctypes.c_int64,
+                                        P(ctypes.c_int64), _DP, _DP]
         L.or_relax_cell.argtypes = [P(Fluid), _DP, _DP]
         L.or_relax.argtypes = [P(Fluid), P(Grid), _DP]
         L.or_dt.argtypes = [P(Fluid), P(Grid), _DP, ctypes.c_double, _DP]
@@ -190,6 +198,12 @@ def weno_left(u, eps=1e-15):
     return v, om
 
 
+def weno_lin(u):
+    """Left-biased interpolation with the linear weights d_k (the gated value)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return lib().or_weno_lin(_ptr(u))
+
+
 def hllc(f: Fluid, dir_, VL, VR):
     VL = np.ascontiguousarray(VL, dtype=np.float64)
     VR = np.ascontiguousarray(VR, dtype=np.float64)
@@ -218,12 +232,46 @@ def face(f: Fluid, p: Params, dir_, lam, W6):
     return Gm, Gp, d
 
 
-def rhs(f: Fluid, p: Params, g: Grid, W, lam):
+def _gate_ptrs(g: Grid, gates):
+    """Per-direction byte arrays over each direction's midpoint grid (or None)."""
+    keep, ptrs = [], []
+    for d in range(3):
+        a = None if gates is None or d >= len(gates) else gates[d]
+        if a is None:
+            ptrs.append(None)
+            continue
+        nf = 1
+        for e in range(g.D):
+            nf *= g.n[e] + (e == d)
+        a = np.ascontiguousarray(a, dtype=np.uint8).reshape(-1)
+        assert a.size == nf, (a.size, nf)
+        keep.append(a)
+        ptrs.append(a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return keep, ptrs
+
+
+def rhs(f: Fluid, p: Params, g: Grid, W, lam, gates=None):
+    """L(W) with the given lambdas; `gates` (optional): per direction, a byte
+    per midpoint (nonzero = linear WENO weights there)."""
     W = np.ascontiguousarray(W, dtype=np.float64)
     R = np.zeros_like(W)
     lam = np.ascontiguousarray(np.resize(np.asarray(lam, dtype=np.float64), 3))
-    lib().or_rhs(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), _ptr(lam), _ptr(R))
+    keep, gp = _gate_ptrs(g, gates)
+    lib().or_rhs_gated(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), _ptr(lam),
+                       gp[0], gp[1], gp[2], _ptr(R))
     return R
+
+
+def stencil_sample(f: Fluid, p: Params, g: Grid, W, dir_, idx):
+    """Learned-detector data of midpoints `idx` of direction `dir_`: the 30
+    normalised stencil features (n, 30) and the WENO-IS weight deviation (n,)."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    feat = np.zeros((idx.size, 30))
+    dev = np.zeros(idx.size)
+    lib().or_stencil_sample(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), dir_, idx.size,
+                            idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(feat), _ptr(dev))
+    return feat, dev
 
 
 def relax_cell(f: Fluid, W):
@@ -253,12 +301,17 @@ def lambdas(f: Fluid, g: Grid, W, dt_):
     return lam
 
 
-def step(f: Fluid, p: Params, g: Grid, W, dt_, nsteps=1, count=False):
+def step(f: Fluid, p: Params, g: Grid, W, dt_, nsteps=1, count=False, gates=None):
     W = np.array(W, dtype=np.float64, order="C")
     L = lib(count)
     if count:
         L.or_count_reset()
-    L.or_step(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), dt_, nsteps)
+    if gates is not None:
+        keep, gp = _gate_ptrs(g, gates)
+        L.or_step_gated(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), dt_, nsteps,
+                        gp[0], gp[1], gp[2])
+    else:
+        L.or_step(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), dt_, nsteps)
     if count:
         out = (ctypes.c_ulonglong * 5)()
         L.or_count_get(out)

@@ -397,6 +397,19 @@ static real weno_is_left(const real* u, double eps, real* omega_out) {
   return w0 * s0 + w1 * s1 + w2 * s2 + w3 * s3;
 }
 
+// The same interpolation with every nonlinear weight replaced by its linear
+// (optimal) weight d_k: the value a smoothness gate selects where it judges
+// the stencil smooth (the nonlinear weights then differ little from d_k).
+static real weno_lin_left(const real* u) {
+  const real um2 = u[0], um1 = u[1], u0 = u[2], up1 = u[3], up2 = u[4];
+  real s0 = real(0.5) * (u0 + up1);
+  real s1 = real(0.5) * (real(3.0) * u0 - um1);
+  real s2 = real(1.0 / 8.0) * (real(3.0) * u0 + real(6.0) * up1 - up2);
+  real s3 = real(1.0 / 8.0) * (real(3.0) * um2 - real(10.0) * um1 + real(15.0) * u0);
+  const double d0 = 15.0 / 32.0, d1 = 5.0 / 32.0, d2 = 5.0 / 16.0, d3 = 1.0 / 16.0;
+  return real(d0) * s0 + real(d1) * s1 + real(d2) * s2 + real(d3) * s3;
+}
+
 // ---------------------------------------------------------------------------
 // Positivity-preserving interpolation limiter (Sec. 4.3.2, Alg.
 // interp_limit_densities, Alg. interp_limit_vol_frac and the hard switch).
@@ -574,13 +587,48 @@ struct FaceDiag {
   int hsL, hsR, flux_flags;
 };
 
+// Characteristic fields of the six-node stencil of a midpoint (App. D): the
+// matrices come from the arithmetic averages of the partial densities, mixture
+// density and sound speed at nodes i, i+1. Slot order of U: 0 -> u - p/(rho c),
+// 1..N -> alpha_k rho_k - alpha_k rho_k p/(rho c^2), N+1.. -> tangential
+// velocities (increasing direction), then the N-1 alpha_k, last -> u + p/(rho c).
+static void project_stencil(const FluidK& f, int dir, const Cell* nd, real U[6][OR_MAXM], real* arb,
+                            real& rhob, real& cb) {
+  const int M = f.M, N = f.N, D = f.D;
+  const int un = sMOM(f, dir), sp = sE(f);
+  const Cell& ci = nd[2];
+  const Cell& cj = nd[3];
+  for (int k = 0; k < N; ++k) arb[k] = real(0.5) * (ci.V[k] + cj.V[k]);
+  rhob = real(0.5) * (ci.rho + cj.rho);
+  cb = real(0.5) * (ci.c + cj.c);
+  int tang[2], nt = 0;
+  for (int d = 0; d < D; ++d)
+    if (d != dir) tang[nt++] = d;
+  // entries of R^{-1}: 1/(rho c) and alpha_k rho_k/(rho c^2) of the averaged state
+  const real inv_rc = real(1.0) / (rhob * cb);
+  const real rc2b = rhob * cb * cb;
+  real ark_rc2[OR_MAXN];
+  for (int k = 0; k < N; ++k) ark_rc2[k] = arb[k] / rc2b;
+  for (int j = 0; j < 6; ++j) {
+    const real* V = nd[j].V;
+    real p = V[sp];
+    U[j][0] = V[un] - inv_rc * p;
+    for (int k = 0; k < N; ++k) U[j][1 + k] = V[k] - ark_rc2[k] * p;
+    for (int t = 0; t < nt; ++t) U[j][N + 1 + t] = V[sMOM(f, tang[t])];
+    for (int k = 0; k < N - 1; ++k) U[j][N + D + k] = V[sAL(f, k)];
+    U[j][M - 1] = V[un] + inv_rc * p;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // One midpoint x_{i+1/2} in direction `dir` from the six node cells
 // nd[0..5] = i-2 .. i+3. Produces the quasi-conservative fluxes
 // Gm = G^-_{i+1/2} (used by cell i) and Gp = G^+_{i+1/2} (used by cell i+1).
 // ---------------------------------------------------------------------------
+// lin: the midpoint is gated smooth -- every WENO-IS weight is replaced by its
+// linear weight d_k; everything else is unchanged.
 static void face_flux(const FluidK& f, const or_params* P, int dir, real lam, const Cell* nd,
-                      real* Gm, real* Gp, FaceDiag* dg) {
+                      real* Gm, real* Gp, FaceDiag* dg, int lin = 0) {
   const int M = f.M, N = f.N, D = f.D;
   const Cell& ci = nd[2];
   const Cell& cj = nd[3];
@@ -595,41 +643,26 @@ static void face_flux(const FluidK& f, const or_params* P, int dir, real lam, co
     for (int m = 0; m < M; ++m) Ghat[m] = GH[m];
     uhat = uH;
   } else {
-    // ---- characteristic projection (App. D): matrices from the arithmetic
-    // averages of the partial densities, mixture density and sound speed.
-    real arb[OR_MAXN];
-    for (int k = 0; k < N; ++k) arb[k] = real(0.5) * (ci.V[k] + cj.V[k]);
-    real rhob = real(0.5) * (ci.rho + cj.rho);
-    real cb = real(0.5) * (ci.c + cj.c);
+    // ---- characteristic projection (App. D)
+    real arb[OR_MAXN], rhob, cb;
+    real U[6][OR_MAXM];
+    project_stencil(f, dir, nd, U, arb, rhob, cb);
     // tangential directions in increasing order
     int tang[2], nt = 0;
     for (int d = 0; d < D; ++d)
       if (d != dir) tang[nt++] = d;
-    // U = R^{-1} V at the six nodes. Slot order of U: 0 -> u - p/(rho c),
-    // 1..N -> alpha_k rho_k - alpha_k rho_k p/(rho c^2), N+1.. -> tangential
-    // velocities, then the N-1 alpha_k, last -> u + p/(rho c).
-    // entries of R^{-1}: 1/(rho c) and alpha_k rho_k/(rho c^2) of the averaged state
-    const real inv_rc = real(1.0) / (rhob * cb);
-    const real rc2b = rhob * cb * cb;
-    real ark_rc2[OR_MAXN];
-    for (int k = 0; k < N; ++k) ark_rc2[k] = arb[k] / rc2b;
-    real U[6][OR_MAXM];
-    for (int j = 0; j < 6; ++j) {
-      const real* V = nd[j].V;
-      real p = V[sp];
-      U[j][0] = V[un] - inv_rc * p;
-      for (int k = 0; k < N; ++k) U[j][1 + k] = V[k] - ark_rc2[k] * p;
-      for (int t = 0; t < nt; ++t) U[j][N + 1 + t] = V[sMOM(f, tang[t])];
-      for (int k = 0; k < N - 1; ++k) U[j][N + D + k] = V[sAL(f, k)];
-      U[j][M - 1] = V[un] + inv_rc * p;
-    }
     // ---- WENO-IS left- and right-biased interpolation of each field (App. C)
     real UL[OR_MAXM], UR[OR_MAXM];
     for (int m = 0; m < M; ++m) {
       real sl[5] = {U[0][m], U[1][m], U[2][m], U[3][m], U[4][m]};
       real sr[5] = {U[5][m], U[4][m], U[3][m], U[2][m], U[1][m]};
-      UL[m] = weno_is_left(sl, P->weno_eps, nullptr);
-      UR[m] = weno_is_left(sr, P->weno_eps, nullptr);
+      if (lin) {
+        UL[m] = weno_lin_left(sl);
+        UR[m] = weno_lin_left(sr);
+      } else {
+        UL[m] = weno_is_left(sl, P->weno_eps, nullptr);
+        UR[m] = weno_is_left(sr, P->weno_eps, nullptr);
+      }
     }
     // ---- back to primitive variables: V~ = R U~ (App. D)
     // entries of R: alpha_k rho_k/(2c) and rho c/2 of the averaged state
@@ -763,8 +796,10 @@ static void load_W(const FluidK& f, const double* W, int64_t nc, int64_t c, real
 
 // L(W): the semi-discrete right-hand side of Eq. semi_W_G_pm_eqn, direction by
 // direction: RHS_i = -sum_d (G^{d,-}_{i+1/2} - G^{d,+}_{i-1/2}) / dx_d.
+// gate (nullable): per direction, one byte per midpoint over that direction's
+// midpoint grid (n_d + 1 midpoints along d, x fastest); nonzero = gated smooth.
 static void rhs_impl(const FluidK& f, const or_params* P, const or_grid* g, const double* W,
-                     const real* lam, real* RHS) {
+                     const real* lam, real* RHS, const uint8_t* const* gate = nullptr) {
   const int M = f.M;
   const int64_t nc = ncells(g);
   for (int64_t c = 0; c < nc * M; ++c) RHS[c] = 0.0;
@@ -792,8 +827,17 @@ static void rhs_impl(const FluidK& f, const or_params* P, const or_grid* g, cons
         cell_from_W(f, w, line[j + 3]);
       }
       // faces f = 0..n: face f lies between cells f-1 and f; stencil f-3..f+2
-      for (int64_t fc = 0; fc <= n; ++fc)
-        face_flux(f, P, dir, lam[dir], &line[fc], &Gm[fc * M], &Gp[fc * M], nullptr);
+      for (int64_t fc = 0; fc <= n; ++fc) {
+        int lin_gate = 0;
+        if (gate && gate[dir]) {
+          int64_t q[3] = {ijk[0], ijk[1], ijk[2]};
+          q[dir] = fc;
+          const int64_t f0 = g->n[0] + (dir == 0);
+          const int64_t f1 = (g->D > 1 ? g->n[1] : 1) + (dir == 1);
+          lin_gate = gate[dir][(q[2] * f1 + q[1]) * f0 + q[0]] != 0;
+        }
+        face_flux(f, P, dir, lam[dir], &line[fc], &Gm[fc * M], &Gp[fc * M], nullptr, lin_gate);
+      }
       for (int64_t i = 0; i < n; ++i) {
         int64_t q[3] = {ijk[0], ijk[1], ijk[2]};
         q[dir] = i;
@@ -1006,14 +1050,20 @@ void or_face(const or_fluid* fl, const or_params* P, int dir, double lam, const 
   }
 }
 
-void or_rhs(const or_fluid* fl, const or_params* P, const or_grid* g, const double* W,
-            const double* lam, double* RHS) {
+void or_rhs_gated(const or_fluid* fl, const or_params* P, const or_grid* g, const double* W,
+                  const double* lam, const uint8_t* gx, const uint8_t* gy, const uint8_t* gz, double* RHS) {
   FluidK f = make_fluid(fl);
   int64_t nc = ncells(g);
   std::vector<real> r(nc * f.M);
   real l[3] = {lam[0], lam[1], lam[2]};
-  rhs_impl(f, P, g, W, l, r.data());
+  const uint8_t* gates[3] = {gx, gy, gz};
+  rhs_impl(f, P, g, W, l, r.data(), gates);
   for (int64_t c = 0; c < nc * f.M; ++c) RHS[c] = val(r[c]);
+}
+
+void or_rhs(const or_fluid* fl, const or_params* P, const or_grid* g, const double* W,
+            const double* lam, double* RHS) {
+  or_rhs_gated(fl, P, g, W, lam, nullptr, nullptr, nullptr, RHS);
 }
 
 // In place; pT (optional, 2 doubles) receives p* and T* of the last cell.
@@ -1060,8 +1110,12 @@ void or_lambdas(const or_fluid* fl, const or_grid* g, const double* W, double dt
 // step of the hyperbolic system followed by the thermal relaxation
 // (relax_mode 1); SSP-RK3 in the Shu-Osher form, SSP-RK2 or forward Euler.
 // lambda_d come from the state at the start of each step.
-void or_step(const or_fluid* fl, const or_params* P, const or_grid* g, double* W, double dt,
-             int nsteps) {
+// gx, gy, gz (nullable): a fixed smoothness gate per direction (see rhs_impl),
+// applied at every stage of every step.
+void or_step_gated(const or_fluid* fl, const or_params* P, const or_grid* g, double* W, double dt,
+                   int nsteps, const uint8_t* gx, const uint8_t* gy, const uint8_t* gz) {
+  const uint8_t* gates[3] = {gx, gy, gz};
+  const uint8_t* const* gate = (gx || gy || gz) ? gates : nullptr;
   FluidK f = make_fluid(fl);
   const int64_t nc = ncells(g), tot = nc * f.M;
   std::vector<double> W0(tot), W1(tot), W2(tot);
@@ -1073,7 +1127,7 @@ void or_step(const or_fluid* fl, const or_params* P, const or_grid* g, double* W
     for (int64_t c = 0; c < tot; ++c) W0[c] = W[c];
     const int relax_stage = (P->relax_mode == 1);
     // stage 1: W1 = W0 + dt L(W0)
-    rhs_impl(f, P, g, W0.data(), lam, L.data());
+    rhs_impl(f, P, g, W0.data(), lam, L.data(), gate);
     for (int64_t c = 0; c < tot; ++c) W1[c] = val(real(W0[c]) + real(dt) * L[c]);
     if (P->integrator == 1) {
       if (P->relax_mode != 0) relax_grid(f, nc, W1.data());
@@ -1081,7 +1135,7 @@ void or_step(const or_fluid* fl, const or_params* P, const or_grid* g, double* W
       continue;
     }
     if (relax_stage) relax_grid(f, nc, W1.data());
-    rhs_impl(f, P, g, W1.data(), lam, L.data());
+    rhs_impl(f, P, g, W1.data(), lam, L.data(), gate);
     if (P->integrator == 2) {
       // SSP-RK2: W^{n+1} = 1/2 W0 + 1/2 (W1 + dt L(W1))
       for (int64_t c = 0; c < tot; ++c)
@@ -1094,11 +1148,16 @@ void or_step(const or_fluid* fl, const or_params* P, const or_grid* g, double* W
       W2[c] = val(real(0.75) * real(W0[c]) + real(0.25) * (real(W1[c]) + real(dt) * L[c]));
     if (relax_stage) relax_grid(f, nc, W2.data());
     // stage 3: W^{n+1} = 1/3 W0 + 2/3 (W2 + dt L(W2))
-    rhs_impl(f, P, g, W2.data(), lam, L.data());
+    rhs_impl(f, P, g, W2.data(), lam, L.data(), gate);
     for (int64_t c = 0; c < tot; ++c)
       W[c] = val(real(1.0 / 3.0) * real(W0[c]) + real(2.0 / 3.0) * (real(W2[c]) + real(dt) * L[c]));
     if (P->relax_mode != 0) relax_grid(f, nc, W);
   }
+}
+
+void or_step(const or_fluid* fl, const or_params* P, const or_grid* g, double* W, double dt,
+             int nsteps) {
+  or_step_gated(fl, P, g, W, dt, nsteps, nullptr, nullptr, nullptr);
 }
 
 // Admissibility counters (Sec. 2, sets G and script-G): counts[0] cells with a
@@ -1263,6 +1322,86 @@ int64_t or_faces_flops(const or_fluid* fl, const or_params* P, const or_grid* g,
   }
   for (int i = 0; i < 5; ++i) out[i] = acc[i];
   return nl * (n + 1);
+}
+
+// Learned smoothness detector data. For the midpoints idx[0..n) of direction
+// dir (indices over that direction's midpoint grid, n_d + 1 along d, x
+// fastest): feat[30 s ..] the normalised stencil features -- for q in
+// (alpha_1, alpha_2, rho, u_dir, p) over the six nodes i-2 .. i+3,
+// (q_j - mean q) / (max q - min q + 1e-30) evaluated on the differences
+// q_j - q_i, zero where alpha_2 does not exist --
+// and dev[s] = the largest |omega_k - d_k| of the WENO-IS weights (App. C)
+// over both biases and all characteristic fields of the midpoint (App. D).
+void or_stencil_sample(const or_fluid* fl, const or_params* P, const or_grid* g, const double* W,
+                       int dir, int64_t n, const int64_t* idx, double* feat, double* dev) {
+  FluidK f = make_fluid(fl);
+  const int64_t nc = ncells(g);
+  int64_t ext[3] = {1, 1, 1};
+  for (int d = 0; d < g->D; ++d) ext[d] = g->n[d];
+  const int64_t f0 = ext[0] + (dir == 0), f1 = ext[1] + (dir == 1);
+  const double dk[4] = {15.0 / 32.0, 5.0 / 32.0, 5.0 / 16.0, 1.0 / 16.0};
+  for (int64_t s = 0; s < n; ++s) {
+    const int64_t t = idx[s];
+    const int64_t q[3] = {t % f0, (t / f0) % f1, t / (f0 * f1)};
+    Cell nd[6];
+    for (int j = 0; j < 6; ++j) {
+      int64_t r[3] = {q[0], q[1], q[2]};
+      r[dir] = map_index(g, dir, q[dir] - 3 + j);
+      real w[OR_MAXM];
+      load_W(f, W, nc, lin(g, r), w);
+      cell_from_W(f, w, nd[j]);
+    }
+    for (int a = 0; a < 5; ++a) {
+      double v[6];
+      const bool present = a >= 2 || a < f.N - 1;
+      for (int j = 0; j < 6; ++j) {
+        if (!present)
+          v[j] = 0.0;
+        else if (a < 2)
+          v[j] = val(nd[j].V[sAL(f, a)]);
+        else if (a == 2)
+          v[j] = val(nd[j].rho);
+        else if (a == 3)
+          v[j] = val(nd[j].V[sMOM(f, dir)]);
+        else
+          v[j] = val(nd[j].V[sE(f)]);
+      }
+      // differences from node i first, so that a uniform stencil gives exact
+      // zeros (the normalisation is invariant under the shift)
+      double dq[6], mean = 0.0, lo = 0.0, hi = 0.0;
+      for (int j = 0; j < 6; ++j) {
+        dq[j] = v[j] - v[2];
+        mean += dq[j];
+        lo = dq[j] < lo ? dq[j] : lo;
+        hi = dq[j] > hi ? dq[j] : hi;
+      }
+      mean /= 6.0;
+      for (int j = 0; j < 6; ++j) feat[30 * s + 6 * a + j] = (dq[j] - mean) / ((hi - lo) + 1e-30);
+    }
+    real U[6][OR_MAXM], arb[OR_MAXN], rhob, cb;
+    project_stencil(f, dir, nd, U, arb, rhob, cb);
+    double mx = 0.0;
+    for (int m = 0; m < f.M; ++m) {
+      for (int side = 0; side < 2; ++side) {
+        real s5[5];
+        for (int j = 0; j < 5; ++j) s5[j] = side == 0 ? U[j][m] : U[5 - j][m];
+        real om[4];
+        weno_is_left(s5, P->weno_eps, om);
+        for (int k = 0; k < 4; ++k) {
+          const double d = std::fabs(val(om[k]) - dk[k]);
+          if (!(d <= mx)) mx = d;  // NaN propagates
+        }
+      }
+    }
+    dev[s] = mx;
+  }
+}
+
+// Linear-weight interpolation of a left-biased five-point stencil (the gated value).
+double or_weno_lin(const double* u) {
+  real r[5];
+  for (int j = 0; j < 5; ++j) r[j] = u[j];
+  return val(weno_lin_left(r));
 }
 
 double or_tanh(double x) { return tanh_explicit(x); }
