@@ -1,7 +1,10 @@
 """Benchmark: cell-updates/s of the PP-WCNS-IS fractional step on the
 1024 x 512 three-species 2D shock-bubble workload (water, air, helium; SSP-RK3
-with relaxation after every stage, CFL 0.4), FP64 plain, with the FP32-bulk
-form reported beside it at its relative L1 error against FP64.
+with relaxation after every stage, CFL 0.4), FP64 plain, with the other forms
+reported beside it at their relative L1 error against FP64: the FP32-bulk
+form, and the FP32 and FP64 forms with the learned smoothness gate (trained
+first, on the GPU, on stencils of the method's own runs), here and on the
+2048 x 1024 shock-water-column workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -157,11 +160,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def time_steps(torch, s, K, flush, ev_stream):
+def time_steps(torch, s, K, flush, ev_stream, dt=0.0):
     """K single steps, each bracketed by CUDA events on the library's stream,
     with an L2 flush (a write larger than L2) before each. The step graph
     carries an event pair around every kernel (hrm_set_profiling), read after
-    each step. Returns (seconds, {kernel kind: (launches, seconds)})."""
+    each step; dt <= 0: the automatic CFL step. Returns (seconds,
+    {kernel kind: (launches, seconds)})."""
     total = 0.0
     per = {}
     for _ in range(K):
@@ -169,7 +173,7 @@ def time_steps(torch, s, K, flush, ev_stream):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(ev_stream)
-        s.step(0.0, 1)
+        s.step(dt, 1)
         e1.record(ev_stream)
         e1.synchronize()
         total += e0.elapsed_time(e1) * 1e-3
@@ -217,6 +221,110 @@ def measure_batched(torch, hrm, problems, stream, flush, args):
     return out
 
 
+def gated_face_flops(problem, cfl):
+    """Algorithmic flops per midpoint with every midpoint gated to the linear
+    WENO weights (oracle counting build), per direction."""
+    import oracle
+    f, g, W = oracle.setup(problem)
+    dt, _ = oracle.dt(f, g, W, cfl)
+    lam = oracle.lambdas(f, g, W, dt)
+    return [sum(oracle.faces_flops(f, oracle.make_params(), g, W, lam, d, gated=True)[0].values())
+            / oracle.faces_flops(f, oracle.make_params(), g, W, lam, d, gated=True)[1] for d in range(problem.D)]
+
+
+def train_detector(hrm, stream):
+    """The learned smoothness gate, trained on the GPU on stencils of the
+    method's own runs (1D shock tube, 2D shock-bubble 1024x512, 3D interface
+    128^3); returns (detector, report dict)."""
+    from paper_2208_04488_gb300 import learned
+    det, rep = learned.build_detector(scale="full", steps=4000, stream=stream)
+    ev = det.evaluate(0.5, bf16=True)
+    n = max(1, ev["tp"] + ev["fp"] + ev["tn"] + ev["fn"])
+    return det, {"samples": rep.samples, "rough_fraction": rep.rough / max(1, rep.samples),
+                 "per_source": rep.per_source, "collect_s": rep.collect_s, "train_s": rep.train_s,
+                 "adam_steps": rep.steps, "batch": 4096, "delta": 0.01,
+                 "loss_first_last": [float(rep.losses[:20].mean()), float(rep.losses[-200:].mean())],
+                 "train_accuracy_bf16": (ev["tp"] + ev["tn"]) / n,
+                 "train_rough_as_smooth_rate": ev["fp"] / max(1, ev["fp"] + ev["tn"])}
+
+
+def run_form(torch, hrm, pr, precision, det, dt, steps, warmup, flush, stream, threshold=0.5):
+    """One form of the method on a problem: W warm-up steps, restart from the
+    initial condition, then `steps` timed steps of size dt (L2 flushed before
+    each). Returns timing, per-kernel times, gated share, final state."""
+    prm = hrm.params_default(cfl=pr.cfl, check=0, precision=precision)
+    s = hrm.Solver.from_problem(pr, params=prm, stream=stream)
+    if det is not None:
+        s.set_detector(det)
+        s.set_params(hrm.params_default(cfl=pr.cfl, check=0, precision=precision, learned=hrm.LEARNED_GATE,
+                                        learned_threshold=threshold))
+    s.set_profiling(True)
+    for _ in range(warmup):
+        s.step(dt, 1)
+    s.set_primitive(pr.prim)
+    torch.cuda.synchronize()
+    l0 = s.kernel_launches()
+    t, per = time_steps(torch, s, steps, flush, stream, dt)
+    out = {"t": t, "per": per, "launches": s.kernel_launches() - l0, "adm": s.admissibility(),
+           "W": s.get(hrm.FIELD_W)}
+    out["gated"] = (float(np.mean(np.concatenate([s.get_gate(d) for d in range(pr.D)]))) if det is not None
+                    else 0.0)
+    s.close()
+    return out
+
+
+def form_summary(hrm, pr, r, ref_W, steps, face_fl, face_fl_gated, peak, peak_name):
+    """JSON block of one form: throughput, L1 error against plain FP64 after the
+    same equal steps, and the per-midpoint kernel's achieved fraction of the
+    pipe peak (algorithmic flops of the midpoints as gated)."""
+    from paper_2208_04488_gb300.metrics import rel_l1_state
+    kinds = [hrm.KERNEL_FACE_X + d for d in range(pr.D)]
+    n = sum(r["per"][k][0] for k in kinds)
+    tf = sum(r["per"][k][1] for k in kinds)
+    g = r["gated"]
+    fl = sum((g * face_fl_gated[d] + (1 - g) * face_fl[d][0]) * face_fl[d][1] for d in range(pr.D)) / pr.D
+    gate_t = r["per"].get(hrm.KERNEL_GATE, (0, 0.0))
+    l1 = rel_l1_state(r["W"], ref_W, pr.N, pr.D).tolist() if ref_W is not None else None
+    return {"value": pr.ncells * steps / r["t"], "unit": UNIT, "ms_per_step": 1e3 * r["t"] / steps,
+            "gated_share": g,
+            "rel_l1_vs_fp64": None if l1 is None else {"max_over_variables": max(l1), "per_variable": l1},
+            "admissibility_after": r["adm"],
+            "launches_per_step": r["launches"] / steps,
+            "face_kernel": {"avg_launch_ms": 1e3 * tf / n, "achieved_tflops": fl / (tf / n) / 1e12,
+                            "peak_tflops": peak / 1e12, "peak": peak_name, "frac": fl / (tf / n) / peak},
+            "gate_kernel_ms_per_step": 1e3 * gate_t[1] / steps}
+
+
+def measure_learned_workload(torch, hrm, problems, det, stream, flush, args, fp64_peak, fp32_peak):
+    """The learned-detector workload: 2D shock-water column with an SF6 bubble,
+    2048 x 1024 (Sec. 5.7 shape, paper fluids), a problem the detector was not
+    trained on. Plain FP64, FP32, FP32+learned and FP64+learned, equal fixed
+    steps from the initial condition; errors against plain FP64."""
+    from paper_2208_04488_gb300 import learned
+    pr = problems.shock_water_column_2d(2048, 1024)
+    s0 = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, check=0), stream=stream)
+    dt0, _ = s0.dt(pr.cfl)
+    s0.close()
+    dt = 0.8 * dt0
+    K = max(4, args.steps // 2)
+    faces = algorithmic_face_flops(pr, pr.cfl)
+    faces_g = gated_face_flops(pr, pr.cfl)
+    ref = run_form(torch, hrm, pr, hrm.FP64, None, dt, K, args.warmup, flush, stream)
+    out = {"workload": "2D shock-water column + SF6 bubble, 2048x1024, Mach 1.47, paper fluids, CFL 0.5 "
+                       "(0.8 x the initial CFL step, fixed)", "cells": pr.ncells, "steps": K, "dt": dt,
+           "validation_on_this_workload": learned.validation(det, problems.shock_water_column_2d(1024, 512), 100,
+                                                             3, 0.5, stream=stream)}
+    out["fp64"] = form_summary(hrm, pr, ref, None, K, faces, faces_g, fp64_peak, "fp64 fma probe")
+    for name, prec, d in (("fp32", hrm.FP32, None), ("fp32_learned", hrm.FP32, det),
+                          ("fp64_learned", hrm.FP64, det)):
+        r = run_form(torch, hrm, pr, prec, d, dt, K, args.warmup, flush, stream)
+        out[name] = form_summary(hrm, pr, r, ref["W"], K, faces, faces_g,
+                                 fp64_peak if prec == hrm.FP64 else fp32_peak,
+                                 "fp64 fma probe" if prec == hrm.FP64 else "fp32 fma probe")
+    out["speedup_fp32_learned_vs_fp64"] = out["fp32_learned"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -225,6 +333,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
     args = ap.parse_args()
@@ -286,6 +395,15 @@ def main():
     l1_32 = rel_l1_state(Wb, Wa, pr.N, pr.D).tolist()
     del ea, eb, s32
 
+    # learned smoothness gate (rank 0): trained on the GPU on the method's own
+    # stencils, then the gated forms on this workload (same fixed steps as the
+    # error runs above) and on the shock-water-column workload
+    det = learned_runs = None
+    if rank == 0 and not args.no_learned:
+        det, train_rep = train_detector(hrm, stream)
+        learned_runs = {name: run_form(torch, hrm, pr, prec, det, dt0, args.steps, args.warmup, flush, stream)
+                        for name, prec in (("fp32_learned", hrm.FP32), ("fp64_learned", hrm.FP64))}
+
     # batched form: the 64 seeded uneven instances, one persistent launch per phase
     batched = measure_batched(torch, hrm, problems, stream, flush, args) if rank == 0 and not args.no_batch else None
 
@@ -337,6 +455,13 @@ def main():
         ach32 = fl_launch / (tf32 / n32)
         share32 = {hrm.KERNEL_NAMES[k]: round(v[1] / sum(x[1] for x in per32.values()), 4)
                    for k, v in sorted(per32.items())}
+        learned_block = None
+        if learned_runs is not None:
+            faces_g = gated_face_flops(pr, pr.cfl)
+            learned_block = {"detector": train_rep,
+                             "threshold": 0.5,
+                             "shock_water_column": measure_learned_workload(torch, hrm, problems, det, stream, flush,
+                                                                            args, fp64_peak, fp32_peak)}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -372,12 +497,22 @@ def main():
                                       "traffic": TRAFFIC_BYTES["k_face32"]}},
             },
             "batched": batched,
+            "learned": learned_block,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "admissibility_after": adm,
             "peaks": {"fp64_fma_tflops": fp64_peak / 1e12, "fp32_fma_tflops": fp32_peak / 1e12,
                       "hbm_gbs": pk.get("hbm_gbs"), "hbm_source": pk_src},
         }
+        if learned_runs is not None:
+            for name, r in learned_runs.items():
+                prec_peak = fp32_peak if name.startswith("fp32") else fp64_peak
+                line["forms"][name] = form_summary(hrm, pr, r, Wa, args.steps, faces, faces_g, prec_peak,
+                                                   "fp32 fma probe" if name.startswith("fp32") else "fp64 fma probe")
+                line["forms"][name]["description"] = (
+                    "learned smoothness gate (30-32-32-1 MLP, bf16 tensor-core inference) selects the linear "
+                    "WENO weights where it predicts every weight within 0.01 of d_k; limiters always on; "
+                    f"fixed dt = {dt0:.6g} s, errors after {args.steps} steps against plain FP64")
     if dist is not None:
         dist.barrier()
     if rank == 0:

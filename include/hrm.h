@@ -82,13 +82,14 @@ typedef struct {
   int32_t scheme;      /* HRM_SCHEME_* */
   int32_t integrator;  /* HRM_RK3 / HRM_EULER / HRM_RK2 */
   int32_t precision;   /* HRM_FP64 / HRM_FP32 */
-  int32_t learned;     /* 1: MLP smoothness gate before the WENO weights */
+  int32_t learned;     /* 0 off; 1 learned gate (needs hrm_set_detector); 2 fixed gate
+                          (needs hrm_set_gate for every direction) -- see below */
   int32_t check;       /* 1: hrm_step synchronises and reports admissibility */
   double eps_ar, eps_a, eps_rhoe;      /* limiter thresholds 1e-10, 1e-10, 1e-8 */
   double hs_ar, hs_a, hs_rc2, hs_rhoe; /* hard switches 1e-11, 1e-11, 1e-9, 1e-9 */
   double weno_eps;                     /* 1e-15 (App. C) */
   double Cs, q_sensor;                 /* shock sensor 1e12 and 2 (Sec. 4.3.1) */
-  double learned_threshold;            /* gate probability above which d_k are used */
+  double learned_threshold;            /* gate probability in (0, 1) above which d_k are used */
 } hrm_params;
 
 /* Field selectors of hrm_get. */
@@ -175,7 +176,8 @@ enum {
   HRM_KERNEL_PRIM = 0,      /* per-cell primitives (+ CFL reduction at the first stage) */
   HRM_KERNEL_FINALIZE = 1,  /* dt, sigma_d, lambda_d */
   HRM_KERNEL_FACE_X = 2,    /* per-midpoint sweep in x (HRM_KERNEL_FACE_X + d for direction d) */
-  HRM_KERNEL_UPDATE = 5     /* flux difference, RK combination, relaxation */
+  HRM_KERNEL_UPDATE = 5,    /* flux difference, RK combination, relaxation */
+  HRM_KERNEL_GATE = 6       /* learned smoothness gate of one direction */
 };
 
 /* Tracing: with on != 0 the step graph is (re)captured with a CUDA event pair
@@ -186,6 +188,87 @@ hrm_status hrm_set_profiling(hrm_ctx* ctx, int32_t on);
  * kernels of the last step in launch order, their device time in ms and their
  * kind (HRM_KERNEL_*). Returns how many were written (at most max). */
 int32_t hrm_profile_read(hrm_ctx* ctx, int32_t max, float* ms, int32_t* kind);
+
+/* ------------------------------------------------------------------------
+ * Learned smoothness gate (not a part of the paper's method: an optional
+ * acceleration of its WENO-IS interpolation, App. C).
+ *
+ * Per midpoint x_{i+1/2} and direction, a multilayer perceptron reads the
+ * six-node stencil i-2 .. i+3 -- for q in (alpha_1, alpha_2, rho, u_n, p) the
+ * normalised shape (q_j - mean q) / (max q - min q + 1e-30), formed on the
+ * differences q_j - q_i, zero for an absent alpha_2: 30 inputs -- through
+ * 32 and 32 ReLU units to one logit. Where sigmoid(logit) > learned_threshold
+ * the midpoint is gated: both biased interpolations of every characteristic
+ * field use the linear weights d_k instead of the WENO-IS weights; the
+ * characteristic projection (App. D), both positivity limiters (Sec. 4.3.2),
+ * the Riemann solves, HCS and blending are unchanged. Inference: bfloat16
+ * inputs and weights, FP32 accumulation on the tensor cores.
+ *
+ * Training data come from states the method produces: the label of a midpoint
+ * is 1 when every WENO-IS weight of every characteristic field and both biases
+ * lies within delta of its linear weight d_k (FP64), else 0.
+ *
+ * Parameter vector (2081 floats): W1[30][32], b1[32], W2[32][32], b2[32],
+ * w3[32], b3 with h1 = relu(x W1 + b1), h2 = relu(h1 W2 + b2),
+ * logit = h2 . w3 + b3. Loss: binary cross-entropy, batch mean; Adam
+ * (beta 0.9, 0.999, eps 1e-8).
+ * ------------------------------------------------------------------------ */
+typedef struct hrm_detector hrm_detector; /* opaque: weights, Adam state, samples */
+
+#define HRM_DETECTOR_PARAMS 2081
+#define HRM_DETECTOR_INPUTS 30
+
+/* capacity: samples the detector can hold (each 136 B of device memory);
+ * seed: initial weights (He-uniform) and the sample draws. stream: nullable.
+ * Errors: HRM_E_INVAL (capacity outside 0..2^31), HRM_E_NOMEM, HRM_E_CUDA. */
+hrm_status hrm_detector_create(hrm_detector** out, int64_t capacity, uint64_t seed, void* stream);
+void hrm_detector_destroy(hrm_detector* det);
+const char* hrm_detector_last_error(const hrm_detector* det);
+/* Host arrays of HRM_DETECTOR_PARAMS floats; set_weights also resets Adam. */
+hrm_status hrm_detector_set_weights(hrm_detector* det, const float* theta);
+hrm_status hrm_detector_get_weights(hrm_detector* det, float* theta);
+int64_t hrm_detector_size(const hrm_detector* det);
+hrm_status hrm_detector_clear(hrm_detector* det);
+/* Append samples: X host [n][30], y host [n] (labels 0/1). INVAL beyond capacity. */
+hrm_status hrm_detector_add_samples(hrm_detector* det, const float* X, const float* y, int64_t n);
+/* Read samples [first, first+n) into host arrays (each nullable): X [n][30],
+ * y [n], dev [n] (the weight deviation of collected samples, 0 for added ones). */
+hrm_status hrm_detector_samples(hrm_detector* det, int64_t first, int64_t n, float* X, float* y, float* dev);
+/* Append samples from every midpoint of every direction of ctx's current
+ * state (runs its primitive kernel): label 1 when the deviation is below
+ * delta. Each midpoint is kept with probability keep_rough (label 0),
+ * keep_flat (label 1, all features zero) or keep_smooth (other label 1),
+ * drawn from a hash of (seed, call, direction, midpoint); kept midpoints are
+ * stored in index order; beyond the capacity they are dropped. *added: count. */
+hrm_status hrm_detector_collect(hrm_detector* det, hrm_ctx* ctx, double delta, double keep_rough,
+                                double keep_smooth, double keep_flat, int64_t* added);
+/* Summed loss and its gradient (host [2081]) at the current weights over
+ * samples [first, first+n), FP32 training arithmetic. */
+hrm_status hrm_detector_gradient(hrm_detector* det, int64_t first, int64_t n, float* grad, double* loss);
+/* steps Adam steps with learning rate lr on batches of `batch` samples drawn
+ * with replacement (batch <= 0 or >= size: the whole set, in order, every
+ * step); loss_per_step (host, nullable): the batch-mean loss before each step. */
+hrm_status hrm_detector_train(hrm_detector* det, int32_t steps, int32_t batch, double lr, float* loss_per_step);
+/* Logits of samples [first, first+n) into host z: bf16 = 1 the inference
+ * (tensor-core) arithmetic, 0 the FP32 training arithmetic. */
+hrm_status hrm_detector_logits(hrm_detector* det, int64_t first, int64_t n, int32_t bf16, float* z);
+/* Over all samples at probability threshold: counts = {gated & smooth,
+ * gated & not smooth, not gated & not smooth, not gated & smooth}; *loss = mean
+ * cross-entropy. */
+hrm_status hrm_detector_evaluate(hrm_detector* det, double threshold, int32_t bf16, int64_t counts[4],
+                                 double* loss);
+
+/* Copy det's current inference weights into ctx (a snapshot; det may be
+ * destroyed afterwards) and allocate its gate buffers; then params.learned = 1
+ * is accepted. The gate runs once per direction and stage, on the FP32 planes
+ * that the primitive kernel then also writes in the FP64 form. */
+hrm_status hrm_set_detector(hrm_ctx* ctx, const hrm_detector* det);
+/* Fixed gate of direction dir (host, one byte per midpoint over the midpoint
+ * grid of dir: n_d + 1 along d, x fastest; nonzero = gated), used at every
+ * stage while params.learned = 2. */
+hrm_status hrm_set_gate(hrm_ctx* ctx, int32_t dir, const uint8_t* gate);
+/* The gate bytes last used in direction dir (host, same layout). */
+hrm_status hrm_get_gate(hrm_ctx* ctx, int32_t dir, uint8_t* gate);
 
 /* Diagnostic, not a step of the method: measured FMA-pipe throughput of the
  * current device in flop/s (2 flops per FMA) for HRM_FP64 or HRM_FP32, from

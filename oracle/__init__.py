@@ -117,6 +117,9 @@ def lib(count: bool = False):
         L.or_tanh.restype = ctypes.c_double
         L.or_faces_flops.argtypes = [P(Fluid), P(Params), P(Grid), _DP, _DP, ctypes.c_int, _DP]
         L.or_faces_flops.restype = ctypes.c_int64
+        L.or_faces_flops_gated.argtypes = [P(Fluid), P(Params), P(Grid), _DP, _DP, ctypes.c_int, ctypes.c_int,
+                                           _DP]
+        L.or_faces_flops_gated.restype = ctypes.c_int64
         if count:
             L.or_count_reset.argtypes = []
             L.or_count_get.argtypes = [P(ctypes.c_ulonglong)]
@@ -351,14 +354,15 @@ def setup(problem):
     return f, g, ic_from_prim(f, problem.prim)
 
 
-def faces_flops(f: Fluid, p: Params, g: Grid, W, lam, dir_):
+def faces_flops(f: Fluid, p: Params, g: Grid, W, lam, dir_, gated=False):
     """Algorithmic operation counts of the midpoint computations of one
-    direction (counting build): (counts dict, number of faces)."""
+    direction (counting build): (counts dict, number of faces). gated: every
+    midpoint with the linear WENO weights."""
     W = np.ascontiguousarray(W, dtype=np.float64)
     lam = np.ascontiguousarray(np.resize(np.asarray(lam, dtype=np.float64), 3))
     out = np.zeros(5)
-    nf = lib(True).or_faces_flops(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), _ptr(lam),
-                                  dir_, _ptr(out))
+    nf = lib(True).or_faces_flops_gated(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), _ptr(lam),
+                                        dir_, 1 if gated else 0, _ptr(out))
     return dict(zip(["add", "mul", "div", "sqrt", "tanh"], out.tolist())), nf
 
 

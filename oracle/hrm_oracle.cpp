@@ -1285,8 +1285,10 @@ void or_ic_from_prim(const or_fluid* fl, int64_t nc, const double* prim, double*
 // limiter) over every face of direction `dir`; the primitive variables of the
 // node cells are computed outside the counted region. out[0..4] = add, mul, div,
 // sqrt, tanh; returns the number of faces. Zero counts in the normal build.
-int64_t or_faces_flops(const or_fluid* fl, const or_params* P, const or_grid* g, const double* W,
-                       const double* lam, int dir, double* out) {
+// gated: every midpoint gated to the linear WENO weights (the operation count
+// of a gated midpoint).
+int64_t or_faces_flops_gated(const or_fluid* fl, const or_params* P, const or_grid* g, const double* W,
+                             const double* lam, int dir, int gated, double* out) {
   FluidK f = make_fluid(fl);
   const int M = f.M;
   const int64_t nc = ncells(g), n = g->n[dir], nl = nc / n;
@@ -1311,7 +1313,8 @@ int64_t or_faces_flops(const or_fluid* fl, const or_params* P, const or_grid* g,
 #ifdef OR_COUNT
     OrCounts before = g_cnt;
 #endif
-    for (int64_t fc = 0; fc <= n; ++fc) face_flux(f, P, dir, real(lam[dir]), &line[fc], Gm.data(), Gp.data(), nullptr);
+    for (int64_t fc = 0; fc <= n; ++fc)
+      face_flux(f, P, dir, real(lam[dir]), &line[fc], Gm.data(), Gp.data(), nullptr, gated);
 #ifdef OR_COUNT
     acc[0] += (double)(g_cnt.add - before.add);
     acc[1] += (double)(g_cnt.mul - before.mul);
@@ -1322,6 +1325,11 @@ int64_t or_faces_flops(const or_fluid* fl, const or_params* P, const or_grid* g,
   }
   for (int i = 0; i < 5; ++i) out[i] = acc[i];
   return nl * (n + 1);
+}
+
+int64_t or_faces_flops(const or_fluid* fl, const or_params* P, const or_grid* g, const double* W,
+                       const double* lam, int dir, double* out) {
+  return or_faces_flops_gated(fl, P, g, W, lam, dir, 0, out);
 }
 
 // Learned smoothness detector data. For the midpoints idx[0..n) of direction

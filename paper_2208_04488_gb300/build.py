@@ -34,6 +34,8 @@ UNITS = {
     "hrm_batch64_d2.cu": ["--fmad=false"],
     "hrm_batch32_d2.cu": [],
     "hrm_batch_api.cu": [],
+    "hrm_learned.cu": [],
+    "hrm_learned_data.cu": ["--fmad=false"],
 }
 
 

@@ -11,6 +11,7 @@
 
 #include "../../include/hrm.h"
 #include "hrm_launch.h"
+#include "hrm_learned.h"
 
 using namespace hrm;
 
@@ -33,8 +34,13 @@ struct hrm_ctx {
   double* V = nullptr;             // primitive planes (M) -- also scratch for I/O
   double* AUX = nullptr;           // c, rho, rho c^2
   float* P32 = nullptr;            // FP32 planes of the precision form (M + D + 4 + N - 1)
+  float* R32 = nullptr;            // FP32 residues of rho, u_d, p for the learned gate (D + 2)
   double* F[3] = {nullptr, nullptr, nullptr};  // midpoint fluxes per direction (M + N - 1 planes)
   StepState* st = nullptr;
+  mlp::GateBlob* blob = nullptr;   // learned gate weights (hrm_set_detector)
+  uint8_t* gate[3] = {nullptr, nullptr, nullptr};  // gate bytes per direction (midpoint grids)
+  int gate_set[3] = {0, 0, 0};     // fixed gate provided (hrm_set_gate)
+  int gate_blocks = 0;             // persistent blocks of the gate kernel
   const CellKernels* ck = nullptr;
   const FaceKernels* fk = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -81,7 +87,15 @@ hrm_status check_params(hrm_ctx* c, const hrm_params* p) {
   if (p->relax_mode < 0 || p->relax_mode > 2) return fail(c, HRM_E_INVAL, "unknown relax_mode %d", p->relax_mode);
   if (p->integrator < 0 || p->integrator > 2) return fail(c, HRM_E_INVAL, "unknown integrator %d", p->integrator);
   if (p->precision < 0 || p->precision > 1) return fail(c, HRM_E_INVAL, "unknown precision %d", p->precision);
-  if (p->learned) return fail(c, HRM_E_INVAL, "learned gate not loaded on this context");
+  if (p->learned < 0 || p->learned > 2) return fail(c, HRM_E_INVAL, "unknown learned mode %d", p->learned);
+  if (p->learned && !(p->learned_threshold > 0.0 && p->learned_threshold < 1.0))
+    return fail(c, HRM_E_INVAL, "learned_threshold must lie in (0, 1)");
+  if (p->learned == 1 && !c->blob) return fail(c, HRM_E_INVAL, "learned gate: call hrm_set_detector first");
+  if (p->learned == 2)
+    for (int d = 0; d < c->D; ++d)
+      if (!c->gate_set[d]) return fail(c, HRM_E_INVAL, "fixed gate: call hrm_set_gate for direction %d", d);
+  if (p->learned && p->scheme != HRM_SCHEME_WCNS)
+    return fail(c, HRM_E_INVAL, "the gate acts on the WENO-IS interpolation (scheme WCNS only)");
   if (p->q_sensor < 1.0 || p->q_sensor != std::floor(p->q_sensor))
     return fail(c, HRM_E_INVAL, "q_sensor must be a positive integer");
   return HRM_OK;
@@ -126,21 +140,44 @@ void traced(hrm_ctx* c, cudaStream_t s, int kind, F&& launch) {
   }
 }
 
-// One RK stage: primitives of Wsrc, midpoint fluxes, update into Wout.
+float gate_logit_threshold(const hrm_ctx* c) {
+  const double t = c->params.learned_threshold;
+  return (float)std::log(t / (1.0 - t));
+}
+
+// FP32 planes are written by the primitive kernel in the precision form and
+// whenever the learned gate reads them.
+float* p32_target(hrm_ctx* c) {
+  return (c->params.precision == HRM_FP32 || c->params.learned == 1) ? c->P32 : nullptr;
+}
+
+float* r32_target(hrm_ctx* c) { return c->params.learned == 1 ? c->R32 : nullptr; }
+
+const uint8_t* gate_of(const hrm_ctx* c, int d) { return c->params.learned ? c->gate[d] : nullptr; }
+
+// One RK stage: primitives of Wsrc, (gates,) midpoint fluxes, update into Wout.
 int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, double a, double b, int relax,
                   int count, bool first) {
   int k = 0;
-  float* p32 = c->params.precision == HRM_FP32 ? c->P32 : nullptr;
+  float* p32 = p32_target(c);
   traced(c, s, HRM_KERNEL_PRIM,
-         [&] { c->ck->prim(Wsrc, c->V, c->AUX, p32, c->dg, c->fl, c->st, first ? 1 : 0, s); });
+         [&] { c->ck->prim(Wsrc, c->V, c->AUX, p32, r32_target(c), c->dg, c->fl, c->st, first ? 1 : 0, s); });
   ++k;
   if (first) {
     traced(c, s, HRM_KERNEL_FINALIZE, [&] { launch_finalize(c->st, c->dg, c->D, c->params.cfl, 0, s); });
     ++k;
   }
   for (int d = 0; d < c->D; ++d) {
+    if (c->params.learned == 1) {
+      traced(c, s, HRM_KERNEL_GATE, [&] {
+        launch_gate(c->N, c->D, d, c->P32, c->R32, c->dg, c->blob, gate_logit_threshold(c), c->gate[d],
+                    c->gate_blocks, s);
+      });
+      ++k;
+    }
     traced(c, s, HRM_KERNEL_FACE_X + d, [&] {
-      c->fk->face[d](c->params.precision, Wsrc, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st, s);
+      c->fk->face[d](c->params.precision, Wsrc, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st,
+                     gate_of(c, d), s);
     });
     ++k;
   }
@@ -315,6 +352,8 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
   if ((s = cuda_check(c, cudaMalloc(&c->AUX, plane * 3), "alloc aux"))) return bail(s);
   if ((s = cuda_check(c, cudaMalloc(&c->P32, sizeof(float) * (size_t)c->nc * (M + D + 4 + N - 1)), "alloc fp32 planes")))
     return bail(s);
+  if ((s = cuda_check(c, cudaMalloc(&c->R32, sizeof(float) * (size_t)c->nc * (D + 2)), "alloc fp32 residues")))
+    return bail(s);
   for (int d = 0; d < D; ++d) {
     size_t nf = 1;
     for (int e = 0; e < 3; ++e) nf *= (size_t)(c->dg.n[e] + (e == d));
@@ -337,8 +376,11 @@ void hrm_destroy(hrm_ctx* c) {
   cudaFree(c->V);
   cudaFree(c->AUX);
   cudaFree(c->P32);
+  cudaFree(c->R32);
   for (int d = 0; d < 3; ++d) cudaFree(c->F[d]);
   cudaFree(c->st);
+  cudaFree(c->blob);
+  for (int d = 0; d < 3; ++d) cudaFree(c->gate[d]);
   for (int i = 0; i < 2 * kMaxProf; ++i)
     if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -414,7 +456,7 @@ hrm_status hrm_set_primitive(hrm_ctx* c, const double* prim, int32_t on_device) 
 
 hrm_status hrm_dt(hrm_ctx* c, double cfl, double* dt_out, double* tau_out) {
   if (!c || !(cfl > 0.0)) return c ? fail(c, HRM_E_INVAL, "cfl must be positive") : HRM_E_INVAL;
-  c->ck->prim(c->Wn, c->V, c->AUX, nullptr, c->dg, c->fl, c->st, 1, c->stream);
+  c->ck->prim(c->Wn, c->V, c->AUX, nullptr, nullptr, c->dg, c->fl, c->st, 1, c->stream);
   launch_finalize(c->st, c->dg, c->D, cfl, 1, c->stream);
   c->launches += 2;
   StepState h;
@@ -468,11 +510,16 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
   hrm_status s = cuda_check(c, cudaMemcpyAsync(c->st->lam, l3, sizeof l3, cudaMemcpyHostToDevice, c->stream),
                             "copy lambda");
   if (s) return s;
-  c->ck->prim(c->Wn, c->V, c->AUX, c->params.precision == HRM_FP32 ? c->P32 : nullptr, c->dg, c->fl, c->st, 0,
-              c->stream);
-  for (int d = 0; d < c->D; ++d)
+  c->ck->prim(c->Wn, c->V, c->AUX, p32_target(c), r32_target(c), c->dg, c->fl, c->st, 0, c->stream);
+  for (int d = 0; d < c->D; ++d) {
+    if (c->params.learned == 1) {
+      launch_gate(c->N, c->D, d, c->P32, c->R32, c->dg, c->blob, gate_logit_threshold(c), c->gate[d],
+                  c->gate_blocks, c->stream);
+      ++c->launches;
+    }
     c->fk->face[d](c->params.precision, c->Wn, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st,
-                   c->stream);
+                   gate_of(c, d), c->stream);
+  }
   c->fk->update(1, 0, c->Wn, c->Wn, rhs, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, 0.0, 1.0, 0, 0,
                 c->stream);
   c->launches += 2 + c->D;
@@ -545,8 +592,93 @@ int64_t hrm_kernel_launches(const hrm_ctx* c) { return c ? c->launches : 0; }
 
 }  // extern "C"
 
+namespace {
+size_t gate_bytes(const hrm_ctx* c, int d) { return (size_t)face_total(c->dg, d); }
+
+hrm_status ensure_gates(hrm_ctx* c) {
+  for (int d = 0; d < c->D; ++d) {
+    if (c->gate[d]) continue;
+    hrm_status s = cuda_check(c, cudaMalloc(&c->gate[d], gate_bytes(c, d)), "alloc gate");
+    if (s) return s;
+    cudaMemsetAsync(c->gate[d], 0, gate_bytes(c, d), c->stream);
+  }
+  return HRM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+hrm_status hrm_set_detector(hrm_ctx* c, const hrm_detector* det) {
+  if (!c || !det || !detector_blob(det)) return c ? fail(c, HRM_E_INVAL, "null detector") : HRM_E_INVAL;
+  hrm_status s;
+  if (!c->blob && (s = cuda_check(c, cudaMalloc(&c->blob, sizeof(mlp::GateBlob)), "alloc gate weights")))
+    return s;
+  if ((s = ensure_gates(c))) return s;
+  // the detector's weights are final once its own stream has drained
+  if ((s = cuda_check(c, cudaDeviceSynchronize(), "detector sync"))) return s;
+  if ((s = cuda_check(c,
+                      cudaMemcpyAsync(c->blob, detector_blob(det), sizeof(mlp::GateBlob), cudaMemcpyDeviceToDevice,
+                                      c->stream),
+                      "copy gate weights")))
+    return s;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  c->gate_blocks = (sms > 0 ? sms : 1) * 8;
+  drop_graph(c);
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "set detector");
+}
+
+hrm_status hrm_set_gate(hrm_ctx* c, int32_t dir, const uint8_t* gate) {
+  if (!c || !gate) return HRM_E_INVAL;
+  if (dir < 0 || dir >= c->D) return fail(c, HRM_E_INVAL, "direction %d outside 0..%d", dir, c->D - 1);
+  hrm_status s;
+  if ((s = ensure_gates(c))) return s;
+  if ((s = cuda_check(c, cudaMemcpyAsync(c->gate[dir], gate, gate_bytes(c, dir), cudaMemcpyHostToDevice, c->stream),
+                      "copy gate")))
+    return s;
+  c->gate_set[dir] = 1;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "set gate");
+}
+
+hrm_status hrm_get_gate(hrm_ctx* c, int32_t dir, uint8_t* gate) {
+  if (!c || !gate) return HRM_E_INVAL;
+  if (dir < 0 || dir >= c->D) return fail(c, HRM_E_INVAL, "direction %d outside 0..%d", dir, c->D - 1);
+  if (!c->gate[dir]) return fail(c, HRM_E_INVAL, "no gate on this context");
+  hrm_status s = cuda_check(
+      c, cudaMemcpyAsync(gate, c->gate[dir], gate_bytes(c, dir), cudaMemcpyDeviceToHost, c->stream), "read gate");
+  if (s) return s;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "get gate");
+}
+
+}  // extern "C"
+
 namespace hrm {
 void set_thread_error(const char* msg) { g_create_error = msg; }
+
+hrm_status ctx_view(hrm_ctx* c, CtxView* v) {
+  if (!c || !v) return HRM_E_INVAL;
+  v->N = c->N;
+  v->D = c->D;
+  v->M = c->M;
+  v->nc = c->nc;
+  v->dg = c->dg;
+  v->fl = c->fl;
+  v->dp = c->dp;
+  v->Wn = c->Wn;
+  v->V = c->V;
+  v->AUX = c->AUX;
+  v->P32 = c->P32;
+  v->R32 = c->R32;
+  v->st = c->st;
+  v->ck = c->ck;
+  v->stream = c->stream;
+  return HRM_OK;
+}
+
+void ctx_add_launches(hrm_ctx* c, int64_t n) {
+  if (c) c->launches += n;
+}
 
 const FaceKernels* face_kernels(int N, int D) {
   if (D == 1) return face_kernels_d1(N);

@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
     for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
       double sc[D];
       if (I.N == 2)
-        prim_body<2, D>(c, W, I.V, I.AUX, P32, I.g, I.f, sc);
+        prim_body<2, D>(c, W, I.V, I.AUX, P32, nullptr, I.g, I.f, sc);
       else
-        prim_body<3, D>(c, W, I.V, I.AUX, P32, I.g, I.f, sc);
+        prim_body<3, D>(c, W, I.V, I.AUX, P32, nullptr, I.g, I.f, sc);
 #pragma unroll
       for (int d = 0; d < D; ++d) s[d] = (sc[d] != sc[d]) ? sc[d] : (sc[d] > s[d] ? sc[d] : s[d]);
     }

@@ -36,9 +36,9 @@ __global__ void k_set_dt(StepState* st, double dt_req) {
 namespace {
 
 template <int N, int D>
-void prim_l(const double* W, double* V, double* AUX, float* P32, const DevGrid& g, const DevFluid& f, StepState* st,
-            int tau, cudaStream_t s) {
-  k_prim<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, V, AUX, P32, g, f, st, tau);
+void prim_l(const double* W, double* V, double* AUX, float* P32, float* R32, const DevGrid& g, const DevFluid& f,
+            StepState* st, int tau, cudaStream_t s) {
+  k_prim<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, V, AUX, P32, R32, g, f, st, tau);
 }
 template <int N, int D>
 void ic_l(const double* prim, double* W, const DevGrid& g, const DevFluid& f, cudaStream_t s) {

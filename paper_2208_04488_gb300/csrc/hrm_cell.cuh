@@ -42,11 +42,13 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
 // Per cell: V (M planes), AUX = (c, rho, rho c^2). With `tau`, also the running
 // maxima tau_d = max(|u_d| + c)/dx_d (Sec. 4.1.2): warp shuffles, then one
 // atomicMax per block and direction on the order-preserving bits.
-// One cell c < ncells: primitives, AUX, optional FP32 planes; s[d] = (|u_d| + c)/dx_d.
+// One cell c < ncells: primitives, AUX, optional FP32 planes and, for the
+// learned gate, the FP32 rounding residues of rho, u_d and p (R32, D + 2
+// planes: rho, u_0 .. u_{D-1}, p); s[d] = (|u_d| + c)/dx_d.
 template <int N, int D>
 __device__ __forceinline__ void prim_body(int64_t c, const double* __restrict__ W, double* __restrict__ V,
-                                          double* __restrict__ AUX, float* __restrict__ P32, const DevGrid& g,
-                                          const DevFluid& f, double* s) {
+                                          double* __restrict__ AUX, float* __restrict__ P32,
+                                          float* __restrict__ R32, const DevGrid& g, const DevFluid& f, double* s) {
   using L = Lay<N, D>;
   constexpr int M = L::M;
   const int64_t nc = g.ncells;
@@ -75,6 +77,15 @@ __device__ __forceinline__ void prim_body(int64_t c, const double* __restrict__ 
         const double a = w[L::AL + k];
         P32[(M + 4 + D + k) * nc + c] = (float)(a - (double)(float)a);  // rounding residue
       }
+    }
+    if (R32) {
+      R32[c] = (float)(rho - (double)(float)rho);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const double u = v[L::MOM + d];
+        R32[(1 + d) * nc + c] = (float)(u - (double)(float)u);
+      }
+      R32[(1 + D) * nc + c] = (float)(v[L::EN] - (double)(float)v[L::EN]);
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) s[d] = (fabs(v[L::MOM + d]) + cs) / g.dx[d];
@@ -111,12 +122,12 @@ __device__ __forceinline__ void block_tau_max(const double* s, unsigned long lon
 template <int N, int D>
 __global__ void __launch_bounds__(kCellThreads)
     k_prim(const double* __restrict__ W, double* __restrict__ V, double* __restrict__ AUX,
-           float* __restrict__ P32, DevGrid g, DevFluid f, StepState* st, int tau) {
+           float* __restrict__ P32, float* __restrict__ R32, DevGrid g, DevFluid f, StepState* st, int tau) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double s[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) s[d] = 0.0;
-  if (c < g.ncells) prim_body<N, D>(c, W, V, AUX, P32, g, f, s);
+  if (c < g.ncells) prim_body<N, D>(c, W, V, AUX, P32, R32, g, f, s);
   if (!tau) return;
   block_tau_max<D>(s, st->tau_bits);
 }

@@ -171,6 +171,60 @@ __device__ __forceinline__ R weno_is(R um2, R um1, R u0, R up1, R up2, R eps) {
   return (e0 / es) * s0 + (e1 / es) * s1 + (e2 / es) * s2 + (e3 / es) * s3;
 }
 
+// The same interpolation with every nonlinear weight replaced by its linear
+// weight d_k (the value a smoothness gate selects): sum_k d_k S_k, evaluated
+// in the order written so that the FP64 units reproduce it bit for bit.
+template <typename R>
+__device__ __forceinline__ R weno_lin(R um2, R um1, R u0, R up1, R up2) {
+  const R s0 = R(0.5) * (u0 + up1);
+  const R s1 = R(0.5) * (R(3) * u0 - um1);
+  const R s2 = R(0.125) * (R(3) * u0 + R(6) * up1 - up2);
+  const R s3 = R(0.125) * (R(3) * um2 - R(10) * um1 + R(15) * u0);
+  return R(15.0 / 32.0) * s0 + R(5.0 / 32.0) * s1 + R(5.0 / 16.0) * s2 + R(1.0 / 16.0) * s3;
+}
+
+template <typename R>
+__device__ __forceinline__ R weno_sel(bool lin, R um2, R um1, R u0, R up1, R up2, R eps) {
+  return lin ? weno_lin<R>(um2, um1, u0, up1, up2) : weno_is<R>(um2, um1, u0, up1, up2, eps);
+}
+
+// Largest |omega_k - d_k| of the WENO-IS weights of one stencil (App. C): the
+// smoothness label of the learned gate. NaN propagates.
+template <typename R>
+__device__ __forceinline__ R weno_dev(R um2, R um1, R u0, R up1, R up2, R eps) {
+  const R c13_12 = R(13.0 / 12.0);
+  R t;
+  const R b0 = (u0 - up1) * (u0 - up1);
+  const R b1 = (um1 - u0) * (um1 - u0);
+  t = um1 - R(2) * u0 + up1;
+  const R t01 = um1 - up1;
+  const R b01 = c13_12 * t * t + R(0.25) * t01 * t01;
+  t = u0 - R(2) * up1 + up2;
+  R tt = R(3) * u0 - R(4) * up1 + up2;
+  const R b2 = c13_12 * t * t + R(0.25) * tt * tt;
+  t = um2 - R(2) * um1 + u0;
+  tt = um2 - R(4) * um1 + R(3) * u0;
+  const R b3 = c13_12 * t * t + R(0.25) * tt * tt;
+  t = up2 - R(4) * up1 + R(6) * u0 - R(4) * um1 + um2;
+  tt = up2 - R(2) * up1 + R(2) * um1 - um2;
+  const R tau5 = c13_12 * t * t + R(0.25) * tt * tt;
+  const R q01 = tau5 / (b01 + eps);
+  const R e0 = R(15.0 / 32.0) * (R(1) + (tau5 / (b0 + eps)) * q01);
+  const R e1 = R(5.0 / 32.0) * (R(1) + (tau5 / (b1 + eps)) * q01);
+  const R e2 = R(5.0 / 16.0) * (R(1) + tau5 / (b2 + eps));
+  const R e3 = R(1.0 / 16.0) * (R(1) + tau5 / (b3 + eps));
+  const R es = e0 + e1 + e2 + e3;
+  const R dv[4] = {e0 / es - R(15.0 / 32.0), e1 / es - R(5.0 / 32.0), e2 / es - R(5.0 / 16.0),
+                   e3 / es - R(1.0 / 16.0)};
+  R mx = R(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const R d = dv[k] < R(0) ? -dv[k] : dv[k];
+    if (!(d <= mx)) mx = d;
+  }
+  return mx;
+}
+
 // ---------------------------------------------------------------- HLLC (Sec. 4.1.1)
 
 // Conservative vector, total energy and sound speed of a primitive state.

@@ -29,8 +29,16 @@ struct P32Lay {
 // would leave the normal float range (1/s = inf for subnormal s).
 constexpr float kTinyRange = 1e-30f;
 
-__device__ __forceinline__ float weno_is_scaled(float um2, float um1, float u0, float up1, float up2, float eps) {
+// Linear-weight (gated) interpolation on the differences from the central value:
+// sum_k d_k S_k = u_0 + (3 a - 20 b + 60 d - 5 e) / 128.
+__device__ __forceinline__ float lin_increment(float a, float b, float d, float e) {
+  return (3.f * a - 20.f * b + 60.f * d - 5.f * e) * (1.f / 128.f);
+}
+
+__device__ __forceinline__ float weno_is_scaled(float um2, float um1, float u0, float up1, float up2, float eps,
+                                                bool lin = false) {
   float a = um2 - u0, b = um1 - u0, d = up1 - u0, e = up2 - u0;
+  if (lin) return u0 + lin_increment(a, b, d, e);
   const float s = fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(d), fabsf(e)));
   if (!(s > kTinyRange)) return u0;
   const float inv = 1.f / s;
@@ -44,7 +52,8 @@ __device__ __forceinline__ float weno_is_scaled(float um2, float um1, float u0, 
 
 // WENO-IS increment from already-formed differences (u_j - u_0) of a stencil
 // whose central value is the reference (left-biased order um2, um1, up1, up2).
-__device__ __forceinline__ float weno_increment(float a, float b, float d, float e, float eps) {
+__device__ __forceinline__ float weno_increment(float a, float b, float d, float e, float eps, bool lin = false) {
+  if (lin) return lin_increment(a, b, d, e);
   const float s = fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(d), fabsf(e)));
   if (!(s > kTinyRange)) return 0.f;
   const float inv = 1.f / s;
@@ -127,7 +136,8 @@ template <int N, int D, int DIR>
 __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const double* __restrict__ W,
                                             const double* __restrict__ V, const double* __restrict__ AUX,
                                             const float* __restrict__ P32, double* __restrict__ out,
-                                            const DevGrid& g, const DevFluid& f, const DevParams& pr, double lam) {
+                                            const DevGrid& g, const DevFluid& f, const DevParams& pr, double lam,
+                                            bool lin = false) {
   using L = Lay<N, D>;
   using Q = P32Lay<N, D>;
   constexpr int M = L::M;
@@ -184,12 +194,12 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
     float UL[M], UR[M], w6[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) w6[j] = u6[j] - inv_rc * p6[j];
-    UL[0] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-    UR[0] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+    UL[0] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
+    UR[0] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
 #pragma unroll
     for (int j = 0; j < 6; ++j) w6[j] = u6[j] + inv_rc * p6[j];
-    UL[M - 1] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-    UR[M - 1] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+    UL[M - 1] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
+    UR[M - 1] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
     float arb[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -199,8 +209,8 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
       const float coef = arb[k] / rc2b;
 #pragma unroll
       for (int j = 0; j < 6; ++j) w6[j] = w6[j] - coef * p6[j];
-      UL[1 + k] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-      UR[1 + k] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+      UL[1 + k] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
+      UR[1 + k] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
     }
     {
       int t_ = 0;
@@ -209,8 +219,8 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
         if (d == DIR) continue;
 #pragma unroll
         for (int j = 0; j < 6; ++j) w6[j] = ld(L::MOM + d, j);
-        UL[N + 1 + t_] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-        UR[N + 1 + t_] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+        UL[N + 1 + t_] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
+        UR[N + 1 + t_] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
         ++t_;
       }
     }
@@ -226,8 +236,8 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
         lo6[j] = ld(Q::ALO + k, j);
       }
       auto dl = [&](int j, int c) { return (hi6[j] - hi6[c]) + (lo6[j] - lo6[c]); };
-      aL[k] = Vi[L::AL + k] + (double)weno_increment(dl(0, 2), dl(1, 2), dl(3, 2), dl(4, 2), eps);
-      aR[k] = Vj[L::AL + k] + (double)weno_increment(dl(5, 3), dl(4, 3), dl(2, 3), dl(1, 3), eps);
+      aL[k] = Vi[L::AL + k] + (double)weno_increment(dl(0, 2), dl(1, 2), dl(3, 2), dl(4, 2), eps, lin);
+      aR[k] = Vj[L::AL + k] + (double)weno_increment(dl(5, 3), dl(4, 3), dl(2, 3), dl(1, 3), eps, lin);
       UL[N + D + k] = (float)aL[k];
       UR[N + D + k] = (float)aR[k];
     }
@@ -324,7 +334,7 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
       double Fi[L::NC], Fj[L::NC];
       node_flux<N, D, DIR>(Wi, Vi, Fi);
       node_flux<N, D, DIR>(Wj, Vj, Fj);
-      flux_limit<N, D>(Wi, Wj, Fi, Fj, lam, G, H, f, pr);
+      flux_limit<N, D, DIR, true>(Wi, Wj, Fi, Fj, lam, G, H, f, pr, Vi, Vj);
     }
   }
 #pragma unroll
@@ -340,11 +350,12 @@ template <int N, int D, int DIR>
 __global__ void __launch_bounds__(kFaceThreads)
     k_face32(const double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ AUX,
              const float* __restrict__ P32, double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr,
-             const StepState* __restrict__ st) {
+             const StepState* __restrict__ st, const uint8_t* __restrict__ gate) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Nodes6 nd;
   if (!face_nodes<DIR>(g, t, nd)) return;
-  face32_body<N, D, DIR>(t, nd, W, V, AUX, P32, out, g, f, pr, st->lam[DIR]);
+  const bool lin = gate != nullptr && gate[t] != 0;
+  face32_body<N, D, DIR>(t, nd, W, V, AUX, P32, out, g, f, pr, st->lam[DIR], lin);
 }
 
 }  // namespace hrm

@@ -10,10 +10,10 @@ constexpr int kD = 1;
 
 template <int N, int DIR>
 void launch(const double* W, const double* V, const double* AUX, const float* P32, double* out, const DevGrid& g,
-            const DevFluid& f, const DevParams& p, const StepState* st, cudaStream_t s) {
+            const DevFluid& f, const DevParams& p, const StepState* st, const uint8_t* gate, cudaStream_t s) {
   if constexpr (DIR < kD) {
     const long long nf = (g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
-    k_face32<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, P32, out, g, f, p, st);
+    k_face32<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, P32, out, g, f, p, st, gate);
   }
 }
 
@@ -30,15 +30,16 @@ void update32_d1(int N, const double* Wn, const double* Wsrc, double* Wout, cons
 }
 
 void face32_d1(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
-               const DevGrid& g, const DevFluid& f, const DevParams& p, const StepState* st, cudaStream_t s) {
+               const DevGrid& g, const DevFluid& f, const DevParams& p, const StepState* st, const uint8_t* gate,
+               cudaStream_t s) {
   if (N == 2) {
-    if (dir == 0) launch<2, 0>(W, V, AUX, P32, out, g, f, p, st, s);
-    if (dir == 1) launch<2, 1>(W, V, AUX, P32, out, g, f, p, st, s);
-    if (dir == 2) launch<2, 2>(W, V, AUX, P32, out, g, f, p, st, s);
+    if (dir == 0) launch<2, 0>(W, V, AUX, P32, out, g, f, p, st, gate, s);
+    if (dir == 1) launch<2, 1>(W, V, AUX, P32, out, g, f, p, st, gate, s);
+    if (dir == 2) launch<2, 2>(W, V, AUX, P32, out, g, f, p, st, gate, s);
   } else if (N == 3) {
-    if (dir == 0) launch<3, 0>(W, V, AUX, P32, out, g, f, p, st, s);
-    if (dir == 1) launch<3, 1>(W, V, AUX, P32, out, g, f, p, st, s);
-    if (dir == 2) launch<3, 2>(W, V, AUX, P32, out, g, f, p, st, s);
+    if (dir == 0) launch<3, 0>(W, V, AUX, P32, out, g, f, p, st, gate, s);
+    if (dir == 1) launch<3, 1>(W, V, AUX, P32, out, g, f, p, st, gate, s);
+    if (dir == 2) launch<3, 2>(W, V, AUX, P32, out, g, f, p, st, gate, s);
   }
 }
 

@@ -162,27 +162,66 @@ __device__ __forceinline__ void all_alpha_W(const double* W, double* al) {
 // flux_limit_densities_vol_frac, Alg. flux_limit_energy, hard switch), FP64.
 // Wi/Wj: W_i, W_{i+1}; Fi/Fj: conservative fluxes F(W_i), F(W_{i+1});
 // G: high-order midpoint flux, H: first-order HLLC flux; the result replaces G.
-template <int N, int D>
+//
+// The limiter's guarantee rests on the first-order half-cell states being
+// admissible, which holds for the HLLC flux in exact arithmetic with no margin
+// at CFL 1/2. REPAIR (the precision form, whose H is an FP32 evaluation):
+// where a first-order half-cell state comes out inadmissible, H is evaluated
+// again in FP64 from the node states Vi, Vj, as the FP64 form does.
+template <int N, int D, int DIR = 0, bool REPAIR = false>
 __device__ __forceinline__ void flux_limit(const double* Wi, const double* Wj, const double* Fi,
                                            const double* Fj, double lam, FluxPack<N, D>& G,
-                                           const FluxPack<N, D>& H, const DevFluid& f,
-                                           const DevParams& pr) {
+                                           const FluxPack<N, D>& H_in, const DevFluid& f,
+                                           const DevParams& pr, const double* Vi = nullptr,
+                                           const double* Vj = nullptr) {
   using L = Lay<N, D>;
   constexpr int M = L::M;
   const double m2l = -2.0 * lam, p2l = 2.0 * lam;
   double Wp[M], Wm[M], WHp[M], WHm[M];
+  FluxPack<N, D> H = H_in;
   half_state<N, D>(Wi, Fi, G, m2l, true, Wp);    // W_i^{+}
   half_state<N, D>(Wj, Fj, G, p2l, false, Wm);   // W_{i+1}^{-}
   half_state<N, D>(Wi, Fi, H, m2l, true, WHp);   // W_i^{HLLC,+}
   half_state<N, D>(Wj, Fj, H, p2l, false, WHm);  // W_{i+1}^{HLLC,-}
+  // first-order states: volume fractions and rho e~ (also the limiter's lower ends)
+  double aHp[N], aHm[N];
+  all_alpha_W<N, D>(WHp, aHp);
+  all_alpha_W<N, D>(WHm, aHm);
+  double rHp = rhoe_tilde<N, D>(WHp, f), rHm = rhoe_tilde<N, D>(WHm, f);
+  if constexpr (REPAIR) {
+    bool bad = !(rHp > 0.0) || !(rHm > 0.0);
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      bad |= !(WHp[k] >= 0.0) || !(WHm[k] >= 0.0) || !(aHp[k] >= 0.0) || !(aHm[k] >= 0.0);
+    if (bad) {
+      PrimState<double, N, D> a, b;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        a.V[m] = Vi[m];
+        b.V[m] = Vj[m];
+      }
+      double GH[M];
+      const double uH = hllc<double, N, D, DIR>(f, a, b, GH);
+#pragma unroll
+      for (int m = 0; m < L::NC; ++m) H.Gc[m] = GH[m];
+#pragma unroll
+      for (int k = 0; k < N - 1; ++k) {
+        H.gm[k] = GH[L::AL + k] - uH * Vi[L::AL + k];
+        H.gp[k] = GH[L::AL + k] - uH * Vj[L::AL + k];
+      }
+      half_state<N, D>(Wi, Fi, H, m2l, true, WHp);
+      half_state<N, D>(Wj, Fj, H, p2l, false, WHm);
+      all_alpha_W<N, D>(WHp, aHp);
+      all_alpha_W<N, D>(WHm, aHm);
+      rHp = rhoe_tilde<N, D>(WHp, f);
+      rHm = rhoe_tilde<N, D>(WHm, f);
+    }
+  }
   double th = 1.0;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     th = dmin(th, dmin(theta_of(WHp[k], Wp[k], pr.eps_ar), theta_of(WHm[k], Wm[k], pr.eps_ar)));
   }
-  double aHp[N], aHm[N];
-  all_alpha_W<N, D>(WHp, aHp);
-  all_alpha_W<N, D>(WHm, aHm);
   {
     double ap[N], am[N];
     all_alpha_W<N, D>(Wp, ap);
@@ -202,7 +241,6 @@ __device__ __forceinline__ void flux_limit(const double* Wi, const double* Wj, c
     Gs = G;
   }
   // energy stage
-  const double rHp = rhoe_tilde<N, D>(WHp, f), rHm = rhoe_tilde<N, D>(WHm, f);
   const double th2 = dmin(theta_of(rHp, rhoe_tilde<N, D>(Wp, f), pr.eps_rhoe),
                           theta_of(rHm, rhoe_tilde<N, D>(Wm, f), pr.eps_rhoe));
   FluxPack<N, D> Gss;
@@ -272,11 +310,13 @@ __device__ __forceinline__ void node_flux(const double* W, const double* V, doub
 // the NC conservative flux slots, the N-1 alpha slots of G^-_{i+1/2} (planes
 // AL..M-1) and the N-1 alpha slots of G^+_{i+1/2} (planes M..M+N-2).
 // One midpoint t of direction DIR (t inside the face grid); lam = lambda_DIR.
+// lin: the midpoint is gated smooth -- the WENO-IS weights are replaced by the
+// linear weights d_k; everything else is unchanged.
 template <typename R, int N, int D, int DIR>
 __device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const double* __restrict__ W,
                                           const double* __restrict__ V, const double* __restrict__ AUX,
                                           double* __restrict__ out, const DevGrid& g, const DevFluid& f,
-                                          const DevParams& pr, double lam) {
+                                          const DevParams& pr, double lam, bool lin = false) {
   using L = Lay<N, D>;
   constexpr int M = L::M;
   const int64_t nc = g.ncells;
@@ -335,12 +375,12 @@ __device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const dou
     R w6[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) w6[j] = u6[j] - inv_rc * p6[j];
-    UL[0] = weno_is<R>(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-    UR[0] = weno_is<R>(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+    UL[0] = weno_sel<R>(lin, w6[0], w6[1], w6[2], w6[3], w6[4], eps);
+    UR[0] = weno_sel<R>(lin, w6[5], w6[4], w6[3], w6[2], w6[1], eps);
 #pragma unroll
     for (int j = 0; j < 6; ++j) w6[j] = u6[j] + inv_rc * p6[j];
-    UL[M - 1] = weno_is<R>(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-    UR[M - 1] = weno_is<R>(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+    UL[M - 1] = weno_sel<R>(lin, w6[0], w6[1], w6[2], w6[3], w6[4], eps);
+    UR[M - 1] = weno_sel<R>(lin, w6[5], w6[4], w6[3], w6[2], w6[1], eps);
     R arb[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -350,8 +390,8 @@ __device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const dou
       const R coef = arb[k] / rc2b;
 #pragma unroll
       for (int j = 0; j < 6; ++j) w6[j] = w6[j] - coef * p6[j];
-      UL[1 + k] = weno_is<R>(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-      UR[1 + k] = weno_is<R>(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+      UL[1 + k] = weno_sel<R>(lin, w6[0], w6[1], w6[2], w6[3], w6[4], eps);
+      UR[1 + k] = weno_sel<R>(lin, w6[5], w6[4], w6[3], w6[2], w6[1], eps);
     }
     {
       int t_ = 0;
@@ -360,8 +400,8 @@ __device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const dou
         if (d == DIR) continue;
 #pragma unroll
         for (int j = 0; j < 6; ++j) w6[j] = R(V[(L::MOM + d) * nc + nd.c[j]]);
-        UL[N + 1 + t_] = weno_is<R>(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-        UR[N + 1 + t_] = weno_is<R>(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+        UL[N + 1 + t_] = weno_sel<R>(lin, w6[0], w6[1], w6[2], w6[3], w6[4], eps);
+        UR[N + 1 + t_] = weno_sel<R>(lin, w6[5], w6[4], w6[3], w6[2], w6[1], eps);
         ++t_;
       }
     }
@@ -369,8 +409,8 @@ __device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const dou
     for (int k = 0; k < N - 1; ++k) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) w6[j] = R(V[(L::AL + k) * nc + nd.c[j]]);
-      UL[N + D + k] = weno_is<R>(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-      UR[N + D + k] = weno_is<R>(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+      UL[N + D + k] = weno_sel<R>(lin, w6[0], w6[1], w6[2], w6[3], w6[4], eps);
+      UR[N + D + k] = weno_sel<R>(lin, w6[5], w6[4], w6[3], w6[2], w6[1], eps);
     }
     // back to primitive variables, V~ = R U~
     PrimState<R, N, D> sl, sr;
@@ -481,11 +521,13 @@ __device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const dou
 template <typename R, int N, int D, int DIR>
 __global__ void __launch_bounds__(kFaceThreads)
     k_face(const double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ AUX,
-           double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr, const StepState* __restrict__ st) {
+           double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr, const StepState* __restrict__ st,
+           const uint8_t* __restrict__ gate) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Nodes6 nd;
   if (!face_nodes<DIR>(g, t, nd)) return;
-  face_body<R, N, D, DIR>(t, nd, W, V, AUX, out, g, f, pr, st->lam[DIR]);
+  const bool lin = gate != nullptr && gate[t] != 0;
+  face_body<R, N, D, DIR>(t, nd, W, V, AUX, out, g, f, pr, st->lam[DIR], lin);
 }
 
 // ---------------------------------------------------------------- thermal relaxation (Sec. 4.2)

@@ -10,9 +10,10 @@
 namespace hrm {
 
 struct CellKernels {
-  // P32 (nullable): FP32 planes for the precision form
-  void (*prim)(const double* W, double* V, double* AUX, float* P32, const DevGrid&, const DevFluid&, StepState*,
-               int tau, cudaStream_t);
+  // P32 (nullable): FP32 planes for the precision form; R32 (nullable): FP32
+  // rounding residues of rho, u_d, p for the learned gate
+  void (*prim)(const double* W, double* V, double* AUX, float* P32, float* R32, const DevGrid&, const DevFluid&,
+               StepState*, int tau, cudaStream_t);
   void (*ic)(const double* prim, double* W, const DevGrid&, const DevFluid&, cudaStream_t);
   void (*relax)(double* W, const DevGrid&, const DevFluid&, cudaStream_t);
   void (*fields)(const double* W, double* out, int field, const DevGrid&, const DevFluid&, cudaStream_t);
@@ -21,8 +22,10 @@ struct CellKernels {
 
 struct FaceKernels {
   // precision: 0 FP64, 1 FP32 bulk
+  // gate (nullable): one byte per midpoint, nonzero = linear WENO weights there
   void (*face[3])(int precision, const double* W, const double* V, const double* AUX, const float* P32,
-                  double* out, const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+                  double* out, const DevGrid&, const DevFluid&, const DevParams&, const StepState*,
+                  const uint8_t* gate, cudaStream_t);
   // mode 0: RK combination, mode 1: write the RHS; fast: precision-form variant
   void (*update)(int mode, int fast, const double* Wn, const double* Wsrc, double* Wout, const double* F0,
                  const double* F1, const double* F2, const DevGrid&, const DevFluid&, StepState*, double a,
@@ -40,17 +43,20 @@ void update32_d1(int N, const double* Wn, const double* Wsrc, double* Wout, cons
                  const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
                  int count, cudaStream_t);
 void face32_d1(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
-               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, const uint8_t* gate,
+               cudaStream_t);
 void update32_d2(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
                  const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
                  int count, cudaStream_t);
 void face32_d2(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
-               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, const uint8_t* gate,
+               cudaStream_t);
 void update32_d3(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
                  const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
                  int count, cudaStream_t);
 void face32_d3(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
-               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, cudaStream_t);
+               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, const uint8_t* gate,
+               cudaStream_t);
 
 void launch_finalize(StepState* st, const DevGrid& g, int D, double cfl, int mode, cudaStream_t s);
 void launch_set_dt(StepState* st, double dt, cudaStream_t s);

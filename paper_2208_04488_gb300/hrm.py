@@ -25,7 +25,10 @@ FP64, FP32 = 0, 1
 RK3, EULER, RK2 = 0, 1, 2
 RELAX_OFF, RELAX_STAGE, RELAX_STEP = 0, 1, 2
 KERNEL_PRIM, KERNEL_FINALIZE, KERNEL_FACE_X, KERNEL_FACE_Y, KERNEL_FACE_Z, KERNEL_UPDATE = 0, 1, 2, 3, 4, 5
-KERNEL_NAMES = {0: "prim", 1: "finalize", 2: "face_x", 3: "face_y", 4: "face_z", 5: "update"}
+KERNEL_GATE = 6
+KERNEL_NAMES = {0: "prim", 1: "finalize", 2: "face_x", 3: "face_y", 4: "face_z", 5: "update", 6: "gate"}
+LEARNED_OFF, LEARNED_GATE, LEARNED_FIXED = 0, 1, 2
+DETECTOR_PARAMS, DETECTOR_INPUTS = 2081, 30
 
 
 class HrmGrid(ctypes.Structure):
@@ -125,6 +128,35 @@ def lib():
     for name in ("hrm_batch_create", "hrm_batch_set_primitive", "hrm_batch_set", "hrm_batch_get",
                  "hrm_batch_step", "hrm_batch_time", "hrm_batch_admissibility", "hrm_batch_set_launch",
                  "hrm_batch_tune"):
+        getattr(L, name).restype = ctypes.c_int
+    _FP = ctypes.POINTER(ctypes.c_float)
+    _U8 = ctypes.POINTER(ctypes.c_uint8)
+    _I64 = ctypes.POINTER(ctypes.c_int64)
+    L.hrm_detector_create.argtypes = [P(_VP), ctypes.c_int64, ctypes.c_uint64, _VP]
+    L.hrm_detector_destroy.argtypes = [_VP]
+    L.hrm_detector_destroy.restype = None
+    L.hrm_detector_last_error.argtypes = [_VP]
+    L.hrm_detector_last_error.restype = ctypes.c_char_p
+    L.hrm_detector_set_weights.argtypes = [_VP, _FP]
+    L.hrm_detector_get_weights.argtypes = [_VP, _FP]
+    L.hrm_detector_size.argtypes = [_VP]
+    L.hrm_detector_size.restype = ctypes.c_int64
+    L.hrm_detector_clear.argtypes = [_VP]
+    L.hrm_detector_add_samples.argtypes = [_VP, _FP, _FP, ctypes.c_int64]
+    L.hrm_detector_samples.argtypes = [_VP, ctypes.c_int64, ctypes.c_int64, _FP, _FP, _FP]
+    L.hrm_detector_collect.argtypes = [_VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, _I64]
+    L.hrm_detector_gradient.argtypes = [_VP, ctypes.c_int64, ctypes.c_int64, _FP, _DP]
+    L.hrm_detector_train.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _FP]
+    L.hrm_detector_logits.argtypes = [_VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _FP]
+    L.hrm_detector_evaluate.argtypes = [_VP, ctypes.c_double, ctypes.c_int32, _I64, _DP]
+    L.hrm_set_detector.argtypes = [_VP, _VP]
+    L.hrm_set_gate.argtypes = [_VP, ctypes.c_int32, _U8]
+    L.hrm_get_gate.argtypes = [_VP, ctypes.c_int32, _U8]
+    for name in ("hrm_detector_create", "hrm_detector_set_weights", "hrm_detector_get_weights",
+                 "hrm_detector_clear", "hrm_detector_add_samples", "hrm_detector_samples", "hrm_detector_collect",
+                 "hrm_detector_gradient", "hrm_detector_train", "hrm_detector_logits", "hrm_detector_evaluate",
+                 "hrm_set_detector", "hrm_set_gate", "hrm_get_gate"):
         getattr(L, name).restype = ctypes.c_int
     L.hrm_probe_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, _VP, _DP]
     L.hrm_probe_fma_peak.restype = ctypes.c_int
@@ -299,6 +331,122 @@ class Solver:
 
     def kernel_launches(self) -> int:
         return int(lib().hrm_kernel_launches(self.h))
+
+    # -- learned smoothness gate
+    def face_count(self, d):
+        n = 1
+        for e in range(self.D):
+            n *= self.n[e] + (e == d)
+        return n
+
+    def set_detector(self, det: "Detector"):
+        """Snapshot of the detector's inference weights; params.learned = 1 then allowed."""
+        self._check(lib().hrm_set_detector(self.h, det.h))
+
+    def set_gate(self, d, gate):
+        g = np.ascontiguousarray(gate, dtype=np.uint8).reshape(-1)
+        assert g.size == self.face_count(d)
+        self._check(lib().hrm_set_gate(self.h, d, g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+
+    def get_gate(self, d):
+        g = np.empty(self.face_count(d), dtype=np.uint8)
+        self._check(lib().hrm_get_gate(self.h, d, g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+        return g
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Detector:
+    """One hrm_detector: the learned smoothness gate's weights, Adam state and
+    training samples, all on the GPU."""
+
+    def __init__(self, capacity=1 << 20, seed=0, stream=None):
+        L = lib()
+        self.stream = _stream_handle(stream)
+        h = _VP()
+        st = L.hrm_detector_create(ctypes.byref(h), int(capacity), int(seed), _VP(self.stream))
+        if st != HRM_OK:
+            raise HrmError(st, "hrm_detector_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hrm_detector_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != HRM_OK:
+            raise HrmError(st, lib().hrm_detector_last_error(self.h).decode())
+        return st
+
+    def set_weights(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == DETECTOR_PARAMS
+        self._check(lib().hrm_detector_set_weights(self.h, _fptr(t)))
+
+    def get_weights(self):
+        t = np.empty(DETECTOR_PARAMS, dtype=np.float32)
+        self._check(lib().hrm_detector_get_weights(self.h, _fptr(t)))
+        return t
+
+    def size(self) -> int:
+        return int(lib().hrm_detector_size(self.h))
+
+    def clear(self):
+        self._check(lib().hrm_detector_clear(self.h))
+
+    def add_samples(self, X, y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        assert X.shape == (y.size, DETECTOR_INPUTS)
+        self._check(lib().hrm_detector_add_samples(self.h, _fptr(X), _fptr(y), y.size))
+
+    def samples(self, first=0, n=None):
+        n = self.size() - first if n is None else n
+        X = np.empty((n, DETECTOR_INPUTS), dtype=np.float32)
+        y = np.empty(n, dtype=np.float32)
+        dv = np.empty(n, dtype=np.float32)
+        self._check(lib().hrm_detector_samples(self.h, first, n, _fptr(X), _fptr(y), _fptr(dv)))
+        return X, y, dv
+
+    def collect(self, solver: Solver, delta=0.01, keep_rough=1.0, keep_smooth=0.1, keep_flat=0.01) -> int:
+        added = ctypes.c_int64()
+        self._check(lib().hrm_detector_collect(self.h, solver.h, delta, keep_rough, keep_smooth, keep_flat,
+                                               ctypes.byref(added)))
+        return added.value
+
+    def gradient(self, first=0, n=None):
+        n = self.size() - first if n is None else n
+        g = np.empty(DETECTOR_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(lib().hrm_detector_gradient(self.h, first, n, _fptr(g), ctypes.byref(loss)))
+        return g, loss.value
+
+    def train(self, steps, batch=4096, lr=1e-3):
+        losses = np.empty(max(steps, 1), dtype=np.float32)
+        self._check(lib().hrm_detector_train(self.h, int(steps), int(batch), float(lr), _fptr(losses)))
+        return losses[:steps]
+
+    def logits(self, first=0, n=None, bf16=True):
+        n = self.size() - first if n is None else n
+        z = np.empty(n, dtype=np.float32)
+        self._check(lib().hrm_detector_logits(self.h, first, n, 1 if bf16 else 0, _fptr(z)))
+        return z
+
+    def evaluate(self, threshold=0.5, bf16=True):
+        """{'tp','fp','tn','fn','loss'}: positive = gated (predicted smooth)."""
+        c = (ctypes.c_int64 * 4)()
+        loss = ctypes.c_double()
+        self._check(lib().hrm_detector_evaluate(self.h, float(threshold), 1 if bf16 else 0, c, ctypes.byref(loss)))
+        return {"tp": c[0], "fp": c[1], "tn": c[2], "fn": c[3], "loss": loss.value}
 
 
 class BatchSolver:

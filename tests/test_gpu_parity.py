@@ -312,3 +312,15 @@ def test_fp32_form_extreme_shock_tube_admissible(hrm):
     for _ in range(40):
         s.step(4.0e-8, 1)
     assert s.admissibility() == [0, 0, 0, 0]
+
+
+def test_fp32_form_shock_water_column_admissible(hrm):
+    """Sec. 5.7 shape at CFL 1/2, where the first-order half-cell states have no
+    margin: the precision form re-evaluates an inadmissible first-order flux in
+    FP64 and stays admissible, as the FP64 form does."""
+    pr = P.shock_water_column_2d(512, 256)
+    for precision in (hrm.FP64, hrm.FP32):
+        s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, precision=precision, check=0))
+        s.step(0.0, 30)
+        assert s.admissibility() == [0, 0, 0, 0], precision
+        s.close()
