@@ -90,6 +90,11 @@ typedef struct {
   double weno_eps;                     /* 1e-15 (App. C) */
   double Cs, q_sensor;                 /* shock sensor 1e12 and 2 (Sec. 4.3.1) */
   double learned_threshold;            /* gate probability in (0, 1) above which d_k are used */
+  int32_t screen;      /* precision form: 1 (default) first certifies in FP32, with rounding
+                          margins, that the limiters would leave a midpoint unchanged (every
+                          checked quantity above its threshold) and evaluates them in FP64
+                          only where it cannot; results are the same as with 0 (always FP64) */
+  int32_t pad_screen;
 } hrm_params;
 
 /* Field selectors of hrm_get. */

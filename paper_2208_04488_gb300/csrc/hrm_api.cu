@@ -117,6 +117,7 @@ void fill_dev_params(hrm_ctx* c) {
   d.hs_rhoe = p.hs_rhoe;
   d.weno_eps = p.weno_eps;
   d.Cs = p.Cs;
+  fill_screen(d, p.screen);
 }
 
 void drop_graph(hrm_ctx* c) {
@@ -261,6 +262,7 @@ void hrm_params_default(hrm_params* p) {
   p->Cs = 1.0e12;
   p->q_sensor = 2.0;
   p->learned_threshold = 0.5;
+  p->screen = 1;
 }
 
 const char* hrm_last_error(const hrm_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }

@@ -222,6 +222,7 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
   b->dp.hs_rhoe = p.hs_rhoe;
   b->dp.weno_eps = p.weno_eps;
   b->dp.Cs = p.Cs;
+  fill_screen(b->dp, p.screen);
   b->ninst = ninst;
   b->stream = (cudaStream_t)cuda_stream;
   hrm_status s;

@@ -35,6 +35,10 @@ struct DevGrid {
 struct DevParams {
   int32_t limiters, blend, scheme, qexp;
   double eps_ar, eps_a, eps_rhoe, hs_ar, hs_a, hs_rc2, hs_rhoe, weno_eps, Cs;
+  // precision form: certify the limiters' no-op in FP32 first (screen), with
+  // the thresholds rounded up to FP32
+  int32_t screen, pad_;
+  float eps_ar_f, eps_rhoe_f, hs_rc2_f, pad2_;
 };
 
 // Per-step scalars kept on the device so that a captured graph needs no host input.

@@ -132,6 +132,126 @@ __device__ __forceinline__ double alpha_flux(double aL, double aR, double ss) {
   return 0.5 * (aL * ss) + 0.5 * (aR * ss);
 }
 
+// ---------------------------------------------------------------- FP32 screens
+// Each screen returns true only when the FP64 limiter is certain to leave its
+// input unchanged: every quantity the limiter tests lies at or above the
+// limiter threshold (which implies theta = 1 -- the target is min(eps, first-
+// order value) -- and, with hard-switch thresholds not above the limiter
+// thresholds, no hard switch). FP32 values are tested with a bound on their
+// rounding error against the FP64 evaluation; FP64 values with a margin of a
+// few units in the last place. Where a screen fails, the FP64 limiter runs.
+
+// u32 = 2^-24; the bounds below allow 16 u32 (partial densities, momenta,
+// energy: inputs rounded once, a product, a difference and an FMA) and
+// 32 u32 (rho c^2, rho e~).
+constexpr float kScreenRel = 16.0f * 5.9604645e-8f;
+constexpr float kScreenRel2 = 32.0f * 5.9604645e-8f;
+constexpr double kAlphaMargin = 1e-15;  // FP64 volume fractions: sums of a few terms of size <= 1
+
+// Interpolation limiter (Sec. 4.3.2) on one side: partial densities of the
+// FP32 midpoint state, FP64 volume fractions, rho c^2 for the hard switch.
+template <int N, int D>
+__device__ __forceinline__ bool interp_screen32(const float* Vt, const double* at, const DevFluid& f,
+                                                const DevParams& pr) {
+  using L = Lay<N, D>;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < N; ++k) ok &= Vt[k] >= pr.eps_ar_f;  // float >= (eps rounded up) => double >= eps
+  double s = 0.0;
+  float a[N];
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) {
+    ok &= at[k] >= pr.eps_a + kAlphaMargin;
+    s += at[k];
+    a[k] = (float)at[k];
+  }
+  const double aN = 1.0 - s;
+  ok &= aN >= pr.eps_a + kAlphaMargin;
+  a[N - 1] = (float)aN;
+  float S = 0.f, P = 0.f;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    S += a[k] * (float)f.inv_gm1[k];
+    P += a[k] * (float)f.gpinf_gm1[k];
+  }
+  const float iS = 1.f / S;
+  const float t1 = (1.f + iS) * Vt[L::EN], t2 = P * iS;
+  ok &= (t1 + t2) - kScreenRel2 * (fabsf(t1) + fabsf(t2)) >= pr.hs_rc2_f;
+  return ok;
+}
+
+// Flux limiter (Sec. 4.3.2): the high-order half-cell states W_i^+ and
+// W_{i+1}^- from the FP32 node states and the FP32 midpoint flux g32;
+// partial densities and rho e~ in FP32 with error bounds, volume fractions in
+// FP64 from the FP64 alpha slots (ai, aj: node volume fractions).
+template <int N, int D, int DIR>
+__device__ __forceinline__ bool flux_screen32(const float* __restrict__ P32, int64_t nc, const Nodes6& nd,
+                                              const float* g32, const FluxPack<N, D>& G, const double* ai,
+                                              const double* aj, double lam, const DevFluid& f,
+                                              const DevParams& pr) {
+  using L = Lay<N, D>;
+  using Q = P32Lay<N, D>;
+  bool ok = true;
+  const double m2l = -2.0 * lam, p2l = 2.0 * lam;
+  // volume fractions of both half-cell states (the limiter's own expressions)
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+      const double a = side == 0 ? ai[k] + m2l * G.gm[k] : aj[k] + p2l * G.gp[k];
+      ok &= a >= pr.eps_a + kAlphaMargin;
+      s += a;
+    }
+    ok &= 1.0 - s >= pr.eps_a + kAlphaMargin;
+  }
+  const float s2 = (float)(2.0 * lam);
+  float qmax = 0.f;
+#pragma unroll
+  for (int k = 0; k < N; ++k) qmax = fmaxf(qmax, fabsf((float)f.q[k]));
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int64_t c = nd.c[2 + side];
+    const float sg = side == 0 ? -s2 : s2;
+    const float un = P32[(int64_t)(L::MOM + DIR) * nc + c], p = P32[(int64_t)L::EN * nc + c];
+    // partial densities
+    float rho = 0.f, rq = 0.f, erho = 0.f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const float w = P32[(int64_t)k * nc + c];
+      const float F = w * un;
+      const float h = w + sg * (g32[k] - F);
+      const float e = kScreenRel * (fabsf(w) + s2 * (fabsf(g32[k]) + fabsf(F)));
+      ok &= h - e >= pr.eps_ar_f;
+      rho += h;
+      rq += h * (float)f.q[k];
+      erho += e;
+    }
+    // momentum and energy, and rho e~ = E - |rho u|^2 / (2 rho) - sum alpha_k rho_k q_k
+    float m2 = 0.f, emom = 0.f;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const float w = P32[(int64_t)(Q::MOM + d) * nc + c];
+      const float F = w * un + (d == DIR ? p : 0.f);
+      const float h = w + sg * (g32[L::MOM + d] - F);
+      m2 += h * h;
+      emom += kScreenRel * (fabsf(w) + s2 * (fabsf(g32[L::MOM + d]) + fabsf(w * un) + fabsf(p))) * fabsf(h);
+    }
+    const float wE = P32[(int64_t)Q::E * nc + c];
+    const float FE = (wE + p) * un;
+    const float E = wE + sg * (g32[L::EN] - FE);
+    const float eE = kScreenRel * (fabsf(wE) + s2 * (fabsf(g32[L::EN]) + fabsf(wE * un) + fabsf(p * un)));
+    const float irho = 1.f / rho;
+    const float kin = 0.5f * m2 * irho;
+    const float re = E - kin - rq;
+    // error: E, |m| |dm| / rho, (|u|^2 / 2 + max|q|) drho, evaluation rounding
+    const float err = eE + emom * irho + (kin * irho + qmax) * erho +
+                      kScreenRel2 * (fabsf(E) + kin + fabsf(rq));
+    ok &= re - err >= pr.eps_rhoe_f;
+  }
+  return ok;
+}
+
 template <int N, int D, int DIR>
 __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const double* __restrict__ W,
                                             const double* __restrict__ V, const double* __restrict__ AUX,
@@ -144,20 +264,15 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
   const int64_t nc = g.ncells;
   const int64_t nf = face_count<DIR>(g);
   auto ld = [&](int plane, int j) -> float { return P32[(int64_t)plane * nc + nd.c[j]]; };
-
-  // node states i, i+1 in FP64 for the limiters
-  double Vi[M], Vj[M], Wi[M], Wj[M];
+  auto load_node = [&](int j, double* Vn, double* Wn) {
 #pragma unroll
-  for (int m = 0; m < M; ++m) {
-    Vi[m] = V[m * nc + nd.c[2]];
-    Vj[m] = V[m * nc + nd.c[3]];
-    Wi[m] = W[m * nc + nd.c[2]];
-    Wj[m] = W[m * nc + nd.c[3]];
-  }
-
-  // first-order HLLC in FP32 from the node states
-  FluxPack<N, D> H;
-  {
+    for (int m = 0; m < M; ++m) {
+      Vn[m] = V[m * nc + nd.c[j]];
+      if (Wn) Wn[m] = W[m * nc + nd.c[j]];
+    }
+  };
+  // first-order HLLC in FP32 from the node states, alpha slots in FP64
+  auto first_order = [&](const double* Vi, const double* Vj, FluxPack<N, D>& H) {
     PrimState<float, N, D> a, b;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -174,11 +289,22 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
       H.gm[k] = ga - uH * Vi[L::AL + k];
       H.gp[k] = ga - uH * Vj[L::AL + k];
     }
+  };
+
+  // FP64 volume fractions of nodes i, i+1
+  double ai[N > 1 ? N - 1 : 1], aj[N > 1 ? N - 1 : 1];
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) {
+    ai[k] = V[(L::AL + k) * nc + nd.c[2]];
+    aj[k] = V[(L::AL + k) * nc + nd.c[3]];
   }
 
   FluxPack<N, D> G;
   if (pr.scheme == 1) {
-    G = H;
+    double Vi[M], Vj[M];
+    load_node(2, Vi, nullptr);
+    load_node(3, Vj, nullptr);
+    first_order(Vi, Vj, G);
   } else {
     float p6[6], u6[6];
 #pragma unroll
@@ -236,8 +362,8 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
         lo6[j] = ld(Q::ALO + k, j);
       }
       auto dl = [&](int j, int c) { return (hi6[j] - hi6[c]) + (lo6[j] - lo6[c]); };
-      aL[k] = Vi[L::AL + k] + (double)weno_increment(dl(0, 2), dl(1, 2), dl(3, 2), dl(4, 2), eps, lin);
-      aR[k] = Vj[L::AL + k] + (double)weno_increment(dl(5, 3), dl(4, 3), dl(2, 3), dl(1, 3), eps, lin);
+      aL[k] = ai[k] + (double)weno_increment(dl(0, 2), dl(1, 2), dl(3, 2), dl(4, 2), eps, lin);
+      aR[k] = aj[k] + (double)weno_increment(dl(5, 3), dl(4, 3), dl(2, 3), dl(1, 3), eps, lin);
       UL[N + D + k] = (float)aL[k];
       UR[N + D + k] = (float)aR[k];
     }
@@ -267,8 +393,16 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
       }
     }
     if (pr.limiters) {
-      interp_limit32<N, D>(sl.V, aL, Vi, AUX[2 * nc + nd.c[2]], f, pr);
-      interp_limit32<N, D>(sr.V, aR, Vj, AUX[2 * nc + nd.c[3]], f, pr);
+      if (!(pr.screen && interp_screen32<N, D>(sl.V, aL, f, pr))) {
+        double Vn[M];
+        load_node(2, Vn, nullptr);
+        interp_limit32<N, D>(sl.V, aL, Vn, AUX[2 * nc + nd.c[2]], f, pr);
+      }
+      if (!(pr.screen && interp_screen32<N, D>(sr.V, aR, f, pr))) {
+        double Vn[M];
+        load_node(3, Vn, nullptr);
+        interp_limit32<N, D>(sr.V, aR, Vn, AUX[2 * nc + nd.c[3]], f, pr);
+      }
     }
     float Gt[M];
     const float ut = hllc<float, N, D, DIR>(f, sl, sr, Gt);
@@ -297,6 +431,7 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
     const float one_m = 1.f - sig;
     const float uhcs = psi * ut - a1 * (u6[2] + u6[3]) + a2 * (u6[1] + u6[4]) - a3 * (u6[0] + u6[5]);
     const double uhat = (double)(sig * ut + one_m * uhcs);
+    float g32[L::NC];
 #pragma unroll
     for (int m = 0; m < L::NC; ++m) {
       float Gn[6];
@@ -313,7 +448,8 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
         Gn[j] = v;
       }
       const float ghcs = psi * Gt[m] - a1 * (Gn[2] + Gn[3]) + a2 * (Gn[1] + Gn[4]) - a3 * (Gn[0] + Gn[5]);
-      G.Gc[m] = (double)(sig * Gt[m] + one_m * ghcs);
+      g32[m] = sig * Gt[m] + one_m * ghcs;
+      G.Gc[m] = (double)g32[m];
     }
     // alpha slots in FP64: node fluxes alpha_j u_j, HCS, blend, quasi-conservative form
     {
@@ -326,11 +462,16 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
         for (int j = 0; j < 6; ++j) gn[j] = V[(L::AL + k) * nc + nd.c[j]] * (double)u6[j];
         const double ghcs = dpsi * Gt_a[k] - d1 * (gn[2] + gn[3]) + d2 * (gn[1] + gn[4]) - d3 * (gn[0] + gn[5]);
         const double gh = sg * Gt_a[k] + om * ghcs;
-        G.gm[k] = gh - uhat * Vi[L::AL + k];
-        G.gp[k] = gh - uhat * Vj[L::AL + k];
+        G.gm[k] = gh - uhat * ai[k];
+        G.gp[k] = gh - uhat * aj[k];
       }
     }
-    if (pr.limiters) {
+    if (pr.limiters && !(pr.screen && flux_screen32<N, D, DIR>(P32, nc, nd, g32, G, ai, aj, lam, f, pr))) {
+      double Vi[M], Vj[M], Wi[M], Wj[M];
+      load_node(2, Vi, Wi);
+      load_node(3, Vj, Wj);
+      FluxPack<N, D> H;
+      first_order(Vi, Vj, H);
       double Fi[L::NC], Fj[L::NC];
       node_flux<N, D, DIR>(Wi, Vi, Fi);
       node_flux<N, D, DIR>(Wj, Vj, Fj);

@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "hrm_device.cuh"
 
 namespace hrm {
@@ -62,5 +64,24 @@ void launch_finalize(StepState* st, const DevGrid& g, int D, double cfl, int mod
 void launch_set_dt(StepState* st, double dt, cudaStream_t s);
 
 inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// Smallest float not below x (thresholds of the FP32 screens).
+inline float float_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+// The screens certify "theta = 1 and no hard switch" from "every checked
+// quantity >= its limiter threshold", which implies the hard-switch tests only
+// when each hard-switch threshold is at most the limiter threshold.
+inline void fill_screen(DevParams& d, int requested) {
+  d.screen = requested && d.hs_ar <= d.eps_ar && d.hs_a <= d.eps_a && d.hs_rhoe <= d.eps_rhoe;
+  d.eps_ar_f = float_up(d.eps_ar);
+  d.eps_rhoe_f = float_up(d.eps_rhoe);
+  d.hs_rc2_f = float_up(d.hs_rc2);
+  d.pad_ = 0;
+  d.pad2_ = 0.f;
+}
 
 }  // namespace hrm

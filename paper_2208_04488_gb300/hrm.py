@@ -44,7 +44,8 @@ class HrmParams(ctypes.Structure):
                 ("eps_ar", ctypes.c_double), ("eps_a", ctypes.c_double), ("eps_rhoe", ctypes.c_double),
                 ("hs_ar", ctypes.c_double), ("hs_a", ctypes.c_double), ("hs_rc2", ctypes.c_double),
                 ("hs_rhoe", ctypes.c_double), ("weno_eps", ctypes.c_double), ("Cs", ctypes.c_double),
-                ("q_sensor", ctypes.c_double), ("learned_threshold", ctypes.c_double)]
+                ("q_sensor", ctypes.c_double), ("learned_threshold", ctypes.c_double),
+                ("screen", ctypes.c_int32), ("pad_screen", ctypes.c_int32)]
 
 
 class HrmInstance(ctypes.Structure):

@@ -1,7 +1,7 @@
 """Command-line runner: advance one of the built-in workloads on the GPU.
 
     python -m paper_2208_04488_gb300.run --workload shock_bubble --nx 1024 --ny 512 \
-        --steps 10 [--precision fp64|fp32] [--dt 0]
+        --steps 10 [--precision fp64|fp32] [--dt 0] [--gate none|all|learned]
 
 Prints the wall time per step (CUDA events), the simulated time and the
 admissibility counters. Used for profiling captures of single kernels.
@@ -42,6 +42,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--dt", type=float, default=0.0, help="0: CFL step of the workload")
+    ap.add_argument("--gate", default="none", choices=["none", "all", "learned"],
+                    help="all: every midpoint gated (fixed gate); learned: a detector trained on the small "
+                         "training set")
     a = ap.parse_args(argv)
     import torch
     from paper_2208_04488_gb300 import build, hrm
@@ -49,6 +52,16 @@ def main(argv=None):
     pr = make_problem(a.workload, a.nx, a.ny, a.nz)
     prec = hrm.FP64 if a.precision == "fp64" else hrm.FP32
     s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, precision=prec, check=0))
+    if a.gate == "all":
+        import numpy as np
+        for d in range(pr.D):
+            s.set_gate(d, np.ones(s.face_count(d), dtype=np.uint8))
+        s.set_params(hrm.params_default(cfl=pr.cfl, precision=prec, check=0, learned=hrm.LEARNED_FIXED))
+    elif a.gate == "learned":
+        from paper_2208_04488_gb300 import learned
+        det, _ = learned.build_detector(scale="small", steps=1000, capacity=1 << 21)
+        s.set_detector(det)
+        s.set_params(hrm.params_default(cfl=pr.cfl, precision=prec, check=0, learned=hrm.LEARNED_GATE))
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
