@@ -333,6 +333,7 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
     c->fl.pinf[k] = p_inf[k];
     c->fl.gamma[k] = gamma[k];
   }
+  fill_fluid_f(c->fl);
   if (params)
     c->params = *params;
   else

@@ -257,6 +257,7 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
       I.f.gamma[k] = in.gamma[k];
     }
     I.f.liq = liq < 0 ? 0 : liq;
+    fill_fluid_f(I.f);
     I.N = N;
     b->N[i] = N;
     I.g.ncells = 1;

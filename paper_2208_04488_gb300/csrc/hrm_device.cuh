@@ -23,7 +23,26 @@ struct DevFluid {
   double gpinf_gm1[HRM_MAXN];  // gamma_k p_inf_k / (gamma_k - 1)
   double cv[HRM_MAXN], cp[HRM_MAXN], Rg[HRM_MAXN];  // c_v, c_p, c_p - c_v
   double q[HRM_MAXN], pinf[HRM_MAXN], gamma[HRM_MAXN];
+  // FP32 roundings of inv_gm1, gpinf_gm1 and q for the precision form
+  float inv_gm1_f[HRM_MAXN], gpinf_gm1_f[HRM_MAXN], q_f[HRM_MAXN];
 };
+
+// Fill the FP32 copies of the species constants (host).
+inline void fill_fluid_f(DevFluid& f) {
+  for (int k = 0; k < HRM_MAXN; ++k) {
+    f.inv_gm1_f[k] = (float)f.inv_gm1[k];
+    f.gpinf_gm1_f[k] = (float)f.gpinf_gm1[k];
+    f.q_f[k] = (float)f.q[k];
+  }
+}
+
+// Species constants in the arithmetic type R.
+__device__ __forceinline__ double inv_gm1_of(const DevFluid& f, int k, double) { return f.inv_gm1[k]; }
+__device__ __forceinline__ float inv_gm1_of(const DevFluid& f, int k, float) { return f.inv_gm1_f[k]; }
+__device__ __forceinline__ double gpinf_gm1_of(const DevFluid& f, int k, double) { return f.gpinf_gm1[k]; }
+__device__ __forceinline__ float gpinf_gm1_of(const DevFluid& f, int k, float) { return f.gpinf_gm1_f[k]; }
+__device__ __forceinline__ double q_of(const DevFluid& f, int k, double) { return f.q[k]; }
+__device__ __forceinline__ float q_of(const DevFluid& f, int k, float) { return f.q_f[k]; }
 
 struct DevGrid {
   int64_t n[3];
@@ -38,7 +57,7 @@ struct DevParams {
   // precision form: certify the limiters' no-op in FP32 first (screen), with
   // the thresholds rounded up to FP32
   int32_t screen, pad_;
-  float eps_ar_f, eps_rhoe_f, hs_rc2_f, pad2_;
+  float eps_ar_f, eps_rhoe_f, hs_rc2_f, eps_a_mf;  // eps_a_mf: eps_a + 1e-13 (float-float margin)
 };
 
 // Per-step scalars kept on the device so that a captured graph needs no host input.
@@ -128,8 +147,8 @@ __device__ __forceinline__ void mix_SP(const DevFluid& f, const R* al_stored, R&
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     R a = (k < N - 1) ? al_stored[k] : last;
-    S = S + a * R(f.inv_gm1[k]);
-    P = P + a * R(f.gpinf_gm1[k]);
+    S = S + a * inv_gm1_of(f, k, R());
+    P = P + a * gpinf_gm1_of(f, k, R());
   }
 }
 
@@ -245,7 +264,7 @@ __device__ __forceinline__ void prim_state(const DevFluid& f, PrimState<R, N, D>
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     rho = rho + s.V[k];
-    rq = rq + s.V[k] * R(f.q[k]);
+    rq = rq + s.V[k] * q_of(f, k, R());
   }
 #pragma unroll
   for (int d = 0; d < D; ++d) kin = kin + s.V[L::MOM + d] * s.V[L::MOM + d];

@@ -132,47 +132,85 @@ __device__ __forceinline__ double alpha_flux(double aL, double aR, double ss) {
   return 0.5 * (aL * ss) + 0.5 * (aR * ss);
 }
 
+// ---------------------------------------------------------------- float-float
+// Unevaluated sums hi + lo of two floats built with error-free
+// transformations (Knuth's TwoSum, the FMA TwoProduct): about 2^-48 relative
+// precision, on the FP32 pipe. The volume-fraction slots of the precision form
+// use them: differences of volume fractions near 1 must keep the minor phase
+// (1e-8) exact to far below its size.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff ff_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = ff_sum(a.hi, b.hi);
+  return ff_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.hi, -b.lo}); }
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {
+  const ff p = ff_prod(a.hi, b);
+  return ff_sum(p.hi, fmaf(a.lo, b, p.lo));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const ff p = ff_prod(a.hi, b.hi);
+  return ff_sum(p.hi, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo)));
+}
+__device__ __forceinline__ ff ff_of(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double ff_d(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ float ff_f(ff a) { return a.hi + a.lo; }
+#define HRM_FF(c) ff{(float)(c), (float)((c) - (double)(float)(c))}
+
 // ---------------------------------------------------------------- FP32 screens
 // Each screen returns true only when the FP64 limiter is certain to leave its
 // input unchanged: every quantity the limiter tests lies at or above the
 // limiter threshold (which implies theta = 1 -- the target is min(eps, first-
 // order value) -- and, with hard-switch thresholds not above the limiter
 // thresholds, no hard switch). FP32 values are tested with a bound on their
-// rounding error against the FP64 evaluation; FP64 values with a margin of a
-// few units in the last place. Where a screen fails, the FP64 limiter runs.
+// rounding error against the FP64 evaluation; float-float volume fractions
+// with an absolute margin (pr.eps_a_mf = eps_a + 1e-13, rounded up). Where a
+// screen fails, the FP64 limiter runs.
 
 // u32 = 2^-24; the bounds below allow 16 u32 (partial densities, momenta,
 // energy: inputs rounded once, a product, a difference and an FMA) and
 // 32 u32 (rho c^2, rho e~).
 constexpr float kScreenRel = 16.0f * 5.9604645e-8f;
 constexpr float kScreenRel2 = 32.0f * 5.9604645e-8f;
-constexpr double kAlphaMargin = 1e-15;  // FP64 volume fractions: sums of a few terms of size <= 1
 
 // Interpolation limiter (Sec. 4.3.2) on one side: partial densities of the
-// FP32 midpoint state, FP64 volume fractions, rho c^2 for the hard switch.
+// FP32 midpoint state, the volume fractions at (float-float, the N-1 stored
+// ones), rho c^2 for the hard switch.
 template <int N, int D>
-__device__ __forceinline__ bool interp_screen32(const float* Vt, const double* at, const DevFluid& f,
+__device__ __forceinline__ bool interp_screen32(const float* Vt, const ff* at, const DevFluid& f,
                                                 const DevParams& pr) {
   using L = Lay<N, D>;
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < N; ++k) ok &= Vt[k] >= pr.eps_ar_f;  // float >= (eps rounded up) => double >= eps
-  double s = 0.0;
+  ff rest{1.f, 0.f};
   float a[N];
 #pragma unroll
   for (int k = 0; k < N - 1; ++k) {
-    ok &= at[k] >= pr.eps_a + kAlphaMargin;
-    s += at[k];
-    a[k] = (float)at[k];
+    a[k] = ff_f(at[k]);
+    ok &= a[k] >= pr.eps_a_mf;
+    rest = ff_sub(rest, at[k]);
   }
-  const double aN = 1.0 - s;
-  ok &= aN >= pr.eps_a + kAlphaMargin;
-  a[N - 1] = (float)aN;
+  a[N - 1] = ff_f(rest);
+  ok &= a[N - 1] >= pr.eps_a_mf;
   float S = 0.f, P = 0.f;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    S += a[k] * (float)f.inv_gm1[k];
-    P += a[k] * (float)f.gpinf_gm1[k];
+    S += a[k] * f.inv_gm1_f[k];
+    P += a[k] * f.gpinf_gm1_f[k];
   }
   const float iS = 1.f / S;
   const float t1 = (1.f + iS) * Vt[L::EN], t2 = P * iS;
@@ -181,34 +219,32 @@ __device__ __forceinline__ bool interp_screen32(const float* Vt, const double* a
 }
 
 // Flux limiter (Sec. 4.3.2): the high-order half-cell states W_i^+ and
-// W_{i+1}^- from the FP32 node states and the FP32 midpoint flux g32;
-// partial densities and rho e~ in FP32 with error bounds, volume fractions in
-// FP64 from the FP64 alpha slots (ai, aj: node volume fractions).
+// W_{i+1}^- from the FP32 node states and the FP32 midpoint flux g32 --
+// partial densities and rho e~ in FP32 with error bounds -- and their volume
+// fractions in float-float from the node values (ai, aj) and the alpha slots
+// (gm, gp); lam2 = 2 lambda as float-float.
 template <int N, int D, int DIR>
 __device__ __forceinline__ bool flux_screen32(const float* __restrict__ P32, int64_t nc, const Nodes6& nd,
-                                              const float* g32, const FluxPack<N, D>& G, const double* ai,
-                                              const double* aj, double lam, const DevFluid& f,
-                                              const DevParams& pr) {
+                                              const float* g32, const ff* gm, const ff* gp, const ff* ai,
+                                              const ff* aj, ff lam2, const DevFluid& f, const DevParams& pr) {
   using L = Lay<N, D>;
   using Q = P32Lay<N, D>;
   bool ok = true;
-  const double m2l = -2.0 * lam, p2l = 2.0 * lam;
-  // volume fractions of both half-cell states (the limiter's own expressions)
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
-    double s = 0.0;
+    ff rest{1.f, 0.f};
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) {
-      const double a = side == 0 ? ai[k] + m2l * G.gm[k] : aj[k] + p2l * G.gp[k];
-      ok &= a >= pr.eps_a + kAlphaMargin;
-      s += a;
+      const ff a = side == 0 ? ff_sub(ai[k], ff_mul(lam2, gm[k])) : ff_add(aj[k], ff_mul(lam2, gp[k]));
+      ok &= ff_f(a) >= pr.eps_a_mf;
+      rest = ff_sub(rest, a);
     }
-    ok &= 1.0 - s >= pr.eps_a + kAlphaMargin;
+    ok &= ff_f(rest) >= pr.eps_a_mf;
   }
-  const float s2 = (float)(2.0 * lam);
+  const float s2 = lam2.hi;
   float qmax = 0.f;
 #pragma unroll
-  for (int k = 0; k < N; ++k) qmax = fmaxf(qmax, fabsf((float)f.q[k]));
+  for (int k = 0; k < N; ++k) qmax = fmaxf(qmax, fabsf(f.q_f[k]));
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     const int64_t c = nd.c[2 + side];
@@ -224,7 +260,7 @@ __device__ __forceinline__ bool flux_screen32(const float* __restrict__ P32, int
       const float e = kScreenRel * (fabsf(w) + s2 * (fabsf(g32[k]) + fabsf(F)));
       ok &= h - e >= pr.eps_ar_f;
       rho += h;
-      rq += h * (float)f.q[k];
+      rq += h * f.q_f[k];
       erho += e;
     }
     // momentum and energy, and rho e~ = E - |rho u|^2 / (2 rho) - sum alpha_k rho_k q_k
@@ -291,14 +327,6 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
     }
   };
 
-  // FP64 volume fractions of nodes i, i+1
-  double ai[N > 1 ? N - 1 : 1], aj[N > 1 ? N - 1 : 1];
-#pragma unroll
-  for (int k = 0; k < N - 1; ++k) {
-    ai[k] = V[(L::AL + k) * nc + nd.c[2]];
-    aj[k] = V[(L::AL + k) * nc + nd.c[3]];
-  }
-
   FluxPack<N, D> G;
   if (pr.scheme == 1) {
     double Vi[M], Vj[M];
@@ -350,9 +378,13 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
         ++t_;
       }
     }
-    // volume fractions: increments of the identity fields on exact differences
-    // (FP32 value differences plus residue differences), added to the FP64 node values
-    double aL[N > 1 ? N - 1 : 1], aR[N > 1 ? N - 1 : 1];
+    // volume fractions (float-float): node values ai, aj from the value and
+    // residue planes, node differences dA[k][j] = alpha_j - alpha_i, and the
+    // WENO-IS increments of the identity fields (on FP32 differences) that give
+    // the midpoint values aL = ai + incL, aR = aj + incR
+    constexpr int NA = N > 1 ? N - 1 : 1;
+    ff ai[NA], aj[NA], dA[NA][6], at_L[NA], at_R[NA];
+    float incL[NA], incR[NA];
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) {
       float hi6[6], lo6[6];
@@ -361,11 +393,20 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
         hi6[j] = ld(L::AL + k, j);
         lo6[j] = ld(Q::ALO + k, j);
       }
+      ai[k] = ff{hi6[2], lo6[2]};
+      aj[k] = ff{hi6[3], lo6[3]};
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const ff dh = ff_sum(hi6[j], -hi6[2]);
+        dA[k][j] = ff_sum(dh.hi, dh.lo + (lo6[j] - lo6[2]));
+      }
       auto dl = [&](int j, int c) { return (hi6[j] - hi6[c]) + (lo6[j] - lo6[c]); };
-      aL[k] = ai[k] + (double)weno_increment(dl(0, 2), dl(1, 2), dl(3, 2), dl(4, 2), eps, lin);
-      aR[k] = aj[k] + (double)weno_increment(dl(5, 3), dl(4, 3), dl(2, 3), dl(1, 3), eps, lin);
-      UL[N + D + k] = (float)aL[k];
-      UR[N + D + k] = (float)aR[k];
+      incL[k] = weno_increment(dl(0, 2), dl(1, 2), dl(3, 2), dl(4, 2), eps, lin);
+      incR[k] = weno_increment(dl(5, 3), dl(4, 3), dl(2, 3), dl(1, 3), eps, lin);
+      at_L[k] = ff_add(ai[k], ff{incL[k], 0.f});
+      at_R[k] = ff_add(aj[k], ff{incR[k], 0.f});
+      UL[N + D + k] = ff_f(at_L[k]);
+      UR[N + D + k] = ff_f(at_R[k]);
     }
     PrimState<float, N, D> sl, sr;
     {
@@ -392,23 +433,49 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
         for (int k = 0; k < N - 1; ++k) Vt[L::AL + k] = U[N + D + k];
       }
     }
+    // midpoint volume fractions relative to node i (the upwind candidates of
+    // the alpha flux): dL = aL - alpha_i, dR = aR - alpha_i
+    ff dL[NA], dR[NA];
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+      dL[k] = ff{incL[k], 0.f};
+      dR[k] = ff_add(dA[k][3], ff{incR[k], 0.f});
+    }
     if (pr.limiters) {
-      if (!(pr.screen && interp_screen32<N, D>(sl.V, aL, f, pr))) {
-        double Vn[M];
+      // FP64 limiter where the screen cannot certify it; volume fractions it
+      // leaves unchanged keep their float-float values (so that the result
+      // does not depend on whether the screen ran)
+      if (!(pr.screen && interp_screen32<N, D>(sl.V, at_L, f, pr))) {
+        double Vn[M], a0[NA], a1[NA];
         load_node(2, Vn, nullptr);
-        interp_limit32<N, D>(sl.V, aL, Vn, AUX[2 * nc + nd.c[2]], f, pr);
+#pragma unroll
+        for (int k = 0; k < N - 1; ++k) a0[k] = a1[k] = Vn[L::AL + k] + (double)incL[k];
+        interp_limit32<N, D>(sl.V, a1, Vn, AUX[2 * nc + nd.c[2]], f, pr);
+#pragma unroll
+        for (int k = 0; k < N - 1; ++k) {
+          if (a1[k] != a0[k])
+            dL[k] = ff_of(a1[k] - Vn[L::AL + k]);
+          else
+            sl.V[L::AL + k] = UL[N + D + k];
+        }
       }
-      if (!(pr.screen && interp_screen32<N, D>(sr.V, aR, f, pr))) {
-        double Vn[M];
+      if (!(pr.screen && interp_screen32<N, D>(sr.V, at_R, f, pr))) {
+        double Vn[M], a0[NA], a1[NA];
         load_node(3, Vn, nullptr);
-        interp_limit32<N, D>(sr.V, aR, Vn, AUX[2 * nc + nd.c[3]], f, pr);
+#pragma unroll
+        for (int k = 0; k < N - 1; ++k) a0[k] = a1[k] = Vn[L::AL + k] + (double)incR[k];
+        interp_limit32<N, D>(sr.V, a1, Vn, AUX[2 * nc + nd.c[3]], f, pr);
+#pragma unroll
+        for (int k = 0; k < N - 1; ++k) {
+          if (a1[k] != a0[k])
+            dR[k] = ff_of(a1[k] - V[(L::AL + k) * nc + nd.c[2]]);
+          else
+            sr.V[L::AL + k] = UR[N + D + k];
+        }
       }
     }
     float Gt[M];
     const float ut = hllc<float, N, D, DIR>(f, sl, sr, Gt);
-    double Gt_a[N > 1 ? N - 1 : 1];
-#pragma unroll
-    for (int k = 0; k < N - 1; ++k) Gt_a[k] = alpha_flux(aL[k], aR[k], (double)ut);
     constexpr float psi = 256.0f / 175.0f;
     constexpr float a1 = 101.0f / 420.0f, a2 = 1.0f / 105.0f, a3 = 1.0f / 2100.0f;
     float sig = 0.f;
@@ -430,7 +497,7 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
     }
     const float one_m = 1.f - sig;
     const float uhcs = psi * ut - a1 * (u6[2] + u6[3]) + a2 * (u6[1] + u6[4]) - a3 * (u6[0] + u6[5]);
-    const double uhat = (double)(sig * ut + one_m * uhcs);
+    const float uhat = sig * ut + one_m * uhcs;
     float g32[L::NC];
 #pragma unroll
     for (int m = 0; m < L::NC; ++m) {
@@ -451,22 +518,32 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
       g32[m] = sig * Gt[m] + one_m * ghcs;
       G.Gc[m] = (double)g32[m];
     }
-    // alpha slots in FP64: node fluxes alpha_j u_j, HCS, blend, quasi-conservative form
+    // alpha slots, quasi-conservative form (Eq. G_pm): with alpha_j = alpha_i +
+    // dA_j, the blended HCS alpha flux is alpha_i u^ + Rh, where u^ is the blended
+    // HCS velocity and Rh the same combination of dA_j u_j and of the upwind
+    // midpoint difference times u~; so G^- = Rh and G^+ = Rh - u^ dA_{i+1}
+    // exactly, and both are formed in float-float (a uniform alpha gives zero).
+    ff gmf[NA], gpf[NA];
     {
-      constexpr double dpsi = 256.0 / 175.0, d1 = 101.0 / 420.0, d2 = 1.0 / 105.0, d3 = 1.0 / 2100.0;
-      const double sg = (double)sig, om = 1.0 - sg;
+      const ff PSI = HRM_FF(256.0 / 175.0), C1 = HRM_FF(101.0 / 420.0), C2 = HRM_FF(1.0 / 105.0),
+               C3 = HRM_FF(1.0 / 2100.0);
+      const ff om = ff_sum(1.f, -sig);
 #pragma unroll
       for (int k = 0; k < N - 1; ++k) {
-        double gn[6];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) gn[j] = V[(L::AL + k) * nc + nd.c[j]] * (double)u6[j];
-        const double ghcs = dpsi * Gt_a[k] - d1 * (gn[2] + gn[3]) + d2 * (gn[1] + gn[4]) - d3 * (gn[0] + gn[5]);
-        const double gh = sg * Gt_a[k] + om * ghcs;
-        G.gm[k] = gh - uhat * ai[k];
-        G.gp[k] = gh - uhat * aj[k];
+        const ff dup = ut > 0.f ? dL[k] : (ut < 0.f ? dR[k] : ff{0.f, 0.f});
+        const ff A = ff_mulf(dup, ut);
+        ff B = ff_mul(PSI, A);
+        B = ff_sub(B, ff_mul(C1, ff_mulf(dA[k][3], u6[3])));
+        B = ff_add(B, ff_mul(C2, ff_add(ff_mulf(dA[k][1], u6[1]), ff_mulf(dA[k][4], u6[4]))));
+        B = ff_sub(B, ff_mul(C3, ff_add(ff_mulf(dA[k][0], u6[0]), ff_mulf(dA[k][5], u6[5]))));
+        gmf[k] = ff_add(ff_mulf(A, sig), ff_mul(om, B));
+        gpf[k] = ff_sub(gmf[k], ff_mulf(dA[k][3], uhat));
+        G.gm[k] = ff_d(gmf[k]);
+        G.gp[k] = ff_d(gpf[k]);
       }
     }
-    if (pr.limiters && !(pr.screen && flux_screen32<N, D, DIR>(P32, nc, nd, g32, G, ai, aj, lam, f, pr))) {
+    if (pr.limiters &&
+        !(pr.screen && flux_screen32<N, D, DIR>(P32, nc, nd, g32, gmf, gpf, ai, aj, ff_of(2.0 * lam), f, pr))) {
       double Vi[M], Vj[M], Wi[M], Wj[M];
       load_node(2, Vi, Wi);
       load_node(3, Vj, Wj);

@@ -80,8 +80,8 @@ inline void fill_screen(DevParams& d, int requested) {
   d.eps_ar_f = float_up(d.eps_ar);
   d.eps_rhoe_f = float_up(d.eps_rhoe);
   d.hs_rc2_f = float_up(d.hs_rc2);
+  d.eps_a_mf = float_up(d.eps_a + 1e-13);
   d.pad_ = 0;
-  d.pad2_ = 0.f;
 }
 
 }  // namespace hrm

@@ -192,6 +192,7 @@ extern "C" hrm_status hrm_dt_noalloc(int32_t nspecies, int32_t ndim, const int64
     f.gamma[k] = gamma[k];
   }
   f.liq = liq < 0 ? 0 : liq;
+  fill_fluid_f(f);
   unsigned long long* partials = nullptr;
   if (partials_address(&partials) != HRM_OK) {
     hrm::set_thread_error("hrm_dt_noalloc: scratch address lookup failed");
