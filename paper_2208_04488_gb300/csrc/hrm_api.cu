@@ -161,8 +161,12 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
                   int count, bool first) {
   int k = 0;
   float* p32 = p32_target(c);
-  traced(c, s, HRM_KERNEL_PRIM,
-         [&] { c->ck->prim(Wsrc, c->V, c->AUX, p32, r32_target(c), c->dg, c->fl, c->st, first ? 1 : 0, s); });
+  traced(c, s, HRM_KERNEL_PRIM, [&] {
+    if (c->params.precision == HRM_FP32)
+      launch_prim32(c->N, c->D, Wsrc, c->P32, r32_target(c), c->dg, c->fl, c->st, first ? 1 : 0, s);
+    else
+      c->ck->prim(Wsrc, c->V, c->AUX, p32, r32_target(c), c->dg, c->fl, c->st, first ? 1 : 0, s);
+  });
   ++k;
   if (first) {
     traced(c, s, HRM_KERNEL_FINALIZE, [&] { launch_finalize(c->st, c->dg, c->D, c->params.cfl, 0, s); });
@@ -513,7 +517,10 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
   hrm_status s = cuda_check(c, cudaMemcpyAsync(c->st->lam, l3, sizeof l3, cudaMemcpyHostToDevice, c->stream),
                             "copy lambda");
   if (s) return s;
-  c->ck->prim(c->Wn, c->V, c->AUX, p32_target(c), r32_target(c), c->dg, c->fl, c->st, 0, c->stream);
+  if (c->params.precision == HRM_FP32)
+    launch_prim32(c->N, c->D, c->Wn, c->P32, r32_target(c), c->dg, c->fl, c->st, 0, c->stream);
+  else
+    c->ck->prim(c->Wn, c->V, c->AUX, p32_target(c), r32_target(c), c->dg, c->fl, c->st, 0, c->stream);
   for (int d = 0; d < c->D; ++d) {
     if (c->params.learned == 1) {
       launch_gate(c->N, c->D, d, c->P32, c->R32, c->dg, c->blob, gate_logit_threshold(c), c->gate[d],

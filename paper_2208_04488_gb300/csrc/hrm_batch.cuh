@@ -64,6 +64,31 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
   }
 }
 
+// FP32 planes (and CFL maxima) of every instance for the precision form.
+template <int D>
+__global__ void __launch_bounds__(kBatchMaxThreads)
+    k_batch_prim32(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
+                   int tau) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const WorkItem w = items[it];
+    const BatchInst& I = insts[w.inst];
+    double s[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) s[d] = 0.0;
+    const double* W = pick(I, src);
+    for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
+      double sc[D];
+      if (I.N == 2)
+        prim32_body<2, D>(c, W, I.P32, nullptr, I.g, I.f, sc);
+      else
+        prim32_body<3, D>(c, W, I.P32, nullptr, I.g, I.f, sc);
+#pragma unroll
+      for (int d = 0; d < D; ++d) s[d] = (sc[d] != sc[d]) ? sc[d] : (sc[d] > s[d] ? sc[d] : s[d]);
+    }
+    if (tau) block_tau_max<D>(s, I.st->tau_bits);
+  }
+}
+
 // Midpoints of direction DIR of every instance; FP64 (bit-exact) or precision form.
 template <int D, int DIR, bool FP32>
 __global__ void __launch_bounds__(kBatchMaxThreads)
@@ -122,6 +147,7 @@ struct BatchLaunch {
 
 void batch_prim_d2(const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int fp32, int tau,
                    cudaStream_t);
+void batch_prim32_d2(const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int tau, cudaStream_t);
 void batch_finalize(const BatchInst*, int ninst, int D, double cfl, cudaStream_t);
 void batch_face64_d2(int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
                      const DevParams&, cudaStream_t);

@@ -1,5 +1,5 @@
-// Batched-form kernels for D = 2 of the precision form: FP32-bulk midpoints
-// and the fast update (built with FMA contraction).
+// Batched-form kernels for D = 2 of the precision form: FP32 planes, FP32-bulk
+// midpoints and the fast update (built with FMA contraction).
 #include "hrm_batch.cuh"
 
 namespace hrm {
@@ -10,6 +10,11 @@ void batch_face32_d2(int dir, const BatchLaunch& L, const BatchInst* insts, cons
     k_batch_face<2, 0, true><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
   else
     k_batch_face<2, 1, true><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+}
+
+void batch_prim32_d2(const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems, int src, int tau,
+                     cudaStream_t s) {
+  k_batch_prim32<2><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, tau);
 }
 
 void batch_update32_d2(const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems, int src,

@@ -114,7 +114,10 @@ int enqueue_stage(hrm_batch* b, cudaStream_t s, int src, int dst, double a, doub
                        b->shape.cell_threads};
   const BatchLaunch lf{b->sms * b->shape.blocks_per_sm, b->shape.face_threads};
   int k = 0;
-  batch_prim_d2(lc, b->d_insts, b->d_items, b->n_cell_items, src, fp32 ? 1 : 0, first ? 1 : 0, s);
+  if (fp32)
+    batch_prim32_d2(lc, b->d_insts, b->d_items, b->n_cell_items, src, first ? 1 : 0, s);
+  else
+    batch_prim_d2(lc, b->d_insts, b->d_items, b->n_cell_items, src, 0, first ? 1 : 0, s);
   ++k;
   if (first) {
     batch_finalize(b->d_insts, b->ninst, b->D, b->params.cfl, s);

@@ -4,7 +4,7 @@
 // everything downstream (flux difference, RK combination, relaxation) in FP64.
 #pragma once
 
-#include "hrm_kernels.cuh"
+#include "hrm_cell.cuh"
 
 namespace hrm {
 
@@ -288,6 +288,98 @@ __device__ __forceinline__ bool flux_screen32(const float* __restrict__ P32, int
   return ok;
 }
 
+// ---------------------------------------------------------------- per-cell planes
+// Primitive kernel of the precision form: writes only the FP32 planes the
+// midpoint kernel reads (P32Lay) -- the stored values, u_d, p, c, rho, rho c^2,
+// the volume-fraction rounding residues -- and, for the learned gate, the
+// residues of rho, u_d and p (R32); with `tau`, the CFL maxima. FP64 only where
+// the EOS cancels: the mixture constants S, P, the energy sums and the pressure
+// numerator rho e~ - P (E ~ P ~ 1e9 against p ~ 1e5 for a stiffened gas); the
+// division by S, the velocities, rho c^2 and c in FP32 (their FP32 values are
+// all the midpoint kernel uses). The node states the FP64 limiters need where a
+// screen fails are evaluated from W there.
+template <int N, int D>
+__device__ __forceinline__ void prim32_body(int64_t c, const double* __restrict__ W, float* __restrict__ P32,
+                                            float* __restrict__ R32, const DevGrid& g, const DevFluid& f,
+                                            double* s) {
+  using L = Lay<N, D>;
+  using Q = P32Lay<N, D>;
+  constexpr int M = L::M;
+  const int64_t nc = g.ncells;
+  double w[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) w[m] = W[m * nc + c];
+  double rho = 0.0, sa = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) rho += w[k];
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) sa += w[L::AL + k];
+  const double aN = 1.0 - sa;
+  double S = 0.0, P = 0.0, rq = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double a = k < N - 1 ? w[L::AL + k] : aN;
+    S += a * f.inv_gm1[k];
+    P += a * f.gpinf_gm1[k];
+    rq += w[k] * f.q[k];
+  }
+  const double irho = 1.0 / rho;
+  double m2 = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) m2 += w[L::MOM + d] * w[L::MOM + d];
+  const double num = ((w[L::EN] - rq) - 0.5 * m2 * irho) - P;  // rho e~ - P
+  const float rho32 = (float)rho, irho32 = (float)irho;
+  const float S32 = (float)S, iS = 1.f / S32;
+  const float p = (float)num * iS;
+  const float Pf = (float)P;
+  const float rc2 = (1.f + iS) * p + Pf * iS;
+  const float cs = sqrtf(rc2 * irho32);
+  float u[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) u[d] = (float)w[L::MOM + d] * irho32;
+#pragma unroll
+  for (int k = 0; k < N; ++k) P32[k * nc + c] = (float)w[k];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    P32[(L::MOM + d) * nc + c] = u[d];
+    P32[(Q::MOM + d) * nc + c] = (float)w[L::MOM + d];
+  }
+  P32[L::EN * nc + c] = p;
+  P32[Q::C * nc + c] = cs;
+  P32[Q::RHO * nc + c] = rho32;
+  P32[Q::RC2 * nc + c] = rc2;
+  P32[Q::E * nc + c] = (float)w[L::EN];
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) {
+    const double a = w[L::AL + k];
+    const float ah = (float)a;
+    P32[(L::AL + k) * nc + c] = ah;
+    P32[(Q::ALO + k) * nc + c] = (float)(a - (double)ah);
+  }
+  if (R32) {
+    // residues: rho exactly; u_d and p from the FP64 remainders of m - u rho and num - p S
+    R32[c] = (float)(rho - (double)rho32);
+#pragma unroll
+    for (int d = 0; d < D; ++d) R32[(1 + d) * nc + c] = (float)(w[L::MOM + d] - (double)u[d] * rho) * irho32;
+    R32[(1 + D) * nc + c] = (float)(num - (double)p * S) * iS;
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) s[d] = (double)((fabsf(u[d]) + cs) * (float)g.inv_dx[d]);
+}
+
+template <int N, int D>
+__global__ void __launch_bounds__(kCellThreads)
+    k_prim32(const double* __restrict__ W, float* __restrict__ P32, float* __restrict__ R32, DevGrid g, DevFluid f,
+             StepState* st, int tau) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double s[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) s[d] = 0.0;
+  if (c < g.ncells) prim32_body<N, D>(c, W, P32, R32, g, f, s);
+  if (!tau) return;
+  block_tau_max<D>(s, st->tau_bits);
+}
+
 template <int N, int D, int DIR>
 __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const double* __restrict__ W,
                                             const double* __restrict__ V, const double* __restrict__ AUX,
@@ -300,12 +392,17 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
   const int64_t nc = g.ncells;
   const int64_t nf = face_count<DIR>(g);
   auto ld = [&](int plane, int j) -> float { return P32[(int64_t)plane * nc + nd.c[j]]; };
-  auto load_node = [&](int j, double* Vn, double* Wn) {
+  // node state j in FP64 from W (the FP64 limiters' inputs where a screen fails);
+  // returns rho c^2
+  auto load_node = [&](int j, double* Vn, double* Wn) -> double {
+    double w[M], rho, cs, rc2;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      Vn[m] = V[m * nc + nd.c[j]];
-      if (Wn) Wn[m] = W[m * nc + nd.c[j]];
+      w[m] = W[m * nc + nd.c[j]];
+      if (Wn) Wn[m] = w[m];
     }
+    cell_prim<N, D>(w, f, Vn, rho, cs, rc2);
+    return rc2;
   };
   // first-order HLLC in FP32 from the node states, alpha slots in FP64
   auto first_order = [&](const double* Vi, const double* Vj, FluxPack<N, D>& H) {
@@ -447,10 +544,10 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
       // does not depend on whether the screen ran)
       if (!(pr.screen && interp_screen32<N, D>(sl.V, at_L, f, pr))) {
         double Vn[M], a0[NA], a1[NA];
-        load_node(2, Vn, nullptr);
+        const double rc2n = load_node(2, Vn, nullptr);
 #pragma unroll
         for (int k = 0; k < N - 1; ++k) a0[k] = a1[k] = Vn[L::AL + k] + (double)incL[k];
-        interp_limit32<N, D>(sl.V, a1, Vn, AUX[2 * nc + nd.c[2]], f, pr);
+        interp_limit32<N, D>(sl.V, a1, Vn, rc2n, f, pr);
 #pragma unroll
         for (int k = 0; k < N - 1; ++k) {
           if (a1[k] != a0[k])
@@ -461,14 +558,14 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
       }
       if (!(pr.screen && interp_screen32<N, D>(sr.V, at_R, f, pr))) {
         double Vn[M], a0[NA], a1[NA];
-        load_node(3, Vn, nullptr);
+        const double rc2n = load_node(3, Vn, nullptr);
 #pragma unroll
         for (int k = 0; k < N - 1; ++k) a0[k] = a1[k] = Vn[L::AL + k] + (double)incR[k];
-        interp_limit32<N, D>(sr.V, a1, Vn, AUX[2 * nc + nd.c[3]], f, pr);
+        interp_limit32<N, D>(sr.V, a1, Vn, rc2n, f, pr);
 #pragma unroll
         for (int k = 0; k < N - 1; ++k) {
           if (a1[k] != a0[k])
-            dR[k] = ff_of(a1[k] - V[(L::AL + k) * nc + nd.c[2]]);
+            dR[k] = ff_of(a1[k] - W[(L::AL + k) * nc + nd.c[2]]);
           else
             sr.V[L::AL + k] = UR[N + D + k];
         }

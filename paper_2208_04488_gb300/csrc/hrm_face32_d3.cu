@@ -43,4 +43,13 @@ void face32_d3(int N, int dir, const double* W, const double* V, const double* A
   }
 }
 
+void prim32_d3(int N, const double* W, float* P32, float* R32, const DevGrid& g, const DevFluid& f, StepState* st,
+               int tau, cudaStream_t s) {
+  const unsigned gr = grid_for(g.ncells, kCellThreads);
+  if (N == 2)
+    k_prim32<2, kD><<<gr, kCellThreads, 0, s>>>(W, P32, R32, g, f, st, tau);
+  else if (N == 3)
+    k_prim32<3, kD><<<gr, kCellThreads, 0, s>>>(W, P32, R32, g, f, st, tau);
+}
+
 }  // namespace hrm

@@ -547,7 +547,18 @@ __device__ __forceinline__ void relax_cell(double* W, const DevFluid& f, double*
   const double inv_rho = FAST ? 1.0 / rho : 0.0;
 #pragma unroll
   for (int k = 0; k < N; ++k) Y[k] = FAST ? W[k] * inv_rho : W[k] / rho;
-  const double re = rhoe_tilde<N, D>(W, f);
+  double re;
+  if (FAST) {
+    // rho e~ with the reciprocal of rho (rhoe_tilde divides)
+    double kin = 0.0, rq = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) kin += W[L::MOM + d] * W[L::MOM + d];
+#pragma unroll
+    for (int k = 0; k < N; ++k) rq += W[k] * f.q[k];
+    re = W[L::EN] - 0.5 * kin * inv_rho - rq;
+  } else {
+    re = rhoe_tilde<N, D>(W, f);
+  }
   double cvb = 0.0, cpb = 0.0;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
@@ -560,16 +571,26 @@ __device__ __forceinline__ void relax_cell(double* W, const DevFluid& f, double*
   const double Cp = -(re * pinf1 * ((cpb - cvb) - Yl * R1));
   const double sq = sqrt(Bp * Bp - 4.0 * Ap * Cp);
   const double ps = (Bp > 0.0) ? (-2.0 * Cp) / (Bp + sq) : (sq - Bp) / (2.0 * Ap);
+  if (FAST) {
+    // one reciprocal per distinct p* + p_inf (the stiffened gas and the ideal gases)
+    const double inv_pl = 1.0 / (ps + pinf1), inv_p = 1.0 / ps;
+    const double den = Yl * (ps + f.gamma[l] * pinf1) * f.cv[l] * inv_pl + cvb - Yl * f.cv[l];
+    const double Ts = re * inv_rho / den;
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k)  // alpha_k = rho Y_k / rho_k(p*, T*)
+      W[L::AL + k] = W[k] * (f.Rg[k] * Ts) * (k == l ? inv_pl : (f.pinf[k] == 0.0 ? inv_p : 1.0 / (ps + f.pinf[k])));
+    if (pT) {
+      pT[0] = ps;
+      pT[1] = Ts;
+    }
+    return;
+  }
   const double den = Yl * (ps + f.gamma[l] * pinf1) * f.cv[l] / (ps + pinf1) + cvb - Yl * f.cv[l];
   const double Ts = (re / rho) / den;
 #pragma unroll
   for (int k = 0; k < N - 1; ++k) {
-    if (FAST) {
-      W[L::AL + k] = W[k] * (f.Rg[k] * Ts) / (ps + f.pinf[k]);  // alpha_k = rho Y_k / rho_k(p*, T*)
-    } else {
-      const double rhok = (ps + f.pinf[k]) / (f.Rg[k] * Ts);
-      W[L::AL + k] = W[k] / rhok;
-    }
+    const double rhok = (ps + f.pinf[k]) / (f.Rg[k] * Ts);
+    W[L::AL + k] = W[k] / rhok;
   }
   if (pT) {
     pT[0] = ps;

@@ -60,6 +60,20 @@ void face32_d3(int N, int dir, const double* W, const double* V, const double* A
                const DevGrid&, const DevFluid&, const DevParams&, const StepState*, const uint8_t* gate,
                cudaStream_t);
 
+// Primitive kernel of the precision form (FP32 planes only; hrm_face32_dD.cu).
+void prim32_d1(int N, const double* W, float* P32, float* R32, const DevGrid&, const DevFluid&, StepState*, int tau,
+               cudaStream_t);
+void prim32_d2(int N, const double* W, float* P32, float* R32, const DevGrid&, const DevFluid&, StepState*, int tau,
+               cudaStream_t);
+void prim32_d3(int N, const double* W, float* P32, float* R32, const DevGrid&, const DevFluid&, StepState*, int tau,
+               cudaStream_t);
+inline void launch_prim32(int N, int D, const double* W, float* P32, float* R32, const DevGrid& g, const DevFluid& f,
+                          StepState* st, int tau, cudaStream_t s) {
+  if (D == 1) prim32_d1(N, W, P32, R32, g, f, st, tau, s);
+  if (D == 2) prim32_d2(N, W, P32, R32, g, f, st, tau, s);
+  if (D == 3) prim32_d3(N, W, P32, R32, g, f, st, tau, s);
+}
+
 void launch_finalize(StepState* st, const DevGrid& g, int D, double cfl, int mode, cudaStream_t s);
 void launch_set_dt(StepState* st, double dt, cudaStream_t s);
 
