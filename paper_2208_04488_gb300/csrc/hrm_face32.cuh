@@ -662,7 +662,7 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
 }
 
 template <int N, int D, int DIR>
-__global__ void __launch_bounds__(kFaceThreads)
+__global__ void __launch_bounds__(kFaceThreads, 3)
     k_face32(const double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ AUX,
              const float* __restrict__ P32, double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr,
              const StepState* __restrict__ st, const uint8_t* __restrict__ gate) {
