@@ -154,7 +154,23 @@ float* p32_target(hrm_ctx* c) {
 
 float* r32_target(hrm_ctx* c) { return c->params.learned == 1 ? c->R32 : nullptr; }
 
-const uint8_t* gate_of(const hrm_ctx* c, int d) { return c->params.learned ? c->gate[d] : nullptr; }
+// The gate of direction d's sweep: fixed bytes (learned 2, and learned 1 in the
+// FP64 form after the gate kernel), or the detector inside the FP32 sweep.
+GateArgs gate_of(const hrm_ctx* c, int d) {
+  GateArgs g;
+  if (c->params.learned == 1 && c->params.precision == HRM_FP32) {
+    g.blob = c->blob;
+    g.R32 = c->R32;
+    g.out = c->gate[d];
+    g.zthr = gate_logit_threshold(c);
+  } else if (c->params.learned) {
+    g.fixed = c->gate[d];
+  }
+  return g;
+}
+
+// The FP64 form runs the detector as its own kernel before each sweep.
+bool separate_gate(const hrm_ctx* c) { return c->params.learned == 1 && c->params.precision != HRM_FP32; }
 
 // One RK stage: primitives of Wsrc, (gates,) midpoint fluxes, update into Wout.
 int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, double a, double b, int relax,
@@ -173,7 +189,7 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
     ++k;
   }
   for (int d = 0; d < c->D; ++d) {
-    if (c->params.learned == 1) {
+    if (separate_gate(c)) {
       traced(c, s, HRM_KERNEL_GATE, [&] {
         launch_gate(c->N, c->D, d, c->P32, c->R32, c->dg, c->blob, gate_logit_threshold(c), c->gate[d],
                     c->gate_blocks, s);
@@ -522,7 +538,7 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
   else
     c->ck->prim(c->Wn, c->V, c->AUX, p32_target(c), r32_target(c), c->dg, c->fl, c->st, 0, c->stream);
   for (int d = 0; d < c->D; ++d) {
-    if (c->params.learned == 1) {
+    if (separate_gate(c)) {
       launch_gate(c->N, c->D, d, c->P32, c->R32, c->dg, c->blob, gate_logit_threshold(c), c->gate[d],
                   c->gate_blocks, c->stream);
       ++c->launches;

@@ -1,6 +1,6 @@
 // FP32-bulk per-midpoint kernels for D = 3, N = 2..3 species (the precision
 // form: interpolation, Riemann fluxes and HCS in FP32; limiter theta in FP64).
-#include "hrm_face32.cuh"
+#include "hrm_learned.cuh"
 #include "hrm_launch.h"
 
 namespace hrm {
@@ -10,10 +10,15 @@ constexpr int kD = 3;
 
 template <int N, int DIR>
 void launch(const double* W, const double* V, const double* AUX, const float* P32, double* out, const DevGrid& g,
-            const DevFluid& f, const DevParams& p, const StepState* st, const uint8_t* gate, cudaStream_t s) {
+            const DevFluid& f, const DevParams& p, const StepState* st, const GateArgs& gate, cudaStream_t s) {
   if constexpr (DIR < kD) {
     const long long nf = (g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
-    k_face32<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, P32, out, g, f, p, st, gate);
+    if (gate.blob)
+      k_face32_learned<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(
+          W, P32, gate.R32, out, g, f, p, st, gate.blob, gate.zthr, gate.out);
+    else
+      k_face32<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, P32, out, g, f, p, st,
+                                                                                gate.fixed);
   }
 }
 
@@ -30,7 +35,7 @@ void update32_d3(int N, const double* Wn, const double* Wsrc, double* Wout, cons
 }
 
 void face32_d3(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
-               const DevGrid& g, const DevFluid& f, const DevParams& p, const StepState* st, const uint8_t* gate,
+               const DevGrid& g, const DevFluid& f, const DevParams& p, const StepState* st, const GateArgs& gate,
                cudaStream_t s) {
   if (N == 2) {
     if (dir == 0) launch<2, 0>(W, V, AUX, P32, out, g, f, p, st, gate, s);

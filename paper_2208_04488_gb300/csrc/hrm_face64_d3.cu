@@ -11,7 +11,7 @@ constexpr int kD = 3;
 
 template <int N, int DIR>
 void face_l(int precision, const double* W, const double* V, const double* AUX, const float* P32, double* out,
-            const DevGrid& g, const DevFluid& f, const DevParams& p, const StepState* st, const uint8_t* gate,
+            const DevGrid& g, const DevFluid& f, const DevParams& p, const StepState* st, const GateArgs& gate,
             cudaStream_t s) {
   if constexpr (DIR < kD) {
     if (precision == 1) {
@@ -19,7 +19,7 @@ void face_l(int precision, const double* W, const double* V, const double* AUX, 
       return;
     }
     const long long nf = (g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
-    k_face<double, N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, out, g, f, p, st, gate);
+    k_face<double, N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, out, g, f, p, st, gate.fixed);
   }
 }
 

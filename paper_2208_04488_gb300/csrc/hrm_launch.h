@@ -22,12 +22,27 @@ struct CellKernels {
   void (*admiss)(const double* W, const DevGrid&, const DevFluid&, StepState*, cudaStream_t);
 };
 
+namespace mlp {
+struct GateBlob;
+}
+
+// Smoothness gate of a midpoint sweep: `fixed` (nullable) one byte per
+// midpoint, nonzero = linear WENO weights there; or, for the precision form,
+// the detector itself (`blob`, logit threshold `zthr`, residue planes `R32`)
+// evaluated inside the sweep, which writes its decisions to `out`.
+struct GateArgs {
+  const uint8_t* fixed = nullptr;
+  const mlp::GateBlob* blob = nullptr;
+  const float* R32 = nullptr;
+  uint8_t* out = nullptr;
+  float zthr = 0.f;
+};
+
 struct FaceKernels {
   // precision: 0 FP64, 1 FP32 bulk
-  // gate (nullable): one byte per midpoint, nonzero = linear WENO weights there
   void (*face[3])(int precision, const double* W, const double* V, const double* AUX, const float* P32,
                   double* out, const DevGrid&, const DevFluid&, const DevParams&, const StepState*,
-                  const uint8_t* gate, cudaStream_t);
+                  const GateArgs& gate, cudaStream_t);
   // mode 0: RK combination, mode 1: write the RHS; fast: precision-form variant
   void (*update)(int mode, int fast, const double* Wn, const double* Wsrc, double* Wout, const double* F0,
                  const double* F1, const double* F2, const DevGrid&, const DevFluid&, StepState*, double a,
@@ -45,19 +60,19 @@ void update32_d1(int N, const double* Wn, const double* Wsrc, double* Wout, cons
                  const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
                  int count, cudaStream_t);
 void face32_d1(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
-               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, const uint8_t* gate,
+               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, const GateArgs& gate,
                cudaStream_t);
 void update32_d2(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
                  const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
                  int count, cudaStream_t);
 void face32_d2(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
-               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, const uint8_t* gate,
+               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, const GateArgs& gate,
                cudaStream_t);
 void update32_d3(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
                  const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
                  int count, cudaStream_t);
 void face32_d3(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,
-               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, const uint8_t* gate,
+               const DevGrid&, const DevFluid&, const DevParams&, const StepState*, const GateArgs& gate,
                cudaStream_t);
 
 // Primitive kernel of the precision form (FP32 planes only; hrm_face32_dD.cu).

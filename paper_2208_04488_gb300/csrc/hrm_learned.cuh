@@ -187,4 +187,45 @@ __device__ __forceinline__ void store_row(__nv_bfloat16* row, const float (&x)[k
 }
 
 }  // namespace mlp
+
+// Precision-form midpoint sweep with the detector evaluated in the same
+// kernel: each warp forms its 32 stencils' features, runs the network on the
+// tensor cores, records the decisions in gate_out and then computes its
+// midpoints with the linear weights where gated. All lanes take part in the
+// network even past the last midpoint.
+template <int N, int D, int DIR>
+__global__ void __launch_bounds__(kFaceThreads, 3)
+    k_face32_learned(const double* __restrict__ W, const float* __restrict__ P32, const float* __restrict__ R32,
+                     double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr, const StepState* __restrict__ st,
+                     const mlp::GateBlob* __restrict__ blob, float zthr, uint8_t* __restrict__ gate_out) {
+  __shared__ __align__(16) mlp::GateBlob Wb;
+  __shared__ __align__(16) __nv_bfloat16 X[kFaceThreads / 32][32][mlp::kRow];
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(blob);
+    uint4* dst = reinterpret_cast<uint4*>(&Wb);
+    for (int i = threadIdx.x; i < (int)(sizeof(mlp::GateBlob) / 16); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  Nodes6 nd;
+  const bool ok = face_nodes<DIR>(g, t, nd);
+  bool lin;
+  {
+    float x[mlp::kIn];
+    if (ok) {
+      mlp::stencil_features<N, D, DIR>(nd, P32, R32, g.ncells, x);
+    } else {
+#pragma unroll
+      for (int k = 0; k < mlp::kIn; ++k) x[k] = 0.f;
+    }
+    mlp::store_row(X[warp][lane], x);
+    __syncwarp();
+    lin = mlp::warp_logit(Wb, X[warp], lane) > zthr;
+  }
+  if (!ok) return;
+  gate_out[t] = lin ? 1 : 0;
+  face32_body<N, D, DIR>(t, nd, W, nullptr, nullptr, P32, out, g, f, pr, st->lam[DIR], lin);
+}
+
 }  // namespace hrm
