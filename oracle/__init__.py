@@ -28,23 +28,35 @@ _LOCK = threading.Lock()
 MAXN = 4
 
 
-def _lib_path(count: bool) -> str:
-    return os.path.join(_BUILD, "liboracle_count.so" if count else "liboracle.so")
+def _lib_path(count) -> str:
+    name = {False: "liboracle.so", True: "liboracle_count.so", "omp": "liboracle_omp.so"}[count]
+    return os.path.join(_BUILD, name)
 
 
 def build(force: bool = False) -> None:
-    """Compile both oracle shared libraries with gcc (seconds)."""
+    """Compile the oracle shared libraries with gcc (seconds): serial, counting,
+    and (where the compiler has OpenMP) the multi-threaded build."""
     os.makedirs(_BUILD, exist_ok=True)
-    for count in (False, True):
+    for count in (False, True, "omp"):
         out = _lib_path(count)
         if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
             continue
         cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                "-shared", _SRC, "-o", out + ".tmp"]
-        if count:
+        if count is True:
             cmd.insert(1, "-DOR_COUNT")
-        subprocess.run(cmd, check=True)
+        if count == "omp":
+            cmd[1:1] = ["-DOR_OMP", "-fopenmp"]
+            if subprocess.run(cmd, capture_output=True).returncode != 0:
+                continue  # no OpenMP: the serial build serves
+        else:
+            subprocess.run(cmd, check=True)
         os.replace(out + ".tmp", out)
+
+
+def has_omp() -> bool:
+    build()
+    return os.path.exists(_lib_path("omp"))
 
 
 class Fluid(ctypes.Structure):
@@ -120,9 +132,13 @@ def lib(count: bool = False):
         L.or_faces_flops_gated.argtypes = [P(Fluid), P(Params), P(Grid), _DP, _DP, ctypes.c_int, ctypes.c_int,
                                            _DP]
         L.or_faces_flops_gated.restype = ctypes.c_int64
-        if count:
+        if count is True:
             L.or_count_reset.argtypes = []
             L.or_count_get.argtypes = [P(ctypes.c_ulonglong)]
+        L.or_step_exact.argtypes = [P(Fluid), P(Params), P(Grid), _DP, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_double, _DP]
+        L.or_threads.argtypes = []
+        L.or_threads.restype = ctypes.c_int
         _libs[count] = L
         return L
 
@@ -304,9 +320,15 @@ def lambdas(f: Fluid, g: Grid, W, dt_):
     return lam
 
 
-def step(f: Fluid, p: Params, g: Grid, W, dt_, nsteps=1, count=False, gates=None):
+def threads(omp: bool = False) -> int:
+    """Host threads the oracle's sweeps use (the OpenMP build: all available)."""
+    return int(lib("omp" if omp and has_omp() else False).or_threads())
+
+
+def step(f: Fluid, p: Params, g: Grid, W, dt_, nsteps=1, count=False, gates=None, omp=False):
+    """nsteps steps of size dt_. omp: the multi-threaded build (same results)."""
     W = np.array(W, dtype=np.float64, order="C")
-    L = lib(count)
+    L = lib("omp" if omp and not count and has_omp() else count)
     if count:
         L.or_count_reset()
     if gates is not None:
@@ -319,6 +341,15 @@ def step(f: Fluid, p: Params, g: Grid, W, dt_, nsteps=1, count=False, gates=None
         out = (ctypes.c_ulonglong * 5)()
         L.or_count_get(out)
         return W, {"add": out[0], "mul": out[1], "div": out[2], "sqrt": out[3], "tanh": out[4]}
+    return W
+
+
+def step_exact(f: Fluid, p: Params, g: Grid, W, dt_, nsteps, t0, adv):
+    """Steps with the exact-derivative right-hand side of the Sec. 5.1 temporal
+    test; adv = (a0, a1, k, u, p, rho_1, rho_2, x0)."""
+    W = np.array(W, dtype=np.float64, order="C")
+    a = np.ascontiguousarray(adv, dtype=np.float64)
+    lib().or_step_exact(ctypes.byref(f), ctypes.byref(p), ctypes.byref(g), _ptr(W), dt_, nsteps, t0, _ptr(a))
     return W
 
 

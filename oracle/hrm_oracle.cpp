@@ -24,14 +24,19 @@
 // Where the paper is silent or ambiguous the reading taken is stated inline
 // (the same list is kept in the design notes).
 //
-// Built twice: normally (real == double) and with -DOR_COUNT, where `real`
+// Built three times: normally (real == double); with -DOR_COUNT, where `real`
 // is a counting wrapper so that a run reports the algorithmic number of
-// floating-point operations the method performs.
+// floating-point operations the method performs; and with -DOR_OMP -fopenmp,
+// where the independent grid lines of each sweep and the cells of the
+// relaxation are shared among host threads (identical results).
 
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
+#ifdef OR_OMP
+#include <omp.h>
+#endif
 
 // tanh of the shock sensor (Sec. 4.3.1), evaluated explicitly so that its
 // rounding does not depend on a math library: tanh|x| = m / (m + 2) with
@@ -805,10 +810,18 @@ static void rhs_impl(const FluidK& f, const or_params* P, const or_grid* g, cons
   for (int64_t c = 0; c < nc * M; ++c) RHS[c] = 0.0;
   for (int dir = 0; dir < g->D; ++dir) {
     const int64_t n = g->n[dir];
-    // iterate over all lines along dir
+    // iterate over all lines along dir (independent: each writes its own cells;
+    // with -DOR_OMP they are shared among threads, which changes no result)
     int64_t nl = nc / n;
+#ifdef OR_OMP
+#pragma omp parallel
+#endif
+    {
     std::vector<Cell> line(n + 6);
     std::vector<real> Gm((n + 1) * M), Gp((n + 1) * M);
+#ifdef OR_OMP
+#pragma omp for schedule(static)
+#endif
     for (int64_t l = 0; l < nl; ++l) {
       // the other two indices of line l
       int64_t ijk[3] = {0, 0, 0};
@@ -846,6 +859,7 @@ static void rhs_impl(const FluidK& f, const or_params* P, const or_grid* g, cons
           RHS[(int64_t)m * nc + c] =
               RHS[(int64_t)m * nc + c] - (Gm[(i + 1) * M + m] - Gp[i * M + m]) / real(g->dx[dir]);
       }
+    }
     }
   }
 }
@@ -895,6 +909,9 @@ static void relax_cell(const FluidK& f, real* W, real* pT_out) {
 }
 
 static void relax_grid(const FluidK& f, int64_t nc, double* W) {
+#ifdef OR_OMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int64_t c = 0; c < nc; ++c) {
     real w[OR_MAXM];
     load_W(f, W, nc, c, w);
@@ -1112,22 +1129,24 @@ void or_lambdas(const or_fluid* fl, const or_grid* g, const double* W, double dt
 // lambda_d come from the state at the start of each step.
 // gx, gy, gz (nullable): a fixed smoothness gate per direction (see rhs_impl),
 // applied at every stage of every step.
-void or_step_gated(const or_fluid* fl, const or_params* P, const or_grid* g, double* W, double dt,
-                   int nsteps, const uint8_t* gx, const uint8_t* gy, const uint8_t* gz) {
-  const uint8_t* gates[3] = {gx, gy, gz};
-  const uint8_t* const* gate = (gx || gy || gz) ? gates : nullptr;
-  FluidK f = make_fluid(fl);
+}  // extern "C"
+
+// The time integrators (Sec. 4.4, Sec. 5.1): SSP-RK3 in Shu-Osher form, SSP-RK2
+// or forward Euler, relaxation after every stage (relax_mode 1), after the
+// step (2) or never (0). rhs(Wstage, t_stage, L) supplies L(W); the stage
+// times are t^n, t^n + dt and t^n + dt/2 (SSP-RK3), t^n and t^n + dt (SSP-RK2).
+template <typename Rhs>
+static void step_impl(const FluidK& f, const or_params* P, const or_grid* g, double* W, double dt, int nsteps,
+                      double t0, Rhs&& rhs) {
   const int64_t nc = ncells(g), tot = nc * f.M;
   std::vector<double> W0(tot), W1(tot), W2(tot);
   std::vector<real> L(tot);
   for (int s = 0; s < nsteps; ++s) {
-    real t[3] = {0.0, 0.0, 0.0}, lam[3] = {0.0, 0.0, 0.0};
-    tau_impl(f, g, W, t);
-    lambdas(g, t, real(dt), lam);
+    const double tn = t0 + s * dt;
     for (int64_t c = 0; c < tot; ++c) W0[c] = W[c];
     const int relax_stage = (P->relax_mode == 1);
     // stage 1: W1 = W0 + dt L(W0)
-    rhs_impl(f, P, g, W0.data(), lam, L.data(), gate);
+    rhs(W0.data(), tn, L.data(), true);
     for (int64_t c = 0; c < tot; ++c) W1[c] = val(real(W0[c]) + real(dt) * L[c]);
     if (P->integrator == 1) {
       if (P->relax_mode != 0) relax_grid(f, nc, W1.data());
@@ -1135,7 +1154,7 @@ void or_step_gated(const or_fluid* fl, const or_params* P, const or_grid* g, dou
       continue;
     }
     if (relax_stage) relax_grid(f, nc, W1.data());
-    rhs_impl(f, P, g, W1.data(), lam, L.data(), gate);
+    rhs(W1.data(), tn + dt, L.data(), false);
     if (P->integrator == 2) {
       // SSP-RK2: W^{n+1} = 1/2 W0 + 1/2 (W1 + dt L(W1))
       for (int64_t c = 0; c < tot; ++c)
@@ -1148,11 +1167,64 @@ void or_step_gated(const or_fluid* fl, const or_params* P, const or_grid* g, dou
       W2[c] = val(real(0.75) * real(W0[c]) + real(0.25) * (real(W1[c]) + real(dt) * L[c]));
     if (relax_stage) relax_grid(f, nc, W2.data());
     // stage 3: W^{n+1} = 1/3 W0 + 2/3 (W2 + dt L(W2))
-    rhs_impl(f, P, g, W2.data(), lam, L.data(), gate);
+    rhs(W2.data(), tn + 0.5 * dt, L.data(), false);
     for (int64_t c = 0; c < tot; ++c)
       W[c] = val(real(1.0 / 3.0) * real(W0[c]) + real(2.0 / 3.0) * (real(W2[c]) + real(dt) * L[c]));
     if (P->relax_mode != 0) relax_grid(f, nc, W);
   }
+}
+
+extern "C" {
+
+// gx, gy, gz (nullable): a fixed smoothness gate per direction (see rhs_impl),
+// applied at every stage of every step. lambda_d come from the state at the
+// start of each step.
+void or_step_gated(const or_fluid* fl, const or_params* P, const or_grid* g, double* W, double dt,
+                   int nsteps, const uint8_t* gx, const uint8_t* gy, const uint8_t* gz) {
+  const uint8_t* gates[3] = {gx, gy, gz};
+  const uint8_t* const* gate = (gx || gy || gz) ? gates : nullptr;
+  FluidK f = make_fluid(fl);
+  real lam[3] = {0.0, 0.0, 0.0};
+  step_impl(f, P, g, W, dt, nsteps, 0.0, [&](const double* Ws, double, real* L, bool first) {
+    if (first) {
+      real t[3] = {0.0, 0.0, 0.0};
+      tau_impl(f, g, Ws, t);
+      lambdas(g, t, real(dt), lam);
+    }
+    rhs_impl(f, P, g, Ws, lam, L, gate);
+  });
+}
+
+// Temporal convergence test of Sec. 5.1: the spatial operator replaced by the
+// exact convective derivatives of the advected solution alpha_1 = a0 + a1
+// sin(k (x - u t)) at constant u, p and species densities (two species, 1D):
+// d(a_k r_k u)/dx = r_k u da_k/dx, d(rho u^2 + p)/dx = u^2 drho/dx,
+// d((E + p) u)/dx = u d(rho e)/dx + u^3/2 drho/dx, u da_1/dx, with
+// d(rho e)/dx = sum_k (rho_k e_k) da_k/dx and rho_k e_k = p/(g_k - 1) +
+// g_k pinf_k/(g_k - 1) + rho_k q_k, evaluated at each stage's time.
+// adv = {a0, a1, k, u, p, rho_1, rho_2, x0 (left end of the domain)}; t0: time
+// of the initial state.
+void or_step_exact(const or_fluid* fl, const or_params* P, const or_grid* g, double* W, double dt, int nsteps,
+                   double t0, const double* adv) {
+  FluidK f = make_fluid(fl);
+  const int64_t n = g->n[0];
+  const double a1 = adv[1], k = adv[2], u = adv[3], p = adv[4], r1 = adv[5], r2 = adv[6], x0 = adv[7];
+  double re[2];
+  for (int s = 0; s < 2; ++s)
+    re[s] = p * f.inv_gm1[s] + f.gpinf_gm1[s] + (s == 0 ? r1 : r2) * f.q[s];
+  step_impl(f, P, g, W, dt, nsteps, t0, [&](const double*, double t, real* L, bool) {
+    for (int64_t i = 0; i < n; ++i) {
+      const double x = x0 + (i + 0.5) * g->dx[0];
+      const double da1 = a1 * k * std::cos(k * (x - u * t)), da2 = -da1;
+      const double drho = r1 * da1 + r2 * da2;
+      const double drhoe = re[0] * da1 + re[1] * da2;
+      L[0 * n + i] = -(r1 * u * da1);
+      L[1 * n + i] = -(r2 * u * da2);
+      L[2 * n + i] = -(u * u * drho);
+      L[3 * n + i] = -(u * drhoe + u * u * u / 2.0 * drho);
+      L[4 * n + i] = -(u * da1);
+    }
+  });
 }
 
 void or_step(const or_fluid* fl, const or_params* P, const or_grid* g, double* W, double dt,
@@ -1410,6 +1482,15 @@ double or_weno_lin(const double* u) {
   real r[5];
   for (int j = 0; j < 5; ++j) r[j] = u[j];
   return val(weno_lin_left(r));
+}
+
+// Threads the line loops use (1 unless built with -DOR_OMP -fopenmp).
+int or_threads(void) {
+#ifdef OR_OMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 double or_tanh(double x) { return tanh_explicit(x); }

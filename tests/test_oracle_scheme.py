@@ -2,6 +2,7 @@
 conservation, positivity, equilibrium preservation and the exact Riemann
 solution. The expected values come from the paper or from mathematics, never
 from the oracle itself or from the CUDA path."""
+import math
 import os
 
 import numpy as np
@@ -204,3 +205,52 @@ def test_counting_build_matches_and_counts(orc):
     np.testing.assert_array_equal(a, b)
     per_cell = sum(counts.values()) / W.shape[1]
     assert 5e3 < per_cell < 1e5
+
+
+def test_openmp_build_gives_identical_results(orc):
+    """The multi-threaded oracle build shares the independent grid lines and
+    cells among host threads; its states equal the serial build's exactly."""
+    if not orc.has_omp():
+        pytest.skip("no OpenMP in this compiler")
+    pr = P.shock_bubble_2d(48, 24)
+    f, g, W = orc.setup(pr)
+    p = orc.make_params()
+    dt, _ = orc.dt(f, g, W, pr.cfl)
+    np.testing.assert_array_equal(orc.step(f, p, g, W, dt, 3), orc.step(f, p, g, W, dt, 3, omp=True))
+    assert orc.threads(True) >= 1
+
+
+def _golden_temporal():
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "temporal_1d.txt")
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, steps, *vals = line.split()
+        rows[(name, int(steps))] = [float(v) for v in vals]
+    return rows
+
+
+@pytest.mark.parametrize("integrator,name", [(1, "euler"), (2, "rk2"), (0, "rk3")])
+def test_temporal_convergence_tables(orc, integrator, name):
+    """Sec. 5.1, Tables 1D_errors_and_rate_of_temporal_convergence_advection_*:
+    the 64-cell periodic advection with the exact spatial derivatives evaluated
+    at each stage's time (t^n, t^n + dt, t^n + dt/2) and the thermal relaxation
+    after every stage; the L2 and Linf errors of rho and alpha_1 at t = 0.1 s for
+    10-80 steps of forward Euler, SSP-RK2 and SSP-RK3, as printed (4 digits)."""
+    ref = _golden_temporal()
+    pr = P.advection_1d_smooth(64)
+    f, g, W = orc.setup(pr)
+    r1 = W[0, 0] / pr.prim[0, 0]
+    r2 = W[1, 0] / (1.0 - pr.prim[0, 0])
+    adv = [0.5, 0.25, math.pi, 10.0, 101325.0, r1, r2, -1.0]
+    x = -1.0 + (np.arange(64) + 0.5) * (2.0 / 64)
+    a_ex = 0.5 + 0.25 * np.sin(math.pi * (x - 10.0 * 0.1))
+    rho_ex = r1 * a_ex + r2 * (1.0 - a_ex)
+    for ns in (10, 20, 40, 80):
+        W1 = orc.step_exact(f, orc.make_params(integrator=integrator), g, W, 0.1 / ns, ns, 0.0, adv)
+        rho, a1 = W1[0] + W1[1], W1[4]
+        got = [np.sqrt(np.mean((rho - rho_ex) ** 2)), np.max(np.abs(rho - rho_ex)),
+               np.sqrt(np.mean((a1 - a_ex) ** 2)), np.max(np.abs(a1 - a_ex))]
+        for gv, rv in zip(got, ref[(name, ns)]):
+            assert gv == pytest.approx(rv, rel=1e-3), (name, ns, got, ref[(name, ns)])
