@@ -122,7 +122,20 @@ def host_cpu():
                 break
     except OSError:
         pass
-    return {"model": model, "nproc": os.cpu_count()}
+    if model is None:
+        # Arm hosts list implementer and part codes instead of a model name
+        try:
+            fields = {}
+            for line in open("/proc/cpuinfo"):
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip(), v.strip())
+            if "CPU implementer" in fields:
+                model = f"implementer {fields['CPU implementer']} part {fields.get('CPU part')}"
+        except OSError:
+            pass
+    import platform
+    return {"model": model, "machine": platform.machine(), "nproc": os.cpu_count()}
 
 
 def cpu_baseline(problem, seconds_budget=25.0):

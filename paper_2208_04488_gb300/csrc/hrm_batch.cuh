@@ -38,8 +38,13 @@ constexpr int kBatchMaxThreads = 256;
 __device__ __forceinline__ const double* pick(const BatchInst& I, int sel) { return sel == 0 ? I.Wn : I.Ws; }
 __device__ __forceinline__ double* pick_mut(const BatchInst& I, int sel) { return sel == 0 ? I.Wn : I.Ws; }
 
-// Primitives of every cell of every instance (+ per-instance CFL maxima).
-template <int D>
+// Each kernel is instantiated per species count N and runs over the work items
+// of the instances with that N (the item lists are grouped by N), so that its
+// body is one specialisation and its register count that of the single-context
+// kernel.
+
+// Primitives of every cell of the instances (+ per-instance CFL maxima).
+template <int D, int N>
 __global__ void __launch_bounds__(kBatchMaxThreads)
     k_batch_prim(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
                  int fp32, int tau) {
@@ -53,10 +58,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
     float* P32 = fp32 ? I.P32 : nullptr;
     for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
       double sc[D];
-      if (I.N == 2)
-        prim_body<2, D>(c, W, I.V, I.AUX, P32, nullptr, I.g, I.f, sc);
-      else
-        prim_body<3, D>(c, W, I.V, I.AUX, P32, nullptr, I.g, I.f, sc);
+      prim_body<N, D>(c, W, I.V, I.AUX, P32, nullptr, I.g, I.f, sc);
 #pragma unroll
       for (int d = 0; d < D; ++d) s[d] = (sc[d] != sc[d]) ? sc[d] : (sc[d] > s[d] ? sc[d] : s[d]);
     }
@@ -64,8 +66,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
   }
 }
 
-// FP32 planes (and CFL maxima) of every instance for the precision form.
-template <int D>
+// FP32 planes (and CFL maxima) of the instances for the precision form.
+template <int D, int N>
 __global__ void __launch_bounds__(kBatchMaxThreads)
     k_batch_prim32(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
                    int tau) {
@@ -78,10 +80,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
     const double* W = pick(I, src);
     for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
       double sc[D];
-      if (I.N == 2)
-        prim32_body<2, D>(c, W, I.P32, nullptr, I.g, I.f, sc);
-      else
-        prim32_body<3, D>(c, W, I.P32, nullptr, I.g, I.f, sc);
+      prim32_body<N, D>(c, W, I.P32, nullptr, I.g, I.f, sc);
 #pragma unroll
       for (int d = 0; d < D; ++d) s[d] = (sc[d] != sc[d]) ? sc[d] : (sc[d] > s[d] ? sc[d] : s[d]);
     }
@@ -89,11 +88,15 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
   }
 }
 
-// Midpoints of direction DIR of every instance; FP64 (bit-exact) or precision form.
-template <int D, int DIR, bool FP32>
-__global__ void __launch_bounds__(kBatchMaxThreads)
-    k_batch_face(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
-                 DevParams pr) {
+// Midpoints of direction DIR of the instances: FP64 (bit-exact; up to 256
+// threads per block) or the precision form (at most 128 threads, three blocks
+// per SM, as the single-context sweep).
+constexpr int kBatchFace32Threads = 128;
+
+template <int D, int DIR, int N>
+__device__ __forceinline__ void batch_face_items(const BatchInst* __restrict__ insts,
+                                                 const WorkItem* __restrict__ items, int nitems, int src,
+                                                 const DevParams& pr, bool fp32) {
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const WorkItem w = items[it];
     const BatchInst& I = insts[w.inst];
@@ -102,23 +105,30 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
     for (int64_t t = w.begin + threadIdx.x; t < w.end; t += blockDim.x) {
       Nodes6 nd;
       if (!face_nodes<DIR>(I.g, t, nd)) continue;
-      if constexpr (FP32) {
-        if (I.N == 2)
-          face32_body<2, D, DIR>(t, nd, W, I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr, lam);
-        else
-          face32_body<3, D, DIR>(t, nd, W, I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr, lam);
-      } else {
-        if (I.N == 2)
-          face_body<double, 2, D, DIR>(t, nd, W, I.V, I.AUX, I.F[DIR], I.g, I.f, pr, lam);
-        else
-          face_body<double, 3, D, DIR>(t, nd, W, I.V, I.AUX, I.F[DIR], I.g, I.f, pr, lam);
-      }
+      if (fp32)
+        face32_body<N, D, DIR>(t, nd, W, I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr, lam);
+      else
+        face_body<double, N, D, DIR>(t, nd, W, I.V, I.AUX, I.F[DIR], I.g, I.f, pr, lam);
     }
   }
 }
 
-// Flux difference, SSP-RK combination and relaxation of every cell of every instance.
-template <int D, bool FAST>
+template <int D, int DIR, int N>
+__global__ void __launch_bounds__(kBatchMaxThreads)
+    k_batch_face64(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
+                   DevParams pr) {
+  batch_face_items<D, DIR, N>(insts, items, nitems, src, pr, false);
+}
+
+template <int D, int DIR, int N>
+__global__ void __launch_bounds__(kBatchFace32Threads, 3)
+    k_batch_face32(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
+                   DevParams pr) {
+  batch_face_items<D, DIR, N>(insts, items, nitems, src, pr, true);
+}
+
+// Flux difference, SSP-RK combination and relaxation of every cell of the instances.
+template <int D, bool FAST, int N>
 __global__ void __launch_bounds__(kBatchMaxThreads)
     k_batch_update(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
                    int dst, double a, double b, int relax, int count) {
@@ -128,14 +138,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
     const double* Wsrc = pick(I, src);
     double* Wout = pick_mut(I, dst);
     const double dt = I.st->dt;
-    for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
-      if (I.N == 2)
-        update_body<2, D, 0, FAST>(c, I.Wn, Wsrc, Wout, I.F[0], I.F[1], I.F[2], I.g, I.f, I.st, dt, a, b, relax,
-                                   count);
-      else
-        update_body<3, D, 0, FAST>(c, I.Wn, Wsrc, Wout, I.F[0], I.F[1], I.F[2], I.g, I.f, I.st, dt, a, b, relax,
-                                   count);
-    }
+    for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x)
+      update_body<N, D, 0, FAST>(c, I.Wn, Wsrc, Wout, I.F[0], I.F[1], I.F[2], I.g, I.f, I.st, dt, a, b, relax,
+                                 count);
   }
 }
 
@@ -145,17 +150,18 @@ struct BatchLaunch {
   int threads;   // threads per block
 };
 
-void batch_prim_d2(const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int fp32, int tau,
+void batch_prim_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int tau,
                    cudaStream_t);
-void batch_prim32_d2(const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int tau, cudaStream_t);
+void batch_prim32_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int tau,
+                     cudaStream_t);
 void batch_finalize(const BatchInst*, int ninst, int D, double cfl, cudaStream_t);
-void batch_face64_d2(int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
+void batch_face64_d2(int N, int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
                      const DevParams&, cudaStream_t);
-void batch_face32_d2(int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
+void batch_face32_d2(int N, int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
                      const DevParams&, cudaStream_t);
-void batch_update64_d2(const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst, double a,
-                       double b, int relax, int count, cudaStream_t);
-void batch_update32_d2(const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst, double a,
-                       double b, int relax, int count, cudaStream_t);
+void batch_update64_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst,
+                       double a, double b, int relax, int count, cudaStream_t);
+void batch_update32_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst,
+                       double a, double b, int relax, int count, cudaStream_t);
 
 }  // namespace hrm

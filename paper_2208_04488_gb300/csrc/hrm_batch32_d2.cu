@@ -4,22 +4,35 @@
 
 namespace hrm {
 
-void batch_face32_d2(int dir, const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems, int src,
-                     const DevParams& p, cudaStream_t s) {
-  if (dir == 0)
-    k_batch_face<2, 0, true><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+void batch_face32_d2(int N, int dir, const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems,
+                     int src, const DevParams& p, cudaStream_t s) {
+  if (N == 2) {
+    if (dir == 0)
+      k_batch_face32<2, 0, 2><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+    else
+      k_batch_face32<2, 1, 2><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+  } else {
+    if (dir == 0)
+      k_batch_face32<2, 0, 3><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+    else
+      k_batch_face32<2, 1, 3><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+  }
+}
+
+void batch_prim32_d2(int N, const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems, int src,
+                     int tau, cudaStream_t s) {
+  if (N == 2)
+    k_batch_prim32<2, 2><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, tau);
   else
-    k_batch_face<2, 1, true><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+    k_batch_prim32<2, 3><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, tau);
 }
 
-void batch_prim32_d2(const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems, int src, int tau,
-                     cudaStream_t s) {
-  k_batch_prim32<2><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, tau);
-}
-
-void batch_update32_d2(const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems, int src,
-                       int dst, double a, double b, int relax, int count, cudaStream_t s) {
-  k_batch_update<2, true><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, dst, a, b, relax, count);
+void batch_update32_d2(int N, const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems,
+                       int src, int dst, double a, double b, int relax, int count, cudaStream_t s) {
+  if (N == 2)
+    k_batch_update<2, true, 2><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, dst, a, b, relax, count);
+  else
+    k_batch_update<2, true, 3><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, dst, a, b, relax, count);
 }
 
 }  // namespace hrm

@@ -29,26 +29,39 @@ __global__ void k_batch_finalize(const BatchInst* __restrict__ insts, int ninst,
 }
 
 
-void batch_prim_d2(const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems, int src, int fp32,
+void batch_prim_d2(int N, const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems, int src,
                    int tau, cudaStream_t s) {
-  k_batch_prim<2><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, fp32, tau);
+  if (N == 2)
+    k_batch_prim<2, 2><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, 0, tau);
+  else
+    k_batch_prim<2, 3><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, 0, tau);
 }
 
 void batch_finalize(const BatchInst* insts, int ninst, int D, double cfl, cudaStream_t s) {
   k_batch_finalize<<<(ninst + 127) / 128, 128, 0, s>>>(insts, ninst, D, cfl);
 }
 
-void batch_face64_d2(int dir, const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems, int src,
-                     const DevParams& p, cudaStream_t s) {
-  if (dir == 0)
-    k_batch_face<2, 0, false><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
-  else
-    k_batch_face<2, 1, false><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+void batch_face64_d2(int N, int dir, const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems,
+                     int src, const DevParams& p, cudaStream_t s) {
+  if (N == 2) {
+    if (dir == 0)
+      k_batch_face64<2, 0, 2><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+    else
+      k_batch_face64<2, 1, 2><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+  } else {
+    if (dir == 0)
+      k_batch_face64<2, 0, 3><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+    else
+      k_batch_face64<2, 1, 3><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
+  }
 }
 
-void batch_update64_d2(const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems, int src,
-                       int dst, double a, double b, int relax, int count, cudaStream_t s) {
-  k_batch_update<2, false><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, dst, a, b, relax, count);
+void batch_update64_d2(int N, const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems,
+                       int src, int dst, double a, double b, int relax, int count, cudaStream_t s) {
+  if (N == 2)
+    k_batch_update<2, false, 2><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, dst, a, b, relax, count);
+  else
+    k_batch_update<2, false, 3><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, dst, a, b, relax, count);
 }
 
 }  // namespace hrm

@@ -40,8 +40,10 @@ struct hrm_batch {
   std::vector<int> N;
   BatchInst* d_insts = nullptr;
   WorkItem* d_items = nullptr;   // [cells | faces x | faces y]
-  int n_cell_items = 0, n_face_items[2] = {0, 0};
-  int off_face_items[2] = {0, 0};
+  // work-item lists grouped by species count: [g] = N = 2, 3; cells first,
+  // then the faces of each direction
+  int off_cell[2] = {0, 0}, n_cell[2] = {0, 0};
+  int off_face[2][2] = {{0, 0}, {0, 0}}, n_face[2][2] = {{0, 0}, {0, 0}};
   Shape shape;
   int sms = 0;
   cudaGraphExec_t gexec = nullptr;
@@ -77,25 +79,35 @@ void drop_graph(hrm_batch* b) {
 }
 
 // Work items: every instance's cells in chunks of cell_tile, its faces of
-// each direction in chunks of face_tile; no item spans two instances.
+// each direction in chunks of face_tile; no item spans two instances; each list
+// grouped by the instances' species count.
 hrm_status build_items(hrm_batch* b) {
-  std::vector<WorkItem> cells, faces[2];
-  for (int i = 0; i < b->ninst; ++i) {
-    const DevGrid& g = b->host[i].g;
-    for (int64_t c = 0; c < g.ncells; c += b->shape.cell_tile)
-      cells.push_back({i, 0, c, std::min<int64_t>(c + b->shape.cell_tile, g.ncells)});
-    for (int d = 0; d < 2; ++d) {
-      const int64_t nf = (g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * g.n[2];
-      for (int64_t t = 0; t < nf; t += b->shape.face_tile)
-        faces[d].push_back({i, 0, t, std::min<int64_t>(t + b->shape.face_tile, nf)});
+  std::vector<WorkItem> all;
+  for (int kind = 0; kind < 3; ++kind) {  // 0 cells, 1 x faces, 2 y faces
+    for (int gN = 0; gN < 2; ++gN) {
+      const int begin = (int)all.size();
+      for (int i = 0; i < b->ninst; ++i) {
+        if (b->N[i] != 2 + gN) continue;
+        const DevGrid& g = b->host[i].g;
+        if (kind == 0) {
+          for (int64_t c = 0; c < g.ncells; c += b->shape.cell_tile)
+            all.push_back({i, 0, c, std::min<int64_t>(c + b->shape.cell_tile, g.ncells)});
+        } else {
+          const int d = kind - 1;
+          const int64_t nf = (g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * g.n[2];
+          for (int64_t t = 0; t < nf; t += b->shape.face_tile)
+            all.push_back({i, 0, t, std::min<int64_t>(t + b->shape.face_tile, nf)});
+        }
+      }
+      const int n = (int)all.size() - begin;
+      if (kind == 0) {
+        b->off_cell[gN] = begin;
+        b->n_cell[gN] = n;
+      } else {
+        b->off_face[kind - 1][gN] = begin;
+        b->n_face[kind - 1][gN] = n;
+      }
     }
-  }
-  std::vector<WorkItem> all(cells);
-  b->n_cell_items = (int)cells.size();
-  for (int d = 0; d < 2; ++d) {
-    b->off_face_items[d] = (int)all.size();
-    b->n_face_items[d] = (int)faces[d].size();
-    all.insert(all.end(), faces[d].begin(), faces[d].end());
   }
   if (b->d_items) cudaFree(b->d_items);
   b->d_items = nullptr;
@@ -114,28 +126,38 @@ int enqueue_stage(hrm_batch* b, cudaStream_t s, int src, int dst, double a, doub
                        b->shape.cell_threads};
   const BatchLaunch lf{b->sms * b->shape.blocks_per_sm, b->shape.face_threads};
   int k = 0;
-  if (fp32)
-    batch_prim32_d2(lc, b->d_insts, b->d_items, b->n_cell_items, src, first ? 1 : 0, s);
-  else
-    batch_prim_d2(lc, b->d_insts, b->d_items, b->n_cell_items, src, 0, first ? 1 : 0, s);
-  ++k;
+  for (int gN = 0; gN < 2; ++gN) {
+    if (!b->n_cell[gN]) continue;
+    const WorkItem* it = b->d_items + b->off_cell[gN];
+    if (fp32)
+      batch_prim32_d2(2 + gN, lc, b->d_insts, it, b->n_cell[gN], src, first ? 1 : 0, s);
+    else
+      batch_prim_d2(2 + gN, lc, b->d_insts, it, b->n_cell[gN], src, first ? 1 : 0, s);
+    ++k;
+  }
   if (first) {
     batch_finalize(b->d_insts, b->ninst, b->D, b->params.cfl, s);
     ++k;
   }
-  for (int d = 0; d < 2; ++d) {
-    const WorkItem* it = b->d_items + b->off_face_items[d];
+  for (int d = 0; d < 2; ++d)
+    for (int gN = 0; gN < 2; ++gN) {
+      if (!b->n_face[d][gN]) continue;
+      const WorkItem* it = b->d_items + b->off_face[d][gN];
+      if (fp32)
+        batch_face32_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, s);
+      else
+        batch_face64_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, s);
+      ++k;
+    }
+  for (int gN = 0; gN < 2; ++gN) {
+    if (!b->n_cell[gN]) continue;
+    const WorkItem* it = b->d_items + b->off_cell[gN];
     if (fp32)
-      batch_face32_d2(d, lf, b->d_insts, it, b->n_face_items[d], src, b->dp, s);
+      batch_update32_d2(2 + gN, lc, b->d_insts, it, b->n_cell[gN], src, dst, a, bb, relax, count, s);
     else
-      batch_face64_d2(d, lf, b->d_insts, it, b->n_face_items[d], src, b->dp, s);
+      batch_update64_d2(2 + gN, lc, b->d_insts, it, b->n_cell[gN], src, dst, a, bb, relax, count, s);
     ++k;
   }
-  if (fp32)
-    batch_update32_d2(lc, b->d_insts, b->d_items, b->n_cell_items, src, dst, a, bb, relax, count, s);
-  else
-    batch_update64_d2(lc, b->d_insts, b->d_items, b->n_cell_items, src, dst, a, bb, relax, count, s);
-  ++k;
   return k;
 }
 
@@ -411,6 +433,8 @@ hrm_status hrm_batch_set_launch(hrm_batch* b, int32_t face_threads, int32_t face
   if ((face_threads != 64 && face_threads != 128 && face_threads != 256) || face_tile < face_threads ||
       cell_tile < 256 || blocks_per_sm < 1 || blocks_per_sm > 32)
     return bfail(b, HRM_E_INVAL, "invalid launch shape");
+  if (b->params.precision == HRM_FP32 && face_threads > kBatchFace32Threads)
+    return bfail(b, HRM_E_INVAL, "precision form: at most %d threads per midpoint block", kBatchFace32Threads);
   b->shape.face_threads = face_threads;
   b->shape.face_tile = face_tile;
   b->shape.cell_tile = cell_tile;
@@ -445,6 +469,7 @@ hrm_status hrm_batch_tune(hrm_batch* b, int32_t steps_per_trial, int32_t* best) 
       for (int bp : bps) {
         if (s) break;
         if (th * bp > 2 * 256) continue;  // at most two 256-thread blocks of the register-heavy sweep per SM
+        if (b->params.precision == HRM_FP32 && th > kBatchFace32Threads) continue;
         if ((s = hrm_batch_set_launch(b, th, th * tl, 4096, bp))) break;
         if ((s = build_graph(b))) break;
         cudaGraphLaunch(b->gexec, b->stream);  // warm-up
