@@ -41,7 +41,11 @@ typedef enum {
   HRM_E_NOMEM = -5          /* device allocation failed */
 } hrm_status;
 
-enum { HRM_BC_TRANSMISSIVE = 0, HRM_BC_PERIODIC = 1 };
+/* Boundary conditions of a grid side. Transmissive: the three ghost layers copy
+ * the adjacent interior cell (zeroth-order extrapolation). Periodic: pairs with
+ * the opposite side. Dirichlet: every ghost layer holds a prescribed state, one
+ * value per boundary cell (hrm_set_boundary), e.g. the jet inflow of Sec. 5.9. */
+enum { HRM_BC_TRANSMISSIVE = 0, HRM_BC_PERIODIC = 1, HRM_BC_DIRICHLET = 2 };
 
 enum {
   HRM_SCHEME_WCNS = 0,      /* PP-WCNS-IS (Sec. 4.3) */
@@ -155,6 +159,20 @@ hrm_status hrm_step(hrm_ctx* ctx, double dt, int32_t nsteps);
 
 /* Apply the thermal relaxation (Sec. 4.2) to the current state in place. */
 hrm_status hrm_relax(hrm_ctx* ctx);
+
+/* Prescribed state of Dirichlet side `side` (= 2 d + 0 for the low side of
+ * direction d, 2 d + 1 for the high side). `values` holds one value per cell of
+ * the boundary slice (the other directions' cell indices, lowest fastest):
+ * with primitive = 0 the M conservative planes of W (layout above), with
+ * primitive = 1 the N + D + 1 primitive planes of hrm_set_primitive, converted
+ * in p-T equilibrium. Host or device memory; copied, not retained. The state
+ * stays until the next call (hrm_set does not clear it); it enters the
+ * reconstruction stencils of the side's first three midpoints and the CFL
+ * maximum (Sec. 4.1.2). Every Dirichlet side needs a state before hrm_step,
+ * hrm_dt or hrm_rhs, which otherwise return HRM_E_INVAL.
+ * Errors: HRM_E_INVAL (NULL, or `side` not a Dirichlet side), HRM_E_CUDA. */
+hrm_status hrm_set_boundary(hrm_ctx* ctx, int32_t side, const double* values, int32_t primitive,
+                            int32_t on_device);
 
 /* Semi-discrete right-hand side L(W) of the current state (Eq. semi_W_G_pm_eqn)
  * with flux-limiter lambda_d = lam[d], into rhs (M x ncells, device memory). */
@@ -295,7 +313,7 @@ hrm_status hrm_probe_fma_peak(int32_t precision, int32_t iters, void* stream, do
 typedef struct hrm_batch hrm_batch; /* opaque, owned by the library */
 
 typedef struct {
-  hrm_grid grid;       /* ndim must be 2 */
+  hrm_grid grid;       /* ndim must be 2; transmissive or periodic sides only */
   int32_t nspecies;    /* 2 or 3 */
   int32_t pad;
   double gamma[4], p_inf[4], c_v[4], q[4];

@@ -81,7 +81,7 @@ class Params(ctypes.Structure):
 class Grid(ctypes.Structure):
     _fields_ = [("D", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("n", ctypes.c_int64 * 3), ("dx", ctypes.c_double * 3),
-                ("bc", ctypes.c_int32 * 6)]
+                ("bc", ctypes.c_int32 * 6), ("bnd", ctypes.c_void_p * 6)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -174,7 +174,9 @@ def make_params(**kw) -> Params:
     return p
 
 
-def make_grid(n, dx, bc=None) -> Grid:
+def make_grid(n, dx, bc=None, bnd=None) -> Grid:
+    """bnd (optional): {side b = 2 d + s: W of the boundary slice, (M, cells of
+    the side)} for the Dirichlet sides (bc 2)."""
     g = Grid()
     g.D = len(n)
     for d in range(3):
@@ -183,6 +185,11 @@ def make_grid(n, dx, bc=None) -> Grid:
     bc = bc or [0] * (2 * len(n))
     for i in range(6):
         g.bc[i] = bc[i] if i < len(bc) else 0
+    g._keep = {}
+    for b, Wb in (bnd or {}).items():
+        Wb = np.ascontiguousarray(Wb, dtype=np.float64)
+        g._keep[b] = Wb
+        g.bnd[b] = Wb.ctypes.data
     return g
 
 
@@ -381,7 +388,8 @@ def setup(problem):
     """Oracle descriptions (fluid, grid) and the initial W of a problem from
     paper_2208_04488_gb300.problems."""
     f = make_fluid(problem.gamma, problem.pinf, problem.cv, problem.q, D=problem.D, liq=problem.liq)
-    g = make_grid(problem.n, problem.dx, problem.bc)
+    bnd = {b: ic_from_prim(f, prim) for b, prim in getattr(problem, "boundary", {}).items()}
+    g = make_grid(problem.n, problem.dx, problem.bc, bnd)
     return f, g, ic_from_prim(f, problem.prim)
 
 

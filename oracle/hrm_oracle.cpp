@@ -141,12 +141,16 @@ struct or_params {
 
 // Uniform Cartesian grid. n[d] cells in direction d (x fastest), spacing dx[d].
 // bc[2d] / bc[2d+1]: low / high side, 0 = transmissive (zeroth-order
-// extrapolation into the ghost cells), 1 = periodic.
+// extrapolation into the ghost cells), 1 = periodic, 2 = Dirichlet: every ghost
+// cell of that side holds the prescribed state bnd[2d + side], the conservative
+// vector W (M planes) of the boundary slice, one entry per cell of the side
+// (the other directions' indices, lowest direction fastest).
 struct or_grid {
   int32_t D, pad;
   int64_t n[3];
   double dx[3];
   int32_t bc[6];
+  const double* bnd[6];
 };
 
 }  // extern "C"
@@ -799,6 +803,37 @@ static void load_W(const FluidK& f, const double* W, int64_t nc, int64_t c, real
   for (int m = 0; m < f.M; ++m) out[m] = real(W[(int64_t)m * nc + c]);
 }
 
+// Cells of the boundary slice normal to d and the index of the slice cell that
+// continues line ijk (the other directions' indices, lowest fastest).
+static int64_t slice_cells(const or_grid* g, int d) {
+  int64_t s = 1;
+  for (int e = 0; e < g->D; ++e)
+    if (e != d) s *= g->n[e];
+  return s;
+}
+static int64_t slice_index(const or_grid* g, int d, const int64_t* ijk) {
+  int64_t s = 0, stride = 1;
+  for (int e = 0; e < g->D; ++e) {
+    if (e == d) continue;
+    s += ijk[e] * stride;
+    stride *= g->n[e];
+  }
+  return s;
+}
+
+// W of node j (possibly outside the grid) on the line through ijk along d.
+static void load_node(const FluidK& f, const or_grid* g, const double* W, int d, const int64_t* ijk, int64_t j,
+                      real* out) {
+  const int side = j < 0 ? 0 : (j >= g->n[d] ? 1 : -1);
+  if (side >= 0 && g->bc[2 * d + side] == 2) {
+    load_W(f, g->bnd[2 * d + side], slice_cells(g, d), slice_index(g, d, ijk), out);
+    return;
+  }
+  int64_t q[3] = {ijk[0], ijk[1], ijk[2]};
+  q[d] = map_index(g, d, j);
+  load_W(f, W, ncells(g), lin(g, q), out);
+}
+
 // L(W): the semi-discrete right-hand side of Eq. semi_W_G_pm_eqn, direction by
 // direction: RHS_i = -sum_d (G^{d,-}_{i+1/2} - G^{d,+}_{i-1/2}) / dx_d.
 // gate (nullable): per direction, one byte per midpoint over that direction's
@@ -833,10 +868,8 @@ static void rhs_impl(const FluidK& f, const or_params* P, const or_grid* g, cons
       }
       // node cells j = -3 .. n+2 with boundary conditions
       for (int64_t j = -3; j < n + 3; ++j) {
-        int64_t q[3] = {ijk[0], ijk[1], ijk[2]};
-        q[dir] = map_index(g, dir, j);
         real w[OR_MAXM];
-        load_W(f, W, nc, lin(g, q), w);
+        load_node(f, g, W, dir, ijk, j, w);
         cell_from_W(f, w, line[j + 3]);
       }
       // faces f = 0..n: face f lies between cells f-1 and f; stencil f-3..f+2
@@ -922,19 +955,27 @@ static void relax_grid(const FluidK& f, int64_t nc, double* W) {
 
 // Max wave speed per direction (Sec. 4.1.2): tau_d = max(|u_d| + c)/dx_d with the
 // five-equation sound speed.
+// Reading: the prescribed states of Dirichlet sides enter the maximum too (their
+// waves enter the domain at once).
 static void tau_impl(const FluidK& f, const or_grid* g, const double* W, real* tau) {
   const int64_t nc = ncells(g);
   for (int d = 0; d < g->D; ++d) tau[d] = 0.0;
-  for (int64_t c = 0; c < nc; ++c) {
+  auto visit = [&](const double* X, int64_t n, int64_t c) {
     real w[OR_MAXM];
-    load_W(f, W, nc, c, w);
+    load_W(f, X, n, c, w);
     Cell C;
     cell_from_W(f, w, C);
     for (int d = 0; d < g->D; ++d) {
       real s = (rabs_(C.V[sMOM(f, d)]) + C.c) / real(g->dx[d]);
       tau[d] = rmax(tau[d], s);
     }
-  }
+  };
+  for (int64_t c = 0; c < nc; ++c) visit(W, nc, c);
+  for (int b = 0; b < 2 * g->D; ++b)
+    if (g->bc[b] == 2) {
+      const int64_t ns = slice_cells(g, b / 2);
+      for (int64_t c = 0; c < ns; ++c) visit(g->bnd[b], ns, c);
+    }
 }
 
 // Directional split: sigma_d = tau_d / sum tau, lambda_d = dt/(sigma_d dx_d)
@@ -1425,10 +1466,8 @@ void or_stencil_sample(const or_fluid* fl, const or_params* P, const or_grid* g,
     const int64_t q[3] = {t % f0, (t / f0) % f1, t / (f0 * f1)};
     Cell nd[6];
     for (int j = 0; j < 6; ++j) {
-      int64_t r[3] = {q[0], q[1], q[2]};
-      r[dir] = map_index(g, dir, q[dir] - 3 + j);
       real w[OR_MAXM];
-      load_W(f, W, nc, lin(g, r), w);
+      load_node(f, g, W, dir, q, q[dir] - 3 + j, w);
       cell_from_W(f, w, nd[j]);
     }
     for (int a = 0; a < 5; ++a) {

@@ -21,7 +21,9 @@ constexpr int kMaxProf = 32;  // kernels of one step: at most 3 stages x (2 + 3 
 
 struct hrm_ctx {
   int N = 0, D = 0, M = 0;
-  int64_t nc = 0;
+  int64_t nc = 0;                  // stored cells per plane (interior + Dirichlet slices)
+  int64_t nint = 0;                // interior cells
+  int bnd_need = 0, bnd_set = 0;   // Dirichlet sides (bit b = side b) and those given a state
   hrm_grid grid{};
   hrm_params params{};
   DevFluid fl{};
@@ -249,6 +251,28 @@ hrm_status build_graph(hrm_ctx* c) {
   return HRM_OK;
 }
 
+// Copy `planes` planes of `cells` doubles between plane strides (in cells).
+hrm_status copy_planes(hrm_ctx* c, double* dst, int64_t dpitch, const double* src, int64_t spitch, int64_t cells,
+                       int planes, cudaMemcpyKind kind, const char* what) {
+  if (dpitch == cells && spitch == cells)
+    return cuda_check(c, cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)cells * planes, kind, c->stream), what);
+  for (int m = 0; m < planes; ++m)  // one copy per plane (no pitch limit)
+    if (hrm_status s = cuda_check(c,
+                                  cudaMemcpyAsync(dst + (size_t)m * dpitch, src + (size_t)m * spitch,
+                                                  sizeof(double) * (size_t)cells, kind, c->stream),
+                                  what))
+      return s;
+  return HRM_OK;
+}
+
+hrm_status check_boundaries(hrm_ctx* c) {
+  const int missing = c->bnd_need & ~c->bnd_set;
+  if (!missing) return HRM_OK;
+  for (int b = 0; b < 6; ++b)
+    if (missing >> b & 1) return fail(c, HRM_E_INVAL, "Dirichlet side %d has no boundary state (hrm_set_boundary)", b);
+  return HRM_OK;
+}
+
 void reset_step_state(hrm_ctx* c) {
   StepState z{};
   z.cfl = c->params.cfl;
@@ -328,9 +352,10 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
       c->dg.inv_dx[d] = 1.0 / c->dg.dx[d];
       for (int side = 0; side < 2; ++side) {
         const int b = grid->bc[2 * d + side];
-        if (b != HRM_BC_TRANSMISSIVE && b != HRM_BC_PERIODIC)
+        if (b != HRM_BC_TRANSMISSIVE && b != HRM_BC_PERIODIC && b != HRM_BC_DIRICHLET)
           return bail(fail(c, HRM_E_INVAL, "unknown boundary condition %d", b));
         c->dg.bc[2 * d + side] = b;
+        if (b == HRM_BC_DIRICHLET) c->bnd_need |= 1 << (2 * d + side);
       }
       if ((grid->bc[2 * d] == HRM_BC_PERIODIC) != (grid->bc[2 * d + 1] == HRM_BC_PERIODIC))
         return bail(fail(c, HRM_E_INVAL, "periodic boundaries must pair in direction %d", d));
@@ -341,6 +366,14 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
       c->dg.inv_dx[d] = 1.0;
     }
   }
+  // Dirichlet slices after the interior cells of every plane
+  c->nint = c->nc;
+  c->dg.nint = c->nint;
+  for (int b = 0; b < 2 * D; ++b)
+    if (c->bnd_need >> b & 1) {
+      c->dg.goff[b] = c->nc;
+      c->nc += c->nint / c->dg.n[b / 2];
+    }
   c->dg.ncells = c->nc;
   c->fl.liq = liq < 0 ? 0 : liq;
   for (int k = 0; k < N; ++k) {
@@ -454,10 +487,8 @@ hrm_status hrm_set_params(hrm_ctx* c, const hrm_params* p) {
 
 hrm_status hrm_set(hrm_ctx* c, const double* W, int32_t on_device) {
   if (!c || !W) return HRM_E_INVAL;
-  const size_t bytes = sizeof(double) * (size_t)c->nc * c->M;
-  hrm_status s = cuda_check(
-      c, cudaMemcpyAsync(c->Wn, W, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
-      "copy W");
+  hrm_status s = copy_planes(c, c->Wn, c->nc, W, c->nint, c->nint, c->M,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, "copy W");
   if (s) return s;
   reset_step_state(c);
   return last_launch(c, "set");
@@ -465,20 +496,45 @@ hrm_status hrm_set(hrm_ctx* c, const double* W, int32_t on_device) {
 
 hrm_status hrm_set_primitive(hrm_ctx* c, const double* prim, int32_t on_device) {
   if (!c || !prim) return HRM_E_INVAL;
-  const size_t bytes = sizeof(double) * (size_t)c->nc * (c->N + c->D + 1);
-  hrm_status s = cuda_check(
-      c, cudaMemcpyAsync(c->V, prim, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
-      "copy primitives");
+  hrm_status s = copy_planes(c, c->V, c->nc, prim, c->nint, c->nint, c->N + c->D + 1,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, "copy primitives");
   if (s) return s;
-  c->ck->ic(c->V, c->Wn, c->dg, c->fl, c->stream);
+  c->ck->ic(c->V, c->Wn, c->dg, c->fl, 0, c->nint, c->stream);
   ++c->launches;
   if ((s = last_launch(c, "initial state"))) return s;
   reset_step_state(c);
   return last_launch(c, "set primitive");
 }
 
+hrm_status hrm_set_boundary(hrm_ctx* c, int32_t side, const double* values, int32_t primitive,
+                            int32_t on_device) {
+  if (!c || !values) return HRM_E_INVAL;
+  if (side < 0 || side >= 2 * c->D || c->dg.bc[side] != HRM_BC_DIRICHLET)
+    return fail(c, HRM_E_INVAL, "side %d is not a Dirichlet side", side);
+  const int64_t off = c->dg.goff[side], ns = c->nint / c->dg.n[side / 2];
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  hrm_status s;
+  if (primitive) {
+    if ((s = copy_planes(c, c->V + off, c->nc, values, ns, ns, c->N + c->D + 1, k, "copy boundary primitives")))
+      return s;
+    c->ck->ic(c->V, c->Wn, c->dg, c->fl, off, off + ns, c->stream);
+    ++c->launches;
+    if ((s = last_launch(c, "boundary state"))) return s;
+  } else if ((s = copy_planes(c, c->Wn + off, c->nc, values, ns, ns, c->M, k, "copy boundary W"))) {
+    return s;
+  }
+  // the RK stage state reads the same slice
+  if ((s = copy_planes(c, c->Ws + off, c->nc, c->Wn + off, c->nc, ns, c->M, cudaMemcpyDeviceToDevice,
+                       "copy boundary to stage state")))
+    return s;
+  c->bnd_set |= 1 << side;
+  if (!on_device) return cuda_check(c, cudaStreamSynchronize(c->stream), "boundary sync");
+  return HRM_OK;
+}
+
 hrm_status hrm_dt(hrm_ctx* c, double cfl, double* dt_out, double* tau_out) {
   if (!c || !(cfl > 0.0)) return c ? fail(c, HRM_E_INVAL, "cfl must be positive") : HRM_E_INVAL;
+  if (hrm_status s = check_boundaries(c)) return s;
   c->ck->prim(c->Wn, c->V, c->AUX, nullptr, nullptr, c->dg, c->fl, c->st, 1, c->stream);
   launch_finalize(c->st, c->dg, c->D, cfl, 1, c->stream);
   c->launches += 2;
@@ -497,6 +553,7 @@ hrm_status hrm_step(hrm_ctx* c, double dt, int32_t nsteps) {
   if (nsteps < 0) return fail(c, HRM_E_INVAL, "nsteps must be non-negative");
   if (nsteps == 0) return HRM_OK;
   hrm_status s;
+  if ((s = check_boundaries(c))) return s;
   if (!c->gexec && (s = build_graph(c))) return s;
   launch_set_dt(c->st, dt > 0.0 ? dt : 0.0, c->stream);
   ++c->launches;
@@ -530,9 +587,13 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
   if (!c || !lam || !rhs) return HRM_E_INVAL;
   double l3[3] = {0.0, 0.0, 0.0};
   for (int d = 0; d < c->D; ++d) l3[d] = lam[d];
-  hrm_status s = cuda_check(c, cudaMemcpyAsync(c->st->lam, l3, sizeof l3, cudaMemcpyHostToDevice, c->stream),
-                            "copy lambda");
-  if (s) return s;
+  hrm_status s;
+  if ((s = check_boundaries(c))) return s;
+  if ((s = cuda_check(c, cudaMemcpyAsync(c->st->lam, l3, sizeof l3, cudaMemcpyHostToDevice, c->stream),
+                      "copy lambda")))
+    return s;
+  // with Dirichlet slices the planes are staged at the stored stride
+  double* out = c->nint == c->nc ? rhs : c->Ws;
   if (c->params.precision == HRM_FP32)
     launch_prim32(c->N, c->D, c->Wn, c->P32, r32_target(c), c->dg, c->fl, c->st, 0, c->stream);
   else
@@ -546,10 +607,14 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
     c->fk->face[d](c->params.precision, c->Wn, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st,
                    gate_of(c, d), c->stream);
   }
-  c->fk->update(1, 0, c->Wn, c->Wn, rhs, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, 0.0, 1.0, 0, 0,
+  c->fk->update(1, 0, c->Wn, c->Wn, out, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, 0.0, 1.0, 0, 0,
                 c->stream);
   c->launches += 2 + c->D;
   if ((s = last_launch(c, "rhs"))) return s;
+  // (the update writes interior cells only: the stage state's slices stay)
+  if (out != rhs &&
+      (s = copy_planes(c, rhs, c->nint, out, c->nc, c->nint, c->M, cudaMemcpyDeviceToDevice, "copy rhs")))
+    return s;
   return cuda_check(c, cudaStreamSynchronize(c->stream), "rhs sync");
 }
 
@@ -580,10 +645,8 @@ hrm_status hrm_get(hrm_ctx* c, int32_t field, double* dst, int32_t on_device) {
     ++c->launches;
     src = c->Ws;
   }
-  const size_t bytes = sizeof(double) * (size_t)c->nc * planes;
-  hrm_status s = cuda_check(
-      c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
-      "copy field");
+  hrm_status s = copy_planes(c, dst, c->nint, src, c->nc, c->nint, planes,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, "copy field");
   if (s) return s;
   if (!on_device) return cuda_check(c, cudaStreamSynchronize(c->stream), "get sync");
   return last_launch(c, "get");

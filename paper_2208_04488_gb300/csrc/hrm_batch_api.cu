@@ -309,6 +309,7 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
         I.g.inv_dx[d] = 1.0;
       }
     }
+    I.g.nint = I.g.ncells;
     const int M = 2 * N + 2;
     const size_t plane = sizeof(double) * (size_t)I.g.ncells;
     b->total_cells += I.g.ncells;
@@ -350,7 +351,7 @@ hrm_status hrm_batch_set_primitive(hrm_batch* b, int32_t i, const double* prim, 
   hrm_status s = bcuda(b, cudaMemcpyAsync(I.V, prim, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                           b->stream), "copy primitives");
   if (s) return s;
-  cell_kernels(N, 2)->ic(I.V, I.Wn, I.g, I.f, b->stream);
+  cell_kernels(N, 2)->ic(I.V, I.Wn, I.g, I.f, 0, I.g.nint, b->stream);
   ++b->launches;
   reset_instance(b, i);
   return bcuda(b, cudaGetLastError(), "initial state");

@@ -41,20 +41,22 @@ void prim_l(const double* W, double* V, double* AUX, float* P32, float* R32, con
   k_prim<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, V, AUX, P32, R32, g, f, st, tau);
 }
 template <int N, int D>
-void ic_l(const double* prim, double* W, const DevGrid& g, const DevFluid& f, cudaStream_t s) {
-  k_ic<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(prim, W, g, f);
+void ic_l(const double* prim, double* W, const DevGrid& g, const DevFluid& f, int64_t c0, int64_t c1,
+          cudaStream_t s) {
+  if (c1 <= c0) return;
+  k_ic<N, D><<<grid_for(c1 - c0, kCellThreads), kCellThreads, 0, s>>>(prim, W, g, f, c0, c1);
 }
 template <int N, int D>
 void relax_l(double* W, const DevGrid& g, const DevFluid& f, cudaStream_t s) {
-  k_relax<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, g, f);
+  k_relax<N, D><<<grid_for(g.nint, kCellThreads), kCellThreads, 0, s>>>(W, g, f);
 }
 template <int N, int D>
 void fields_l(const double* W, double* out, int field, const DevGrid& g, const DevFluid& f, cudaStream_t s) {
-  k_fields<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, out, field, g, f);
+  k_fields<N, D><<<grid_for(g.nint, kCellThreads), kCellThreads, 0, s>>>(W, out, field, g, f);
 }
 template <int N, int D>
 void admiss_l(const double* W, const DevGrid& g, const DevFluid& f, StepState* st, cudaStream_t s) {
-  k_admiss<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, g, f, st);
+  k_admiss<N, D><<<grid_for(g.nint, kCellThreads), kCellThreads, 0, s>>>(W, g, f, st);
 }
 
 template <int N, int D>

@@ -133,14 +133,15 @@ __global__ void __launch_bounds__(kCellThreads)
 }
 
 // Initial state from primitive planes (alpha_1..alpha_{N-1}, u_d, p, T) in p-T
-// equilibrium: rho_k = (p + p_inf_k) / ((gamma_k - 1) c_v,k T) and the mixture EOS.
+// equilibrium: rho_k = (p + p_inf_k) / ((gamma_k - 1) c_v,k T) and the mixture EOS;
+// cells c0 <= c < c1.
 template <int N, int D>
 __global__ void __launch_bounds__(kCellThreads)
-    k_ic(const double* __restrict__ prim, double* __restrict__ W, DevGrid g, DevFluid f) {
+    k_ic(const double* __restrict__ prim, double* __restrict__ W, DevGrid g, DevFluid f, int64_t c0, int64_t c1) {
   using L = Lay<N, D>;
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t c = c0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nc = g.ncells;
-  if (c >= nc) return;
+  if (c >= c1) return;
   double al[N], s = 0.0;
 #pragma unroll
   for (int k = 0; k < N - 1; ++k) {
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(kCellThreads) k_relax(double* W, DevGrid g, De
   using L = Lay<N, D>;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nc = g.ncells;
-  if (c >= nc) return;
+  if (c >= g.nint) return;
   double w[L::M];
 #pragma unroll
   for (int m = 0; m < L::M; ++m) w[m] = W[m * nc + c];
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kCellThreads)
   constexpr int M = L::M;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nc = g.ncells;
-  if (c >= nc) return;
+  if (c >= g.nint) return;
   double w[M], v[M], rho, cs, rc2;
 #pragma unroll
   for (int m = 0; m < M; ++m) w[m] = W[m * nc + c];
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kCellThreads)
   using L = Lay<N, D>;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nc = g.ncells;
-  if (c >= nc) return;
+  if (c >= g.nint) return;
   double w[L::M];
 #pragma unroll
   for (int m = 0; m < L::M; ++m) w[m] = W[m * nc + c];

@@ -44,11 +44,17 @@ __device__ __forceinline__ float gpinf_gm1_of(const DevFluid& f, int k, float) {
 __device__ __forceinline__ double q_of(const DevFluid& f, int k, double) { return f.q[k]; }
 __device__ __forceinline__ float q_of(const DevFluid& f, int k, float) { return f.q_f[k]; }
 
+// Cells are stored plane by plane (x fastest). A Dirichlet side keeps its
+// boundary state as one slice of ghost cells stored after the nint interior
+// cells of every plane (slice cells: the other directions' indices, lowest
+// fastest), so ncells = nint + the slices and every per-plane stride is ncells.
 struct DevGrid {
   int64_t n[3];
-  int64_t ncells;
+  int64_t ncells;   // stored cells per plane (interior + Dirichlet slices)
+  int64_t nint;     // interior cells
+  int64_t goff[6];  // first cell of side b's slice (bc[b] == 2), else 0
   double dx[3], inv_dx[3];
-  int32_t bc[6];  // 0 transmissive, 1 periodic
+  int32_t bc[6];  // 0 transmissive, 1 periodic, 2 Dirichlet
 };
 
 struct DevParams {
@@ -116,7 +122,8 @@ __device__ __forceinline__ float tanh_r(float x) { return tanhf(x); }
 
 // Index of cell j (may lie in the 3 ghost layers) along direction d under the
 // boundary condition of that side: transmissive copies the first interior cell
-// (zeroth-order extrapolation), periodic wraps.
+// (zeroth-order extrapolation), periodic wraps. (Dirichlet sides are resolved
+// by the caller, which knows the transverse index.)
 __device__ __forceinline__ int64_t bc_map(const DevGrid& g, int d, int64_t j) {
   const int64_t n = g.n[d];
   if (j < 0) return g.bc[2 * d] == 1 ? j + n : 0;

@@ -27,7 +27,7 @@ void launch(const double* W, const double* V, const double* AUX, const float* P3
 void update32_d2(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
                  const double* F2, const DevGrid& g, const DevFluid& f, StepState* st, double a, double b, int relax,
                  int count, cudaStream_t s) {
-  const unsigned gr = grid_for(g.ncells, kCellThreads);
+  const unsigned gr = grid_for(g.nint, kCellThreads);
   if (N == 2)
     k_update<2, kD, 0, true><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count);
   else if (N == 3)

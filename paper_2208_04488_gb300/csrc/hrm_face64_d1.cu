@@ -31,7 +31,7 @@ void update_l(int mode, int fast, const double* Wn, const double* Wsrc, double* 
     update32_d1(N, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, s);
     return;
   }
-  const unsigned gr = grid_for(g.ncells, kCellThreads);
+  const unsigned gr = grid_for(g.nint, kCellThreads);
   if (mode == 1)
     k_update<N, kD, 1><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count);
   else

@@ -285,11 +285,17 @@ __device__ __forceinline__ bool face_nodes(const DevGrid& g, int64_t t, Nodes6& 
   const int64_t r = t / f0;
   const int64_t i1 = r % f1, i2 = r / f1;
   const int64_t fp = DIR == 0 ? i0 : (DIR == 1 ? i1 : i2);
+  const bool dlo = g.bc[2 * DIR] == 2, dhi = g.bc[2 * DIR + 1] == 2;
+  // cell of the Dirichlet slice that continues this line
+  const int64_t tr = DIR == 0 ? i2 * g.n[1] + i1 : (DIR == 1 ? i2 * g.n[0] + i0 : i1 * g.n[0] + i0);
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
-    const int64_t q = bc_map(g, DIR, fp - 3 + j);
+    const int64_t jj = fp - 3 + j;
+    const int64_t q = bc_map(g, DIR, jj);
     nd.c[j] = DIR == 0 ? (i2 * g.n[1] + i1) * g.n[0] + q
                        : (DIR == 1 ? (i2 * g.n[1] + q) * g.n[0] + i0 : (q * g.n[1] + i1) * g.n[0] + i0);
+    if (jj < 0 && dlo) nd.c[j] = g.goff[2 * DIR] + tr;
+    if (jj >= g.n[DIR] && dhi) nd.c[j] = g.goff[2 * DIR + 1] + tr;
   }
   return true;
 }
@@ -636,7 +642,7 @@ __device__ __forceinline__ void count_bits(StepState* st, int b) {
 // MODE 1 writes RHS instead of the combination. In-place (W_out == W_src or W^n)
 // is allowed: each thread reads its own cell before writing it.
 // FAST (precision form): reciprocal of dx and of rho instead of divisions.
-// One cell c < ncells.
+// One interior cell c < nint (Dirichlet slices keep their state).
 template <int N, int D, int MODE, bool FAST = false>
 __device__ __forceinline__ void update_body(int64_t c, const double* Wn, const double* Wsrc, double* Wout,
                                             const double* __restrict__ F0, const double* __restrict__ F1,
@@ -702,7 +708,7 @@ __global__ void __launch_bounds__(kCellThreads)
              const double* __restrict__ F1, const double* __restrict__ F2, DevGrid g, DevFluid f,
              StepState* st, double a, double b, int relax, int count) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.ncells) return;
+  if (c >= g.nint) return;
   update_body<N, D, MODE, FAST>(c, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, MODE == 1 ? 0.0 : st->dt, a, b, relax,
                                 count);
 }

@@ -16,7 +16,7 @@ struct CellKernels {
   // rounding residues of rho, u_d, p for the learned gate
   void (*prim)(const double* W, double* V, double* AUX, float* P32, float* R32, const DevGrid&, const DevFluid&,
                StepState*, int tau, cudaStream_t);
-  void (*ic)(const double* prim, double* W, const DevGrid&, const DevFluid&, cudaStream_t);
+  void (*ic)(const double* prim, double* W, const DevGrid&, const DevFluid&, int64_t c0, int64_t c1, cudaStream_t);
   void (*relax)(double* W, const DevGrid&, const DevFluid&, cudaStream_t);
   void (*fields)(const double* W, double* out, int field, const DevGrid&, const DevFluid&, cudaStream_t);
   void (*admiss)(const double* W, const DevGrid&, const DevFluid&, StepState*, cudaStream_t);

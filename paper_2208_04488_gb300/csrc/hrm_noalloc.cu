@@ -173,6 +173,7 @@ extern "C" hrm_status hrm_dt_noalloc(int32_t nspecies, int32_t ndim, const int64
     }
     g.ncells *= nd;
   }
+  g.nint = g.ncells;
   DevFluid f;
   std::memset(&f, 0, sizeof f);
   int liq = -1;

@@ -28,6 +28,7 @@ KERNEL_PRIM, KERNEL_FINALIZE, KERNEL_FACE_X, KERNEL_FACE_Y, KERNEL_FACE_Z, KERNE
 KERNEL_GATE = 6
 KERNEL_NAMES = {0: "prim", 1: "finalize", 2: "face_x", 3: "face_y", 4: "face_z", 5: "update", 6: "gate"}
 LEARNED_OFF, LEARNED_GATE, LEARNED_FIXED = 0, 1, 2
+BC_TRANSMISSIVE, BC_PERIODIC, BC_DIRICHLET = 0, 1, 2
 DETECTOR_PARAMS, DETECTOR_INPUTS = 2081, 30
 
 
@@ -92,6 +93,7 @@ def lib():
     L.hrm_set_params.argtypes = [_VP, P(HrmParams)]
     L.hrm_set.argtypes = [_VP, _VP, ctypes.c_int32]
     L.hrm_set_primitive.argtypes = [_VP, _VP, ctypes.c_int32]
+    L.hrm_set_boundary.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.c_int32]
     L.hrm_dt.argtypes = [_VP, ctypes.c_double, _DP, _DP]
     L.hrm_step.argtypes = [_VP, ctypes.c_double, ctypes.c_int32]
     L.hrm_relax.argtypes = [_VP]
@@ -235,6 +237,8 @@ class Solver:
     def from_problem(cls, problem, params: Optional[HrmParams] = None, stream=None, set_state=True):
         s = cls(problem.n, problem.lo, problem.hi, problem.bc, problem.gamma, problem.pinf, problem.cv,
                 problem.q, params=params, stream=stream)
+        for b, prim in getattr(problem, "boundary", {}).items():
+            s.set_boundary(b, prim, primitive=True)
         if set_state:
             s.set_primitive(problem.prim)
         return s
@@ -273,6 +277,13 @@ class Solver:
     def set_primitive(self, prim):
         ptr, dev = self._ptr(np.ascontiguousarray(prim, dtype=np.float64) if isinstance(prim, np.ndarray) else prim)
         self._check(lib().hrm_set_primitive(self.h, _VP(ptr), dev))
+
+    def set_boundary(self, side, values, primitive=True):
+        """State of Dirichlet side `side` (2 d + 0 low, 2 d + 1 high): primitive
+        planes (N + D + 1, slice cells) or, with primitive=False, W planes (M, slice cells)."""
+        ptr, dev = self._ptr(np.ascontiguousarray(values, dtype=np.float64)
+                             if isinstance(values, np.ndarray) else values)
+        self._check(lib().hrm_set_boundary(self.h, int(side), _VP(ptr), 1 if primitive else 0, dev))
 
     def set_params(self, params: HrmParams):
         self._check(lib().hrm_set_params(self.h, ctypes.byref(params)))

@@ -52,13 +52,16 @@ class Problem:
     n: List[int]                 # cells per direction (x first)
     lo: List[float]
     hi: List[float]
-    bc: List[int]                # 0 transmissive, 1 periodic; [lo_x, hi_x, lo_y, ...]
+    bc: List[int]                # 0 transmissive, 1 periodic, 2 Dirichlet; [lo_x, hi_x, lo_y, ...]
     prim: np.ndarray             # (N + D + 1, ncells) float64
     cfl: float = 0.5
     dt: Optional[float] = None   # constant time step, if the problem uses one
     t_end: Optional[float] = None
     nsteps: Optional[int] = None
     extra: dict = dataclasses.field(default_factory=dict)
+    # Dirichlet sides (bc 2): {b = 2 d + side: primitive planes of the boundary
+    # slice, (N + D + 1, cells of the side), lowest other direction fastest}
+    boundary: dict = dataclasses.field(default_factory=dict)
 
     @property
     def N(self) -> int:
@@ -307,6 +310,78 @@ def shock_water_column_2d(nx: int = 2048, ny: int = 1024, third_species: bool = 
                      np.where(post, T_post, T1))
     return Problem("shock_water_column_2d", gamma, pinf, cv, q, [nx, ny], [-10 * Dm, -5 * Dm],
                    [10 * Dm, 5 * Dm], [0, 0, 0, 0], prim, cfl=0.5)
+
+
+def undex_2d(nx: int = 1536, ny: int = 1920) -> Problem:
+    """Three-species extreme underwater explosion of Sec. 5.10 with the paper's
+    fluids (water, air, detonation products gamma 1.25, c_p 1000): a 16 L x
+    20 L domain, L = 1 m, with the free surface at y = 0 and 6 L of water below
+    it (the schematic's proportions; the text's y-range is read as [-6 L, 14 L]),
+    a detonation-gas bubble of radius 0.3 L centred at (0, -0.5 L) at 1e12 Pa and
+    1250 kg/m^3, water and air at 101325 Pa and 298 K, minor volume fractions
+    1e-8, sharp interfaces, constant extrapolation at every boundary."""
+    fl = [PAPER_WATER, PAPER_AIR, PAPER_DETONATION]
+    gamma, pinf, cv, q = _species(fl)
+    x, y = cell_centers([nx, ny], [-8.0, -6.0], [8.0, 14.0])
+    bubble = np.hypot(x, y + 0.5) < 0.3
+    water = (y < 0.0) & ~bubble
+    air = (y >= 0.0) & ~bubble
+    a1 = np.where(water, 1.0 - 2.0 * MINOR, MINOR)
+    a2 = np.where(air, 1.0 - 2.0 * MINOR, MINOR)
+    p_det, rho_det = 1.0e12, 1250.0
+    T_det = temperature_of(PAPER_DETONATION, p_det, rho_det)
+    p = np.where(bubble, p_det, 101325.0)
+    T = np.where(bubble, T_det, 298.0)
+    nc = nx * ny
+    prim = _assemble(3, 2, [a1, a2], [np.zeros(nc), np.zeros(nc)], p, T)
+    return Problem("undex_2d", gamma, pinf, cv, q, [nx, ny], [-8.0, -6.0], [8.0, 14.0], [0, 0, 0, 0], prim,
+                   cfl=0.5, t_end=2.5e-4)
+
+
+def mach100_jet_2d(nx: int = 1024, ny: int = 512) -> Problem:
+    """Two-dimensional Mach 100 water jet of Sec. 5.9 with the paper's fluids:
+    [0, L] x [-0.25 L, 0.25 L], L = 1 m, essentially pure air at 101325 Pa and
+    298 K; a Dirichlet left boundary with a water jet (alpha_1 = 1 - 1e-8,
+    u = 1.5e5 m/s) for |y| <= 0.05 L and ambient air elsewhere; constant
+    extrapolation at the top, bottom and right."""
+    fl = [PAPER_WATER, PAPER_AIR]
+    gamma, pinf, cv, q = _species(fl)
+    nc = nx * ny
+    prim = _assemble(2, 2, [np.full(nc, MINOR)], [np.zeros(nc), np.zeros(nc)], np.full(nc, 101325.0),
+                     np.full(nc, 298.0))
+    yb = -0.25 + (np.arange(ny) + 0.5) * (0.5 / ny)
+    jet = np.abs(yb) <= 0.05
+    left = _assemble(2, 2, [np.where(jet, 1.0 - MINOR, MINOR)], [np.where(jet, 1.5e5, 0.0), np.zeros(ny)],
+                     np.full(ny, 101325.0), np.full(ny, 298.0))
+    return Problem("mach100_jet_2d", gamma, pinf, cv, q, [nx, ny], [0.0, -0.25], [1.0, 0.25], [2, 0, 0, 0], prim,
+                   cfl=0.5, boundary={0: left})
+
+
+def dirichlet_box(n, seed: int = 7) -> Problem:
+    """Seeded two-species state (the paper's water and air) on [0, 1]^D, D =
+    len(n), with a Dirichlet state on every side: the interior is smooth
+    (alpha_1 = 0.5 + 0.4 sin, |u| <= 50 m/s, p in 1e5..2e5 Pa, T in 300..400 K),
+    each boundary cell an independent random state, so the stencils next to
+    every side see jumps. For the boundary's wiring: ghost layers, sides and
+    transverse indices."""
+    rng = np.random.default_rng(seed)
+    D = len(n)
+    fl = [PAPER_WATER, PAPER_AIR]
+    gamma, pinf, cv, q = _species(fl)
+    X = cell_centers(list(n), [0.0] * D, [1.0] * D)
+    ph = rng.uniform(0.0, 2.0 * math.pi, size=(4, D))
+    wave = [sum(np.sin(2.0 * math.pi * (d + 1) * X[d] + ph[j, d]) for d in range(D)) / D for j in range(4)]
+    prim = _assemble(2, D, [0.5 + 0.4 * wave[0]], [50.0 * wave[1 + (d % 2)] for d in range(D)],
+                     1.5e5 + 0.5e5 * wave[3], 350.0 + 50.0 * wave[2])
+    nc = int(np.prod(n))
+    boundary = {}
+    for b in range(2 * D):
+        ns = nc // n[b // 2]
+        boundary[b] = _assemble(2, D, [rng.uniform(1e-6, 1.0 - 1e-6, ns)],
+                                [rng.normal(0.0, 100.0, ns) for _ in range(D)],
+                                10.0 ** rng.uniform(5.0, 6.0, ns), rng.uniform(250.0, 600.0, ns))
+    return Problem("dirichlet_box_%dd" % D, gamma, pinf, cv, q, list(n), [0.0] * D, [1.0] * D, [2] * (2 * D), prim,
+                   cfl=0.45, boundary=boundary)
 
 
 def interface_3d(n: int = 256, mach: float = 1.5, seed: int = 20221003) -> Problem:

@@ -39,6 +39,9 @@ def small_problems():
     out.append(sw)
     b = P.batch_instances(count=2, scale=16)
     out.extend(b)
+    # Dirichlet sides (Sec. 5.9 inflow): random boundary states on every side, and the jet
+    out.extend([P.dirichlet_box([13]), P.dirichlet_box([11, 9]), P.dirichlet_box([7, 6, 5]),
+                P.mach100_jet_2d(48, 24)])
     return out
 
 
@@ -249,8 +252,10 @@ def test_invalid_arguments_do_not_touch_state(hrm):
 
 
 @pytest.mark.parametrize("pr", [P.shock_tube_1d_baseline(400), P.shock_bubble_2d(64, 32),
-                                P.shock_tube_1d_paper(200, extreme=True), P.interface_3d(12)],
-                         ids=["shock_tube_400", "shock_bubble_64x32", "extreme_200", "interface_3d_12"])
+                                P.shock_tube_1d_paper(200, extreme=True), P.interface_3d(12), P.undex_2d(48, 60),
+                                P.mach100_jet_2d(48, 24), P.dirichlet_box([10, 8, 7])],
+                         ids=["shock_tube_400", "shock_bubble_64x32", "extreme_200", "interface_3d_12", "undex_48x60",
+                              "mach100_jet_48x24", "dirichlet_box_10x8x7"])
 def test_fp64_path_reproduces_oracle_bit_for_bit(hrm, orc, pr):
     """The FP64 path evaluates every operation of the method in the oracle's
     order with IEEE rounding (no contraction, the same explicit tanh), so the
@@ -370,3 +375,85 @@ def test_modes_reproduce_oracle_bit_for_bit(hrm, orc, pr, mode):
         W = orc.step(f, p, g, W, dt, 1)
         s.step(dt, 1)
     np.testing.assert_array_equal(s.get(hrm.FIELD_W), W)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_undex_robustness(hrm, precision):
+    """Sec. 5.10 (three-species underwater explosion, 1e12 Pa detonation gas):
+    with the positivity limiters every cell stays admissible over 150 steps in
+    both forms; without them the solution leaves the admissible set."""
+    pr = P.undex_2d(192, 240)
+    prec = hrm.FP64 if precision == "fp64" else hrm.FP32
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, precision=prec, check=0))
+    s.step(0.0, 150)
+    assert s.admissibility() == [0, 0, 0, 0]
+    t, n = s.time()
+    assert n == 150 and t > 0.0
+    s.close()
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, precision=prec, check=0, limiters=0))
+    failed = False
+    for _ in range(30):
+        s.step(0.0, 5)
+        if s.admissibility() != [0, 0, 0, 0]:
+            failed = True
+            break
+    assert failed
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mach100_jet_robustness(hrm, precision):
+    """Sec. 5.9 (Mach 100 water jet into air through a Dirichlet inflow): with
+    the positivity limiters every cell stays admissible over 300 steps in both
+    forms; without them the first step already leaves the admissible set."""
+    pr = P.mach100_jet_2d(512, 256)
+    prec = hrm.FP64 if precision == "fp64" else hrm.FP32
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, precision=prec, check=0))
+    s.step(0.0, 300)
+    assert s.admissibility() == [0, 0, 0, 0]
+    W = s.get(hrm.FIELD_W)
+    assert W.shape == (pr.M, pr.ncells)
+    # water has entered the domain through the inflow
+    water = W[0].reshape(pr.n[1], pr.n[0])
+    assert water[:, 20:].max() > 100.0
+    s.close()
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, precision=prec, check=0, limiters=0))
+    s.step(0.0, 1)
+    assert s.admissibility() != [0, 0, 0, 0]
+    s.close()
+
+
+def test_dirichlet_api(hrm):
+    """A Dirichlet side must be given a state before stepping; other sides
+    refuse one; the batched form refuses Dirichlet sides; hrm_set and hrm_get
+    keep the interior layout, and the boundary state survives hrm_set."""
+    pr = P.mach100_jet_2d(32, 16)
+    s = hrm.Solver.from_problem(pr, set_state=False)  # from_problem sets the boundary
+    s2 = hrm.Solver(pr.n, pr.lo, pr.hi, pr.bc, pr.gamma, pr.pinf, pr.cv, pr.q)
+    s2.set_primitive(pr.prim)
+    for call in (lambda: s2.step(0.0, 1), lambda: s2.dt(0.5)):
+        with pytest.raises(hrm.HrmError) as e:
+            call()
+        assert e.value.status == hrm.HRM_E_INVAL
+    with pytest.raises(hrm.HrmError):
+        s2.set_boundary(1, pr.boundary[0])  # the high x side is transmissive
+    with pytest.raises(hrm.HrmError):
+        s2.set_boundary(4, pr.boundary[0])  # no third direction
+    s2.set_boundary(0, pr.boundary[0])
+    s.set_primitive(pr.prim)
+    np.testing.assert_array_equal(s.get(hrm.FIELD_W), s2.get(hrm.FIELD_W))
+    (dta, taua), (dtb, taub) = s.dt(0.5), s2.dt(0.5)
+    assert dta == dtb and np.array_equal(taua, taub)
+    s.step(0.0, 3)
+    s2.step(0.0, 3)
+    np.testing.assert_array_equal(s.get(hrm.FIELD_W), s2.get(hrm.FIELD_W))
+    # conservative boundary planes give the same state as primitive ones
+    import oracle
+    f, g, _ = oracle.setup(pr)
+    s3 = hrm.Solver(pr.n, pr.lo, pr.hi, pr.bc, pr.gamma, pr.pinf, pr.cv, pr.q)
+    s3.set_boundary(0, g._keep[0], primitive=False)
+    s3.set_primitive(pr.prim)
+    s3.step(0.0, 3)
+    np.testing.assert_array_equal(s3.get(hrm.FIELD_W), s2.get(hrm.FIELD_W))
+    with pytest.raises(hrm.HrmError) as e:
+        hrm.BatchSolver([pr])
+    assert e.value.status == hrm.HRM_E_INVAL

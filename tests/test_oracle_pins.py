@@ -394,3 +394,24 @@ def test_explicit_tanh_matches_the_function(orc):
             ref = math.tanh(v)
             assert abs(t - ref) <= 4 * np.spacing(abs(ref)) + 1e-300, (v, t, ref)
             assert orc.tanh(-v) == -t
+
+
+
+def test_ic_table_undex(orc):
+    """Table IC_2D_three_species_extreme_UNDEX_problem (Sec. 5.10): partial
+    densities of the water, air and detonation-product regions (the minor
+    third species, whose alpha is derived as 1 - alpha_1 - alpha_2, to the
+    rounding of that difference)."""
+    pr = P.undex_2d(48, 60)
+    f, g, W = orc.setup(pr)
+    x, y = P.cell_centers(pr.n, pr.lo, pr.hi)
+    water = int(np.argmax((y < -3.0)))
+    air = int(np.argmax((y > 5.0)))
+    det = int(np.argmin(np.hypot(x, y + 0.5)))
+    exp = {water: (1.0227724208197188e3, 1.1817862212832324e-8, 1.7000838926174497e-8),
+           air: (1.0227724412751677e-5, 1.1817861976475079, 1.7000838926174497e-8),
+           det: (8.9361901785714267e-7, 8.6891757696127126e-6, 1.2499999749999999e3)}
+    for c, (a, b, d) in exp.items():
+        assert W[0, c] == pytest.approx(a, rel=1e-14)
+        assert W[1, c] == pytest.approx(b, rel=1e-14)
+        assert W[2, c] == pytest.approx(d, rel=1e-14 if c == det else 1e-7)
