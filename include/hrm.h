@@ -98,7 +98,11 @@ typedef struct {
                           margins, that the limiters would leave a midpoint unchanged (every
                           checked quantity above its threshold) and evaluates them in FP64
                           only where it cannot; results are the same as with 0 (always FP64) */
-  int32_t pad_screen;
+  int32_t cfl_sound;   /* sound speed of the CFL maxima tau_d (Sec. 4.1.2): 0 (default) the
+                          five-equation c of the hyperbolic step, which the positivity bound of
+                          the HLLC fluxes rests on; 1 the four-equation HRM c of Eq. 4_eqn_sos
+                          (smaller, so a larger step without that guarantee). hrm_dt follows it;
+                          hrm_dt_noalloc and the batched form use the five-equation c. */
 } hrm_params;
 
 /* Field selectors of hrm_get. */
@@ -107,7 +111,10 @@ enum {
   HRM_FIELD_V = 1,     /* M planes: alpha_k rho_k, u_d, p (five-equation EOS), alpha_k */
   HRM_FIELD_C5 = 2,    /* 1 plane: five-equation sound speed, rho c^2 = gbar (p + pbar_inf) (Sec. 2) */
   HRM_FIELD_PT = 3,    /* 2 planes: equilibrium p and T of the four-equation HRM (Sec. 4.2) */
-  HRM_FIELD_C4 = 4     /* 1 plane: four-equation HRM sound speed (Eq. 4_eqn_sos) */
+  HRM_FIELD_C4 = 4,    /* 1 plane: four-equation HRM sound speed (Eq. 4_eqn_sos) */
+  HRM_FIELD_PSI_GAMMA = 5 /* N + 1 planes: Psi_1..Psi_N, Gamma of the four-equation HRM at the
+                             equilibrium pressure (Sec. 3: derivatives of the relaxed pressure
+                             with respect to alpha_k rho_k and to rho e) */
 };
 
 /* Fill p with the paper's constants (Sec. 4.3.2, App. C, Sec. 4.3.1), PP-WCNS-IS,

@@ -69,7 +69,7 @@ class Fluid(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("limiters", ctypes.c_int32), ("blend", ctypes.c_int32),
                 ("relax_mode", ctypes.c_int32), ("scheme", ctypes.c_int32),
-                ("integrator", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("integrator", ctypes.c_int32), ("cfl_sound", ctypes.c_int32),
                 ("pad1", ctypes.c_int32), ("pad2", ctypes.c_int32),
                 ("eps_ar", ctypes.c_double), ("eps_a", ctypes.c_double),
                 ("eps_rhoe", ctypes.c_double), ("hs_ar", ctypes.c_double),
@@ -120,6 +120,8 @@ def lib(count: bool = False):
         L.or_relax.argtypes = [P(Fluid), P(Grid), _DP]
         L.or_dt.argtypes = [P(Fluid), P(Grid), _DP, ctypes.c_double, _DP]
         L.or_dt.restype = ctypes.c_double
+        L.or_dt_sound.argtypes = [P(Fluid), P(Grid), _DP, ctypes.c_double, ctypes.c_int, _DP]
+        L.or_dt_sound.restype = ctypes.c_double
         L.or_lambdas.argtypes = [P(Fluid), P(Grid), _DP, ctypes.c_double, _DP]
         L.or_step.argtypes = [P(Fluid), P(Params), P(Grid), _DP, ctypes.c_double, ctypes.c_int]
         L.or_admissibility.argtypes = [P(Fluid), P(Grid), _DP, P(ctypes.c_int64)]
@@ -313,10 +315,12 @@ def relax(f: Fluid, g: Grid, W):
     return W
 
 
-def dt(f: Fluid, g: Grid, W, cfl):
+def dt(f: Fluid, g: Grid, W, cfl, sound=0):
+    """CFL step and tau_d; sound 1: the four-equation HRM sound speed in the
+    wave speeds (Eq. 4_eqn_sos) instead of the five-equation one."""
     W = np.ascontiguousarray(W, dtype=np.float64)
     tau = np.zeros(3)
-    d = lib().or_dt(ctypes.byref(f), ctypes.byref(g), _ptr(W), cfl, _ptr(tau))
+    d = lib().or_dt_sound(ctypes.byref(f), ctypes.byref(g), _ptr(W), cfl, int(sound), _ptr(tau))
     return d, tau[:g.D].copy()
 
 

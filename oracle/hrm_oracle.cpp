@@ -132,7 +132,8 @@ struct or_params {
   int32_t relax_mode;  // 0 off, 1 after every RK stage (Sec. 4.4), 2 after the full step
   int32_t scheme;      // 0 PP-WCNS-IS, 1 first-order HLLC only (Sec. 4.1.1)
   int32_t integrator;  // 0 SSP-RK3, 1 forward Euler, 2 SSP-RK2 (Sec. 5.1)
-  int32_t pad0, pad1, pad2;
+  int32_t cfl_sound;   // sound speed of the CFL maxima: 0 five-equation c, 1 four-equation HRM c (Eq. 4_eqn_sos)
+  int32_t pad1, pad2;
   double eps_ar, eps_a, eps_rhoe;   // limiter thresholds (Sec. 4.3.2)
   double hs_ar, hs_a, hs_rc2, hs_rhoe;  // hard-switch thresholds (Sec. 4.3.2)
   double weno_eps;                  // App. C
@@ -953,11 +954,65 @@ static void relax_grid(const FluidK& f, int64_t nc, double* W) {
   }
 }
 
+// Four-equation HRM sound speed of a cell (Eq. 4_eqn_sos) at its equilibrium
+// state (Sec. 4.2): out = {c4, p, T, Gamma, Psi_1..Psi_N}; Psi_k and Gamma by
+// implicit differentiation of the p* quadratic (Sec. 3 definitions).
+static void c4eq_impl(const FluidK& f, const real* W, real* out) {
+  const int N = f.N, l = f.liq;
+  real w[OR_MAXM];
+  for (int m = 0; m < f.M; ++m) w[m] = W[m];
+  real pT[2];
+  relax_cell(f, w, pT);  // equilibrium p, T of this (alpha_k rho_k, rho u, E)
+  real p = pT[0];
+  real rho = 0.0;
+  for (int k = 0; k < N; ++k) rho = rho + w[k];
+  real Y[OR_MAXN];
+  for (int k = 0; k < N; ++k) Y[k] = w[k] / rho;
+  real re = rhoe_tilde(f, w);
+  real cvb = 0.0, cpb = 0.0;
+  for (int k = 0; k < N; ++k) {
+    cvb = cvb + Y[k] * real(f.cv[k]);
+    cpb = cpb + Y[k] * real(f.cp[k]);
+  }
+  const real pinf1 = f.pinf[l];
+  const real R1 = f.Rgas[l];
+  const real Rb = cpb - cvb;
+  real Ap = cvb;
+  real Bp = -(re * Rb - pinf1 * cvb - pinf1 * Y[l] * R1);
+  real denom = real(2.0) * Ap * p + Bp;
+  // e-derivatives at fixed partial densities: d(rho e~)/de = rho
+  real dB_de = -(rho * Rb);
+  real dC_de = -(pinf1 * rho * (Rb - Y[l] * R1));
+  real Gam = (-(dB_de * p + dC_de) / denom) / rho;
+  real c2 = Gam * p / rho;
+  for (int k = 0; k < N; ++k) {
+    // derivatives at fixed e and other partial densities
+    real e_spec = re / rho;  // e - qbar
+    real qbar = 0.0;
+    for (int s = 0; s < N; ++s) qbar = qbar + Y[s] * real(f.q[s]);
+    real drhoe = (e_spec + qbar) - real(f.q[k]);  // d(rho e - sum ar q)/d ar_k = e - q_k
+    real dcv = (real(f.cv[k]) - cvb) / rho;
+    real dRb = (real(f.Rgas[k]) - Rb) / rho;
+    real dY1 = ((k == l ? real(1.0) : real(0.0)) - Y[l]) / rho;
+    real dA = dcv;
+    real dB = -(drhoe * Rb + re * dRb - pinf1 * dcv - pinf1 * R1 * dY1);
+    real dC = -(pinf1 * (drhoe * (Rb - Y[l] * R1) + re * (dRb - R1 * dY1)));
+    real Psi = -(dA * p * p + dB * p + dC) / denom;
+    out[4 + k] = Psi;
+    c2 = c2 + Y[k] * Psi;
+  }
+  out[0] = rsqrt_(c2);
+  out[1] = p;
+  out[2] = pT[1];
+  out[3] = Gam;
+}
+
+
 // Max wave speed per direction (Sec. 4.1.2): tau_d = max(|u_d| + c)/dx_d with the
 // five-equation sound speed.
 // Reading: the prescribed states of Dirichlet sides enter the maximum too (their
 // waves enter the domain at once).
-static void tau_impl(const FluidK& f, const or_grid* g, const double* W, real* tau) {
+static void tau_impl(const FluidK& f, const or_grid* g, const double* W, real* tau, int sound = 0) {
   const int64_t nc = ncells(g);
   for (int d = 0; d < g->D; ++d) tau[d] = 0.0;
   auto visit = [&](const double* X, int64_t n, int64_t c) {
@@ -965,8 +1020,14 @@ static void tau_impl(const FluidK& f, const or_grid* g, const double* W, real* t
     load_W(f, X, n, c, w);
     Cell C;
     cell_from_W(f, w, C);
+    real cw = C.c;  // five-equation c (sound 0) or the four-equation HRM c (sound 1)
+    if (sound == 1) {
+      real o[4 + OR_MAXN];
+      c4eq_impl(f, w, o);
+      cw = o[0];
+    }
     for (int d = 0; d < g->D; ++d) {
-      real s = (rabs_(C.V[sMOM(f, d)]) + C.c) / real(g->dx[d]);
+      real s = (rabs_(C.V[sMOM(f, d)]) + cw) / real(g->dx[d]);
       tau[d] = rmax(tau[d], s);
     }
   };
@@ -1142,17 +1203,23 @@ void or_relax(const or_fluid* fl, const or_grid* g, double* W) {
   relax_grid(f, ncells(g), W);
 }
 
-// tau[d] and dt = CFL / sum tau (Sec. 4.1.2). Returns dt.
-double or_dt(const or_fluid* fl, const or_grid* g, const double* W, double cfl, double* tau) {
+// tau[d] and dt = CFL / sum tau (Sec. 4.1.2), with the wave speed's sound speed
+// chosen: 0 five-equation c, 1 the four-equation HRM c (Eq. 4_eqn_sos). Returns dt.
+double or_dt_sound(const or_fluid* fl, const or_grid* g, const double* W, double cfl, int sound, double* tau) {
   FluidK f = make_fluid(fl);
   real t[3] = {0.0, 0.0, 0.0};
-  tau_impl(f, g, W, t);
+  tau_impl(f, g, W, t, sound);
   real st = 0.0;
   for (int d = 0; d < g->D; ++d) {
     st = st + t[d];
     if (tau) tau[d] = val(t[d]);
   }
   return val(real(cfl) / st);
+}
+
+// tau[d] and dt with the five-equation c (Sec. 4.1.2). Returns dt.
+double or_dt(const or_fluid* fl, const or_grid* g, const double* W, double cfl, double* tau) {
+  return or_dt_sound(fl, g, W, cfl, 0, tau);
 }
 
 // lambda_d for a given dt from the state W (Sec. 4.1.2).
@@ -1229,7 +1296,7 @@ void or_step_gated(const or_fluid* fl, const or_params* P, const or_grid* g, dou
   step_impl(f, P, g, W, dt, nsteps, 0.0, [&](const double* Ws, double, real* L, bool first) {
     if (first) {
       real t[3] = {0.0, 0.0, 0.0};
-      tau_impl(f, g, Ws, t);
+      tau_impl(f, g, Ws, t, P->cfl_sound);
       lambdas(g, t, real(dt), lam);
     }
     rhs_impl(f, P, g, Ws, lam, L, gate);
@@ -1305,53 +1372,10 @@ void or_admissibility(const or_fluid* fl, const or_grid* g, const double* W, int
 // out: [0] c_4eq, [1] p, [2] T, [3] Gamma, [4..4+N) Psi_k.
 void or_c4eq_cell(const or_fluid* fl, const double* W, double* out) {
   FluidK f = make_fluid(fl);
-  const int N = f.N, l = f.liq;
-  real w[OR_MAXM];
+  real w[OR_MAXM], o[4 + OR_MAXN];
   for (int m = 0; m < f.M; ++m) w[m] = W[m];
-  real pT[2];
-  relax_cell(f, w, pT);  // equilibrium p, T of this (alpha_k rho_k, rho u, E)
-  real p = pT[0];
-  real rho = 0.0;
-  for (int k = 0; k < N; ++k) rho = rho + w[k];
-  real Y[OR_MAXN];
-  for (int k = 0; k < N; ++k) Y[k] = w[k] / rho;
-  real re = rhoe_tilde(f, w);
-  real cvb = 0.0, cpb = 0.0;
-  for (int k = 0; k < N; ++k) {
-    cvb = cvb + Y[k] * real(f.cv[k]);
-    cpb = cpb + Y[k] * real(f.cp[k]);
-  }
-  const real pinf1 = f.pinf[l];
-  const real R1 = f.Rgas[l];
-  const real Rb = cpb - cvb;
-  real Ap = cvb;
-  real Bp = -(re * Rb - pinf1 * cvb - pinf1 * Y[l] * R1);
-  real denom = real(2.0) * Ap * p + Bp;
-  // e-derivatives at fixed partial densities: d(rho e~)/de = rho
-  real dB_de = -(rho * Rb);
-  real dC_de = -(pinf1 * rho * (Rb - Y[l] * R1));
-  real Gam = (-(dB_de * p + dC_de) / denom) / rho;
-  real c2 = Gam * p / rho;
-  for (int k = 0; k < N; ++k) {
-    // derivatives at fixed e and other partial densities
-    real e_spec = re / rho;  // e - qbar
-    real qbar = 0.0;
-    for (int s = 0; s < N; ++s) qbar = qbar + Y[s] * real(f.q[s]);
-    real drhoe = (e_spec + qbar) - real(f.q[k]);  // d(rho e - sum ar q)/d ar_k = e - q_k
-    real dcv = (real(f.cv[k]) - cvb) / rho;
-    real dRb = (real(f.Rgas[k]) - Rb) / rho;
-    real dY1 = ((k == l ? real(1.0) : real(0.0)) - Y[l]) / rho;
-    real dA = dcv;
-    real dB = -(drhoe * Rb + re * dRb - pinf1 * dcv - pinf1 * R1 * dY1);
-    real dC = -(pinf1 * (drhoe * (Rb - Y[l] * R1) + re * (dRb - R1 * dY1)));
-    real Psi = -(dA * p * p + dB * p + dC) / denom;
-    out[4 + k] = val(Psi);
-    c2 = c2 + Y[k] * Psi;
-  }
-  out[0] = val(rsqrt_(c2));
-  out[1] = val(p);
-  out[2] = val(pT[1]);
-  out[3] = val(Gam);
+  c4eq_impl(f, w, o);
+  for (int i = 0; i < 4 + f.N; ++i) out[i] = val(o[i]);
 }
 
 // Initial state in pressure and temperature equilibrium (Sec. 5): from the

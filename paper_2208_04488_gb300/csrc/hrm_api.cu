@@ -100,6 +100,7 @@ hrm_status check_params(hrm_ctx* c, const hrm_params* p) {
     return fail(c, HRM_E_INVAL, "the gate acts on the WENO-IS interpolation (scheme WCNS only)");
   if (p->q_sensor < 1.0 || p->q_sensor != std::floor(p->q_sensor))
     return fail(c, HRM_E_INVAL, "q_sensor must be a positive integer");
+  if (p->cfl_sound < 0 || p->cfl_sound > 1) return fail(c, HRM_E_INVAL, "unknown cfl_sound %d", p->cfl_sound);
   return HRM_OK;
 }
 
@@ -174,6 +175,10 @@ GateArgs gate_of(const hrm_ctx* c, int d) {
 // The FP64 form runs the detector as its own kernel before each sweep.
 bool separate_gate(const hrm_ctx* c) { return c->params.learned == 1 && c->params.precision != HRM_FP32; }
 
+// CFL maxima of the prim kernels: 1 with the five-equation c, 2 with the
+// four-equation HRM c (params.cfl_sound).
+int tau_mode(const hrm_ctx* c) { return c->params.cfl_sound ? 2 : 1; }
+
 // One RK stage: primitives of Wsrc, (gates,) midpoint fluxes, update into Wout.
 int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, double a, double b, int relax,
                   int count, bool first) {
@@ -181,9 +186,9 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
   float* p32 = p32_target(c);
   traced(c, s, HRM_KERNEL_PRIM, [&] {
     if (c->params.precision == HRM_FP32)
-      launch_prim32(c->N, c->D, Wsrc, c->P32, r32_target(c), c->dg, c->fl, c->st, first ? 1 : 0, s);
+      launch_prim32(c->N, c->D, Wsrc, c->P32, r32_target(c), c->dg, c->fl, c->st, first ? tau_mode(c) : 0, s);
     else
-      c->ck->prim(Wsrc, c->V, c->AUX, p32, r32_target(c), c->dg, c->fl, c->st, first ? 1 : 0, s);
+      c->ck->prim(Wsrc, c->V, c->AUX, p32, r32_target(c), c->dg, c->fl, c->st, first ? tau_mode(c) : 0, s);
   });
   ++k;
   if (first) {
@@ -535,7 +540,7 @@ hrm_status hrm_set_boundary(hrm_ctx* c, int32_t side, const double* values, int3
 hrm_status hrm_dt(hrm_ctx* c, double cfl, double* dt_out, double* tau_out) {
   if (!c || !(cfl > 0.0)) return c ? fail(c, HRM_E_INVAL, "cfl must be positive") : HRM_E_INVAL;
   if (hrm_status s = check_boundaries(c)) return s;
-  c->ck->prim(c->Wn, c->V, c->AUX, nullptr, nullptr, c->dg, c->fl, c->st, 1, c->stream);
+  c->ck->prim(c->Wn, c->V, c->AUX, nullptr, nullptr, c->dg, c->fl, c->st, tau_mode(c), c->stream);
   launch_finalize(c->st, c->dg, c->D, cfl, 1, c->stream);
   c->launches += 2;
   StepState h;
@@ -636,6 +641,9 @@ hrm_status hrm_get(hrm_ctx* c, int32_t field, double* dst, int32_t on_device) {
       break;
     case HRM_FIELD_PT:
       planes = 2;
+      break;
+    case HRM_FIELD_PSI_GAMMA:
+      planes = c->N + 1;
       break;
     default:
       return fail(c, HRM_E_INVAL, "unknown field %d", field);

@@ -232,8 +232,9 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
   if (p.cfl <= 0.0 || (p.limiters && p.cfl > 0.5))
     return bail(bfail(b, HRM_E_INVAL, "cfl must be in (0, 0.5] with the limiters on (Sec. 4.1.2)"));
   if (p.scheme != HRM_SCHEME_WCNS || p.integrator != HRM_RK3 || p.learned || p.precision < 0 || p.precision > 1 ||
-      p.relax_mode < 0 || p.relax_mode > 2)
-    return bail(bfail(b, HRM_E_INVAL, "batched form: PP-WCNS-IS with SSP-RK3, FP64 or FP32 precision only"));
+      p.relax_mode < 0 || p.relax_mode > 2 || p.cfl_sound != 0)
+    return bail(bfail(b, HRM_E_INVAL,
+                      "batched form: PP-WCNS-IS with SSP-RK3, FP64 or FP32 precision, five-equation CFL speed only"));
   b->dp.limiters = p.limiters;
   b->dp.blend = p.blend;
   b->dp.scheme = p.scheme;

@@ -39,16 +39,73 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
   return (unsigned long long)__double_as_longlong(x);
 }
 
+// Four-equation HRM sound speed (Eq. 4_eqn_sos): Psi_k and Gamma by implicit
+// differentiation of A_p p^2 + B_p p + C_p = 0 at the relaxed pressure p.
+// Optionally also returns Psi_k (N values) and Gamma.
+template <int N, int D>
+__device__ __forceinline__ double c4eq(const double* W, const DevFluid& f, double p, double* Psi = nullptr,
+                                       double* Gam_out = nullptr) {
+  const int l = f.liq;
+  double rho = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) rho += W[k];
+  double Y[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) Y[k] = W[k] / rho;
+  const double re = rhoe_tilde<N, D>(W, f);
+  double cvb = 0.0, cpb = 0.0, qb = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    cvb += Y[k] * f.cv[k];
+    cpb += Y[k] * f.cp[k];
+    qb += Y[k] * f.q[k];
+  }
+  const double pinf1 = f.pinf[l], R1 = f.Rg[l], Rb = cpb - cvb;
+  const double Bp = -(re * Rb - pinf1 * cvb - pinf1 * Y[l] * R1);
+  const double den = 2.0 * cvb * p + Bp;
+  const double Gam = (-(-(rho * Rb) * p - pinf1 * rho * (Rb - Y[l] * R1)) / den) / rho;
+  if (Gam_out) *Gam_out = Gam;
+  double c2 = Gam * p / rho;
+  const double e = re / rho + qb;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double dre = e - f.q[k];
+    const double dcv = (f.cv[k] - cvb) / rho;
+    const double dRb = (f.Rg[k] - Rb) / rho;
+    const double dY1 = ((k == l ? 1.0 : 0.0) - Y[l]) / rho;
+    const double dB = -(dre * Rb + re * dRb - pinf1 * dcv - pinf1 * R1 * dY1);
+    const double dC = -(pinf1 * (dre * (Rb - Y[l] * R1) + re * (dRb - R1 * dY1)));
+    const double psi = -(dcv * p * p + dB * p + dC) / den;
+    if (Psi) Psi[k] = psi;
+    c2 += Y[k] * psi;
+  }
+  return sqrt(c2);
+}
+
+// Four-equation HRM sound speed of a conservative vector: relaxed p, then Eq.
+// 4_eqn_sos (the CFL speed option params.cfl_sound = 1).
+template <int N, int D>
+__device__ __forceinline__ double c4_of_cell(const double* w, const DevFluid& f) {
+  double wr[Lay<N, D>::M], pT[2];
+#pragma unroll
+  for (int m = 0; m < Lay<N, D>::M; ++m) wr[m] = w[m];
+  relax_cell<N, D>(wr, f, pT);
+  return c4eq<N, D>(w, f, pT[0]);
+}
+
 // Per cell: V (M planes), AUX = (c, rho, rho c^2). With `tau`, also the running
 // maxima tau_d = max(|u_d| + c)/dx_d (Sec. 4.1.2): warp shuffles, then one
-// atomicMax per block and direction on the order-preserving bits.
+// atomicMax per block and direction on the order-preserving bits. tau = 1 takes
+// the five-equation c, tau = 2 the four-equation HRM c (Eq. 4_eqn_sos).
 // One cell c < ncells: primitives, AUX, optional FP32 planes and, for the
 // learned gate, the FP32 rounding residues of rho, u_d and p (R32, D + 2
-// planes: rho, u_0 .. u_{D-1}, p); s[d] = (|u_d| + c)/dx_d.
+// planes: rho, u_0 .. u_{D-1}, p); s[d] = (|u_d| + c)/dx_d, with the
+// four-equation c when c4.
 template <int N, int D>
 __device__ __forceinline__ void prim_body(int64_t c, const double* __restrict__ W, double* __restrict__ V,
                                           double* __restrict__ AUX, float* __restrict__ P32,
-                                          float* __restrict__ R32, const DevGrid& g, const DevFluid& f, double* s) {
+                                          float* __restrict__ R32, const DevGrid& g, const DevFluid& f, double* s,
+                                          bool c4 = false) {
   using L = Lay<N, D>;
   constexpr int M = L::M;
   const int64_t nc = g.ncells;
@@ -87,8 +144,9 @@ __device__ __forceinline__ void prim_body(int64_t c, const double* __restrict__ 
       }
       R32[(1 + D) * nc + c] = (float)(v[L::EN] - (double)(float)v[L::EN]);
     }
+    const double cw = c4 ? c4_of_cell<N, D>(w, f) : cs;  // wave speed of the CFL maxima
 #pragma unroll
-    for (int d = 0; d < D; ++d) s[d] = (fabs(v[L::MOM + d]) + cs) / g.dx[d];
+    for (int d = 0; d < D; ++d) s[d] = (fabs(v[L::MOM + d]) + cw) / g.dx[d];
   }
 }
 
@@ -127,7 +185,7 @@ __global__ void __launch_bounds__(kCellThreads)
   double s[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) s[d] = 0.0;
-  if (c < g.ncells) prim_body<N, D>(c, W, V, AUX, P32, R32, g, f, s);
+  if (c < g.ncells) prim_body<N, D>(c, W, V, AUX, P32, R32, g, f, s, tau == 2);
   if (!tau) return;
   block_tau_max<D>(s, st->tau_bits);
 }
@@ -187,44 +245,6 @@ __global__ void __launch_bounds__(kCellThreads) k_relax(double* W, DevGrid g, De
   for (int k = 0; k < N - 1; ++k) W[(L::AL + k) * nc + c] = w[L::AL + k];
 }
 
-// Four-equation HRM sound speed (Eq. 4_eqn_sos): Psi_k and Gamma by implicit
-// differentiation of A_p p^2 + B_p p + C_p = 0 at the relaxed pressure.
-template <int N, int D>
-__device__ __forceinline__ double c4eq(const double* W, const DevFluid& f, double p) {
-  const int l = f.liq;
-  double rho = 0.0;
-#pragma unroll
-  for (int k = 0; k < N; ++k) rho += W[k];
-  double Y[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) Y[k] = W[k] / rho;
-  const double re = rhoe_tilde<N, D>(W, f);
-  double cvb = 0.0, cpb = 0.0, qb = 0.0;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    cvb += Y[k] * f.cv[k];
-    cpb += Y[k] * f.cp[k];
-    qb += Y[k] * f.q[k];
-  }
-  const double pinf1 = f.pinf[l], R1 = f.Rg[l], Rb = cpb - cvb;
-  const double Bp = -(re * Rb - pinf1 * cvb - pinf1 * Y[l] * R1);
-  const double den = 2.0 * cvb * p + Bp;
-  const double Gam = (-(-(rho * Rb) * p - pinf1 * rho * (Rb - Y[l] * R1)) / den) / rho;
-  double c2 = Gam * p / rho;
-  const double e = re / rho + qb;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const double dre = e - f.q[k];
-    const double dcv = (f.cv[k] - cvb) / rho;
-    const double dRb = (f.Rg[k] - Rb) / rho;
-    const double dY1 = ((k == l ? 1.0 : 0.0) - Y[l]) / rho;
-    const double dB = -(dre * Rb + re * dRb - pinf1 * dcv - pinf1 * R1 * dY1);
-    const double dC = -(pinf1 * (dre * (Rb - Y[l] * R1) + re * (dRb - R1 * dY1)));
-    c2 += Y[k] * (-(dcv * p * p + dB * p + dC) / den);
-  }
-  return sqrt(c2);
-}
-
 // Output fields of the current state (HRM_FIELD_*).
 template <int N, int D>
 __global__ void __launch_bounds__(kCellThreads)
@@ -255,6 +275,12 @@ __global__ void __launch_bounds__(kCellThreads)
   if (field == 3) {
     out[c] = pT[0];
     out[nc + c] = pT[1];
+  } else if (field == 5) {
+    double Psi[N], Gam;
+    c4eq<N, D>(w, f, pT[0], Psi, &Gam);
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k * nc + c] = Psi[k];
+    out[N * nc + c] = Gam;
   } else {
     out[c] = c4eq<N, D>(w, f, pT[0]);
   }

@@ -301,7 +301,7 @@ __device__ __forceinline__ bool flux_screen32(const float* __restrict__ P32, int
 template <int N, int D>
 __device__ __forceinline__ void prim32_body(int64_t c, const double* __restrict__ W, float* __restrict__ P32,
                                             float* __restrict__ R32, const DevGrid& g, const DevFluid& f,
-                                            double* s) {
+                                            double* s, bool c4 = false) {
   using L = Lay<N, D>;
   using Q = P32Lay<N, D>;
   constexpr int M = L::M;
@@ -363,6 +363,12 @@ __device__ __forceinline__ void prim32_body(int64_t c, const double* __restrict_
     for (int d = 0; d < D; ++d) R32[(1 + d) * nc + c] = (float)(w[L::MOM + d] - (double)u[d] * rho) * irho32;
     R32[(1 + D) * nc + c] = (float)(num - (double)p * S) * iS;
   }
+  if (c4) {
+    const double cw = c4_of_cell<N, D>(w, f);  // four-equation HRM c (FP64)
+#pragma unroll
+    for (int d = 0; d < D; ++d) s[d] = ((double)fabsf(u[d]) + cw) * g.inv_dx[d];
+    return;
+  }
 #pragma unroll
   for (int d = 0; d < D; ++d) s[d] = (double)((fabsf(u[d]) + cs) * (float)g.inv_dx[d]);
 }
@@ -375,7 +381,7 @@ __global__ void __launch_bounds__(kCellThreads)
   double s[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) s[d] = 0.0;
-  if (c < g.ncells) prim32_body<N, D>(c, W, P32, R32, g, f, s);
+  if (c < g.ncells) prim32_body<N, D>(c, W, P32, R32, g, f, s, tau == 2);
   if (!tau) return;
   block_tau_max<D>(s, st->tau_bits);
 }

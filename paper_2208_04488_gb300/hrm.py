@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libhrm.so")
 HEADER = os.path.join(HERE, "..", "include", "hrm.h")
 
 HRM_OK, HRM_E_INVAL, HRM_E_CUDA, HRM_E_ADMISSIBILITY, HRM_E_TIMEOUT, HRM_E_NOMEM = 0, -1, -2, -3, -4, -5
-FIELD_W, FIELD_V, FIELD_C5, FIELD_PT, FIELD_C4 = 0, 1, 2, 3, 4
+FIELD_W, FIELD_V, FIELD_C5, FIELD_PT, FIELD_C4, FIELD_PSI_GAMMA = 0, 1, 2, 3, 4, 5
 FP64, FP32 = 0, 1
 RK3, EULER, RK2 = 0, 1, 2
 RELAX_OFF, RELAX_STAGE, RELAX_STEP = 0, 1, 2
@@ -46,7 +46,7 @@ class HrmParams(ctypes.Structure):
                 ("hs_ar", ctypes.c_double), ("hs_a", ctypes.c_double), ("hs_rc2", ctypes.c_double),
                 ("hs_rhoe", ctypes.c_double), ("weno_eps", ctypes.c_double), ("Cs", ctypes.c_double),
                 ("q_sensor", ctypes.c_double), ("learned_threshold", ctypes.c_double),
-                ("screen", ctypes.c_int32), ("pad_screen", ctypes.c_int32)]
+                ("screen", ctypes.c_int32), ("cfl_sound", ctypes.c_int32)]
 
 
 class HrmInstance(ctypes.Structure):
@@ -290,7 +290,8 @@ class Solver:
         self.params = params
 
     def get(self, field=FIELD_W, out=None):
-        planes = {FIELD_W: self.M, FIELD_V: self.M, FIELD_C5: 1, FIELD_PT: 2, FIELD_C4: 1}[field]
+        planes = {FIELD_W: self.M, FIELD_V: self.M, FIELD_C5: 1, FIELD_PT: 2, FIELD_C4: 1,
+                  FIELD_PSI_GAMMA: self.N + 1}[field]
         if out is None:
             out = np.empty((planes, self.ncells))
         ptr, dev = self._ptr(out)

@@ -231,6 +231,38 @@ def test_fields_against_oracle(hrm, orc):
         assert c4[c] == pytest.approx(o["c4"], rel=1e-11)
 
 
+def test_psi_gamma_field_and_four_equation_cfl(hrm, orc):
+    """HRM_FIELD_PSI_GAMMA against the oracle's Psi_k, Gamma (Sec. 3), and the
+    CFL option with the four-equation sound speed: the same dt and tau as the
+    oracle's, and steps that follow the oracle's."""
+    pr = P.shock_bubble_2d(40, 21)
+    f, g, W = orc.setup(pr)
+    s = hrm.Solver.from_problem(pr)
+    s.step(0.0, 2)
+    W = s.get(hrm.FIELD_W)
+    pg = s.get(hrm.FIELD_PSI_GAMMA)
+    assert pg.shape == (pr.N + 1, pr.ncells)
+    for c in range(0, W.shape[1], 37):
+        o = orc.c4eq_cell(f, W[:, c])
+        np.testing.assert_allclose(pg[:pr.N, c], o["Psi"], rtol=1e-11)
+        assert pg[pr.N, c] == pytest.approx(o["Gamma"], rel=1e-11)
+    s4 = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=0.45, check=0, cfl_sound=1))
+    _, _, W0 = orc.setup(pr)
+    dt4, tau4 = s4.dt(0.45)
+    dto, tauo = orc.dt(f, g, W0, 0.45, sound=1)
+    assert dt4 == pytest.approx(dto, rel=1e-13)
+    np.testing.assert_allclose(tau4, tauo, rtol=1e-13)
+    assert dt4 > orc.dt(f, g, W0, 0.45)[0]  # the mixture's four-equation c is smaller
+    p = orc.make_params(cfl_sound=1)
+    Wo = W0
+    for _ in range(3):
+        dt = orc.dt(f, g, Wo, 0.45, sound=1)[0]
+        Wo = orc.step(f, p, g, Wo, dt, 1)
+        s4.step(dt, 1)
+    err = rel_l1(s4.get(hrm.FIELD_W), Wo)
+    assert err.max() <= 1e-12, err
+
+
 def test_admissibility_counters(hrm, orc):
     pr = P.shock_tube_1d_baseline(32)
     f, g, W = orc.setup(pr)

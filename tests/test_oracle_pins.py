@@ -415,3 +415,39 @@ def test_ic_table_undex(orc):
         assert W[0, c] == pytest.approx(a, rel=1e-14)
         assert W[1, c] == pytest.approx(b, rel=1e-14)
         assert W[2, c] == pytest.approx(d, rel=1e-14 if c == det else 1e-7)
+
+
+def test_ic_and_inflow_tables_mach100_jet(orc):
+    """Tables IC_2D_Mach_100_water_jet and BC_2D_Mach_100_water_jet (Sec. 5.9):
+    partial densities of the ambient air and of the jet and ambient parts of the
+    Dirichlet inflow, from p = 101325 Pa, T = 298 K and the volume fractions."""
+    pr = P.mach100_jet_2d(64, 32)
+    f, g, W = orc.setup(pr)
+    assert W[0, 100] == pytest.approx(1.0227724412751677e-5, rel=1e-14)
+    assert W[1, 100] == pytest.approx(1.1817862094653702, rel=1e-14)
+    Wb = g._keep[0]  # left side, one state per row
+    jet, amb = 16, 0  # rows at y = +0.0039 L and y = -0.246 L
+    assert Wb[0, jet] == pytest.approx(1.0227724310474432e3, rel=1e-14)
+    assert Wb[1, jet] == pytest.approx(1.1817862272214237e-8, rel=1e-14)
+    assert Wb[2, jet] == pytest.approx((1.0227724310474432e3 + 1.1817862272214237e-8) * 1.5e5, rel=1e-14)
+    assert Wb[0, amb] == pytest.approx(1.0227724412751677e-5, rel=1e-14)
+    assert Wb[1, amb] == pytest.approx(1.1817862094653702, rel=1e-14)
+    assert Wb[2, amb] == 0.0
+    # the jet occupies the rows whose centres satisfy |y| <= 0.05 L
+    ycen = -0.25 + (np.arange(32) + 0.5) / 64.0
+    np.testing.assert_array_equal(Wb[2] > 0.0, np.abs(ycen) <= 0.05)
+
+
+def test_cfl_with_four_equation_sound_speed(orc):
+    """The CFL option with the four-equation HRM sound speed (Eq. 4_eqn_sos):
+    for a uniform water-air mixture at rest (alpha = 0.5, 101325 Pa, 298 K)
+    tau = c/dx with the printed speeds of Sec. 5.3, 19.897 m/s against the
+    five-equation 913.05 m/s."""
+    f = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR])
+    W = np.repeat(_W_from_prim(orc, f, [0.5, 0.0, 101325.0, 298.0]), 16, axis=1)
+    g = orc.make_grid([16], [0.01])
+    dt5, tau5 = orc.dt(f, g, W, 0.5)
+    dt4, tau4 = orc.dt(f, g, W, 0.5, sound=1)
+    assert tau4[0] * 0.01 == pytest.approx(19.897, abs=0.0005)
+    assert tau5[0] * 0.01 == pytest.approx(913.05, abs=0.005)
+    assert dt4 == pytest.approx(0.5 * 0.01 / (tau4[0] * 0.01), rel=1e-15)
