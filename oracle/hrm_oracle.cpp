@@ -397,14 +397,14 @@ static real weno_is_left(const real* u, double eps, real* omega_out) {
   real e2 = real(d2) * (real(1.0) + tau5 / (b2 + real(eps)));
   real e3 = real(d3) * (real(1.0) + tau5 / (b3 + real(eps)));
   real esum = e0 + e1 + e2 + e3;
-  real w0 = e0 / esum, w1 = e1 / esum, w2 = e2 / esum, w3 = e3 / esum;
-  if (omega_out) {
-    omega_out[0] = w0;
-    omega_out[1] = w1;
-    omega_out[2] = w2;
-    omega_out[3] = w3;
+  if (omega_out) {  // omega_k = e_k / sum of e
+    omega_out[0] = e0 / esum;
+    omega_out[1] = e1 / esum;
+    omega_out[2] = e2 / esum;
+    omega_out[3] = e3 / esum;
   }
-  return w0 * s0 + w1 * s1 + w2 * s2 + w3 * s3;
+  // sum_k omega_k S_k, with the common normalisation applied once
+  return (e0 * s0 + e1 * s1 + e2 * s2 + e3 * s3) / esum;
 }
 
 // The same interpolation with every nonlinear weight replaced by its linear

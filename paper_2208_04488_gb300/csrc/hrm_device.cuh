@@ -198,7 +198,8 @@ __device__ __forceinline__ R weno_is(R um2, R um1, R u0, R up1, R up2, R eps) {
   const R e2 = R(5.0 / 16.0) * (R(1) + tau5 / (b2 + eps));
   const R e3 = R(1.0 / 16.0) * (R(1) + tau5 / (b3 + eps));
   const R es = e0 + e1 + e2 + e3;
-  return (e0 / es) * s0 + (e1 / es) * s1 + (e2 / es) * s2 + (e3 / es) * s3;
+  // sum_k omega_k S_k with omega_k = e_k / es: the normalisation applied once
+  return (e0 * s0 + e1 * s1 + e2 * s2 + e3 * s3) / es;
 }
 
 // The same interpolation with every nonlinear weight replaced by its linear

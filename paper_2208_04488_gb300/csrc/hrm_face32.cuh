@@ -448,39 +448,45 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
     const float inv_rc = 1.f / (rhob * cb);
     const float rc2b = rhob * cb * cb;
     const float eps = (float)pr.weno_eps;
-    float UL[M], UR[M], w6[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) w6[j] = u6[j] - inv_rc * p6[j];
-    UL[0] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
-    UR[0] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) w6[j] = u6[j] + inv_rc * p6[j];
-    UL[M - 1] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
-    UR[M - 1] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
-    float arb[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-#pragma unroll
-      for (int j = 0; j < 6; ++j) w6[j] = ld(k, j);
-      arb[k] = 0.5f * (w6[2] + w6[3]);
-      const float coef = arb[k] / rc2b;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) w6[j] = w6[j] - coef * p6[j];
-      UL[1 + k] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
-      UR[1 + k] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
-    }
-    {
-      int t_ = 0;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        if (d == DIR) continue;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) w6[j] = ld(L::MOM + d, j);
-        UL[N + 1 + t_] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
-        UR[N + 1 + t_] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
-        ++t_;
+    // The N + D + 1 characteristic fields other than the volume fractions in one
+    // loop, so that the WENO-IS code exists once (the sweep is bound by
+    // instruction fetch when it is unrolled): field fi = 0 is u - p/(rho c)
+    // (slot 0), 1..N the species alpha_k rho_k - (alpha_k rho_k)~ p/(rho c^2)
+    // (slots 1..N), then the tangential velocities (slots N+1..N+D-1) and last
+    // u + p/(rho c) (slot M-1). Each field is a node plane (or u_n) plus a
+    // multiple of p; the biased values go through a per-thread shared column.
+    __shared__ float sU[2][M][kFaceThreads];
+    const int tid = threadIdx.x;
+#pragma unroll 1
+    for (int fi = 0; fi < L::NC; ++fi) {
+      int plane = -1;  // -1: the normal velocity
+      float cp;        // coefficient of p
+      if (fi == 0 || fi == N + D) {
+        cp = fi == 0 ? -inv_rc : inv_rc;
+      } else if (fi <= N) {
+        plane = fi - 1;
+        cp = -((0.5f * (ld(plane, 2) + ld(plane, 3))) / rc2b);
+      } else {
+        const int t_ = fi - N - 1;
+        plane = L::MOM + (t_ < DIR ? t_ : t_ + 1);
+        cp = 0.f;
       }
+      float w6[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) w6[j] = (plane < 0 ? u6[j] : ld(plane, j)) + cp * p6[j];
+      const int slot = fi == N + D ? M - 1 : fi;
+      sU[0][slot][tid] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
+      sU[1][slot][tid] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
     }
+    float UL[M], UR[M], arb[N];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      if (m >= N + D && m < M - 1) continue;  // volume fractions: below
+      UL[m] = sU[0][m][tid];
+      UR[m] = sU[1][m][tid];
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) arb[k] = 0.5f * (ld(k, 2) + ld(k, 3));
     // volume fractions (float-float): node values ai, aj from the value and
     // residue planes, node differences dA[k][j] = alpha_j - alpha_i, and the
     // WENO-IS increments of the identity fields (on FP32 differences) that give
