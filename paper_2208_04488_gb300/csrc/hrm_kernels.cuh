@@ -270,6 +270,33 @@ __device__ __forceinline__ void flux_limit(const double* Wi, const double* Wj, c
   G = hs ? H : Gss;
 }
 
+// True when the flux limiter provably leaves G unchanged: every checked quantity
+// of the high-order half-cell states W_i^{+}, W_{i+1}^{-} (alpha_k rho_k, all N
+// alpha_k, rho e~) is at or above both its limiter threshold and its hard-switch
+// threshold. Then no theta trigger fires (a_high >= eps >= min(eps, a_low)) and
+// no hard switch either, whatever the first-order states, so the first-order
+// flux is not needed. The states are those flux_limit forms, bit for bit; NaN
+// fails the test.
+template <int N, int D>
+__device__ __forceinline__ bool flux_limit_noop(const double* Wi, const double* Wj, const double* Fi,
+                                                const double* Fj, double lam, const FluxPack<N, D>& G,
+                                                const DevFluid& f, const DevParams& pr) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+  double Wp[M], Wm[M], ap[N], am[N];
+  half_state<N, D>(Wi, Fi, G, -2.0 * lam, true, Wp);
+  half_state<N, D>(Wj, Fj, G, 2.0 * lam, false, Wm);
+  all_alpha_W<N, D>(Wp, ap);
+  all_alpha_W<N, D>(Wm, am);
+  const double tar = pr.eps_ar > pr.hs_ar ? pr.eps_ar : pr.hs_ar;
+  const double ta = pr.eps_a > pr.hs_a ? pr.eps_a : pr.hs_a;
+  const double tre = pr.eps_rhoe > pr.hs_rhoe ? pr.eps_rhoe : pr.hs_rhoe;
+  bool ok = rhoe_tilde<N, D>(Wp, f) >= tre && rhoe_tilde<N, D>(Wm, f) >= tre;
+#pragma unroll
+  for (int k = 0; k < N; ++k) ok = ok && Wp[k] >= tar && Wm[k] >= tar && ap[k] >= ta && am[k] >= ta;
+  return ok;
+}
+
 // ---------------------------------------------------------------- per-midpoint kernel
 
 // Loads of the six node cells i-2..i+3 of a midpoint.
@@ -341,9 +368,10 @@ __device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const dou
     Wj[m] = W[m * nc + nd.c[3]];
   }
 
-  // first-order HLLC flux and u_* from the node states (Sec. 4.1.1)
+  // first-order HLLC flux and u_* from the node states (Sec. 4.1.1), evaluated
+  // where it is used: the first-order scheme, and the flux limiter where it may act
   FluxPack<N, D> H;
-  {
+  auto first_order = [&]() {
     PrimState<double, N, D> a, b;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -359,10 +387,11 @@ __device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const dou
       H.gm[k] = GH[L::AL + k] - uH * Vi[L::AL + k];
       H.gp[k] = GH[L::AL + k] - uH * Vj[L::AL + k];
     }
-  }
+  };
 
   FluxPack<N, D> G;
   if (pr.scheme == 1) {
+    first_order();
     G = H;
   } else {
     R p6[6], u6[6];
@@ -512,7 +541,10 @@ __device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const dou
       double Fi[L::NC], Fj[L::NC];
       node_flux<N, D, DIR>(Wi, Vi, Fi);
       node_flux<N, D, DIR>(Wj, Vj, Fj);
-      flux_limit<N, D>(Wi, Wj, Fi, Fj, lam, G, H, f, pr);
+      if (!flux_limit_noop<N, D>(Wi, Wj, Fi, Fj, lam, G, f, pr)) {
+        first_order();
+        flux_limit<N, D>(Wi, Wj, Fi, Fj, lam, G, H, f, pr);
+      }
     }
   }
 #pragma unroll
