@@ -111,6 +111,19 @@ def algorithmic_face_flops(problem, cfl):
     return out
 
 
+def first_order_face_flops(problem, cfl, d):
+    """Flops per midpoint of the first-order HLLC flux alone (the scheme with
+    only that flux, oracle counting build): part of the method as written at
+    every midpoint, which the CUDA sweeps evaluate only where the flux limiter
+    can act."""
+    import oracle
+    f, g, W = oracle.setup(problem)
+    dt, _ = oracle.dt(f, g, W, cfl)
+    lam = oracle.lambdas(f, g, W, dt)
+    c, nf = oracle.faces_flops(f, oracle.make_params(scheme=1), g, W, lam, d)
+    return sum(c.values()) / nf
+
+
 def host_cpu():
     """CPU model and logical core count of this host."""
     model = None
@@ -511,6 +524,10 @@ def main():
                          "traffic_unit": "bytes per launch (ncu capture, y sweep)",
                          "peak_source": "measured FP64 FMA-chain probe on this GPU (hrm_probe_fma_peak)",
                          "algorithmic_flops_per_face": [round(x[0], 1) for x in faces],
+                         "of_which_first_order_flux": round(first_order_face_flops(pr, pr.cfl, 0), 1),
+                         "flop_count": "the oracle's count of the method as written (add, mul, div, sqrt, "
+                                       "tanh one flop each); it includes the first-order HLLC flux at every "
+                                       "midpoint, which the sweep evaluates only where the flux limiter can act",
                          "avg_launch_ms": 1e3 * t_face / n_face, "launches_timed": n_face,
                          "kernel_time_share": share},
             "e2e": {"value": pr.ncells * K_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step,

@@ -222,19 +222,20 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
 int enqueue_step(hrm_ctx* c, cudaStream_t s) {
   const int rs = c->params.relax_mode == HRM_RELAX_STAGE;
   const int rf = c->params.relax_mode != HRM_RELAX_OFF;
+  const int ck = c->params.check ? 1 : 0;  // admissibility counters, read only with params.check
   int k = 0;
   switch (c->params.integrator) {
     case HRM_EULER:
-      k += enqueue_stage(c, s, c->Wn, c->Wn, 0.0, 1.0, rf, 1, true);
+      k += enqueue_stage(c, s, c->Wn, c->Wn, 0.0, 1.0, rf, ck, true);
       break;
     case HRM_RK2:
       k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true);
-      k += enqueue_stage(c, s, c->Ws, c->Wn, 0.5, 0.5, rf, 1, false);
+      k += enqueue_stage(c, s, c->Ws, c->Wn, 0.5, 0.5, rf, ck, false);
       break;
     default:
       k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true);
       k += enqueue_stage(c, s, c->Ws, c->Ws, 0.75, 0.25, rs, 0, false);
-      k += enqueue_stage(c, s, c->Ws, c->Wn, 1.0 / 3.0, 2.0 / 3.0, rf, 1, false);
+      k += enqueue_stage(c, s, c->Ws, c->Wn, 1.0 / 3.0, 2.0 / 3.0, rf, ck, false);
       break;
   }
   return k;

@@ -171,7 +171,8 @@ hrm_status build_graph(hrm_batch* b) {
   // SSP-RK3 (Shu-Osher): src/dst 0 = W^n, 1 = stage state
   int k = enqueue_stage(b, b->cap, 0, 1, 0.0, 1.0, rs, 0, true);
   k += enqueue_stage(b, b->cap, 1, 1, 0.75, 0.25, rs, 0, false);
-  k += enqueue_stage(b, b->cap, 1, 0, 1.0 / 3.0, 2.0 / 3.0, rf, 1, false);
+  // (hrm_batch_admissibility counts separately: no counters in the step)
+  k += enqueue_stage(b, b->cap, 1, 0, 1.0 / 3.0, 2.0 / 3.0, rf, 0, false);
   if ((s = bcuda(b, cudaStreamEndCapture(b->cap, &g), "end capture"))) return s;
   cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
   cudaGraphDestroy(g);

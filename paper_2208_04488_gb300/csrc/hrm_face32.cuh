@@ -457,8 +457,9 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
     // multiple of p; the biased values go through a per-thread shared column.
     __shared__ float sU[2][M][kFaceThreads];
     const int tid = threadIdx.x;
+    // (a gated midpoint skips the projection: see below)
 #pragma unroll 1
-    for (int fi = 0; fi < L::NC; ++fi) {
+    for (int fi = 0; fi < (lin ? 0 : L::NC); ++fi) {
       int plane = -1;  // -1: the normal velocity
       float cp;        // coefficient of p
       if (fi == 0 || fi == N + D) {
@@ -479,14 +480,16 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
       sU[1][slot][tid] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
     }
     float UL[M], UR[M], arb[N];
+    if (!lin) {
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      if (m >= N + D && m < M - 1) continue;  // volume fractions: below
-      UL[m] = sU[0][m][tid];
-      UR[m] = sU[1][m][tid];
+      for (int m = 0; m < M; ++m) {
+        if (m >= N + D && m < M - 1) continue;  // volume fractions: below
+        UL[m] = sU[0][m][tid];
+        UR[m] = sU[1][m][tid];
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k) arb[k] = 0.5f * (ld(k, 2) + ld(k, 3));
     }
-#pragma unroll
-    for (int k = 0; k < N; ++k) arb[k] = 0.5f * (ld(k, 2) + ld(k, 3));
     // volume fractions (float-float): node values ai, aj from the value and
     // residue planes, node differences dA[k][j] = alpha_j - alpha_i, and the
     // WENO-IS increments of the identity fields (on FP32 differences) that give
@@ -518,7 +521,28 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
       UR[N + D + k] = ff_f(at_R[k]);
     }
     PrimState<float, N, D> sl, sr;
-    {
+    if (lin) {
+      // Gated midpoint: with the linear weights the interpolation sum_k d_k S_k
+      // is linear in the node values, so it commutes with the characteristic
+      // projection (R sum_k d_k S_k(R^-1 v) = sum_k d_k S_k(v)) and the primitive
+      // variables are interpolated directly; the volume fractions as above.
+      auto lin5 = [](float um2, float um1, float u0, float up1, float up2) {
+        return u0 + lin_increment(um2 - u0, um1 - u0, up1 - u0, up2 - u0);
+      };
+      float v6[6];
+#pragma unroll
+      for (int m = 0; m < L::NC; ++m) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) v6[j] = m == L::MOM + DIR ? u6[j] : (m == L::EN ? p6[j] : ld(m, j));
+        sl.V[m] = lin5(v6[0], v6[1], v6[2], v6[3], v6[4]);
+        sr.V[m] = lin5(v6[5], v6[4], v6[3], v6[2], v6[1]);
+      }
+#pragma unroll
+      for (int k = 0; k < N - 1; ++k) {
+        sl.V[L::AL + k] = UL[N + D + k];
+        sr.V[L::AL + k] = UR[N + D + k];
+      }
+    } else {
       float h[N];
 #pragma unroll
       for (int k = 0; k < N; ++k) h[k] = arb[k] / (2.f * cb);
