@@ -331,7 +331,8 @@ def test_fp32_form_keeps_uniform_states_exactly(hrm):
     (P.shock_tube_1d_baseline(400), 100, 2e-3),
     (P.shock_bubble_2d(128, 64), 40, 1e-3),
     (P.advection_2d_smooth(64), 40, 1e-6),
-], ids=["shock_tube_400", "shock_bubble_128x64", "advection_64"])
+    (P.interface_3d(32), 20, 2e-4),
+], ids=["shock_tube_400", "shock_bubble_128x64", "advection_64", "interface_3d_32"])
 def test_fp32_form_error_against_fp64(hrm, pr, nsteps, tol):
     """The precision form stays within a stated relative L1 error of the FP64
     path and keeps every cell admissible."""
