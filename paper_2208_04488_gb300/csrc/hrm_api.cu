@@ -41,6 +41,8 @@ struct hrm_ctx {
   StepState* st = nullptr;
   mlp::GateBlob* blob = nullptr;   // learned gate weights (hrm_set_detector)
   uint8_t* gate[3] = {nullptr, nullptr, nullptr};  // gate bytes per direction (midpoint grids)
+  uint32_t* defer = nullptr;       // precision form: worklist of deferred midpoints, then its counter
+  int64_t defer_cap = 0;           // worklist entries (the largest midpoint grid; 0: no worklist)
   int gate_set[3] = {0, 0, 0};     // fixed gate provided (hrm_set_gate)
   int gate_blocks = 0;             // persistent blocks of the gate kernel
   const CellKernels* ck = nullptr;
@@ -159,8 +161,23 @@ float* r32_target(hrm_ctx* c) { return c->params.learned == 1 ? c->R32 : nullptr
 
 // The gate of direction d's sweep: fixed bytes (learned 2, and learned 1 in the
 // FP64 form after the gate kernel), or the detector inside the FP32 sweep.
+// The precision form's sweep defers screen failures to a second kernel (one
+// without the FP64 fallbacks inline), except with the learned gate inside the
+// sweep, the first-order scheme or the screens off.
+bool defer_sweep(const hrm_ctx* c) {
+  return c->params.precision == HRM_FP32 && c->defer && c->params.learned != 1 &&
+         c->params.scheme == HRM_SCHEME_WCNS && c->params.screen;
+}
+
+// Kernels one sweep launches.
+int sweep_kernels(const hrm_ctx* c) { return defer_sweep(c) ? 2 : 1; }
+
 GateArgs gate_of(const hrm_ctx* c, int d) {
   GateArgs g;
+  if (defer_sweep(c)) {
+    g.defer_list = c->defer;
+    g.defer_count = c->defer + c->defer_cap;
+  }
   if (c->params.learned == 1 && c->params.precision == HRM_FP32) {
     g.blob = c->blob;
     g.R32 = c->R32;
@@ -207,7 +224,7 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
       c->fk->face[d](c->params.precision, Wsrc, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st,
                      gate_of(c, d), s);
     });
-    ++k;
+    k += sweep_kernels(c);
   }
   traced(c, s, HRM_KERNEL_UPDATE, [&] {
     c->fk->update(0, c->params.precision == HRM_FP32, c->Wn, Wsrc, Wout, c->F[0], c->F[1], c->F[2], c->dg, c->fl,
@@ -420,6 +437,15 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
     size_t nf = 1;
     for (int e = 0; e < 3; ++e) nf *= (size_t)(c->dg.n[e] + (e == d));
     if ((s = cuda_check(c, cudaMalloc(&c->F[d], sizeof(double) * nf * (M + N - 1)), "alloc faces"))) return bail(s);
+    if ((int64_t)nf > c->defer_cap) c->defer_cap = (int64_t)nf;
+  }
+  // worklist of the precision form's deferred midpoints (32-bit entries; none
+  // beyond 2^32 - 1 midpoints, where the sweep keeps its fallbacks inline)
+  if (c->defer_cap < (int64_t)0xffffffffll) {
+    if ((s = cuda_check(c, cudaMalloc(&c->defer, sizeof(uint32_t) * (size_t)(c->defer_cap + 1)), "alloc worklist")))
+      return bail(s);
+  } else {
+    c->defer_cap = 0;
   }
   if ((s = cuda_check(c, cudaMalloc(&c->st, sizeof(StepState)), "alloc step state"))) return bail(s);
   cudaMemsetAsync(c->Wn, 0, plane * M, c->stream);
@@ -435,6 +461,7 @@ void hrm_destroy(hrm_ctx* c) {
   drop_graph(c);
   cudaFree(c->Wn);
   cudaFree(c->Ws);
+  cudaFree(c->defer);
   cudaFree(c->V);
   cudaFree(c->AUX);
   cudaFree(c->P32);
@@ -615,7 +642,7 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
   }
   c->fk->update(1, 0, c->Wn, c->Wn, out, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, 0.0, 1.0, 0, 0,
                 c->stream);
-  c->launches += 2 + c->D;
+  c->launches += 2 + c->D * sweep_kernels(c);
   if ((s = last_launch(c, "rhs"))) return s;
   // (the update writes interior cells only: the stage state's slices stay)
   if (out != rhs &&

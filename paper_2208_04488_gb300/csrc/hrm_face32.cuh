@@ -386,8 +386,12 @@ __global__ void __launch_bounds__(kCellThreads)
   block_tau_max<D>(s, st->tau_bits);
 }
 
-template <int N, int D, int DIR>
-__device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const double* __restrict__ W,
+// DEFER: where a screen fails (or for the first-order scheme) return false
+// without writing the midpoint, so that the FP64 fallback code is not part of
+// the kernel; the midpoint is then computed by the full body (k_face32_fix).
+// Returns true when the midpoint's outputs were written.
+template <int N, int D, int DIR, bool DEFER = false>
+__device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const double* __restrict__ W,
                                             const double* __restrict__ V, const double* __restrict__ AUX,
                                             const float* __restrict__ P32, double* __restrict__ out,
                                             const DevGrid& g, const DevFluid& f, const DevParams& pr, double lam,
@@ -432,6 +436,7 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
 
   FluxPack<N, D> G;
   if (pr.scheme == 1) {
+    if constexpr (DEFER) return false;
     double Vi[M], Vj[M];
     load_node(2, Vi, nullptr);
     load_node(3, Vj, nullptr);
@@ -579,6 +584,7 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
       // leaves unchanged keep their float-float values (so that the result
       // does not depend on whether the screen ran)
       if (!(pr.screen && interp_screen32<N, D>(sl.V, at_L, f, pr))) {
+        if constexpr (DEFER) return false;
         double Vn[M], a0[NA], a1[NA];
         const double rc2n = load_node(2, Vn, nullptr);
 #pragma unroll
@@ -593,6 +599,7 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
         }
       }
       if (!(pr.screen && interp_screen32<N, D>(sr.V, at_R, f, pr))) {
+        if constexpr (DEFER) return false;
         double Vn[M], a0[NA], a1[NA];
         const double rc2n = load_node(3, Vn, nullptr);
 #pragma unroll
@@ -677,6 +684,7 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
     }
     if (pr.limiters &&
         !(pr.screen && flux_screen32<N, D, DIR>(P32, nc, nd, g32, gmf, gpf, ai, aj, ff_of(2.0 * lam), f, pr))) {
+      if constexpr (DEFER) return false;
       double Vi[M], Vj[M], Wi[M], Wj[M];
       load_node(2, Vi, Wi);
       load_node(3, Vj, Wj);
@@ -694,6 +702,49 @@ __device__ __forceinline__ void face32_body(int64_t t, const Nodes6& nd, const d
   for (int k = 0; k < N - 1; ++k) {
     out[(L::AL + k) * nf + t] = G.gm[k];
     out[(M + k) * nf + t] = G.gp[k];
+  }
+  return true;
+}
+
+// Screened sweep without the FP64 fallbacks (about a third of the full body's
+// code and at most 128 registers, so four blocks per SM): midpoints whose
+// screens fail are appended to `list` (warp-aggregated; order not significant)
+// for k_face32_fix. *count must be 0 at launch; list holds one entry per midpoint.
+template <int N, int D, int DIR>
+__global__ void __launch_bounds__(kFaceThreads, 4)
+    k_face32_fast(const double* __restrict__ W, const float* __restrict__ P32, double* __restrict__ out, DevGrid g,
+                  DevFluid f, DevParams pr, const StepState* __restrict__ st, const uint8_t* __restrict__ gate,
+                  uint32_t* __restrict__ list, uint32_t* __restrict__ count) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  Nodes6 nd;
+  bool need = false;
+  if (face_nodes<DIR>(g, t, nd)) {
+    const bool lin = gate != nullptr && gate[t] != 0;
+    need = !face32_body<N, D, DIR, true>(t, nd, W, nullptr, nullptr, P32, out, g, f, pr, st->lam[DIR], lin);
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, need);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (need) list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)t;
+}
+
+// The midpoints a k_face32_fast launch deferred, with the full body (FP64
+// limiters where the screens fail); a grid-stride loop over the *count entries.
+template <int N, int D, int DIR>
+__global__ void __launch_bounds__(kFaceThreads, 2)
+    k_face32_fix(const double* __restrict__ W, const float* __restrict__ P32, double* __restrict__ out, DevGrid g,
+                 DevFluid f, DevParams pr, const StepState* __restrict__ st, const uint8_t* __restrict__ gate,
+                 const uint32_t* __restrict__ list, const uint32_t* __restrict__ count) {
+  const int64_t n = *count;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = list[i];
+    Nodes6 nd;
+    if (!face_nodes<DIR>(g, t, nd)) continue;
+    const bool lin = gate != nullptr && gate[t] != 0;
+    face32_body<N, D, DIR>(t, nd, W, nullptr, nullptr, P32, out, g, f, pr, st->lam[DIR], lin);
   }
 }
 

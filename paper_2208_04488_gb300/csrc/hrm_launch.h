@@ -36,7 +36,15 @@ struct GateArgs {
   const float* R32 = nullptr;
   uint8_t* out = nullptr;
   float zthr = 0.f;
+  // precision form with screens: the sweep defers midpoints whose screens fail
+  // to a second kernel through this worklist (one entry per midpoint of the
+  // direction) and counter; nullptr: one kernel with the fallbacks inline
+  uint32_t* defer_list = nullptr;
+  uint32_t* defer_count = nullptr;
 };
+
+// Blocks of the deferred-midpoint kernel (grid-stride over the worklist).
+constexpr int kFixBlocks = 304;
 
 struct FaceKernels {
   // precision: 0 FP64, 1 FP32 bulk
