@@ -732,14 +732,19 @@ __global__ void __launch_bounds__(kFaceThreads, 4)
 }
 
 // The midpoints a k_face32_fast launch deferred, with the full body (FP64
-// limiters where the screens fail); a grid-stride loop over the *count entries.
+// limiters where the screens fail). The list is short (tens to hundreds of
+// midpoints) and each entry is a long chain of FP64 work, so entries go to
+// one-warp blocks lane-major: entry i to block i mod gridDim, spreading a
+// short list over every SM rather than packing it into a few warps.
 template <int N, int D, int DIR>
 __global__ void __launch_bounds__(kFaceThreads, 2)
     k_face32_fix(const double* __restrict__ W, const float* __restrict__ P32, double* __restrict__ out, DevGrid g,
                  DevFluid f, DevParams pr, const StepState* __restrict__ st, const uint8_t* __restrict__ gate,
                  const uint32_t* __restrict__ list, const uint32_t* __restrict__ count) {
   const int64_t n = *count;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t r = threadIdx.x;; r += blockDim.x) {
+    const int64_t i = r * gridDim.x + blockIdx.x;
+    if (i >= n) break;
     const int64_t t = list[i];
     Nodes6 nd;
     if (!face_nodes<DIR>(g, t, nd)) continue;

@@ -20,7 +20,7 @@ void launch(const double* W, const double* V, const double* AUX, const float* P3
       cudaMemsetAsync(gate.defer_count, 0, sizeof(uint32_t), s);
       k_face32_fast<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(
           W, P32, out, g, f, p, st, gate.fixed, gate.defer_list, gate.defer_count);
-      k_face32_fix<N, kD, DIR><<<kFixBlocks, kFaceThreads, 0, s>>>(W, P32, out, g, f, p, st, gate.fixed,
+      k_face32_fix<N, kD, DIR><<<kFixBlocks, kFixThreads, 0, s>>>(W, P32, out, g, f, p, st, gate.fixed,
                                                                      gate.defer_list, gate.defer_count);
     } else {
       k_face32<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, P32, out, g, f, p, st,

@@ -43,8 +43,9 @@ struct GateArgs {
   uint32_t* defer_count = nullptr;
 };
 
-// Blocks of the deferred-midpoint kernel (grid-stride over the worklist).
-constexpr int kFixBlocks = 304;
+// Launch shape of the deferred-midpoint kernel: one-warp blocks, 16 per SM.
+constexpr int kFixBlocks = 2432;
+constexpr int kFixThreads = 32;
 
 struct FaceKernels {
   // precision: 0 FP64, 1 FP32 bulk
