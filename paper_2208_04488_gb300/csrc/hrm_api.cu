@@ -162,11 +162,10 @@ float* r32_target(hrm_ctx* c) { return c->params.learned == 1 ? c->R32 : nullptr
 // The gate of direction d's sweep: fixed bytes (learned 2, and learned 1 in the
 // FP64 form after the gate kernel), or the detector inside the FP32 sweep.
 // The precision form's sweep defers screen failures to a second kernel (one
-// without the FP64 fallbacks inline), except with the learned gate inside the
-// sweep, the first-order scheme or the screens off.
+// without the FP64 fallbacks inline), except with the first-order scheme or the
+// screens off.
 bool defer_sweep(const hrm_ctx* c) {
-  return c->params.precision == HRM_FP32 && c->defer && c->params.learned != 1 &&
-         c->params.scheme == HRM_SCHEME_WCNS && c->params.screen;
+  return c->params.precision == HRM_FP32 && c->defer && c->params.scheme == HRM_SCHEME_WCNS && c->params.screen;
 }
 
 // Kernels one sweep launches.

@@ -192,12 +192,14 @@ __device__ __forceinline__ void store_row(__nv_bfloat16* row, const float (&x)[k
 // kernel: each warp forms its 32 stencils' features, runs the network on the
 // tensor cores, records the decisions in gate_out and then computes its
 // midpoints with the linear weights where gated. All lanes take part in the
-// network even past the last midpoint.
-template <int N, int D, int DIR>
-__global__ void __launch_bounds__(kFaceThreads, 3)
+// network even past the last midpoint. DEFER: as k_face32_fast, midpoints whose
+// screens fail go to `list` (k_face32_fix then reads their gate bytes).
+template <int N, int D, int DIR, bool DEFER = false>
+__global__ void __launch_bounds__(kFaceThreads, DEFER ? 4 : 3)
     k_face32_learned(const double* __restrict__ W, const float* __restrict__ P32, const float* __restrict__ R32,
                      double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr, const StepState* __restrict__ st,
-                     const mlp::GateBlob* __restrict__ blob, float zthr, uint8_t* __restrict__ gate_out) {
+                     const mlp::GateBlob* __restrict__ blob, float zthr, uint8_t* __restrict__ gate_out,
+                     uint32_t* __restrict__ list = nullptr, uint32_t* __restrict__ count = nullptr) {
   __shared__ __align__(16) mlp::GateBlob Wb;
   __shared__ __align__(16) __nv_bfloat16 X[kFaceThreads / 32][32][mlp::kRow];
   {
@@ -223,9 +225,24 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
     __syncwarp();
     lin = mlp::warp_logit(Wb, X[warp], lane) > zthr;
   }
-  if (!ok) return;
-  gate_out[t] = lin ? 1 : 0;
-  face32_body<N, D, DIR>(t, nd, W, nullptr, nullptr, P32, out, g, f, pr, st->lam[DIR], lin);
+  if constexpr (!DEFER) {
+    if (!ok) return;
+    gate_out[t] = lin ? 1 : 0;
+    face32_body<N, D, DIR>(t, nd, W, nullptr, nullptr, P32, out, g, f, pr, st->lam[DIR], lin);
+  } else {
+    bool need = false;
+    if (ok) {
+      gate_out[t] = lin ? 1 : 0;
+      need = !face32_body<N, D, DIR, true>(t, nd, W, nullptr, nullptr, P32, out, g, f, pr, st->lam[DIR], lin);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (m == 0u) return;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (need) list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)t;
+  }
 }
 
 }  // namespace hrm
