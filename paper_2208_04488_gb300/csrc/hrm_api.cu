@@ -41,8 +41,10 @@ struct hrm_ctx {
   StepState* st = nullptr;
   mlp::GateBlob* blob = nullptr;   // learned gate weights (hrm_set_detector)
   uint8_t* gate[3] = {nullptr, nullptr, nullptr};  // gate bytes per direction (midpoint grids)
-  uint32_t* defer = nullptr;       // precision form: worklist of deferred midpoints, then its counter
+  uint32_t* defer = nullptr;       // precision form: per direction, a worklist of deferred midpoints and its counter
   int64_t defer_cap = 0;           // worklist entries (the largest midpoint grid; 0: no worklist)
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};  // deferred midpoints overlap the next sweep here
+  cudaEvent_t ev_fast[3] = {}, ev_fix[3] = {};
   int gate_set[3] = {0, 0, 0};     // fixed gate provided (hrm_set_gate)
   int gate_blocks = 0;             // persistent blocks of the gate kernel
   const CellKernels* ck = nullptr;
@@ -174,8 +176,8 @@ int sweep_kernels(const hrm_ctx* c) { return defer_sweep(c) ? 2 : 1; }
 GateArgs gate_of(const hrm_ctx* c, int d) {
   GateArgs g;
   if (defer_sweep(c)) {
-    g.defer_list = c->defer;
-    g.defer_count = c->defer + c->defer_cap;
+    g.defer_list = c->defer + (size_t)d * (size_t)(c->defer_cap + 1);
+    g.defer_count = g.defer_list + c->defer_cap;
   }
   if (c->params.learned == 1 && c->params.precision == HRM_FP32) {
     g.blob = c->blob;
@@ -219,12 +221,20 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
       });
       ++k;
     }
+    GateArgs ga = gate_of(c, d);
+    if (ga.defer_list) {  // the deferred midpoints run beside the next sweep
+      ga.side = c->side[d];
+      ga.ev_fast = c->ev_fast[d];
+      ga.ev_fix = c->ev_fix[d];
+    }
     traced(c, s, HRM_KERNEL_FACE_X + d, [&] {
-      c->fk->face[d](c->params.precision, Wsrc, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st,
-                     gate_of(c, d), s);
+      c->fk->face[d](c->params.precision, Wsrc, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st, ga,
+                     s);
     });
     k += sweep_kernels(c);
   }
+  if (defer_sweep(c))
+    for (int d = 0; d < c->D; ++d) cudaStreamWaitEvent(s, c->ev_fix[d], 0);
   traced(c, s, HRM_KERNEL_UPDATE, [&] {
     c->fk->update(0, c->params.precision == HRM_FP32, c->Wn, Wsrc, Wout, c->F[0], c->F[1], c->F[2], c->dg, c->fl,
                   c->st, a, b, relax, count, s);
@@ -441,8 +451,17 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
   // worklist of the precision form's deferred midpoints (32-bit entries; none
   // beyond 2^32 - 1 midpoints, where the sweep keeps its fallbacks inline)
   if (c->defer_cap < (int64_t)0xffffffffll) {
-    if ((s = cuda_check(c, cudaMalloc(&c->defer, sizeof(uint32_t) * (size_t)(c->defer_cap + 1)), "alloc worklist")))
+    if ((s = cuda_check(c, cudaMalloc(&c->defer, sizeof(uint32_t) * (size_t)D * (size_t)(c->defer_cap + 1)),
+                        "alloc worklist")))
       return bail(s);
+    for (int d = 0; d < D; ++d) {
+      if ((s = cuda_check(c, cudaStreamCreateWithFlags(&c->side[d], cudaStreamNonBlocking), "side stream")))
+        return bail(s);
+      if ((s = cuda_check(c, cudaEventCreateWithFlags(&c->ev_fast[d], cudaEventDisableTiming), "event")))
+        return bail(s);
+      if ((s = cuda_check(c, cudaEventCreateWithFlags(&c->ev_fix[d], cudaEventDisableTiming), "event")))
+        return bail(s);
+    }
   } else {
     c->defer_cap = 0;
   }
@@ -472,6 +491,11 @@ void hrm_destroy(hrm_ctx* c) {
   for (int i = 0; i < 2 * kMaxProf; ++i)
     if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
   if (c->cap) cudaStreamDestroy(c->cap);
+  for (int d = 0; d < 3; ++d) {
+    if (c->side[d]) cudaStreamDestroy(c->side[d]);
+    if (c->ev_fast[d]) cudaEventDestroy(c->ev_fast[d]);
+    if (c->ev_fix[d]) cudaEventDestroy(c->ev_fix[d]);
+  }
   delete c;
 }
 

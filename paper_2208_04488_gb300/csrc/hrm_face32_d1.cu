@@ -17,8 +17,10 @@ void launch(const double* W, const double* V, const double* AUX, const float* P3
       cudaMemsetAsync(gate.defer_count, 0, sizeof(uint32_t), s);
       k_face32_learned<N, kD, DIR, true><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(
           W, P32, gate.R32, out, g, f, p, st, gate.blob, gate.zthr, gate.out, gate.defer_list, gate.defer_count);
-      k_face32_fix<N, kD, DIR><<<kFixBlocks, kFixThreads, 0, s>>>(W, P32, out, g, f, p, st, gate.out,
-                                                                   gate.defer_list, gate.defer_count);
+      const cudaStream_t sf = fix_stream(gate, s);
+      k_face32_fix<N, kD, DIR><<<kFixBlocks, kFixThreads, 0, sf>>>(W, P32, out, g, f, p, st, gate.out,
+                                                                    gate.defer_list, gate.defer_count);
+      fix_done(gate);
     } else if (gate.blob) {
       k_face32_learned<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(
           W, P32, gate.R32, out, g, f, p, st, gate.blob, gate.zthr, gate.out);
@@ -26,8 +28,10 @@ void launch(const double* W, const double* V, const double* AUX, const float* P3
       cudaMemsetAsync(gate.defer_count, 0, sizeof(uint32_t), s);
       k_face32_fast<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(
           W, P32, out, g, f, p, st, gate.fixed, gate.defer_list, gate.defer_count);
-      k_face32_fix<N, kD, DIR><<<kFixBlocks, kFixThreads, 0, s>>>(W, P32, out, g, f, p, st, gate.fixed,
-                                                                     gate.defer_list, gate.defer_count);
+      const cudaStream_t sf = fix_stream(gate, s);
+      k_face32_fix<N, kD, DIR><<<kFixBlocks, kFixThreads, 0, sf>>>(W, P32, out, g, f, p, st, gate.fixed,
+                                                                    gate.defer_list, gate.defer_count);
+      fix_done(gate);
     } else {
       k_face32<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, P32, out, g, f, p, st,
                                                                                 gate.fixed);

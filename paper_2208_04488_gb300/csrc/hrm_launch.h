@@ -41,7 +41,24 @@ struct GateArgs {
   // direction) and counter; nullptr: one kernel with the fallbacks inline
   uint32_t* defer_list = nullptr;
   uint32_t* defer_count = nullptr;
+  // optional: run the deferred midpoints on `side` (after ev_fast, recorded on
+  // the sweep's stream) and record ev_fix there, so that they overlap the next
+  // sweep; the caller joins ev_fix before the update
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fast = nullptr, ev_fix = nullptr;
 };
+
+// Stream of the deferred-midpoint kernel: gate.side (forked from s after the
+// sweep) or s itself.
+inline cudaStream_t fix_stream(const GateArgs& gate, cudaStream_t s) {
+  if (!gate.side) return s;
+  cudaEventRecord(gate.ev_fast, s);
+  cudaStreamWaitEvent(gate.side, gate.ev_fast, 0);
+  return gate.side;
+}
+inline void fix_done(const GateArgs& gate) {
+  if (gate.side) cudaEventRecord(gate.ev_fix, gate.side);
+}
 
 // Launch shape of the deferred-midpoint kernel: one-warp blocks, 16 per SM.
 constexpr int kFixBlocks = 2432;
