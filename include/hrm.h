@@ -112,9 +112,11 @@ enum {
   HRM_FIELD_C5 = 2,    /* 1 plane: five-equation sound speed, rho c^2 = gbar (p + pbar_inf) (Sec. 2) */
   HRM_FIELD_PT = 3,    /* 2 planes: equilibrium p and T of the four-equation HRM (Sec. 4.2) */
   HRM_FIELD_C4 = 4,    /* 1 plane: four-equation HRM sound speed (Eq. 4_eqn_sos) */
-  HRM_FIELD_PSI_GAMMA = 5 /* N + 1 planes: Psi_1..Psi_N, Gamma of the four-equation HRM at the
-                             equilibrium pressure (Sec. 3: derivatives of the relaxed pressure
-                             with respect to alpha_k rho_k and to rho e) */
+  HRM_FIELD_PSI_GAMMA = 5, /* N + 1 planes: Psi_1..Psi_N, Gamma of the four-equation HRM at the
+                              equilibrium pressure (Sec. 3: derivatives of the relaxed pressure
+                              with respect to alpha_k rho_k and to rho e) */
+  HRM_FIELD_ALPHA = 6,    /* N planes: alpha_1..alpha_N (alpha_N = 1 - the others, Sec. 2) */
+  HRM_FIELD_Y = 7         /* N planes: mass fractions Y_k = alpha_k rho_k / rho */
 };
 
 /* Fill p with the paper's constants (Sec. 4.3.2, App. C, Sec. 4.3.1), PP-WCNS-IS,
@@ -143,13 +145,17 @@ const char* hrm_last_error(const hrm_ctx* ctx);
 hrm_status hrm_set_params(hrm_ctx* ctx, const hrm_params* params);
 
 /* Set the state from W (layout above, M x ncells doubles), host (on_device = 0)
- * or device memory; resets the time to 0. */
+ * or device memory; resets the time to 0. With params.check the state is then
+ * tested for admissibility (Sec. 2) and HRM_E_INVAL returned, with the four
+ * counts of hrm_admissibility in hrm_last_error, if a cell lies outside the
+ * admissible set (the state stays set). */
 hrm_status hrm_set(hrm_ctx* ctx, const double* W, int32_t on_device);
 
 /* Set the state from primitive planes prim[(N + D + 1) x ncells] =
  * (alpha_1..alpha_{N-1}, u_1..u_D, p, T) in pressure and temperature
  * equilibrium (Sec. 5): rho_k = (p + p_inf_k) / ((gamma_k - 1) c_v,k T)
- * (Eq. rho_k_thermally_relaxed), E from the mixture EOS (Sec. 2). */
+ * (Eq. rho_k_thermally_relaxed), E from the mixture EOS (Sec. 2). The same
+ * admissibility test as hrm_set with params.check. */
 hrm_status hrm_set_primitive(hrm_ctx* ctx, const double* prim, int32_t on_device);
 
 /* Time step of the current state (Sec. 4.1.2): tau_d = max(|u_d| + c) / dx_d,

@@ -305,6 +305,20 @@ hrm_status check_boundaries(hrm_ctx* c) {
   return HRM_OK;
 }
 
+// With params.check, a state set by hrm_set / hrm_set_primitive must be
+// admissible (Sec. 2); the state stays set either way.
+hrm_status check_initial(hrm_ctx* c) {
+  if (!c->params.check) return HRM_OK;
+  int64_t n[4];
+  if (hrm_status s = hrm_admissibility(c, n)) return s;
+  if (n[0] | n[1] | n[2] | n[3])
+    return fail(c, HRM_E_INVAL,
+                "non-admissible initial state: %lld negative partial density, %lld volume fraction out of "
+                "[0,1], %lld rho c^2 <= 0, %lld rho e~ <= 0",
+                (long long)n[0], (long long)n[1], (long long)n[2], (long long)n[3]);
+  return HRM_OK;
+}
+
 void reset_step_state(hrm_ctx* c) {
   StepState z{};
   z.cfl = c->params.cfl;
@@ -547,7 +561,8 @@ hrm_status hrm_set(hrm_ctx* c, const double* W, int32_t on_device) {
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, "copy W");
   if (s) return s;
   reset_step_state(c);
-  return last_launch(c, "set");
+  if ((s = last_launch(c, "set"))) return s;
+  return check_initial(c);
 }
 
 hrm_status hrm_set_primitive(hrm_ctx* c, const double* prim, int32_t on_device) {
@@ -559,7 +574,8 @@ hrm_status hrm_set_primitive(hrm_ctx* c, const double* prim, int32_t on_device) 
   ++c->launches;
   if ((s = last_launch(c, "initial state"))) return s;
   reset_step_state(c);
-  return last_launch(c, "set primitive");
+  if ((s = last_launch(c, "set primitive"))) return s;
+  return check_initial(c);
 }
 
 hrm_status hrm_set_boundary(hrm_ctx* c, int32_t side, const double* values, int32_t primitive,
@@ -695,6 +711,10 @@ hrm_status hrm_get(hrm_ctx* c, int32_t field, double* dst, int32_t on_device) {
       break;
     case HRM_FIELD_PSI_GAMMA:
       planes = c->N + 1;
+      break;
+    case HRM_FIELD_ALPHA:
+    case HRM_FIELD_Y:
+      planes = c->N;
       break;
     default:
       return fail(c, HRM_E_INVAL, "unknown field %d", field);

@@ -257,6 +257,18 @@ __global__ void __launch_bounds__(kCellThreads)
   double w[M], v[M], rho, cs, rc2;
 #pragma unroll
   for (int m = 0; m < M; ++m) w[m] = W[m * nc + c];
+  if (field == 6 || field == 7) {
+    // all N volume fractions (alpha_N = 1 - the others) or mass fractions Y_k
+    double r = 0.0, sa = 0.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r += w[k];
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) sa += w[L::AL + k];
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      out[k * nc + c] = field == 7 ? w[k] / r : (k < N - 1 ? w[L::AL + k] : 1.0 - sa);
+    return;
+  }
   if (field == 1 || field == 2) {
     cell_prim<N, D>(w, f, v, rho, cs, rc2);
     if (field == 1) {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libhrm.so")
 HEADER = os.path.join(HERE, "..", "include", "hrm.h")
 
 HRM_OK, HRM_E_INVAL, HRM_E_CUDA, HRM_E_ADMISSIBILITY, HRM_E_TIMEOUT, HRM_E_NOMEM = 0, -1, -2, -3, -4, -5
-FIELD_W, FIELD_V, FIELD_C5, FIELD_PT, FIELD_C4, FIELD_PSI_GAMMA = 0, 1, 2, 3, 4, 5
+FIELD_W, FIELD_V, FIELD_C5, FIELD_PT, FIELD_C4, FIELD_PSI_GAMMA, FIELD_ALPHA, FIELD_Y = 0, 1, 2, 3, 4, 5, 6, 7
 FP64, FP32 = 0, 1
 RK3, EULER, RK2 = 0, 1, 2
 RELAX_OFF, RELAX_STAGE, RELAX_STEP = 0, 1, 2
@@ -291,7 +291,7 @@ class Solver:
 
     def get(self, field=FIELD_W, out=None):
         planes = {FIELD_W: self.M, FIELD_V: self.M, FIELD_C5: 1, FIELD_PT: 2, FIELD_C4: 1,
-                  FIELD_PSI_GAMMA: self.N + 1}[field]
+                  FIELD_PSI_GAMMA: self.N + 1, FIELD_ALPHA: self.N, FIELD_Y: self.N}[field]
         if out is None:
             out = np.empty((planes, self.ncells))
         ptr, dev = self._ptr(out)

@@ -269,9 +269,31 @@ def test_admissibility_counters(hrm, orc):
     W[0, 3] = -1e-3        # negative partial density
     W[4, 7] = 1.5          # alpha_1 > 1 (and alpha_2 < 0)
     W[3, 9] = -1e9         # negative energy: rho e~ <= 0 and rho c^2 <= 0
-    s = hrm.Solver.from_problem(pr, set_state=False)
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(check=0), set_state=False)
     s.set(np.ascontiguousarray(W))
     assert s.admissibility() == orc.admissibility(f, g, W)
+    # with check on, setting a non-admissible state is reported (the state stays set)
+    s2 = hrm.Solver.from_problem(pr, params=hrm.params_default(check=1), set_state=False)
+    with pytest.raises(hrm.HrmError) as e:
+        s2.set(np.ascontiguousarray(W))
+    assert e.value.status == hrm.HRM_E_INVAL and "non-admissible" in str(e.value)
+    np.testing.assert_array_equal(s2.get(hrm.FIELD_W), W)
+
+
+def test_alpha_and_mass_fraction_fields(hrm, orc):
+    """HRM_FIELD_ALPHA (all N volume fractions) and HRM_FIELD_Y (mass fractions)
+    against their definitions (Sec. 2) on the stepped state."""
+    pr = P.shock_interface_1d_3species(90)
+    s = hrm.Solver.from_problem(pr)
+    s.step(0.0, 3)
+    W = s.get(hrm.FIELD_W)
+    N, D = pr.N, pr.D
+    al = s.get(hrm.FIELD_ALPHA)
+    np.testing.assert_array_equal(al[:N - 1], W[N + D + 1:])
+    np.testing.assert_allclose(al[N - 1], 1.0 - W[N + D + 1:].sum(axis=0), rtol=0, atol=1e-15)
+    Y = s.get(hrm.FIELD_Y)
+    np.testing.assert_allclose(Y, W[:N] / W[:N].sum(axis=0), rtol=1e-15, atol=0)
+    np.testing.assert_allclose(Y.sum(axis=0), 1.0, atol=1e-15)
 
 
 def test_invalid_arguments_do_not_touch_state(hrm):
