@@ -270,6 +270,46 @@ def measure_batched(torch, hrm, problems, stream, flush, args):
     return out
 
 
+def measure_3d(torch, hrm, problems, stream, flush, args):
+    """The 3D configuration: the 256^3 perturbed liquid-gas interface hit by a
+    Mach 1.5 shock (three species, periodic in y and z). Both forms advance the
+    same fixed steps from the initial state (L2 flushed before each, CUDA events
+    around each step); the precision form's relative L1 error against FP64."""
+    from paper_2208_04488_gb300.metrics import rel_l1_state
+    pr = problems.interface_3d(256)
+    out = {"workload": "3D perturbed interface, 256^3 cells, Mach 1.5 shock, water + air + helium, SSP-RK3",
+           "cells": pr.ncells}
+    s64 = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=0.4, check=0), stream=stream)
+    dt, _ = s64.dt(0.4)
+    dt *= 0.8
+    states = {}
+    for name, prec, K in (("fp32", hrm.FP32, max(3, args.steps // 2)), ("fp64", hrm.FP64, 3)):
+        s = s64 if prec == hrm.FP64 else hrm.Solver.from_problem(
+            pr, params=hrm.params_default(cfl=0.4, check=0, precision=prec), stream=stream)
+        total = 0.0
+        for _ in range(K):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(dt, 1)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1) * 1e-3
+        out[name] = {"value": pr.ncells * K / total, "unit": UNIT, "ms_per_step": 1e3 * total / K, "steps": K,
+                     "admissibility_after": s.admissibility()}
+        if prec == hrm.FP32:
+            # the error run: three more steps from the initial state, as the FP64 run does
+            s.set_primitive(pr.prim)
+            s.step(dt, 3)
+        states[name] = s.get(hrm.FIELD_W)
+        s.close()
+    out["fp32"]["rel_l1_vs_fp64"] = {"max_over_variables": float(max(rel_l1_state(states["fp32"], states["fp64"],
+                                                                                 pr.N, pr.D))),
+                                     "after_steps": 3, "dt": dt}
+    return out
+
+
 def gated_face_flops(problem, cfl):
     """Algorithmic flops per midpoint with every midpoint gated to the linear
     WENO weights (oracle counting build), per direction."""
@@ -383,6 +423,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
     args = ap.parse_args()
@@ -455,6 +496,7 @@ def main():
 
     # batched form: the 64 seeded uneven instances, one persistent launch per phase
     batched = measure_batched(torch, hrm, problems, stream, flush, args) if rank == 0 and not args.no_batch else None
+    three_d = measure_3d(torch, hrm, problems, stream, flush, args) if rank == 0 and not args.no_3d else None
 
     t_tensor = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
     if dist is not None:
@@ -550,6 +592,7 @@ def main():
                                       "traffic": TRAFFIC_BYTES["k_face32"]}},
             },
             "batched": batched,
+            "interface_3d": three_d,
             "learned": learned_block,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),

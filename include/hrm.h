@@ -24,6 +24,7 @@
 #ifndef HRM_H
 #define HRM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -118,6 +119,21 @@ enum {
   HRM_FIELD_ALPHA = 6,    /* N planes: alpha_1..alpha_N (alpha_N = 1 - the others, Sec. 2) */
   HRM_FIELD_Y = 7         /* N planes: mass fractions Y_k = alpha_k rho_k / rho */
 };
+
+/* Device memory of contexts. By default a context takes its state and scratch
+ * from cudaMalloc at hrm_create (plus the gate buffers it adds later) and
+ * returns them at hrm_destroy. A caller that manages device memory itself (a
+ * framework's caching allocator, a memory pool) installs alloc / free_fn here:
+ * contexts created afterwards take every buffer from alloc(bytes, stream,
+ * user) -- stream being the context's CUDA stream -- and return it through
+ * free_fn(ptr, stream, user); a NULL result of alloc makes hrm_create fail with
+ * HRM_E_NOMEM. Both NULL restore cudaMalloc. Process-wide, read at hrm_create;
+ * not thread-safe against concurrent hrm_create. Batches and detectors keep
+ * cudaMalloc. (The paper has no counterpart: this is the library's boundary.)
+ * Errors: HRM_E_INVAL when exactly one of the two is NULL. */
+typedef void* (*hrm_alloc_fn)(size_t bytes, void* cuda_stream, void* user);
+typedef void (*hrm_free_fn)(void* ptr, void* cuda_stream, void* user);
+hrm_status hrm_set_allocator(hrm_alloc_fn alloc, hrm_free_fn free_fn, void* user);
 
 /* Fill p with the paper's constants (Sec. 4.3.2, App. C, Sec. 4.3.1), PP-WCNS-IS,
  * SSP-RK3, relaxation after every stage, FP64, CFL 0.5, check on. */

@@ -43,6 +43,9 @@ struct hrm_ctx {
   uint8_t* gate[3] = {nullptr, nullptr, nullptr};  // gate bytes per direction (midpoint grids)
   uint32_t* defer = nullptr;       // precision form: per direction, a worklist of deferred midpoints and its counter
   int64_t defer_cap = 0;           // worklist entries (the largest midpoint grid; 0: no worklist)
+  hrm_alloc_fn alloc = nullptr;    // device memory source (hrm_set_allocator at creation; NULL: cudaMalloc)
+  hrm_free_fn dealloc = nullptr;
+  void* alloc_user = nullptr;
   cudaStream_t side[3] = {nullptr, nullptr, nullptr};  // deferred midpoints overlap the next sweep here
   cudaEvent_t ev_fast[3] = {}, ev_fix[3] = {};
   int gate_set[3] = {0, 0, 0};     // fixed gate provided (hrm_set_gate)
@@ -64,6 +67,32 @@ namespace {
 
 // Message of the last failed hrm_create on this thread (its context is gone).
 thread_local std::string g_create_error = "null context";
+
+// Allocator for contexts created from now on (hrm_set_allocator).
+hrm_alloc_fn g_alloc = nullptr;
+hrm_free_fn g_free = nullptr;
+void* g_alloc_user = nullptr;
+
+// Device memory of a context: its allocator, else cudaMalloc.
+cudaError_t ctx_malloc(hrm_ctx* c, void** p, size_t bytes) {
+  if (!c->alloc) return cudaMalloc(p, bytes);
+  *p = c->alloc(bytes, (void*)c->stream, c->alloc_user);
+  return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+template <typename T>
+cudaError_t ctx_malloc(hrm_ctx* c, T** p, size_t bytes) {
+  void* q = nullptr;
+  const cudaError_t e = ctx_malloc(c, &q, bytes);
+  *p = static_cast<T*>(q);
+  return e;
+}
+void ctx_free(hrm_ctx* c, void* p) {
+  if (!p) return;
+  if (c->dealloc)
+    c->dealloc(p, (void*)c->stream, c->alloc_user);
+  else if (!c->alloc)
+    cudaFree(p);
+}
 
 hrm_status fail(hrm_ctx* c, hrm_status s, const char* fmt, ...) {
   if (c) {
@@ -330,6 +359,14 @@ void reset_step_state(hrm_ctx* c) {
 
 extern "C" {
 
+hrm_status hrm_set_allocator(hrm_alloc_fn alloc, hrm_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return HRM_E_INVAL;
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_user = user;
+  return HRM_OK;
+}
+
 void hrm_params_default(hrm_params* p) {
   std::memset(p, 0, sizeof *p);
   p->cfl = 0.5;
@@ -443,29 +480,32 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
   c->fk = face_kernels(N, D);
   if (!c->ck || !c->fk) return bail(fail(c, HRM_E_INVAL, "no kernels for N=%d D=%d", N, D));
   c->stream = (cudaStream_t)cuda_stream;
+  c->alloc = g_alloc;
+  c->dealloc = g_free;
+  c->alloc_user = g_alloc_user;
   hrm_status s;
   if ((s = cuda_check(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "stream create")))
     return bail(s);
   const size_t plane = sizeof(double) * (size_t)c->nc;
   const int M = c->M;
-  if ((s = cuda_check(c, cudaMalloc(&c->Wn, plane * M), "alloc W"))) return bail(s);
-  if ((s = cuda_check(c, cudaMalloc(&c->Ws, plane * M), "alloc Ws"))) return bail(s);
-  if ((s = cuda_check(c, cudaMalloc(&c->V, plane * M), "alloc V"))) return bail(s);
-  if ((s = cuda_check(c, cudaMalloc(&c->AUX, plane * 3), "alloc aux"))) return bail(s);
-  if ((s = cuda_check(c, cudaMalloc(&c->P32, sizeof(float) * (size_t)c->nc * (M + D + 4 + N - 1)), "alloc fp32 planes")))
+  if ((s = cuda_check(c, ctx_malloc(c, &c->Wn, plane * M), "alloc W"))) return bail(s);
+  if ((s = cuda_check(c, ctx_malloc(c, &c->Ws, plane * M), "alloc Ws"))) return bail(s);
+  if ((s = cuda_check(c, ctx_malloc(c, &c->V, plane * M), "alloc V"))) return bail(s);
+  if ((s = cuda_check(c, ctx_malloc(c, &c->AUX, plane * 3), "alloc aux"))) return bail(s);
+  if ((s = cuda_check(c, ctx_malloc(c, &c->P32, sizeof(float) * (size_t)c->nc * (M + D + 4 + N - 1)), "alloc fp32 planes")))
     return bail(s);
-  if ((s = cuda_check(c, cudaMalloc(&c->R32, sizeof(float) * (size_t)c->nc * (D + 2)), "alloc fp32 residues")))
+  if ((s = cuda_check(c, ctx_malloc(c, &c->R32, sizeof(float) * (size_t)c->nc * (D + 2)), "alloc fp32 residues")))
     return bail(s);
   for (int d = 0; d < D; ++d) {
     size_t nf = 1;
     for (int e = 0; e < 3; ++e) nf *= (size_t)(c->dg.n[e] + (e == d));
-    if ((s = cuda_check(c, cudaMalloc(&c->F[d], sizeof(double) * nf * (M + N - 1)), "alloc faces"))) return bail(s);
+    if ((s = cuda_check(c, ctx_malloc(c, &c->F[d], sizeof(double) * nf * (M + N - 1)), "alloc faces"))) return bail(s);
     if ((int64_t)nf > c->defer_cap) c->defer_cap = (int64_t)nf;
   }
   // worklist of the precision form's deferred midpoints (32-bit entries; none
   // beyond 2^32 - 1 midpoints, where the sweep keeps its fallbacks inline)
   if (c->defer_cap < (int64_t)0xffffffffll) {
-    if ((s = cuda_check(c, cudaMalloc(&c->defer, sizeof(uint32_t) * (size_t)D * (size_t)(c->defer_cap + 1)),
+    if ((s = cuda_check(c, ctx_malloc(c, &c->defer, sizeof(uint32_t) * (size_t)D * (size_t)(c->defer_cap + 1)),
                         "alloc worklist")))
       return bail(s);
     for (int d = 0; d < D; ++d) {
@@ -479,7 +519,7 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
   } else {
     c->defer_cap = 0;
   }
-  if ((s = cuda_check(c, cudaMalloc(&c->st, sizeof(StepState)), "alloc step state"))) return bail(s);
+  if ((s = cuda_check(c, ctx_malloc(c, &c->st, sizeof(StepState)), "alloc step state"))) return bail(s);
   cudaMemsetAsync(c->Wn, 0, plane * M, c->stream);
   reset_step_state(c);
   if ((s = cuda_check(c, cudaGetLastError(), "init"))) return bail(s);
@@ -491,17 +531,17 @@ void hrm_destroy(hrm_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graph(c);
-  cudaFree(c->Wn);
-  cudaFree(c->Ws);
-  cudaFree(c->defer);
-  cudaFree(c->V);
-  cudaFree(c->AUX);
-  cudaFree(c->P32);
-  cudaFree(c->R32);
-  for (int d = 0; d < 3; ++d) cudaFree(c->F[d]);
-  cudaFree(c->st);
-  cudaFree(c->blob);
-  for (int d = 0; d < 3; ++d) cudaFree(c->gate[d]);
+  ctx_free(c, c->Wn);
+  ctx_free(c, c->Ws);
+  ctx_free(c, c->defer);
+  ctx_free(c, c->V);
+  ctx_free(c, c->AUX);
+  ctx_free(c, c->P32);
+  ctx_free(c, c->R32);
+  for (int d = 0; d < 3; ++d) ctx_free(c, c->F[d]);
+  ctx_free(c, c->st);
+  ctx_free(c, c->blob);
+  for (int d = 0; d < 3; ++d) ctx_free(c, c->gate[d]);
   for (int i = 0; i < 2 * kMaxProf; ++i)
     if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -766,7 +806,7 @@ size_t gate_bytes(const hrm_ctx* c, int d) { return (size_t)face_total(c->dg, d)
 hrm_status ensure_gates(hrm_ctx* c) {
   for (int d = 0; d < c->D; ++d) {
     if (c->gate[d]) continue;
-    hrm_status s = cuda_check(c, cudaMalloc(&c->gate[d], gate_bytes(c, d)), "alloc gate");
+    hrm_status s = cuda_check(c, ctx_malloc(c, &c->gate[d], gate_bytes(c, d)), "alloc gate");
     if (s) return s;
     cudaMemsetAsync(c->gate[d], 0, gate_bytes(c, d), c->stream);
   }
@@ -779,7 +819,7 @@ extern "C" {
 hrm_status hrm_set_detector(hrm_ctx* c, const hrm_detector* det) {
   if (!c || !det || !detector_blob(det)) return c ? fail(c, HRM_E_INVAL, "null detector") : HRM_E_INVAL;
   hrm_status s;
-  if (!c->blob && (s = cuda_check(c, cudaMalloc(&c->blob, sizeof(mlp::GateBlob)), "alloc gate weights")))
+  if (!c->blob && (s = cuda_check(c, ctx_malloc(c, &c->blob, sizeof(mlp::GateBlob)), "alloc gate weights")))
     return s;
   if ((s = ensure_gates(c))) return s;
   // the detector's weights are final once its own stream has drained

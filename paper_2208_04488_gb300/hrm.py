@@ -93,6 +93,7 @@ def lib():
     L.hrm_set_params.argtypes = [_VP, P(HrmParams)]
     L.hrm_set.argtypes = [_VP, _VP, ctypes.c_int32]
     L.hrm_set_primitive.argtypes = [_VP, _VP, ctypes.c_int32]
+    L.hrm_set_allocator.argtypes = [_VP, _VP, _VP]
     L.hrm_set_boundary.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.c_int32]
     L.hrm_dt.argtypes = [_VP, ctypes.c_double, _DP, _DP]
     L.hrm_step.argtypes = [_VP, ctypes.c_double, ctypes.c_int32]
@@ -201,6 +202,38 @@ def _stream_handle(stream):
         return int(stream) if isinstance(stream, int) else int(stream.cuda_stream)
     import torch
     return int(torch.cuda.current_stream().cuda_stream)
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_keep = None
+
+
+def use_torch_allocator(on: bool = True):
+    """Solvers created after this call take their device memory from PyTorch's
+    caching allocator (on the solver's stream) instead of cudaMalloc; False
+    restores cudaMalloc. Solvers keep the allocator they were created with."""
+    global _allocator_keep
+    if not on:
+        lib().hrm_set_allocator(None, None, None)
+        _allocator_keep = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+        except Exception:
+            return None
+
+    def _free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC_FN(_alloc), _FREE_FN(_free)
+    _allocator_keep = (a, f)
+    st = lib().hrm_set_allocator(ctypes.cast(a, _VP), ctypes.cast(f, _VP), None)
+    if st != HRM_OK:
+        raise HrmError(st, "hrm_set_allocator")
 
 
 class Solver:

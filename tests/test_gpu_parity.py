@@ -512,3 +512,31 @@ def test_dirichlet_api(hrm):
     with pytest.raises(hrm.HrmError) as e:
         hrm.BatchSolver([pr])
     assert e.value.status == hrm.HRM_E_INVAL
+
+
+def test_torch_allocator(hrm):
+    """hrm_set_allocator: a context created with PyTorch's caching allocator
+    takes every buffer from it (and returns them at destruction) and steps
+    exactly as a context on cudaMalloc."""
+    import torch
+    pr = P.shock_bubble_2d(64, 32)
+    a = hrm.Solver.from_problem(pr)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    hrm.use_torch_allocator(True)
+    try:
+        b = hrm.Solver.from_problem(pr)
+    finally:
+        hrm.use_torch_allocator(False)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() - before >= 3 * pr.M * pr.ncells * 8  # W^n, stage state, V at least
+    a.step(0.0, 5)
+    b.step(0.0, 5)
+    np.testing.assert_array_equal(b.get(hrm.FIELD_W), a.get(hrm.FIELD_W))
+    b.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
+    c = hrm.Solver.from_problem(pr)  # back on cudaMalloc
+    assert torch.cuda.memory_allocated() == before
+    c.close()
+    a.close()
