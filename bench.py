@@ -498,12 +498,8 @@ def main():
     batched = measure_batched(torch, hrm, problems, stream, flush, args) if rank == 0 and not args.no_batch else None
     three_d = measure_3d(torch, hrm, problems, stream, flush, args) if rank == 0 and not args.no_3d else None
 
-    t_tensor = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
-    t_max = float(t_tensor.item())
-    cells_total = pr.ncells * args.steps * ws
-    value = cells_total / t_max
+    from paper_2208_04488_gb300.replicas import whole_job_rate
+    value, t_max = whole_job_rate(pr.ncells * args.steps, t_dev, dist, device="cuda")
 
     # end-to-end through the public API with host buffers: per step the state is
     # uploaded from pinned host memory, advanced one step and read back.
