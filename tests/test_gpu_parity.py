@@ -172,6 +172,25 @@ def test_full_size_one_step_sampled(hrm, orc):
     assert s.admissibility() == [0, 0, 0, 0]
 
 
+def test_full_size_3d_one_step(hrm, orc):
+    """The 256^3 3D configuration (perturbed interface, periodic in y and z) in
+    the launch configuration the benchmark times: one CFL step on the GPU
+    against the oracle's multi-threaded build (identical results to its serial
+    build), every cell compared."""
+    pr = P.interface_3d(256)
+    f, g, W = orc.setup(pr)
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=0.4, check=0))
+    dtg, _ = s.dt(0.4)
+    dto, _ = orc.dt(f, g, W, 0.4)
+    assert dtg == dto
+    s.step(dtg, 1)
+    got = s.get(hrm.FIELD_W)
+    s.close()
+    ref = orc.step(f, orc.make_params(), g, W, dto, 1, omp=True)
+    err = rel_l1(got, ref)
+    assert err.max() <= 1e-12, err
+
+
 def test_extreme_shock_tube_positivity_gpu(hrm, orc):
     """Sec. 5.5 on the GPU: admissible with the limiters; with them off the
     library reports HRM_E_ADMISSIBILITY (no crash, the context stays usable)."""
