@@ -610,8 +610,9 @@ __device__ __forceinline__ void relax_cell(double* W, const DevFluid& f, double*
   const double sq = sqrt(Bp * Bp - 4.0 * Ap * Cp);
   const double ps = (Bp > 0.0) ? (-2.0 * Cp) / (Bp + sq) : (sq - Bp) / (2.0 * Ap);
   if (FAST) {
-    // one reciprocal per distinct p* + p_inf (the stiffened gas and the ideal gases)
-    const double inv_pl = 1.0 / (ps + pinf1), inv_p = 1.0 / ps;
+    // 1/(p* + p_inf,1) and 1/p* from one reciprocal of their product
+    const double r2 = 1.0 / (ps * (ps + pinf1));
+    const double inv_pl = ps * r2, inv_p = (ps + pinf1) * r2;
     const double den = Yl * (ps + f.gamma[l] * pinf1) * f.cv[l] * inv_pl + cvb - Yl * f.cv[l];
     const double Ts = re * inv_rho / den;
 #pragma unroll
@@ -689,7 +690,42 @@ __device__ __forceinline__ void update_body(int64_t c, const double* Wn, const d
   double Ws[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) Ws[m] = Wsrc[m * nc + c];
-  (void)Ws;
+  if constexpr (FAST && MODE == 0) {
+    // precision form: W_src + dt RHS accumulated directly, dt/dx_d folded into
+    // one coefficient per direction (one multiply-add per slot and direction)
+    double acc[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] = Ws[m];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const double* F = d == 0 ? F0 : (d == 1 ? F1 : F2);
+      const int64_t f0 = g.n[0] + (d == 0), f1 = g.n[1] + (d == 1), f2 = g.n[2] + (d == 2);
+      const int64_t nf = f0 * f1 * f2;
+      const int64_t fl = (i2 * f1 + i1) * f0 + i0;
+      const int64_t fr = fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1));
+      const double cd = -dt * g.inv_dx[d];
+#pragma unroll
+      for (int m = 0; m < L::NC; ++m) acc[m] += cd * (F[m * nf + fr] - F[m * nf + fl]);
+#pragma unroll
+      for (int k = 0; k < N - 1; ++k) {
+        const int m = L::AL + k;
+        acc[m] += cd * (F[m * nf + fr] - F[(M + k) * nf + fl]);
+      }
+    }
+    double Wo[M];
+    if (a == 0.0) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) Wo[m] = b * acc[m];
+    } else {
+#pragma unroll
+      for (int m = 0; m < M; ++m) Wo[m] = a * Wn[m * nc + c] + b * acc[m];
+    }
+    if (relax) relax_cell<N, D, FAST>(Wo, f);
+    if (count) count_bits(st, admissibility_bits<N, D>(Wo, f));
+#pragma unroll
+    for (int m = 0; m < M; ++m) Wout[m * nc + c] = Wo[m];
+    return;
+  }
   double rhs[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) rhs[m] = 0.0;
