@@ -127,47 +127,6 @@ __global__ void __launch_bounds__(kBatchFace32Threads, 3)
   batch_face_items<D, DIR, N>(insts, items, nitems, src, pr, true);
 }
 
-// The precision form with deferred fallbacks (as k_face32_fast): midpoints whose
-// screens fail are appended to `list` as (instance << 40 | midpoint) for
-// k_batch_face32_fix. *count must be 0 at launch; list holds one entry per
-// midpoint of the items.
-template <int D, int DIR, int N>
-__global__ void __launch_bounds__(kBatchFace32Threads, 4)
-    k_batch_face32_fast(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems,
-                        int src, DevParams pr, unsigned long long* __restrict__ list, uint32_t* __restrict__ count) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const WorkItem w = items[it];
-    const BatchInst& I = insts[w.inst];
-    const double* W = pick(I, src);
-    const double lam = I.st->lam[DIR];
-    for (int64_t t = w.begin + threadIdx.x; t < w.end; t += blockDim.x) {
-      Nodes6 nd;
-      if (!face_nodes<DIR>(I.g, t, nd)) continue;
-      if (!face32_body<N, D, DIR, true>(t, nd, W, I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr, lam))
-        list[atomicAdd(count, 1u)] = ((unsigned long long)w.inst << 40) | (unsigned long long)t;
-    }
-  }
-}
-
-// The deferred midpoints with the full body, spread lane-major over one-warp
-// blocks (each is a long FP64 chain; see k_face32_fix).
-template <int D, int DIR, int N>
-__global__ void __launch_bounds__(kBatchFace32Threads, 2)
-    k_batch_face32_fix(const BatchInst* __restrict__ insts, int src, DevParams pr,
-                       const unsigned long long* __restrict__ list, const uint32_t* __restrict__ count) {
-  const int64_t n = *count;
-  for (int64_t r = threadIdx.x;; r += blockDim.x) {
-    const int64_t i = r * gridDim.x + blockIdx.x;
-    if (i >= n) break;
-    const unsigned long long e = list[i];
-    const BatchInst& I = insts[(int)(e >> 40)];
-    const int64_t t = (int64_t)(e & ((1ull << 40) - 1ull));
-    Nodes6 nd;
-    if (!face_nodes<DIR>(I.g, t, nd)) continue;
-    face32_body<N, D, DIR>(t, nd, pick(I, src), I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr, I.st->lam[DIR]);
-  }
-}
-
 // Flux difference, SSP-RK combination and relaxation of every cell of the instances.
 template <int D, bool FAST, int N>
 __global__ void __launch_bounds__(kBatchMaxThreads)
@@ -200,10 +159,6 @@ void batch_face64_d2(int N, int dir, const BatchLaunch&, const BatchInst*, const
                      const DevParams&, cudaStream_t);
 void batch_face32_d2(int N, int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
                      const DevParams&, cudaStream_t);
-// With a worklist (list, count): the screened sweep and the fix-up of its
-// deferred midpoints (two kernels after a counter reset).
-void batch_face32_defer_d2(int N, int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
-                           const DevParams&, unsigned long long* list, uint32_t* count, cudaStream_t);
 void batch_update64_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst,
                        double a, double b, int relax, int count, cudaStream_t);
 void batch_update32_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst,

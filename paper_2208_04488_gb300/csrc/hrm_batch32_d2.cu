@@ -1,7 +1,6 @@
 // Batched-form kernels for D = 2 of the precision form: FP32 planes, FP32-bulk
 // midpoints and the fast update (built with FMA contraction).
 #include "hrm_batch.cuh"
-#include "hrm_launch.h"
 
 namespace hrm {
 
@@ -17,32 +16,6 @@ void batch_face32_d2(int N, int dir, const BatchLaunch& L, const BatchInst* inst
       k_batch_face32<2, 0, 3><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
     else
       k_batch_face32<2, 1, 3><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p);
-  }
-}
-
-namespace {
-template <int DIR, int N>
-void defer_l(const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems, int src,
-             const DevParams& p, unsigned long long* list, uint32_t* count, cudaStream_t s) {
-  cudaMemsetAsync(count, 0, sizeof(uint32_t), s);
-  k_batch_face32_fast<2, DIR, N><<<L.grid, L.threads, 0, s>>>(insts, items, nitems, src, p, list, count);
-  k_batch_face32_fix<2, DIR, N><<<kFixBlocks, kFixThreads, 0, s>>>(insts, src, p, list, count);
-}
-}  // namespace
-
-void batch_face32_defer_d2(int N, int dir, const BatchLaunch& L, const BatchInst* insts, const WorkItem* items,
-                           int nitems, int src, const DevParams& p, unsigned long long* list, uint32_t* count,
-                           cudaStream_t s) {
-  if (N == 2) {
-    if (dir == 0)
-      defer_l<0, 2>(L, insts, items, nitems, src, p, list, count, s);
-    else
-      defer_l<1, 2>(L, insts, items, nitems, src, p, list, count, s);
-  } else {
-    if (dir == 0)
-      defer_l<0, 3>(L, insts, items, nitems, src, p, list, count, s);
-    else
-      defer_l<1, 3>(L, insts, items, nitems, src, p, list, count, s);
   }
 }
 

@@ -44,10 +44,6 @@ struct hrm_batch {
   // then the faces of each direction
   int off_cell[2] = {0, 0}, n_cell[2] = {0, 0};
   int off_face[2][2] = {{0, 0}, {0, 0}}, n_face[2][2] = {{0, 0}, {0, 0}};
-  // precision form: worklists of deferred midpoints per direction and group
-  // (one entry per midpoint of the group), and their counters
-  unsigned long long* defer_list[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  uint32_t* defer_count = nullptr;  // [d * 2 + gN]
   Shape shape;
   int sms = 0;
   cudaGraphExec_t gexec = nullptr;
@@ -147,12 +143,6 @@ int enqueue_stage(hrm_batch* b, cudaStream_t s, int src, int dst, double a, doub
     for (int gN = 0; gN < 2; ++gN) {
       if (!b->n_face[d][gN]) continue;
       const WorkItem* it = b->d_items + b->off_face[d][gN];
-      if (fp32 && b->params.screen && b->defer_count) {
-        batch_face32_defer_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, b->defer_list[d][gN],
-                              b->defer_count + d * 2 + gN, s);
-        k += 2;
-        continue;
-      }
       if (fp32)
         batch_face32_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, s);
       else
@@ -219,9 +209,6 @@ void hrm_batch_destroy(hrm_batch* b) {
   }
   cudaFree(b->d_insts);
   cudaFree(b->d_items);
-  for (int d = 0; d < 2; ++d)
-    for (int gN = 0; gN < 2; ++gN) cudaFree(b->defer_list[d][gN]);
-  cudaFree(b->defer_count);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
 }
@@ -347,19 +334,6 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
                  "copy instances")))
     return bail(s);
   if ((s = build_items(b))) return bail(s);
-  // worklists of the precision form's deferred midpoints
-  for (int d = 0; d < 2; ++d)
-    for (int gN = 0; gN < 2; ++gN) {
-      size_t nf = 0;
-      for (int i = 0; i < b->ninst; ++i)
-        if (b->N[i] == 2 + gN) {
-          const DevGrid& g = b->host[i].g;
-          nf += (size_t)((g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * g.n[2]);
-        }
-      if (nf && (s = bcuda(b, cudaMalloc(&b->defer_list[d][gN], sizeof(unsigned long long) * nf), "alloc worklist")))
-        return bail(s);
-    }
-  if ((s = bcuda(b, cudaMalloc(&b->defer_count, sizeof(uint32_t) * 4), "alloc worklist counters"))) return bail(s);
   *out = b;
   return HRM_OK;
 }
