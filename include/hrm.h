@@ -117,7 +117,9 @@ enum {
                               equilibrium pressure (Sec. 3: derivatives of the relaxed pressure
                               with respect to alpha_k rho_k and to rho e) */
   HRM_FIELD_ALPHA = 6,    /* N planes: alpha_1..alpha_N (alpha_N = 1 - the others, Sec. 2) */
-  HRM_FIELD_Y = 7         /* N planes: mass fractions Y_k = alpha_k rho_k / rho */
+  HRM_FIELD_Y = 7,        /* N planes: mass fractions Y_k = alpha_k rho_k / rho */
+  HRM_FIELD_SCHLIEREN = 8 /* 1 plane: numerical schlieren |grad rho| / rho of the paper's figures,
+                             central differences with neighbours through the boundary conditions */
 };
 
 /* Device memory of contexts. By default a context takes its state and scratch
@@ -213,6 +215,12 @@ hrm_status hrm_get(hrm_ctx* ctx, int32_t field, double* dst, int32_t on_device);
 
 /* Simulated time and number of steps taken since the last hrm_set. */
 hrm_status hrm_time(hrm_ctx* ctx, double* t, int64_t* steps);
+
+/* Restore the simulated time and step count (checkpoint / restart: W from
+ * hrm_get, then hrm_set and hrm_set_time; the steps that follow are those of an
+ * uninterrupted run bit for bit, the step size depending only on the state).
+ * Synchronises. Errors: HRM_E_INVAL (steps < 0), HRM_E_CUDA. */
+hrm_status hrm_set_time(hrm_ctx* ctx, double t, int64_t steps);
 
 /* Admissibility counters of the current state (Sec. 2, sets G and script-G):
  * counts[0] cells with a negative partial density, [1] a volume fraction outside

@@ -756,6 +756,9 @@ hrm_status hrm_get(hrm_ctx* c, int32_t field, double* dst, int32_t on_device) {
     case HRM_FIELD_Y:
       planes = c->N;
       break;
+    case HRM_FIELD_SCHLIEREN:
+      planes = 1;
+      break;
     default:
       return fail(c, HRM_E_INVAL, "unknown field %d", field);
   }
@@ -780,6 +783,18 @@ hrm_status hrm_time(hrm_ctx* c, double* t, int64_t* steps) {
   if (t) *t = h.t;
   if (steps) *steps = h.steps;
   return HRM_OK;
+}
+
+hrm_status hrm_set_time(hrm_ctx* c, double t, int64_t steps) {
+  if (!c || steps < 0) return HRM_E_INVAL;
+  const long long n = steps;
+  hrm_status s;
+  if ((s = cuda_check(c, cudaMemcpyAsync(&c->st->t, &t, sizeof t, cudaMemcpyHostToDevice, c->stream), "set time")))
+    return s;
+  if ((s = cuda_check(c, cudaMemcpyAsync(&c->st->steps, &n, sizeof n, cudaMemcpyHostToDevice, c->stream),
+                      "set steps")))
+    return s;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "set time sync");
 }
 
 hrm_status hrm_admissibility(hrm_ctx* c, int64_t counts[4]) {

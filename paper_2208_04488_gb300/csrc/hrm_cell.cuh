@@ -257,6 +257,46 @@ __global__ void __launch_bounds__(kCellThreads)
   double w[M], v[M], rho, cs, rc2;
 #pragma unroll
   for (int m = 0; m < M; ++m) w[m] = W[m * nc + c];
+  if (field == 8) {
+    // numerical schlieren |grad rho| / rho: central differences, neighbours
+    // through the boundary conditions (copy, wrap, or the prescribed state)
+    const int64_t ijk[3] = {c % g.n[0], (c / g.n[0]) % g.n[1], c / (g.n[0] * g.n[1])};
+    auto rho_at = [&](int64_t cell) {
+      double r = 0.0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) r += W[k * nc + cell];
+      return r;
+    };
+    double r0 = 0.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r0 += w[k];
+    double g2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      int64_t nb[2];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int64_t j = ijk[d] + (side ? 1 : -1);
+        int64_t q[3] = {ijk[0], ijk[1], ijk[2]};
+        if ((j < 0 || j >= g.n[d]) && g.bc[2 * d + side] == 2) {
+          int64_t tr = 0, stride = 1;
+          for (int e = 0; e < 3; ++e)
+            if (e != d) {
+              tr += q[e] * stride;
+              stride *= g.n[e];
+            }
+          nb[side] = g.goff[2 * d + side] + tr;
+        } else {
+          q[d] = bc_map(g, d, j);
+          nb[side] = (q[2] * g.n[1] + q[1]) * g.n[0] + q[0];
+        }
+      }
+      const double gd = (rho_at(nb[1]) - rho_at(nb[0])) * (0.5 * g.inv_dx[d]);
+      g2 += gd * gd;
+    }
+    out[c] = sqrt(g2) / r0;
+    return;
+  }
   if (field == 6 || field == 7) {
     // all N volume fractions (alpha_N = 1 - the others) or mass fractions Y_k
     double r = 0.0, sa = 0.0;

@@ -21,6 +21,7 @@ HEADER = os.path.join(HERE, "..", "include", "hrm.h")
 
 HRM_OK, HRM_E_INVAL, HRM_E_CUDA, HRM_E_ADMISSIBILITY, HRM_E_TIMEOUT, HRM_E_NOMEM = 0, -1, -2, -3, -4, -5
 FIELD_W, FIELD_V, FIELD_C5, FIELD_PT, FIELD_C4, FIELD_PSI_GAMMA, FIELD_ALPHA, FIELD_Y = 0, 1, 2, 3, 4, 5, 6, 7
+FIELD_SCHLIEREN = 8
 FP64, FP32 = 0, 1
 RK3, EULER, RK2 = 0, 1, 2
 RELAX_OFF, RELAX_STAGE, RELAX_STEP = 0, 1, 2
@@ -101,6 +102,7 @@ def lib():
     L.hrm_rhs.argtypes = [_VP, _DP, _VP]
     L.hrm_get.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
     L.hrm_time.argtypes = [_VP, _DP, P(ctypes.c_int64)]
+    L.hrm_set_time.argtypes = [_VP, ctypes.c_double, ctypes.c_int64]
     L.hrm_admissibility.argtypes = [_VP, P(ctypes.c_int64)]
     L.hrm_kernel_launches.argtypes = [_VP]
     L.hrm_kernel_launches.restype = ctypes.c_int64
@@ -324,7 +326,7 @@ class Solver:
 
     def get(self, field=FIELD_W, out=None):
         planes = {FIELD_W: self.M, FIELD_V: self.M, FIELD_C5: 1, FIELD_PT: 2, FIELD_C4: 1,
-                  FIELD_PSI_GAMMA: self.N + 1, FIELD_ALPHA: self.N, FIELD_Y: self.N}[field]
+                  FIELD_PSI_GAMMA: self.N + 1, FIELD_ALPHA: self.N, FIELD_Y: self.N, FIELD_SCHLIEREN: 1}[field]
         if out is None:
             out = np.empty((planes, self.ncells))
         ptr, dev = self._ptr(out)
@@ -337,6 +339,10 @@ class Solver:
         tau = (ctypes.c_double * 3)()
         self._check(lib().hrm_dt(self.h, cfl, ctypes.byref(dt), tau))
         return dt.value, np.array(tau[:self.D])
+
+    def set_time(self, t, steps):
+        """Restore the simulated time and step count (checkpoint / restart)."""
+        self._check(lib().hrm_set_time(self.h, float(t), int(steps)))
 
     def step(self, dt=0.0, nsteps=1):
         return self._check(lib().hrm_step(self.h, float(dt), int(nsteps)))

@@ -559,3 +559,47 @@ def test_torch_allocator(hrm):
     assert torch.cuda.memory_allocated() == before
     c.close()
     a.close()
+
+
+@pytest.mark.parametrize("pr", [P.shock_bubble_2d(40, 21), P.advection_2d_smooth(16), P.interface_3d(12)],
+                         ids=["transmissive_2d", "periodic_2d", "periodic_yz_3d"])
+def test_schlieren_field(hrm, pr):
+    """HRM_FIELD_SCHLIEREN against its definition |grad rho| / rho with central
+    differences, the neighbours beyond a side taken by its boundary condition."""
+    s = hrm.Solver.from_problem(pr)
+    s.step(0.0, 3)
+    W = s.get(hrm.FIELD_W)
+    rho = W[:pr.N].sum(axis=0).reshape(pr.n[::-1])
+    g2 = np.zeros_like(rho)
+    for d in range(pr.D):
+        ax = pr.D - 1 - d  # x is the last numpy axis
+        mode = "wrap" if pr.bc[2 * d] == 1 else "edge"
+        pad = [(0, 0)] * pr.D
+        pad[ax] = (1, 1)
+        rp = np.pad(rho, pad, mode=mode)
+        hi = np.take(rp, np.arange(2, rp.shape[ax]), axis=ax)
+        lo = np.take(rp, np.arange(0, rp.shape[ax] - 2), axis=ax)
+        gd = (hi - lo) * (0.5 / pr.dx[d])
+        g2 += gd * gd
+    ref = (np.sqrt(g2) / rho).reshape(-1)
+    got = s.get(hrm.FIELD_SCHLIEREN)[0]
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def test_checkpoint_restart_is_bit_exact(hrm):
+    """W and (t, steps) saved after k steps and restored into a new context give,
+    k steps later, the state of an uninterrupted 2k-step run bit for bit."""
+    pr = P.shock_bubble_2d(64, 32)
+    k = 6
+    a = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=0.4, check=0))
+    a.step(0.0, 2 * k)
+    b = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=0.4, check=0))
+    b.step(0.0, k)
+    W, (t, n) = b.get(hrm.FIELD_W), b.time()
+    b.close()
+    c = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=0.4, check=0), set_state=False)
+    c.set(W)
+    c.set_time(t, n)
+    c.step(0.0, k)
+    np.testing.assert_array_equal(c.get(hrm.FIELD_W), a.get(hrm.FIELD_W))
+    assert c.time() == a.time()
