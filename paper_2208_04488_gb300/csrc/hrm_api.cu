@@ -9,6 +9,8 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hrm.h"
 #include "hrm_launch.h"
 #include "hrm_learned.h"
@@ -64,6 +66,13 @@ struct hrm_ctx {
 };
 
 namespace {
+
+// NVTX range around an entry point (visible in Nsight timelines; no cost when no
+// tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 // Message of the last failed hrm_create on this thread (its context is gone).
 thread_local std::string g_create_error = "null context";
@@ -596,6 +605,7 @@ hrm_status hrm_set_params(hrm_ctx* c, const hrm_params* p) {
 }
 
 hrm_status hrm_set(hrm_ctx* c, const double* W, int32_t on_device) {
+  Range range("hrm_set");
   if (!c || !W) return HRM_E_INVAL;
   hrm_status s = copy_planes(c, c->Wn, c->nc, W, c->nint, c->nint, c->M,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, "copy W");
@@ -606,6 +616,7 @@ hrm_status hrm_set(hrm_ctx* c, const double* W, int32_t on_device) {
 }
 
 hrm_status hrm_set_primitive(hrm_ctx* c, const double* prim, int32_t on_device) {
+  Range range("hrm_set_primitive");
   if (!c || !prim) return HRM_E_INVAL;
   hrm_status s = copy_planes(c, c->V, c->nc, prim, c->nint, c->nint, c->N + c->D + 1,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, "copy primitives");
@@ -620,6 +631,7 @@ hrm_status hrm_set_primitive(hrm_ctx* c, const double* prim, int32_t on_device) 
 
 hrm_status hrm_set_boundary(hrm_ctx* c, int32_t side, const double* values, int32_t primitive,
                             int32_t on_device) {
+  Range range("hrm_set_boundary");
   if (!c || !values) return HRM_E_INVAL;
   if (side < 0 || side >= 2 * c->D || c->dg.bc[side] != HRM_BC_DIRICHLET)
     return fail(c, HRM_E_INVAL, "side %d is not a Dirichlet side", side);
@@ -645,6 +657,7 @@ hrm_status hrm_set_boundary(hrm_ctx* c, int32_t side, const double* values, int3
 }
 
 hrm_status hrm_dt(hrm_ctx* c, double cfl, double* dt_out, double* tau_out) {
+  Range range("hrm_dt");
   if (!c || !(cfl > 0.0)) return c ? fail(c, HRM_E_INVAL, "cfl must be positive") : HRM_E_INVAL;
   if (hrm_status s = check_boundaries(c)) return s;
   c->ck->prim(c->Wn, c->V, c->AUX, nullptr, nullptr, c->dg, c->fl, c->st, tau_mode(c), c->stream);
@@ -661,6 +674,7 @@ hrm_status hrm_dt(hrm_ctx* c, double cfl, double* dt_out, double* tau_out) {
 }
 
 hrm_status hrm_step(hrm_ctx* c, double dt, int32_t nsteps) {
+  Range range("hrm_step");
   if (!c) return HRM_E_INVAL;
   if (nsteps < 0) return fail(c, HRM_E_INVAL, "nsteps must be non-negative");
   if (nsteps == 0) return HRM_OK;
@@ -689,6 +703,7 @@ hrm_status hrm_step(hrm_ctx* c, double dt, int32_t nsteps) {
 }
 
 hrm_status hrm_relax(hrm_ctx* c) {
+  Range range("hrm_relax");
   if (!c) return HRM_E_INVAL;
   c->ck->relax(c->Wn, c->dg, c->fl, c->stream);
   ++c->launches;
@@ -696,6 +711,7 @@ hrm_status hrm_relax(hrm_ctx* c) {
 }
 
 hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
+  Range range("hrm_rhs");
   if (!c || !lam || !rhs) return HRM_E_INVAL;
   double l3[3] = {0.0, 0.0, 0.0};
   for (int d = 0; d < c->D; ++d) l3[d] = lam[d];
@@ -731,6 +747,7 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
 }
 
 hrm_status hrm_get(hrm_ctx* c, int32_t field, double* dst, int32_t on_device) {
+  Range range("hrm_get");
   if (!c || !dst) return HRM_E_INVAL;
   int planes;
   const double* src;
