@@ -362,6 +362,41 @@ def run_form(torch, hrm, pr, precision, det, dt, steps, warmup, flush, stream, t
     return out
 
 
+def final_time_errors(hrm, pr, det, stream, nsteps):
+    """The workload's full run (its configuration's step count): FP64 with the
+    CFL step of each step's start state, then the precision form, FP32 + learned
+    and FP64 + learned with the same sequence of steps; each form's relative L1
+    error against FP64 at the final time."""
+    from paper_2208_04488_gb300.metrics import rel_l1_state
+    prm = hrm.params_default(cfl=pr.cfl, check=0)
+    s = hrm.Solver.from_problem(pr, params=prm, stream=stream)
+    dts = []
+    for _ in range(nsteps):
+        dt, _ = s.dt(pr.cfl)
+        dts.append(dt)
+        s.step(dt, 1)
+    ref = s.get(hrm.FIELD_W)
+    t_final = s.time()[0]
+    out = {"steps": nsteps, "t_final": t_final, "dt_source": "CFL step of the FP64 run, replayed by every form",
+           "fp64_admissibility": s.admissibility()}
+    s.close()
+    forms = [("fp32", hrm.FP32, False), ("fp32_learned", hrm.FP32, True), ("fp64_learned", hrm.FP64, True)]
+    for name, prec, gated in forms:
+        if gated and det is None:
+            continue
+        s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, check=0, precision=prec),
+                                    stream=stream)
+        if gated:
+            s.set_detector(det)
+            s.set_params(hrm.params_default(cfl=pr.cfl, check=0, precision=prec, learned=hrm.LEARNED_GATE))
+        for dt in dts:
+            s.step(dt, 1)
+        l1 = rel_l1_state(s.get(hrm.FIELD_W), ref, pr.N, pr.D).tolist()
+        out[name] = {"rel_l1_vs_fp64": max(l1), "per_variable": l1, "admissibility": s.admissibility()}
+        s.close()
+    return out
+
+
 def form_summary(hrm, pr, r, ref_W, steps, face_fl, face_fl_gated, peak, peak_name):
     """JSON block of one form: throughput, L1 error against plain FP64 after the
     same equal steps, and the per-midpoint kernel's achieved fraction of the
@@ -424,6 +459,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--final-steps", type=int, default=2000,
+                    help="steps of the full-run error comparison (the configuration's 2000; 0: skip)")
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
     args = ap.parse_args()
@@ -497,6 +534,8 @@ def main():
     # batched form: the 64 seeded uneven instances, one persistent launch per phase
     batched = measure_batched(torch, hrm, problems, stream, flush, args) if rank == 0 and not args.no_batch else None
     three_d = measure_3d(torch, hrm, problems, stream, flush, args) if rank == 0 and not args.no_3d else None
+    final = (final_time_errors(hrm, pr, det, stream, args.final_steps)
+             if rank == 0 and args.final_steps > 0 else None)
 
     from paper_2208_04488_gb300.replicas import whole_job_rate
     value, t_max = whole_job_rate(pr.ncells * args.steps, t_dev, dist, device="cuda")
@@ -589,6 +628,7 @@ def main():
             },
             "batched": batched,
             "interface_3d": three_d,
+            "final_time": final,
             "learned": learned_block,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
