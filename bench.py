@@ -34,6 +34,8 @@ sys.path.insert(0, ROOT)
 # ncu --set full capture on this workload (profiles/k_face_fp64_shock_bubble_1024x512.md and
 # profiles/k_face32_shock_bubble_1024x512.md); to be re-taken whenever those kernels change.
 TRAFFIC_BYTES = {"k_face_fp64": 99.21e6, "k_face32": 37.61e6}
+# FP64-pipe activity of the FP64 sweep in the same ncu capture (fraction of peak sustained)
+FP64_PIPE_ACTIVE = {"k_face_fp64": 0.858}
 METRIC = "cell-updates/s (FP64 plain vs FP32+learned) at stated L1 err; % of roofline"
 UNIT = "cell-updates/s"
 WORKLOAD = "2D three-species shock-bubble, 1024x512 cells, Mach 1.5 shock, water+air+helium, SSP-RK3, CFL 0.4"
@@ -599,6 +601,7 @@ def main():
                          "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
                          "frac": frac, "traffic": TRAFFIC_BYTES["k_face_fp64"],
                          "traffic_unit": "bytes per launch (ncu capture, y sweep)",
+                         "fp64_pipe_active_ncu": FP64_PIPE_ACTIVE["k_face_fp64"],
                          "peak_source": "measured FP64 FMA-chain probe on this GPU (hrm_probe_fma_peak)",
                          "algorithmic_flops_per_face": [round(x[0], 1) for x in faces],
                          "of_which_first_order_flux": round(first_order_face_flops(pr, pr.cfl, 0), 1),
