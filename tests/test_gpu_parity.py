@@ -373,7 +373,10 @@ def test_fp32_form_keeps_uniform_states_exactly(hrm):
     (P.shock_bubble_2d(128, 64), 40, 1e-3),
     (P.advection_2d_smooth(64), 40, 1e-6),
     (P.interface_3d(32), 20, 2e-4),
-], ids=["shock_tube_400", "shock_bubble_128x64", "advection_64", "interface_3d_32"])
+    (P.dirichlet_box([24, 20, 16]), 20, 1e-5),
+    (P.mach100_jet_2d(128, 64), 40, 1e-4),  # alpha_1 sums over the thin jet only: 3.3e-5 measured
+], ids=["shock_tube_400", "shock_bubble_128x64", "advection_64", "interface_3d_32", "dirichlet_box_3d",
+        "mach100_jet_128x64"])
 def test_fp32_form_error_against_fp64(hrm, pr, nsteps, tol):
     """The precision form stays within a stated relative L1 error of the FP64
     path and keeps every cell admissible."""
