@@ -606,3 +606,17 @@ def test_checkpoint_restart_is_bit_exact(hrm):
     c.step(0.0, k)
     np.testing.assert_array_equal(c.get(hrm.FIELD_W), a.get(hrm.FIELD_W))
     assert c.time() == a.time()
+
+
+@pytest.mark.parametrize("mach", [1.2, 2.0])
+def test_interface_3d_mach_sweep_admissible(hrm, mach):
+    """The 3D configuration's robustness sweep (Mach 1.2 and 2.0 shocks on the
+    perturbed interface): both forms keep every cell admissible over 30 steps
+    and stay close to each other."""
+    from paper_2208_04488_gb300.metrics import rel_l1_state
+    pr = P.interface_3d(24, mach=mach)
+    a, b = _fp32_vs_fp64(hrm, pr, 30, cfl=0.4)
+    assert a.admissibility() == [0, 0, 0, 0]
+    assert b.admissibility() == [0, 0, 0, 0]
+    err = rel_l1_state(b.get(hrm.FIELD_W), a.get(hrm.FIELD_W), pr.N, pr.D)
+    assert err.max() <= 1e-3, err
