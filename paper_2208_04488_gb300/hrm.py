@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 import re
 from typing import Optional
 
@@ -267,6 +268,8 @@ class Solver:
         if st != HRM_OK:
             raise HrmError(st, L.hrm_last_error(None).decode())
         self.h = h
+        # the allocator callbacks this context returns its memory through
+        self._allocator = _allocator_keep
 
     @classmethod
     def from_problem(cls, problem, params: Optional[HrmParams] = None, stream=None, set_state=True):
@@ -286,6 +289,10 @@ class Solver:
 
     def __del__(self):
         try:
+            # at interpreter exit, memory from PyTorch's allocator is left to the
+            # process teardown (the allocator may already be gone)
+            if getattr(self, "_allocator", None) is not None and sys.is_finalizing():
+                return
             self.close()
         except Exception:
             pass
