@@ -127,6 +127,52 @@ __global__ void __launch_bounds__(kBatchFace32Threads, 3)
   batch_face_items<D, DIR, N>(insts, items, nitems, src, pr, true);
 }
 
+// The precision form's screened sweep over tiles of 128 midpoints of the
+// instances (one block per tile, one launch for all instances of a species
+// count), the body as k_face32_fast's: midpoints whose screens fail are
+// appended to `list` as (instance << 40 | midpoint) for k_batch_face32_fix.
+// *count must be 0 at launch; list holds one entry per midpoint of the tiles.
+template <int D, int DIR, int N>
+__global__ void __launch_bounds__(kBatchFace32Threads, 5)
+    k_batch_face32_tiles(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ tiles, int src,
+                         DevParams pr, unsigned long long* __restrict__ list, uint32_t* __restrict__ count) {
+  const WorkItem w = tiles[blockIdx.x];
+  const BatchInst& I = insts[w.inst];
+  const int64_t t = w.begin + threadIdx.x;
+  Nodes6 nd;
+  bool need = false;
+  if (t < w.end && face_nodes<DIR>(I.g, t, nd))
+    need = !face32_body<N, D, DIR, true>(t, nd, pick(I, src), I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr,
+                                         I.st->lam[DIR]);
+  const unsigned m = __ballot_sync(0xffffffffu, need);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (need)
+    list[base + __popc(m & ((1u << lane) - 1u))] = ((unsigned long long)w.inst << 40) | (unsigned long long)t;
+}
+
+// The deferred midpoints of k_batch_face32_tiles with the full body, spread
+// lane-major over one-warp blocks (each is a long FP64 chain).
+template <int D, int DIR, int N>
+__global__ void __launch_bounds__(kBatchFace32Threads, 2)
+    k_batch_face32_fix(const BatchInst* __restrict__ insts, int src, DevParams pr,
+                       const unsigned long long* __restrict__ list, const uint32_t* __restrict__ count) {
+  const int64_t n = *count;
+  for (int64_t r = threadIdx.x;; r += blockDim.x) {
+    const int64_t i = r * gridDim.x + blockIdx.x;
+    if (i >= n) break;
+    const unsigned long long e = list[i];
+    const BatchInst& I = insts[(int)(e >> 40)];
+    const int64_t t = (int64_t)(e & ((1ull << 40) - 1ull));
+    Nodes6 nd;
+    if (!face_nodes<DIR>(I.g, t, nd)) continue;
+    face32_body<N, D, DIR>(t, nd, pick(I, src), I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr, I.st->lam[DIR]);
+  }
+}
+
 // Flux difference, SSP-RK combination and relaxation of every cell of the instances.
 template <int D, bool FAST, int N>
 __global__ void __launch_bounds__(kBatchMaxThreads)
@@ -159,6 +205,10 @@ void batch_face64_d2(int N, int dir, const BatchLaunch&, const BatchInst*, const
                      const DevParams&, cudaStream_t);
 void batch_face32_d2(int N, int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
                      const DevParams&, cudaStream_t);
+// The screened sweep over ntiles 128-midpoint tiles and the fix-up of its
+// deferred midpoints (after a reset of *count).
+void batch_face32_tiles_d2(int N, int dir, const BatchInst*, const WorkItem* tiles, int ntiles, int src,
+                           const DevParams&, unsigned long long* list, uint32_t* count, cudaStream_t);
 void batch_update64_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst,
                        double a, double b, int relax, int count, cudaStream_t);
 void batch_update32_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst,

@@ -44,6 +44,12 @@ struct hrm_batch {
   // then the faces of each direction
   int off_cell[2] = {0, 0}, n_cell[2] = {0, 0};
   int off_face[2][2] = {{0, 0}, {0, 0}}, n_face[2][2] = {{0, 0}, {0, 0}};
+  // precision form: 128-midpoint tiles of every instance per direction and
+  // species group, the worklists of deferred midpoints and their counters
+  WorkItem* d_tiles = nullptr;
+  int off_tile[2][2] = {{0, 0}, {0, 0}}, n_tile[2][2] = {{0, 0}, {0, 0}};
+  unsigned long long* defer_list[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  uint32_t* defer_count = nullptr;  // [d * 2 + gN]
   Shape shape;
   int sms = 0;
   cudaGraphExec_t gexec = nullptr;
@@ -143,6 +149,12 @@ int enqueue_stage(hrm_batch* b, cudaStream_t s, int src, int dst, double a, doub
     for (int gN = 0; gN < 2; ++gN) {
       if (!b->n_face[d][gN]) continue;
       const WorkItem* it = b->d_items + b->off_face[d][gN];
+      if (fp32 && b->params.screen && b->d_tiles) {
+        batch_face32_tiles_d2(2 + gN, d, b->d_insts, b->d_tiles + b->off_tile[d][gN], b->n_tile[d][gN], src, b->dp,
+                              b->defer_list[d][gN], b->defer_count + d * 2 + gN, s);
+        k += 2;
+        continue;
+      }
       if (fp32)
         batch_face32_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, s);
       else
@@ -209,6 +221,10 @@ void hrm_batch_destroy(hrm_batch* b) {
   }
   cudaFree(b->d_insts);
   cudaFree(b->d_items);
+  cudaFree(b->d_tiles);
+  for (int d = 0; d < 2; ++d)
+    for (int gN = 0; gN < 2; ++gN) cudaFree(b->defer_list[d][gN]);
+  cudaFree(b->defer_count);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
 }
@@ -334,6 +350,32 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
                  "copy instances")))
     return bail(s);
   if ((s = build_items(b))) return bail(s);
+  // precision form: tiles of 128 midpoints and worklists (one entry per midpoint)
+  {
+    std::vector<WorkItem> tiles;
+    for (int d = 0; d < 2; ++d)
+      for (int gN = 0; gN < 2; ++gN) {
+        b->off_tile[d][gN] = (int)tiles.size();
+        size_t nf_all = 0;
+        for (int i = 0; i < b->ninst; ++i) {
+          if (b->N[i] != 2 + gN) continue;
+          const DevGrid& g = b->host[i].g;
+          const int64_t nf = (g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * g.n[2];
+          nf_all += (size_t)nf;
+          for (int64_t t = 0; t < nf; t += kBatchFace32Threads)
+            tiles.push_back({i, 0, t, std::min<int64_t>(t + kBatchFace32Threads, nf)});
+        }
+        b->n_tile[d][gN] = (int)tiles.size() - b->off_tile[d][gN];
+        if (nf_all && (s = bcuda(b, cudaMalloc(&b->defer_list[d][gN], sizeof(unsigned long long) * nf_all),
+                                 "alloc worklist")))
+          return bail(s);
+      }
+    if ((s = bcuda(b, cudaMalloc(&b->d_tiles, sizeof(WorkItem) * tiles.size()), "alloc tiles"))) return bail(s);
+    if ((s = bcuda(b, cudaMemcpy(b->d_tiles, tiles.data(), sizeof(WorkItem) * tiles.size(), cudaMemcpyHostToDevice),
+                   "copy tiles")))
+      return bail(s);
+    if ((s = bcuda(b, cudaMalloc(&b->defer_count, sizeof(uint32_t) * 4), "alloc worklist counters"))) return bail(s);
+  }
   *out = b;
   return HRM_OK;
 }
