@@ -154,6 +154,20 @@ __global__ void __launch_bounds__(kBatchFace32Threads, 5)
     list[base + __popc(m & ((1u << lane) - 1u))] = ((unsigned long long)w.inst << 40) | (unsigned long long)t;
 }
 
+// FP64 midpoints over the same 128-midpoint tiles (one block per tile; the
+// per-midpoint body is the single-context FP64 sweep's, bit for bit).
+template <int D, int DIR, int N>
+__global__ void __launch_bounds__(kBatchFace32Threads)
+    k_batch_face64_tiles(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ tiles, int src,
+                         DevParams pr) {
+  const WorkItem w = tiles[blockIdx.x];
+  const BatchInst& I = insts[w.inst];
+  const int64_t t = w.begin + threadIdx.x;
+  Nodes6 nd;
+  if (t < w.end && face_nodes<DIR>(I.g, t, nd))
+    face_body<double, N, D, DIR>(t, nd, pick(I, src), I.V, I.AUX, I.F[DIR], I.g, I.f, pr, I.st->lam[DIR]);
+}
+
 // The deferred midpoints of k_batch_face32_tiles with the full body, spread
 // lane-major over one-warp blocks (each is a long FP64 chain).
 template <int D, int DIR, int N>
@@ -205,6 +219,9 @@ void batch_face64_d2(int N, int dir, const BatchLaunch&, const BatchInst*, const
                      const DevParams&, cudaStream_t);
 void batch_face32_d2(int N, int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
                      const DevParams&, cudaStream_t);
+// The FP64 sweep over ntiles 128-midpoint tiles.
+void batch_face64_tiles_d2(int N, int dir, const BatchInst*, const WorkItem* tiles, int ntiles, int src,
+                           const DevParams&, cudaStream_t);
 // The screened sweep over ntiles 128-midpoint tiles and the fix-up of its
 // deferred midpoints (after a reset of *count).
 void batch_face32_tiles_d2(int N, int dir, const BatchInst*, const WorkItem* tiles, int ntiles, int src,

@@ -41,6 +41,21 @@ void batch_finalize(const BatchInst* insts, int ninst, int D, double cfl, cudaSt
   k_batch_finalize<<<(ninst + 127) / 128, 128, 0, s>>>(insts, ninst, D, cfl);
 }
 
+void batch_face64_tiles_d2(int N, int dir, const BatchInst* insts, const WorkItem* tiles, int ntiles, int src,
+                           const DevParams& p, cudaStream_t s) {
+  if (N == 2) {
+    if (dir == 0)
+      k_batch_face64_tiles<2, 0, 2><<<ntiles, kBatchFace32Threads, 0, s>>>(insts, tiles, src, p);
+    else
+      k_batch_face64_tiles<2, 1, 2><<<ntiles, kBatchFace32Threads, 0, s>>>(insts, tiles, src, p);
+  } else {
+    if (dir == 0)
+      k_batch_face64_tiles<2, 0, 3><<<ntiles, kBatchFace32Threads, 0, s>>>(insts, tiles, src, p);
+    else
+      k_batch_face64_tiles<2, 1, 3><<<ntiles, kBatchFace32Threads, 0, s>>>(insts, tiles, src, p);
+  }
+}
+
 void batch_face64_d2(int N, int dir, const BatchLaunch& L, const BatchInst* insts, const WorkItem* items, int nitems,
                      int src, const DevParams& p, cudaStream_t s) {
   if (N == 2) {

@@ -157,6 +157,9 @@ int enqueue_stage(hrm_batch* b, cudaStream_t s, int src, int dst, double a, doub
       }
       if (fp32)
         batch_face32_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, s);
+      else if (b->d_tiles)
+        batch_face64_tiles_d2(2 + gN, d, b->d_insts, b->d_tiles + b->off_tile[d][gN], b->n_tile[d][gN], src, b->dp,
+                              s);
       else
         batch_face64_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, s);
       ++k;
