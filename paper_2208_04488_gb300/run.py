@@ -15,7 +15,8 @@ import sys
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
-WORKLOADS = ("shock_bubble", "shock_tube", "interface_3d", "water_column", "advection_2d")
+WORKLOADS = ("shock_bubble", "shock_tube", "interface_3d", "water_column", "advection_2d", "mach100_jet",
+             "undex")
 
 
 def make_problem(name, nx, ny, nz):
@@ -30,6 +31,10 @@ def make_problem(name, nx, ny, nz):
         return P.shock_water_column_2d(nx, ny)
     if name == "advection_2d":
         return P.advection_2d_smooth(nx)
+    if name == "mach100_jet":
+        return P.mach100_jet_2d(nx, ny)
+    if name == "undex":
+        return P.undex_2d(nx, ny)
     raise ValueError(name)
 
 
