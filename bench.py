@@ -179,6 +179,32 @@ def cpu_baseline(problem, seconds_budget=25.0):
                       f"{threads} thread(s))"}
 
 
+def cpu_serial_rates():
+    """The serial oracle (one host core) on the benchmark configurations, per
+    cell-update: the 400-cell tube to its final time, five steps of the
+    1024x512 workload, two steps of a 64^3 box of the 3D configuration."""
+    import oracle
+    from paper_2208_04488_gb300 import problems
+    out = {}
+    for name, pr, nsteps in (("tube_400_full_run", problems.shock_tube_1d_baseline(400), None),
+                             ("shock_bubble_1024x512_5_steps", problems.shock_bubble_2d(1024, 512), 5),
+                             ("interface_3d_64^3_2_steps", problems.interface_3d(64), 2)):
+        f, g, W = oracle.setup(pr)
+        p = oracle.make_params()
+        t0 = time.perf_counter()
+        steps, t = 0, 0.0
+        while (nsteps is None and t < pr.t_end * (1 - 1e-14)) or (nsteps is not None and steps < nsteps):
+            dt, _ = oracle.dt(f, g, W, pr.cfl if pr.D < 3 else 0.4)
+            if nsteps is None:
+                dt = min(dt, pr.t_end - t)
+            W = oracle.step(f, p, g, W, dt, 1)
+            t += dt
+            steps += 1
+        el = time.perf_counter() - t0
+        out[name] = {"value": pr.ncells * steps / el, "unit": UNIT, "steps": steps, "seconds": round(el, 2)}
+    return {"cores": 1, "kind": "oracle (serial build)", "runs": out}
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle timed on the host cores (rank 0 only)."""
     ws, rank, _ = dist_env()
@@ -653,6 +679,7 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(pr)
+            line["cpu_baseline"]["serial"] = cpu_serial_rates()
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
