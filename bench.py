@@ -298,6 +298,34 @@ def measure_batched(torch, hrm, problems, stream, flush, args):
     return out
 
 
+def measure_tube(torch, hrm, problems, stream):
+    """The first configuration: the 400-cell water-air tube run to its final
+    time (CFL steps from the device, one graph launch per step). 16 KB of state:
+    the rate measures the step graph's latency, not the kernels' throughput."""
+    pr = problems.shock_tube_1d_baseline(400)
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, check=0), stream=stream)
+    s.step(0.0, 10)
+    s.set_primitive(pr.prim)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n = 0
+    e0.record(stream)
+    t = 0.0
+    while t < pr.t_end:
+        s.step(0.0, 50)
+        n += 50
+        t, _ = s.time()
+    e1.record(stream)
+    e1.synchronize()
+    el = e0.elapsed_time(e1) * 1e-3
+    out = {"workload": "1D water-air shock tube, 400 cells, CFL 0.4, to t = 2.4e-4 s", "steps": n, "t": t,
+           "value": pr.ncells * n / el, "unit": UNIT, "us_per_step": 1e6 * el / n,
+           "admissibility_after": s.admissibility(), "note": "latency-bound (one graph launch per step)"}
+    s.close()
+    return out
+
+
 def measure_3d(torch, hrm, problems, stream, flush, args):
     """The 3D configuration: the 256^3 perturbed liquid-gas interface hit by a
     Mach 1.5 shock (three species, periodic in y and z). Both forms advance the
@@ -562,6 +590,7 @@ def main():
     # batched form: the 64 seeded uneven instances, one persistent launch per phase
     batched = measure_batched(torch, hrm, problems, stream, flush, args) if rank == 0 and not args.no_batch else None
     three_d = measure_3d(torch, hrm, problems, stream, flush, args) if rank == 0 and not args.no_3d else None
+    tube = measure_tube(torch, hrm, problems, stream) if rank == 0 else None
     final = (final_time_errors(hrm, pr, det, stream, args.final_steps)
              if rank == 0 and args.final_steps > 0 else None)
 
@@ -657,6 +686,7 @@ def main():
             },
             "batched": batched,
             "interface_3d": three_d,
+            "tube_400": tube,
             "final_time": final,
             "learned": learned_block,
             "gpu_launches": int(launches),
