@@ -169,6 +169,7 @@ def test_full_size_one_step_sampled(hrm, orc):
     ref = orc.step(f, orc.make_params(), g, W, dto, 1)
     err = rel_l1(got, ref)
     assert err.max() <= 1e-12, err
+    np.testing.assert_array_equal(got, ref)  # the FP64 path reproduces the oracle bit for bit
     assert s.admissibility() == [0, 0, 0, 0]
 
 
@@ -189,6 +190,7 @@ def test_full_size_3d_one_step(hrm, orc):
     ref = orc.step(f, orc.make_params(), g, W, dto, 1, omp=True)
     err = rel_l1(got, ref)
     assert err.max() <= 1e-12, err
+    np.testing.assert_array_equal(got, ref)  # the FP64 path reproduces the oracle bit for bit
 
 
 def test_extreme_shock_tube_positivity_gpu(hrm, orc):
