@@ -216,6 +216,14 @@ hrm_status hrm_get(hrm_ctx* ctx, int32_t field, double* dst, int32_t on_device);
 /* Simulated time and number of steps taken since the last hrm_set. */
 hrm_status hrm_time(hrm_ctx* ctx, double* t, int64_t* steps);
 
+/* Out-of-range indices met by the kernels of ctx so far, in a library built
+ * with -DHRM_BOUNDS_CHECK (HRM_BOUNDS_CHECK=1 in the environment of the build),
+ * where every midpoint's node index and every cell's midpoint index is checked
+ * against its array and, when outside, counted and replaced by 0; -1 in a
+ * release build or on error. A debugging aid in place of a memory checker (the
+ * paper has no counterpart). Synchronises. */
+int64_t hrm_bounds_violations(hrm_ctx* ctx);
+
 /* Restore the simulated time and step count (checkpoint / restart: W from
  * hrm_get, then hrm_set and hrm_set_time; the steps that follow are those of an
  * uninterrupted run bit for bit, the step size depending only on the state).

@@ -13,13 +13,16 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
+# HRM_BOUNDS_CHECK=1: the bounds-check build (index checks in the kernels, see
+# hrm_bounds_violations) into its own folder
+BOUNDS_CHECK = os.environ.get("HRM_BOUNDS_CHECK", "0") == "1"
+OUT = os.path.join(HERE, "_build_check" if BOUNDS_CHECK else "_build")
 LIB = os.path.join(OUT, "libhrm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no FP contraction either (species constants are derived on the host)
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-         "--expt-relaxed-constexpr"]
+         "--expt-relaxed-constexpr"] + (["-DHRM_BOUNDS_CHECK"] if BOUNDS_CHECK else [])
 UNITS = {
     "hrm_cell.cu": ["--fmad=false"],
     "hrm_face64_d1.cu": ["--fmad=false"],

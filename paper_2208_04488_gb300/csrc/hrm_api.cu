@@ -529,6 +529,11 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
     c->defer_cap = 0;
   }
   if ((s = cuda_check(c, ctx_malloc(c, &c->st, sizeof(StepState)), "alloc step state"))) return bail(s);
+#ifdef HRM_BOUNDS_CHECK
+  if ((s = cuda_check(c, ctx_malloc(c, &c->dg.oob, sizeof(unsigned long long)), "alloc bounds counter")))
+    return bail(s);
+  cudaMemsetAsync(c->dg.oob, 0, sizeof(unsigned long long), c->stream);
+#endif
   cudaMemsetAsync(c->Wn, 0, plane * M, c->stream);
   reset_step_state(c);
   if ((s = cuda_check(c, cudaGetLastError(), "init"))) return bail(s);
@@ -549,6 +554,7 @@ void hrm_destroy(hrm_ctx* c) {
   ctx_free(c, c->R32);
   for (int d = 0; d < 3; ++d) ctx_free(c, c->F[d]);
   ctx_free(c, c->st);
+  ctx_free(c, c->dg.oob);
   ctx_free(c, c->blob);
   for (int d = 0; d < 3; ++d) ctx_free(c, c->gate[d]);
   for (int i = 0; i < 2 * kMaxProf; ++i)
@@ -800,6 +806,15 @@ hrm_status hrm_time(hrm_ctx* c, double* t, int64_t* steps) {
   if (t) *t = h.t;
   if (steps) *steps = h.steps;
   return HRM_OK;
+}
+
+int64_t hrm_bounds_violations(hrm_ctx* c) {
+  if (!c || !c->dg.oob) return -1;
+  unsigned long long n = 0;
+  if (cudaMemcpyAsync(&n, c->dg.oob, sizeof n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return -1;
+  return (int64_t)n;
 }
 
 hrm_status hrm_set_time(hrm_ctx* c, double t, int64_t steps) {

@@ -306,6 +306,7 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
     fill_fluid_f(I.f);
     I.N = N;
     b->N[i] = N;
+    I.g.oob = nullptr;
     I.g.ncells = 1;
     for (int d = 0; d < 3; ++d) {
       const int64_t n = d < 2 ? in.grid.n[d] : 1;

@@ -55,7 +55,21 @@ struct DevGrid {
   int64_t goff[6];  // first cell of side b's slice (bc[b] == 2), else 0
   double dx[3], inv_dx[3];
   int32_t bc[6];  // 0 transmissive, 1 periodic, 2 Dirichlet
+  unsigned long long* oob;  // bounds-check builds: count of out-of-range indices (else unused)
 };
+
+// Bounds-check builds (-DHRM_BOUNDS_CHECK): an index outside [0, n) is counted
+// in g.oob and replaced by 0 instead of being used; release builds use it as is.
+#ifdef HRM_BOUNDS_CHECK
+__device__ __forceinline__ int64_t hrm_checked_index(const DevGrid& g, int64_t i, int64_t n) {
+  if (i >= 0 && i < n) return i;
+  if (g.oob) atomicAdd(g.oob, 1ull);
+  return 0;
+}
+#define HRM_IDX(g, i, n) hrm_checked_index((g), (i), (n))
+#else
+#define HRM_IDX(g, i, n) (i)
+#endif
 
 struct DevParams {
   int32_t limiters, blend, scheme, qexp;

@@ -323,6 +323,7 @@ __device__ __forceinline__ bool face_nodes(const DevGrid& g, int64_t t, Nodes6& 
                        : (DIR == 1 ? (i2 * g.n[1] + q) * g.n[0] + i0 : (q * g.n[1] + i1) * g.n[0] + i0);
     if (jj < 0 && dlo) nd.c[j] = g.goff[2 * DIR] + tr;
     if (jj >= g.n[DIR] && dhi) nd.c[j] = g.goff[2 * DIR + 1] + tr;
+    nd.c[j] = HRM_IDX(g, nd.c[j], g.ncells);
   }
   return true;
 }
@@ -701,8 +702,8 @@ __device__ __forceinline__ void update_body(int64_t c, const double* Wn, const d
       const double* F = d == 0 ? F0 : (d == 1 ? F1 : F2);
       const int64_t f0 = g.n[0] + (d == 0), f1 = g.n[1] + (d == 1), f2 = g.n[2] + (d == 2);
       const int64_t nf = f0 * f1 * f2;
-      const int64_t fl = (i2 * f1 + i1) * f0 + i0;
-      const int64_t fr = fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1));
+      const int64_t fl = HRM_IDX(g, (i2 * f1 + i1) * f0 + i0, nf);
+      const int64_t fr = HRM_IDX(g, fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1)), nf);
       const double cd = -dt * g.inv_dx[d];
 #pragma unroll
       for (int m = 0; m < L::NC; ++m) acc[m] += cd * (F[m * nf + fr] - F[m * nf + fl]);
@@ -734,8 +735,8 @@ __device__ __forceinline__ void update_body(int64_t c, const double* Wn, const d
     const double* F = d == 0 ? F0 : (d == 1 ? F1 : F2);
     const int64_t f0 = g.n[0] + (d == 0), f1 = g.n[1] + (d == 1), f2 = g.n[2] + (d == 2);
     const int64_t nf = f0 * f1 * f2;
-    const int64_t fl = (i2 * f1 + i1) * f0 + i0;
-    const int64_t fr = fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1));
+    const int64_t fl = HRM_IDX(g, (i2 * f1 + i1) * f0 + i0, nf);
+    const int64_t fr = HRM_IDX(g, fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1)), nf);
     const double dx = g.dx[d], idx = g.inv_dx[d];
     // G^-_{i+1/2} - G^+_{i-1/2}: the alpha slots of the right face use alpha_i
     // (planes AL..), those of the left face alpha_i as its right neighbour (planes M..)

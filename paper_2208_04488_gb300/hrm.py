@@ -17,7 +17,8 @@ from typing import Optional
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libhrm.so")
+LIB_PATH = os.path.join(HERE, "_build_check" if os.environ.get("HRM_BOUNDS_CHECK", "0") == "1" else "_build",
+                        "libhrm.so")
 HEADER = os.path.join(HERE, "..", "include", "hrm.h")
 
 HRM_OK, HRM_E_INVAL, HRM_E_CUDA, HRM_E_ADMISSIBILITY, HRM_E_TIMEOUT, HRM_E_NOMEM = 0, -1, -2, -3, -4, -5
@@ -103,6 +104,8 @@ def lib():
     L.hrm_rhs.argtypes = [_VP, _DP, _VP]
     L.hrm_get.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
     L.hrm_time.argtypes = [_VP, _DP, P(ctypes.c_int64)]
+    L.hrm_bounds_violations.argtypes = [_VP]
+    L.hrm_bounds_violations.restype = ctypes.c_int64
     L.hrm_set_time.argtypes = [_VP, ctypes.c_double, ctypes.c_int64]
     L.hrm_admissibility.argtypes = [_VP, P(ctypes.c_int64)]
     L.hrm_kernel_launches.argtypes = [_VP]
@@ -346,6 +349,10 @@ class Solver:
         tau = (ctypes.c_double * 3)()
         self._check(lib().hrm_dt(self.h, cfl, ctypes.byref(dt), tau))
         return dt.value, np.array(tau[:self.D])
+
+    def bounds_violations(self) -> int:
+        """Out-of-range indices the kernels met (bounds-check builds; -1 otherwise)."""
+        return int(lib().hrm_bounds_violations(self.h))
 
     def set_time(self, t, steps):
         """Restore the simulated time and step count (checkpoint / restart)."""
