@@ -384,9 +384,11 @@ hrm_status hrm_batch_step(hrm_batch* b, int32_t nsteps);
 hrm_status hrm_batch_time(hrm_batch* b, int32_t i, double* t, int64_t* steps);
 /* Admissibility counters summed over the instances (as hrm_admissibility). */
 hrm_status hrm_batch_admissibility(hrm_batch* b, int64_t counts[4]);
-/* Launch shape of the persistent kernels: threads per block of the midpoint
- * sweeps (64, 128 or 256), faces per work item (>= face_threads), cells per work
- * item (>= 256), persistent blocks per SM (1..32). */
+/* Launch shape of the persistent per-cell kernels: cells per work item (>= 256)
+ * and persistent blocks per SM (1..32); threads per block (64, 128 or 256) and
+ * faces per work item (>= face_threads) apply to the precision form's sweep
+ * with screen = 0 only -- the other sweeps run one block per 128-midpoint tile
+ * of the instances. */
 hrm_status hrm_batch_set_launch(hrm_batch* b, int32_t face_threads, int32_t face_tile, int32_t cell_tile,
                                 int32_t blocks_per_sm);
 /* Autotuner: times steps_per_trial steps of the batch itself for each candidate
@@ -419,6 +421,8 @@ int64_t hrm_batch_total_cells(const hrm_batch* b);
  * share the array and race. The first call on a device looks up the array's
  * device address for that device (cudaGetSymbolAddress, once per device); make
  * that first call before any stream capture. */
+/* (The state's interior cells only: the prescribed states of a context's
+ * Dirichlet sides, which hrm_dt includes, are not part of W.) */
 hrm_status hrm_dt_noalloc(int32_t nspecies, int32_t ndim, const int64_t* n, const double* dx,
                           const double* gamma, const double* p_inf, const double* c_v,
                           const double* q, const double* W_device, double cfl,
