@@ -701,7 +701,8 @@ def main():
                 line["forms"][name] = form_summary(hrm, pr, r, Wa, args.steps, faces, faces_g, prec_peak,
                                                    "fp32 fma probe" if name.startswith("fp32") else "fp64 fma probe")
                 line["forms"][name]["description"] = (
-                    "learned smoothness gate (30-32-32-1 MLP, bf16 tensor-core inference) selects the linear "
+                    "learned smoothness gate (30-32-32-1 MLP, bf16 tcgen05 inference in a gate kernel before each sweep) "
+                    "selects the linear "
                     "WENO weights where it predicts every weight within 0.01 of d_k; limiters always on; "
                     f"fixed dt = {dt0:.6g} s, errors after {args.steps} steps against plain FP64")
     if dist is not None:

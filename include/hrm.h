@@ -185,7 +185,9 @@ hrm_status hrm_dt(hrm_ctx* ctx, double cfl, double* dt_out, double* tau_out);
  * (footnote of Sec. 5). The directional split sigma_d and lambda_d of the flux
  * limiter come from the step-start state. Launches one captured CUDA graph per
  * step. With params.check it synchronises and returns HRM_E_ADMISSIBILITY when
- * a cell left the admissible set (the state is kept for inspection). */
+ * a cell left the admissible set (the state is kept for inspection), or
+ * HRM_E_TIMEOUT when a bounded wait of the learned gate's tensor-core kernel
+ * ran out (its gate bytes are then unreliable). */
 hrm_status hrm_step(hrm_ctx* ctx, double dt, int32_t nsteps);
 
 /* Apply the thermal relaxation (Sec. 4.2) to the current state in place. */
@@ -270,7 +272,9 @@ int32_t hrm_profile_read(hrm_ctx* ctx, int32_t max, float* ms, int32_t* kind);
  * field use the linear weights d_k instead of the WENO-IS weights; the
  * characteristic projection (App. D), both positivity limiters (Sec. 4.3.2),
  * the Riemann solves, HCS and blending are unchanged. Inference: bfloat16
- * inputs and weights, FP32 accumulation on the tensor cores.
+ * inputs and weights, FP32 accumulation on the fifth-generation tensor cores
+ * (tcgen05: one 128-row tile of midpoints per CTA, accumulators in tensor
+ * memory), in a gate kernel that runs before each sweep in both forms.
  *
  * Training data come from states the method produces: the label of a midpoint
  * is 1 when every WENO-IS weight of every characteristic field and both biases
@@ -318,7 +322,8 @@ hrm_status hrm_detector_gradient(hrm_detector* det, int64_t first, int64_t n, fl
  * step); loss_per_step (host, nullable): the batch-mean loss before each step. */
 hrm_status hrm_detector_train(hrm_detector* det, int32_t steps, int32_t batch, double lr, float* loss_per_step);
 /* Logits of samples [first, first+n) into host z: bf16 = 1 the inference
- * (tensor-core) arithmetic, 0 the FP32 training arithmetic. */
+ * (tensor-core) arithmetic, 0 the FP32 training arithmetic. HRM_E_TIMEOUT (also
+ * from hrm_detector_evaluate): a bounded tensor-core wait ran out. */
 hrm_status hrm_detector_logits(hrm_detector* det, int64_t first, int64_t n, int32_t bf16, float* z);
 /* Over all samples at probability threshold: counts = {gated & smooth,
  * gated & not smooth, not gated & not smooth, not gated & smooth}; *loss = mean
@@ -328,8 +333,9 @@ hrm_status hrm_detector_evaluate(hrm_detector* det, double threshold, int32_t bf
 
 /* Copy det's current inference weights into ctx (a snapshot; det may be
  * destroyed afterwards) and allocate its gate buffers; then params.learned = 1
- * is accepted. The gate runs once per direction and stage, on the FP32 planes
- * that the primitive kernel then also writes in the FP64 form. */
+ * is accepted. The gate kernel runs once per direction and stage, before the
+ * sweep, on the FP32 planes (and their rounding residues) that the primitive
+ * kernel writes. */
 hrm_status hrm_set_detector(hrm_ctx* ctx, const hrm_detector* det);
 /* Fixed gate of direction dir (host, one byte per midpoint over the midpoint
  * grid of dir: n_d + 1 along d, x fastest; nonzero = gated), used at every

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -199,8 +200,8 @@ float* p32_target(hrm_ctx* c) {
 
 float* r32_target(hrm_ctx* c) { return c->params.learned == 1 ? c->R32 : nullptr; }
 
-// The gate of direction d's sweep: fixed bytes (learned 2, and learned 1 in the
-// FP64 form after the gate kernel), or the detector inside the FP32 sweep.
+// The gate of direction d's sweep: fixed bytes (learned 2: the caller's;
+// learned 1: written by the detector's gate kernel just before the sweep).
 // The precision form's sweep defers screen failures to a second kernel (one
 // without the FP64 fallbacks inline), except with the first-order scheme or the
 // screens off.
@@ -217,19 +218,12 @@ GateArgs gate_of(const hrm_ctx* c, int d) {
     g.defer_list = c->defer + (size_t)d * (size_t)(c->defer_cap + 1);
     g.defer_count = g.defer_list + c->defer_cap;
   }
-  if (c->params.learned == 1 && c->params.precision == HRM_FP32) {
-    g.blob = c->blob;
-    g.R32 = c->R32;
-    g.out = c->gate[d];
-    g.zthr = gate_logit_threshold(c);
-  } else if (c->params.learned) {
-    g.fixed = c->gate[d];
-  }
+  if (c->params.learned) g.fixed = c->gate[d];
   return g;
 }
 
-// The FP64 form runs the detector as its own kernel before each sweep.
-bool separate_gate(const hrm_ctx* c) { return c->params.learned == 1 && c->params.precision != HRM_FP32; }
+// With the learned detector, its gate kernel runs before each sweep (both forms).
+bool separate_gate(const hrm_ctx* c) { return c->params.learned == 1; }
 
 // CFL maxima of the prim kernels: 1 with the five-equation c, 2 with the
 // four-equation HRM c (params.cfl_sound).
@@ -255,7 +249,7 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
     if (separate_gate(c)) {
       traced(c, s, HRM_KERNEL_GATE, [&] {
         launch_gate(c->N, c->D, d, c->P32, c->R32, c->dg, c->blob, gate_logit_threshold(c), c->gate[d],
-                    c->gate_blocks, s);
+                    &c->st->waits, c->gate_blocks, s);
       });
       ++k;
     }
@@ -689,17 +683,22 @@ hrm_status hrm_step(hrm_ctx* c, double dt, int32_t nsteps) {
   if (!c->gexec && (s = build_graph(c))) return s;
   launch_set_dt(c->st, dt > 0.0 ? dt : 0.0, c->stream);
   ++c->launches;
-  if (c->params.check) cudaMemsetAsync(&c->st->counts, 0, sizeof(c->st->counts), c->stream);
+  // admissibility counters and the tensor-core wait counter that follows them
+  if (c->params.check) cudaMemsetAsync(&c->st->counts, 0, 5 * sizeof(unsigned long long), c->stream);
   for (int i = 0; i < nsteps; ++i) {
     if ((s = cuda_check(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch"))) return s;
     c->launches += c->graph_kernels;
   }
   if (!c->params.check) return last_launch(c, "step");
-  unsigned long long cnt[4];
+  unsigned long long cnt[5];
+  static_assert(offsetof(StepState, waits) == offsetof(StepState, counts) + 4 * sizeof(unsigned long long),
+                "wait counter follows the admissibility counters");
   if ((s = cuda_check(c, cudaMemcpyAsync(cnt, c->st->counts, sizeof cnt, cudaMemcpyDeviceToHost, c->stream),
                       "read counters")))
     return s;
   if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "step sync"))) return s;
+  if (cnt[4])
+    return fail(c, HRM_E_TIMEOUT, "%llu tensor-core waits of the learned gate ran out", cnt[4]);
   if (cnt[0] | cnt[1] | cnt[2] | cnt[3])
     return fail(c, HRM_E_ADMISSIBILITY,
                 "non-admissible cells: %llu negative partial density, %llu volume fraction out of [0,1], "
@@ -735,7 +734,7 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
   for (int d = 0; d < c->D; ++d) {
     if (separate_gate(c)) {
       launch_gate(c->N, c->D, d, c->P32, c->R32, c->dg, c->blob, gate_logit_threshold(c), c->gate[d],
-                  c->gate_blocks, c->stream);
+                  &c->st->waits, c->gate_blocks, c->stream);
       ++c->launches;
     }
     c->fk->face[d](c->params.precision, c->Wn, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st,

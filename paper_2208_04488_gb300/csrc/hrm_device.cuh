@@ -91,6 +91,7 @@ struct StepState {
   long long steps;
   unsigned long long tau_bits[3];  // running maxima (bit patterns of non-negative doubles)
   unsigned long long counts[4];    // admissibility counters
+  unsigned long long waits;        // bounded tensor-core waits that ran out (learned gate)
 };
 
 // ---------------------------------------------------------------- small helpers

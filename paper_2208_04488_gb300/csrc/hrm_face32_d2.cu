@@ -1,6 +1,6 @@
 // FP32-bulk per-midpoint kernels for D = 2, N = 2..3 species (the precision
 // form: interpolation, Riemann fluxes and HCS in FP32; limiter theta in FP64).
-#include "hrm_learned.cuh"
+#include "hrm_face32.cuh"
 #include "hrm_launch.h"
 
 namespace hrm {
@@ -13,18 +13,7 @@ void launch(const double* W, const double* V, const double* AUX, const float* P3
             const DevFluid& f, const DevParams& p, const StepState* st, const GateArgs& gate, cudaStream_t s) {
   if constexpr (DIR < kD) {
     const long long nf = (g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
-    if (gate.blob && gate.defer_list) {
-      cudaMemsetAsync(gate.defer_count, 0, sizeof(uint32_t), s);
-      k_face32_learned<N, kD, DIR, true><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(
-          W, P32, gate.R32, out, g, f, p, st, gate.blob, gate.zthr, gate.out, gate.defer_list, gate.defer_count);
-      const cudaStream_t sf = fix_stream(gate, s);
-      k_face32_fix<N, kD, DIR><<<kFixBlocks, kFixThreads, 0, sf>>>(W, P32, out, g, f, p, st, gate.out,
-                                                                    gate.defer_list, gate.defer_count);
-      fix_done(gate);
-    } else if (gate.blob) {
-      k_face32_learned<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(
-          W, P32, gate.R32, out, g, f, p, st, gate.blob, gate.zthr, gate.out);
-    } else if (gate.defer_list) {
+    if (gate.defer_list) {
       cudaMemsetAsync(gate.defer_count, 0, sizeof(uint32_t), s);
       k_face32_fast<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(
           W, P32, out, g, f, p, st, gate.fixed, gate.defer_list, gate.defer_count);

@@ -22,20 +22,11 @@ struct CellKernels {
   void (*admiss)(const double* W, const DevGrid&, const DevFluid&, StepState*, cudaStream_t);
 };
 
-namespace mlp {
-struct GateBlob;
-}
-
 // Smoothness gate of a midpoint sweep: `fixed` (nullable) one byte per
-// midpoint, nonzero = linear WENO weights there; or, for the precision form,
-// the detector itself (`blob`, logit threshold `zthr`, residue planes `R32`)
-// evaluated inside the sweep, which writes its decisions to `out`.
+// midpoint, nonzero = linear WENO weights there (a caller's fixed gate, or the
+// bytes the learned detector's gate kernel wrote before the sweep).
 struct GateArgs {
   const uint8_t* fixed = nullptr;
-  const mlp::GateBlob* blob = nullptr;
-  const float* R32 = nullptr;
-  uint8_t* out = nullptr;
-  float zthr = 0.f;
   // precision form with screens: the sweep defers midpoints whose screens fail
   // to a second kernel through this worklist (one entry per midpoint of the
   // direction) and counter; nullptr: one kernel with the fallbacks inline

@@ -33,42 +33,37 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 
 // ---------------------------------------------------------------- inference
 
+// The inference weights from the FP32 parameters: W1 and W2 transposed into
+// bf16 K-major operand tiles (tc::tile_offset), the rest in FP32.
 __global__ void k_pack_blob(const float* __restrict__ th, GateBlob* __restrict__ b) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < kHid * kRow) {
-    const int n = i / kRow, k = i % kRow;
-    b->w1t[n][k] = __float2bfloat16_rn(k < kIn ? th[oW1 + k * kHid + n] : 0.f);
-    b->w2t[n][k] = __float2bfloat16_rn(k < kHid ? th[oW2 + k * kHid + n] : 0.f);
+  if (i < kHid * 32) {
+    const int n = i / 32, k = i % 32;
+    const int e = tc::tile_offset(n, k) / 2;
+    b->w1[e] = __float2bfloat16_rn(k < kIn ? th[oW1 + k * kHid + n] : 0.f);
+    b->w2[e] = __float2bfloat16_rn(th[oW2 + k * kHid + n]);
   }
   if (i < kHid) {
     b->b1[i] = th[oB1 + i];
     b->b2[i] = th[oB2 + i];
     b->w3[i] = th[oW3 + i];
   }
-  if (i == 0) {
-    b->b3 = th[oB3];
-    b->pad[0] = b->pad[1] = b->pad[2] = 0.f;
-  }
-}
-
-__device__ __forceinline__ void load_blob(GateBlob& W, const GateBlob* __restrict__ blob) {
-  const uint4* src = reinterpret_cast<const uint4*>(blob);
-  uint4* dst = reinterpret_cast<uint4*>(&W);
-  for (int i = threadIdx.x; i < (int)(sizeof(GateBlob) / 16); i += blockDim.x) dst[i] = src[i];
+  if (i < 31) b->pad[i] = 0.f;
+  if (i == 0) b->b3 = th[oB3];
 }
 
 // Gate byte of every midpoint of direction DIR: 1 where the logit exceeds zthr.
-// Persistent blocks of 4 warps, each warp 32 consecutive midpoints per tile.
+// Persistent CTAs of 128 threads, one midpoint per thread and tile of 128.
 template <int N, int D, int DIR>
 __global__ void __launch_bounds__(kGateThreads)
     k_gate(const float* __restrict__ P32, const float* __restrict__ R32, DevGrid g, const GateBlob* __restrict__ blob,
-           float zthr, uint8_t* __restrict__ gate) {
-  __shared__ __align__(16) GateBlob W;
-  __shared__ __align__(16) __nv_bfloat16 X[kGateThreads / 32][32][kRow];
-  load_blob(W, blob);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+           float zthr, uint8_t* __restrict__ gate, unsigned long long* __restrict__ waits) {
+  static_assert(kGateThreads == tc::kRows, "one midpoint per MMA row");
+  __shared__ NetTile S;
+  const uint32_t tmem = net_begin(S, blob);
+  uint32_t phase = 0;
   const int64_t nf = face_total(g, DIR);
+  // the trip count is the same for every thread of the CTA (all take part in the MMAs)
   for (int64_t base = (int64_t)blockIdx.x * kGateThreads; base < nf; base += (int64_t)gridDim.x * kGateThreads) {
     const int64_t t = base + threadIdx.x;
     Nodes6 nd;
@@ -80,45 +75,40 @@ __global__ void __launch_bounds__(kGateThreads)
 #pragma unroll
       for (int k = 0; k < kIn; ++k) x[k] = 0.f;
     }
-    store_row(X[warp][lane], x);
-    __syncwarp();
-    const float z = warp_logit(W, X[warp], lane);
+    const float z = net_logit(S, x, tmem, phase, waits);
     if (ok) gate[t] = z > zthr ? 1 : 0;
-    __syncwarp();
   }
+  net_end(tmem);
 }
 
 template <int N, int D>
 void gate_nd(int dir, const float* P32, const float* R32, const DevGrid& g, const GateBlob* blob, float zthr,
-             uint8_t* gate, int max_blocks, cudaStream_t s) {
+             uint8_t* gate, unsigned long long* waits, int max_blocks, cudaStream_t s) {
   const int64_t nf = face_total(g, dir);
   int64_t nb = (nf + kGateThreads - 1) / kGateThreads;
   if (nb > max_blocks) nb = max_blocks;
   if (nb < 1) nb = 1;
-  if (dir == 0) k_gate<N, D, 0><<<(unsigned)nb, kGateThreads, 0, s>>>(P32, R32, g, blob, zthr, gate);
+  if (dir == 0) k_gate<N, D, 0><<<(unsigned)nb, kGateThreads, 0, s>>>(P32, R32, g, blob, zthr, gate, waits);
   if constexpr (D > 1)
-    if (dir == 1) k_gate<N, D, 1><<<(unsigned)nb, kGateThreads, 0, s>>>(P32, R32, g, blob, zthr, gate);
+    if (dir == 1) k_gate<N, D, 1><<<(unsigned)nb, kGateThreads, 0, s>>>(P32, R32, g, blob, zthr, gate, waits);
   if constexpr (D > 2)
-    if (dir == 2) k_gate<N, D, 2><<<(unsigned)nb, kGateThreads, 0, s>>>(P32, R32, g, blob, zthr, gate);
+    if (dir == 2) k_gate<N, D, 2><<<(unsigned)nb, kGateThreads, 0, s>>>(P32, R32, g, blob, zthr, gate, waits);
 }
 
 // Logits of dataset rows [first, first + n): bf16 tensor-core path (as the
 // gate) or the FP32 training arithmetic.
 __global__ void __launch_bounds__(kGateThreads)
     k_logits_bf16(const GateBlob* __restrict__ blob, const float* __restrict__ X, int64_t first, int64_t n,
-                  float* __restrict__ z) {
-  __shared__ __align__(16) GateBlob W;
-  __shared__ __align__(16) __nv_bfloat16 T[kGateThreads / 32][32][kRow];
-  load_blob(W, blob);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                  float* __restrict__ z, unsigned long long* __restrict__ waits) {
+  __shared__ NetTile S;
+  const uint32_t tmem = net_begin(S, blob);
   const int64_t i = (int64_t)blockIdx.x * kGateThreads + threadIdx.x;
   float x[kIn];
 #pragma unroll
   for (int k = 0; k < kIn; ++k) x[k] = i < n ? X[(first + i) * 32 + k] : 0.f;
-  store_row(T[warp][lane], x);
-  __syncwarp();
-  const float v = warp_logit(W, T[warp], lane);
+  uint32_t phase = 0;
+  const float v = net_logit(S, x, tmem, phase, waits);
+  net_end(tmem);
   if (i < n) z[i] = v;
 }
 
@@ -374,6 +364,7 @@ struct hrm_detector {
   int64_t hist_cap = 0;
   float* hist = nullptr;
   GateBlob* blob = nullptr;
+  unsigned long long* waits = nullptr;  // tensor-core waits of the inference that ran out
   int32_t* counts = nullptr;
   int64_t* offsets = nullptr;
   int64_t* total = nullptr;
@@ -402,8 +393,20 @@ hrm_status dcheck(hrm_detector* d, cudaError_t e, const char* what) {
   return dfail(d, e == cudaErrorMemoryAllocation ? HRM_E_NOMEM : HRM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Synchronise the detector's stream and report inference waits that ran out
+// (the counter is cleared once read).
+hrm_status waits_check(hrm_detector* d, const char* what) {
+  unsigned long long w = 0;
+  hrm_status s;
+  if ((s = dcheck(d, cudaMemcpyAsync(&w, d->waits, sizeof w, cudaMemcpyDeviceToHost, d->stream), what))) return s;
+  if ((s = dcheck(d, cudaStreamSynchronize(d->stream), what))) return s;
+  if (w == 0) return HRM_OK;
+  cudaMemsetAsync(d->waits, 0, sizeof w, d->stream);
+  return dfail(d, HRM_E_TIMEOUT, "%s: %llu tensor-core waits ran out", what, w);
+}
+
 hrm_status pack(hrm_detector* d) {
-  k_pack_blob<<<(kHid * kRow + 255) / 256, 256, 0, d->stream>>>(d->theta, d->blob);
+  k_pack_blob<<<(kHid * 32 + 255) / 256, 256, 0, d->stream>>>(d->theta, d->blob);
   return dcheck(d, cudaGetLastError(), "pack weights");
 }
 
@@ -452,15 +455,15 @@ namespace hrm {
 const GateBlob* detector_blob(const hrm_detector* d) { return d ? d->blob : nullptr; }
 
 void launch_gate(int N, int D, int dir, const float* P32, const float* R32, const DevGrid& g, const GateBlob* blob,
-                 float zthr, uint8_t* gate, int max_blocks, cudaStream_t s) {
+                 float zthr, uint8_t* gate, unsigned long long* waits, int max_blocks, cudaStream_t s) {
   const int key = N * 10 + D;
   switch (key) {
-    case 21: gate_nd<2, 1>(dir, P32, R32, g, blob, zthr, gate, max_blocks, s); break;
-    case 22: gate_nd<2, 2>(dir, P32, R32, g, blob, zthr, gate, max_blocks, s); break;
-    case 23: gate_nd<2, 3>(dir, P32, R32, g, blob, zthr, gate, max_blocks, s); break;
-    case 31: gate_nd<3, 1>(dir, P32, R32, g, blob, zthr, gate, max_blocks, s); break;
-    case 32: gate_nd<3, 2>(dir, P32, R32, g, blob, zthr, gate, max_blocks, s); break;
-    case 33: gate_nd<3, 3>(dir, P32, R32, g, blob, zthr, gate, max_blocks, s); break;
+    case 21: gate_nd<2, 1>(dir, P32, R32, g, blob, zthr, gate, waits, max_blocks, s); break;
+    case 22: gate_nd<2, 2>(dir, P32, R32, g, blob, zthr, gate, waits, max_blocks, s); break;
+    case 23: gate_nd<2, 3>(dir, P32, R32, g, blob, zthr, gate, waits, max_blocks, s); break;
+    case 31: gate_nd<3, 1>(dir, P32, R32, g, blob, zthr, gate, waits, max_blocks, s); break;
+    case 32: gate_nd<3, 2>(dir, P32, R32, g, blob, zthr, gate, waits, max_blocks, s); break;
+    case 33: gate_nd<3, 3>(dir, P32, R32, g, blob, zthr, gate, waits, max_blocks, s); break;
     default: break;
   }
 }
@@ -488,6 +491,8 @@ hrm_status hrm_detector_create(hrm_detector** out, int64_t capacity, uint64_t se
   if ((s = dcheck(d, cudaMalloc(&d->v, P), "alloc"))) return bail(s);
   if ((s = dcheck(d, cudaMalloc(&d->scratch, sizeof(float) * (kParams + 4)), "alloc"))) return bail(s);
   if ((s = dcheck(d, cudaMalloc(&d->blob, sizeof(GateBlob)), "alloc"))) return bail(s);
+  if ((s = dcheck(d, cudaMalloc(&d->waits, sizeof(unsigned long long)), "alloc"))) return bail(s);
+  if ((s = dcheck(d, cudaMemsetAsync(d->waits, 0, sizeof(unsigned long long), d->stream), "clear"))) return bail(s);
   if ((s = dcheck(d, cudaMalloc(&d->conf, sizeof(unsigned long long) * 4), "alloc"))) return bail(s);
   if ((s = dcheck(d, cudaMalloc(&d->conf_loss, sizeof(double)), "alloc"))) return bail(s);
   if (capacity > 0) {
@@ -517,6 +522,7 @@ void hrm_detector_destroy(hrm_detector* d) {
   cudaFree(d->v);
   cudaFree(d->scratch);
   cudaFree(d->blob);
+  cudaFree(d->waits);
   cudaFree(d->conf);
   cudaFree(d->conf_loss);
   cudaFree(d->X);
@@ -730,8 +736,8 @@ hrm_status hrm_detector_logits(hrm_detector* d, int64_t first, int64_t n, int32_
   if (!d || !z || first < 0 || n < 0 || first + n > d->size) return HRM_E_INVAL;
   if (n == 0) return HRM_OK;
   if (bf16)
-    k_logits_bf16<<<(unsigned)((n + kGateThreads - 1) / kGateThreads), kGateThreads, 0, d->stream>>>(d->blob, d->X,
-                                                                                                     first, n, d->z);
+    k_logits_bf16<<<(unsigned)((n + kGateThreads - 1) / kGateThreads), kGateThreads, 0, d->stream>>>(
+        d->blob, d->X, first, n, d->z, d->waits);
   else
     k_logits_fp32<<<(unsigned)((n + kTrainThreads - 1) / kTrainThreads), kTrainThreads, 0, d->stream>>>(
         d->theta, d->X, first, n, d->z);
@@ -739,7 +745,7 @@ hrm_status hrm_detector_logits(hrm_detector* d, int64_t first, int64_t n, int32_
   if ((s = dcheck(d, cudaGetLastError(), "logits"))) return s;
   if ((s = dcheck(d, cudaMemcpyAsync(z, d->z, sizeof(float) * n, cudaMemcpyDeviceToHost, d->stream), "read logits")))
     return s;
-  return dcheck(d, cudaStreamSynchronize(d->stream), "logits");
+  return waits_check(d, "logits");
 }
 
 hrm_status hrm_detector_evaluate(hrm_detector* d, double threshold, int32_t bf16, int64_t counts[4], double* loss) {
@@ -751,7 +757,7 @@ hrm_status hrm_detector_evaluate(hrm_detector* d, double threshold, int32_t bf16
   if (n > 0) {
     if (bf16)
       k_logits_bf16<<<(unsigned)((n + kGateThreads - 1) / kGateThreads), kGateThreads, 0, d->stream>>>(
-          d->blob, d->X, 0, n, d->z);
+          d->blob, d->X, 0, n, d->z, d->waits);
     else
       k_logits_fp32<<<(unsigned)((n + kTrainThreads - 1) / kTrainThreads), kTrainThreads, 0, d->stream>>>(
           d->theta, d->X, 0, n, d->z);
@@ -763,7 +769,7 @@ hrm_status hrm_detector_evaluate(hrm_detector* d, double threshold, int32_t bf16
   double l = 0.0;
   cudaMemcpyAsync(h, d->conf, sizeof h, cudaMemcpyDeviceToHost, d->stream);
   cudaMemcpyAsync(&l, d->conf_loss, sizeof l, cudaMemcpyDeviceToHost, d->stream);
-  if ((s = dcheck(d, cudaStreamSynchronize(d->stream), "evaluate"))) return s;
+  if ((s = waits_check(d, "evaluate"))) return s;
   if (counts)
     for (int k = 0; k < 4; ++k) counts[k] = (int64_t)h[k];
   if (loss) *loss = n > 0 ? l / (double)n : 0.0;

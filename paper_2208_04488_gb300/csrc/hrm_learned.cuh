@@ -10,12 +10,14 @@
 // the normalised shape (q_j - mean q) / (max q - min q + 1e-30) over the nodes
 // i-2 .. i+3, formed on the differences q_j - q_i (zero for an absent
 // alpha_2). Inference: bfloat16 inputs and weights on the tensor cores
-// (mma.sync m16n8k16, FP32 accumulation), one warp per 32 midpoints.
+// (tcgen05.mma, FP32 accumulation in tensor memory), one CTA per 128
+// midpoints (hrm_tc.cuh).
 #pragma once
 
 #include <cuda_bf16.h>
 
 #include "hrm_face32.cuh"
+#include "hrm_tc.cuh"
 
 namespace hrm {
 namespace mlp {
@@ -29,15 +31,18 @@ constexpr int oB2 = oW2 + kHid * kHid;
 constexpr int oW3 = oB2 + kHid;
 constexpr int oB3 = oW3 + kHid;
 constexpr int kParams = oB3 + 1;  // 2081
-constexpr int kRow = 40;          // bf16 row stride of the operand tiles (80 B: conflict-free fragments)
 
-// Inference weights in the layout the fragments read (prepared once on the
-// device from the FP32 parameters; copied into shared memory per block).
-struct __align__(16) GateBlob {
-  __nv_bfloat16 w1t[kHid][kRow];  // [hidden n][input k]; k >= kIn zero
-  __nv_bfloat16 w2t[kHid][kRow];  // [hidden n][hidden k]
+// Inference weights, prepared once on the device from the FP32 parameters and
+// copied into shared memory per CTA: W1 and W2 transposed ([hidden n][input k],
+// k >= kIn zero) as bf16 K-major operand tiles for the fifth-generation tensor
+// cores in the no-swizzle core-matrix arrangement (element (n, k) at byte
+// (n / 8) * 512 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2), then the FP32
+// biases, output weights and output bias.
+struct __align__(128) GateBlob {
+  __nv_bfloat16 w1[kHid * 32];
+  __nv_bfloat16 w2[kHid * 32];
   float b1[kHid], b2[kHid], w3[kHid];
-  float b3, pad[3];
+  float b3, pad[31];
 };
 static_assert(sizeof(GateBlob) % 16 == 0, "blob copies in 16-byte words");
 
@@ -46,85 +51,96 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+// Shared memory of one CTA evaluating the network for 128 stencils.
+struct __align__(128) NetTile {
+  __nv_bfloat16 a[tc::kRows * 32];  // A operand: the features, then the first hidden layer (8 KB)
+  GateBlob w;                       // B operands, biases, output weights
+  unsigned long long bar;           // MMA completion barrier
+  uint32_t tmem;                    // tensor-memory base address written by tcgen05.alloc
+};
 
-// D = A B + D, A 16x16 bf16 (row-major fragments), B 16x8 bf16 (column-major), FP32 accumulators.
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// Row r of the A operand from 32 FP32 values rounded to bf16: four 16-byte
+// stores (eight consecutive rows fill 128 contiguous bytes: no bank conflict).
+__device__ __forceinline__ void store_a_row(__nv_bfloat16* a, int r, const float (&x)[32]) {
+  char* base = reinterpret_cast<char*>(a) + tc::tile_offset(r, 0);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    uint4 v;
+    v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
+    v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
+    v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
+    v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
+    *reinterpret_cast<uint4*>(base + c * 128) = v;
+  }
 }
 
-// Logit of the stencil whose features lane r of the warp wrote into row r of X
-// (bf16, kRow stride; columns kIn..31 zero). All 32 lanes must call it.
-// Fragment layout of m16n8k16: lane = 4 g + q holds A rows g, g+8 at columns
-// 2q, 2q+1 (+8), B column g at rows 2q, 2q+1 (+8), C rows g, g+8 at columns
-// 2q, 2q+1. The C tiles of one layer are the A fragments of the next.
-__device__ __forceinline__ float warp_logit(const GateBlob& W, const __nv_bfloat16 (*X)[kRow], int lane) {
-  const int g = lane >> 2, q = lane & 3;
-  float zr[2][2];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    float c1[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) c1[nt][0] = c1[nt][1] = c1[nt][2] = c1[nt][3] = 0.f;
-#pragma unroll
-    for (int kt = 0; kt < 2; ++kt) {
-      uint32_t a[4];
-      a[0] = ld32(&X[16 * mt + g][16 * kt + 2 * q]);
-      a[1] = ld32(&X[16 * mt + g + 8][16 * kt + 2 * q]);
-      a[2] = ld32(&X[16 * mt + g][16 * kt + 2 * q + 8]);
-      a[3] = ld32(&X[16 * mt + g + 8][16 * kt + 2 * q + 8]);
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
-        mma_bf16(c1[nt], a, ld32(&W.w1t[8 * nt + g][16 * kt + 2 * q]), ld32(&W.w1t[8 * nt + g][16 * kt + 2 * q + 8]));
-    }
-    // bias + ReLU, rounded to bf16: the A fragments of the second layer
-    uint32_t h[2][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const int col = 8 * nt + 2 * q;
-      const float b0 = W.b1[col], b1 = W.b1[col + 1];
-      const uint32_t rg = pack_bf16(fmaxf(c1[nt][0] + b0, 0.f), fmaxf(c1[nt][1] + b1, 0.f));
-      const uint32_t rg8 = pack_bf16(fmaxf(c1[nt][2] + b0, 0.f), fmaxf(c1[nt][3] + b1, 0.f));
-      h[nt >> 1][(nt & 1) * 2 + 0] = rg;
-      h[nt >> 1][(nt & 1) * 2 + 1] = rg8;
-    }
-    float c2[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) c2[nt][0] = c2[nt][1] = c2[nt][2] = c2[nt][3] = 0.f;
-#pragma unroll
-    for (int kt = 0; kt < 2; ++kt)
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
-        mma_bf16(c2[nt], h[kt], ld32(&W.w2t[8 * nt + g][16 * kt + 2 * q]),
-                 ld32(&W.w2t[8 * nt + g][16 * kt + 2 * q + 8]));
-    // output layer in FP32: partial dot products over this lane's columns, then the quad
-    float sg = 0.f, sg8 = 0.f;
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const int col = 8 * nt + 2 * q;
-      const float b0 = W.b2[col], b1 = W.b2[col + 1], w0 = W.w3[col], w1 = W.w3[col + 1];
-      sg += fmaxf(c2[nt][0] + b0, 0.f) * w0 + fmaxf(c2[nt][1] + b1, 0.f) * w1;
-      sg8 += fmaxf(c2[nt][2] + b0, 0.f) * w0 + fmaxf(c2[nt][3] + b1, 0.f) * w1;
-    }
-    sg += __shfl_xor_sync(0xffffffffu, sg, 1);
-    sg += __shfl_xor_sync(0xffffffffu, sg, 2);
-    sg8 += __shfl_xor_sync(0xffffffffu, sg8, 1);
-    sg8 += __shfl_xor_sync(0xffffffffu, sg8, 2);
-    zr[mt][0] = sg + W.b3;
-    zr[mt][1] = sg8 + W.b3;
+// CTA set-up (all 128 threads): the weights into shared memory, the completion
+// barrier, 32 tensor-memory columns. Returns the tensor-memory base address.
+__device__ __forceinline__ uint32_t net_begin(NetTile& S, const GateBlob* __restrict__ blob) {
+  const uint4* src = reinterpret_cast<const uint4*>(blob);
+  uint4* dst = reinterpret_cast<uint4*>(&S.w);
+  for (int i = threadIdx.x; i < (int)(sizeof(GateBlob) / 16); i += blockDim.x) dst[i] = src[i];
+  if (threadIdx.x == 0) tc::bar_init(tc::smem_u32(&S.bar));
+  if (threadIdx.x < 32) tc::tmem_alloc(tc::smem_u32(&S.tmem));
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  return S.tmem;
+}
+
+// CTA tear-down (all 128 threads, after their last tensor-memory load): frees
+// the tensor memory.
+__device__ __forceinline__ void net_end(uint32_t tmem) {
+  tc::fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc::fence_after();
+    tc::tmem_free(tmem);
   }
-  // row r = 16 mt + 8 half + g' lives in lanes 4 g'
-  const int src = 4 * (lane & 7);
-  const float v00 = __shfl_sync(0xffffffffu, zr[0][0], src);
-  const float v01 = __shfl_sync(0xffffffffu, zr[0][1], src);
-  const float v10 = __shfl_sync(0xffffffffu, zr[1][0], src);
-  const float v11 = __shfl_sync(0xffffffffu, zr[1][1], src);
-  const int half = (lane >> 3) & 1;
-  return (lane >> 4) ? (half ? v11 : v10) : (half ? v01 : v00);
+}
+
+// One hidden layer: every thread has written its row of S.a; one thread issues
+// D = A B as two K = 16 slices and commits; all wait (bounded) and read their
+// row of D.
+__device__ __forceinline__ void net_layer(NetTile& S, const __nv_bfloat16* b, uint32_t tmem, uint32_t& phase,
+                                          unsigned long long* waits, float (&d)[32]) {
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  const uint32_t bar = tc::smem_u32(&S.bar);
+  if (threadIdx.x == 0) {
+    tc::fence_after();
+    const uint32_t a0 = tc::smem_u32(S.a), b0 = tc::smem_u32(b);
+#pragma unroll
+    for (uint32_t j = 0; j < 2; ++j)
+      tc::mma_bf16(tmem, tc::smem_desc(a0 + 256 * j, 128, 512), tc::smem_desc(b0 + 256 * j, 128, 512), j);
+    tc::mma_commit(bar);
+  }
+  if (!tc::bar_wait(bar, phase) && waits) atomicAdd(waits, 1ull);
+  phase ^= 1u;
+  tc::fence_after();
+  // warp w reads tensor-memory lanes 32 w .. 32 w + 31: its own rows
+  tc::tmem_ld32(tmem + ((uint32_t)(threadIdx.x & ~31) << 16), d);
+}
+
+// Logit of this thread's stencil from its features (all 128 threads call it).
+__device__ __forceinline__ float net_logit(NetTile& S, const float (&x)[kIn], uint32_t tmem, uint32_t& phase,
+                                           unsigned long long* waits) {
+  const int r = threadIdx.x;
+  float v[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = k < kIn ? x[k] : 0.f;
+  store_a_row(S.a, r, v);
+  float d[32];
+  net_layer(S, S.w.w1, tmem, phase, waits, d);
+#pragma unroll
+  for (int n = 0; n < kHid; ++n) v[n] = fmaxf(d[n] + S.w.b1[n], 0.f);
+  store_a_row(S.a, r, v);
+  net_layer(S, S.w.w2, tmem, phase, waits, d);
+  float z = 0.f;
+#pragma unroll
+  for (int n = 0; n < kHid; ++n) z += fmaxf(d[n] + S.w.b2[n], 0.f) * S.w.w3[n];
+  return z + S.w.b3;
 }
 
 // Normalise six differences (d[2] = 0) into x[0..5].
@@ -178,71 +194,6 @@ __device__ __forceinline__ void stencil_features(const Nodes6& nd, const float* 
   }
 }
 
-// Write one lane's features as a bf16 row (columns kIn..31 zero).
-__device__ __forceinline__ void store_row(__nv_bfloat16* row, const float (&x)[kIn]) {
-  uint32_t* r = reinterpret_cast<uint32_t*>(row);
-#pragma unroll
-  for (int k = 0; k < kIn / 2; ++k) r[k] = pack_bf16(x[2 * k], x[2 * k + 1]);
-  r[kIn / 2] = 0u;
-}
-
 }  // namespace mlp
-
-// Precision-form midpoint sweep with the detector evaluated in the same
-// kernel: each warp forms its 32 stencils' features, runs the network on the
-// tensor cores, records the decisions in gate_out and then computes its
-// midpoints with the linear weights where gated. All lanes take part in the
-// network even past the last midpoint. DEFER: as k_face32_fast, midpoints whose
-// screens fail go to `list` (k_face32_fix then reads their gate bytes).
-template <int N, int D, int DIR, bool DEFER = false>
-__global__ void __launch_bounds__(kFaceThreads, DEFER ? 4 : 3)
-    k_face32_learned(const double* __restrict__ W, const float* __restrict__ P32, const float* __restrict__ R32,
-                     double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr, const StepState* __restrict__ st,
-                     const mlp::GateBlob* __restrict__ blob, float zthr, uint8_t* __restrict__ gate_out,
-                     uint32_t* __restrict__ list = nullptr, uint32_t* __restrict__ count = nullptr) {
-  __shared__ __align__(16) mlp::GateBlob Wb;
-  __shared__ __align__(16) __nv_bfloat16 X[kFaceThreads / 32][32][mlp::kRow];
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(blob);
-    uint4* dst = reinterpret_cast<uint4*>(&Wb);
-    for (int i = threadIdx.x; i < (int)(sizeof(mlp::GateBlob) / 16); i += blockDim.x) dst[i] = src[i];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  Nodes6 nd;
-  const bool ok = face_nodes<DIR>(g, t, nd);
-  bool lin;
-  {
-    float x[mlp::kIn];
-    if (ok) {
-      mlp::stencil_features<N, D, DIR>(nd, P32, R32, g.ncells, x);
-    } else {
-#pragma unroll
-      for (int k = 0; k < mlp::kIn; ++k) x[k] = 0.f;
-    }
-    mlp::store_row(X[warp][lane], x);
-    __syncwarp();
-    lin = mlp::warp_logit(Wb, X[warp], lane) > zthr;
-  }
-  if constexpr (!DEFER) {
-    if (!ok) return;
-    gate_out[t] = lin ? 1 : 0;
-    face32_body<N, D, DIR>(t, nd, W, nullptr, nullptr, P32, out, g, f, pr, st->lam[DIR], lin);
-  } else {
-    bool need = false;
-    if (ok) {
-      gate_out[t] = lin ? 1 : 0;
-      need = !face32_body<N, D, DIR, true>(t, nd, W, nullptr, nullptr, P32, out, g, f, pr, st->lam[DIR], lin);
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, need);
-    if (m == 0u) return;
-    const int leader = __ffs(m) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (need) list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)t;
-  }
-}
 
 }  // namespace hrm

@@ -38,8 +38,10 @@ __host__ __device__ inline int64_t face_total(const DevGrid& g, int dir) {
 }
 
 // Gate bytes of every midpoint of direction dir from the FP32 planes.
+// waits: device counter of tensor-core waits that ran out.
 void launch_gate(int N, int D, int dir, const float* P32, const float* R32, const DevGrid& g,
-                 const mlp::GateBlob* blob, float zthr, uint8_t* gate, int max_blocks, cudaStream_t s);
+                 const mlp::GateBlob* blob, float zthr, uint8_t* gate, unsigned long long* waits, int max_blocks,
+                 cudaStream_t s);
 
 // Training-sample collection (hrm_learned_data.cu): pass 0 counts the kept
 // midpoints per block of kCollectThreads, pass 1 writes them at the offsets
