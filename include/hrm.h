@@ -350,6 +350,13 @@ hrm_status hrm_get_gate(hrm_ctx* ctx, int32_t dir, uint8_t* gate);
  * of the ALU roofline of the per-midpoint kernels. Synchronises `stream`. */
 hrm_status hrm_probe_fma_peak(int32_t precision, int32_t iters, void* stream, double* flops_per_s);
 
+/* Diagnostic, not a step of the method: one CTA of 128 threads waits, with the
+ * bounded wait of the tensor-core kernels (2^22 polls or 200 ms), on an
+ * mbarrier phase that nothing completes. Returns HRM_E_TIMEOUT with *expired =
+ * the number of waits that ran out (128); the device stays usable. Synchronises
+ * `stream`. */
+hrm_status hrm_probe_wait_timeout(void* stream, int64_t* expired);
+
 /* ---------------------------------------------------------------------------
  * Batched form: many independent 2D problems of uneven size (each its own grid
  * and species table, N = 2 or 3) advanced together. Each phase of a step (cell

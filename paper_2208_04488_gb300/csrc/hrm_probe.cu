@@ -1,9 +1,12 @@
-// FMA-pipe throughput probe: the denominator of the ALU roofline of the
-// per-midpoint kernels. Independent FMA chains per thread, enough warps to
-// fill every SM; flops = 2 x FMAs.
+// Diagnostics, not steps of the method. The FMA-pipe throughput probe: the
+// denominator of the ALU roofline of the per-midpoint kernels (independent FMA
+// chains per thread, enough warps to fill every SM; flops = 2 x FMAs). The
+// wait probe: the bounded mbarrier wait of the tensor-core kernels, made to run
+// out on a phase that nothing completes.
 #include <cuda_runtime.h>
 
 #include "../../include/hrm.h"
+#include "hrm_tc.cuh"
 
 namespace {
 
@@ -51,7 +54,33 @@ hrm_status run(int iters, cudaStream_t s, double* flops_per_s) {
   return HRM_OK;
 }
 
+// One CTA of 128 threads waits on phase 0 of a fresh mbarrier (count 1) that
+// nothing arrives at, with the library's bounded wait; each wait that runs out
+// is counted.
+__global__ void __launch_bounds__(128) k_wait_probe(unsigned long long* expired) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) hrm::tc::bar_init(hrm::tc::smem_u32(&bar));
+  __syncthreads();
+  if (!hrm::tc::bar_wait(hrm::tc::smem_u32(&bar), 0u)) atomicAdd(expired, 1ull);
+}
+
 }  // namespace
+
+extern "C" hrm_status hrm_probe_wait_timeout(void* stream, int64_t* expired) {
+  if (!expired) return HRM_E_INVAL;
+  *expired = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* d = nullptr;
+  if (cudaMallocAsync(&d, sizeof *d, s) != cudaSuccess) return HRM_E_NOMEM;
+  cudaMemsetAsync(d, 0, sizeof *d, s);
+  k_wait_probe<<<1, 128, 0, s>>>(d);
+  unsigned long long h = 0;
+  cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return HRM_E_CUDA;
+  *expired = (int64_t)h;
+  return h ? HRM_E_TIMEOUT : HRM_OK;
+}
 
 extern "C" hrm_status hrm_probe_fma_peak(int32_t precision, int32_t iters, void* stream, double* flops_per_s) {
   if (!flops_per_s || iters <= 0) return HRM_E_INVAL;

@@ -170,6 +170,8 @@ def lib():
         getattr(L, name).restype = ctypes.c_int
     L.hrm_probe_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, _VP, _DP]
     L.hrm_probe_fma_peak.restype = ctypes.c_int
+    L.hrm_probe_wait_timeout.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64)]
+    L.hrm_probe_wait_timeout.restype = ctypes.c_int
     for name in ("hrm_create", "hrm_set_params", "hrm_set", "hrm_set_primitive", "hrm_dt", "hrm_step",
                  "hrm_relax", "hrm_rhs", "hrm_get", "hrm_time", "hrm_admissibility"):
         getattr(L, name).restype = ctypes.c_int
@@ -184,6 +186,13 @@ def probe_fma_peak(precision=FP64, iters=4096, stream=None) -> float:
     if st != HRM_OK:
         raise HrmError(st, "fma probe failed")
     return v.value
+
+
+def probe_wait_timeout(stream=None):
+    """(status, expired) of the bounded-wait probe: HRM_E_TIMEOUT and 128."""
+    n = ctypes.c_int64()
+    st = lib().hrm_probe_wait_timeout(_VP(_stream_handle(stream)), ctypes.byref(n))
+    return st, n.value
 
 
 def params_default(**overrides) -> HrmParams:

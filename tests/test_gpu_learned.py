@@ -386,3 +386,16 @@ def test_ablation_shock_water_column(hrm, trained):
     assert rows["fp64+learned"][2] > 0.3
     # FP64: the gate removes the WENO-IS weights (the dominant FP64 work) where it is on
     assert rows["fp64+learned"][0] + rows["fp64+learned"][1] < f64_ms
+
+
+def test_bounded_tensor_core_wait_reports_timeout(hrm):
+    """The bounded mbarrier wait of the tensor-core kernels, on a phase that
+    nothing completes: every thread's wait runs out within its limit, the call
+    returns HRM_E_TIMEOUT, and the device stays usable."""
+    import time
+    t0 = time.time()
+    st, expired = hrm.probe_wait_timeout()
+    assert st == hrm.HRM_E_TIMEOUT
+    assert expired == 128
+    assert time.time() - t0 < 30.0
+    assert hrm.probe_fma_peak(hrm.FP32, iters=256) > 0.0
