@@ -242,14 +242,18 @@ def test_logits_match_oracle(hrm):
     np.testing.assert_array_equal(det.logits(17, 45, bf16=True), z16[17:62])
 
 
-def test_gate_kernel_matches_oracle(hrm, orc):
-    """Gate bytes of the gate kernel against the oracle's features through the
-    oracle's bfloat16 network, at a threshold that gates about half of the
-    midpoints: equal wherever the oracle's logit is not within rounding
-    distance of the threshold and the stencil's variation is not at rounding
-    level; and the learned RHS equals the RHS with those bytes as a fixed gate."""
+TC_GATE_PROBLEMS = [P.shock_tube_1d_baseline(64), P.shock_water_column_2d(48, 26), P.interface_3d(12)]
+
+
+@pytest.mark.parametrize("pr", TC_GATE_PROBLEMS, ids=[p.name for p in TC_GATE_PROBLEMS])
+def test_gate_kernel_matches_oracle(hrm, orc, pr):
+    """Gate bytes of the tensor-core gate kernel against the oracle's features
+    through the oracle's bfloat16 network, at a threshold that gates about half
+    of the non-uniform midpoints: equal wherever the oracle's logit is not
+    within rounding distance of the threshold and the stencil's variation is not
+    at rounding level; and the learned RHS equals the RHS with those bytes as a
+    fixed gate. 1D (two species, one partial 128-midpoint tile), 2D and 3D."""
     import torch
-    pr = P.shock_water_column_2d(48, 26)
     f, g, W = oracle_state(orc, pr, 2)
     theta, _, _ = _random_set(8)
     op = orc.make_params()
@@ -271,7 +275,7 @@ def test_gate_kernel_matches_oracle(hrm, orc):
     for precision in (hrm.FP64, hrm.FP32):
         s.set_params(hrm.params_default(cfl=pr.cfl, precision=precision, learned=hrm.LEARNED_GATE,
                                         learned_threshold=thr))
-        lam = [2e-4, 3e-4]
+        lam = [2e-4, 3e-4, 2.5e-4][:pr.D]
         R1 = torch.empty((pr.M, pr.ncells), dtype=torch.float64, device="cuda")
         s.rhs(lam, R1)
         gates = []
@@ -281,7 +285,9 @@ def test_gate_kernel_matches_oracle(hrm, orc):
             firm = (np.abs(z - zthr) > 0.05 * (1 + np.abs(z))) & ~fp32_sensitive(orc, pr, f, W, d)
             assert firm.mean() > 0.4
             np.testing.assert_array_equal(gg[firm], (z[firm] > zthr).astype(np.uint8))
-            assert 0.05 < gg.mean() < 0.95
+            rough = ~np.all(feats[d] == 0.0, axis=1)
+            if rough.sum() >= 20:
+                assert 0.05 < gg[rough].mean() < 0.95
             gates.append(gg)
         for d in range(pr.D):
             s.set_gate(d, gates[d])
