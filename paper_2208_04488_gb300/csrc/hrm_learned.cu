@@ -1,6 +1,8 @@
 // Learned smoothness detector: inference (the gate kernel, tensor cores) and
 // training (forward, back-propagation and Adam kernels in FP32) of the
 // 30 -> 32 -> 32 -> 1 perceptron, and the hrm_detector C ABI.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -81,18 +83,155 @@ __global__ void __launch_bounds__(kGateThreads)
   net_end(tmem);
 }
 
-template <int N, int D>
-void gate_nd(int dir, const float* P32, const float* R32, const DevGrid& g, const GateBlob* blob, float zthr,
-             uint8_t* gate, unsigned long long* waits, int max_blocks, cudaStream_t s) {
-  const int64_t nf = face_total(g, dir);
+// Shared-memory halo tile of the gate kernel's TMA path: for each of the ten
+// (quantity, value | residue) FP32 planes, the six nodes of 128 consecutive y
+// (or z) midpoints as 6 rows of 128 cells, or for 128 consecutive x midpoints
+// one row of 136 cells starting 4 cells left of the first (a 16-byte-aligned
+// start); slots 128-byte aligned.
+template <int DIR>
+struct Halo {
+  static constexpr int kW = DIR == 0 ? 136 : 128;  // box width (cells along x)
+  static constexpr int kH = DIR == 0 ? 1 : 6;      // box height (rows along the sweep direction)
+  static constexpr int kSlot = (kW * kH + 31) / 32 * 32;
+  static constexpr size_t kBytes = sizeof(float) * 2 * kQuant * kSlot;
+};
+
+// The gate kernel with its stencil inputs staged by TMA: per tile of 128
+// midpoints along x (one row of the midpoint grid), one thread loads the halo
+// boxes of the stencil planes from the 4-D tensor maps (x, y, z, plane) of P32
+// and R32 into shared memory, completing on an mbarrier (bounded wait).
+// Midpoints whose six nodes are all interior cells read their features from
+// the tile; the others (boundary mappings, Dirichlet slices) read the planes
+// directly. Both go through features_from, so the features are the same.
+template <int N, int D, int DIR>
+__global__ void __launch_bounds__(kGateThreads)
+    k_gate_tma(const __grid_constant__ CUtensorMap tP, const __grid_constant__ CUtensorMap tR,
+               const float* __restrict__ P32, const float* __restrict__ R32, DevGrid g,
+               const GateBlob* __restrict__ blob, float zthr, uint8_t* __restrict__ gate,
+               unsigned long long* __restrict__ waits) {
+  static_assert(kGateThreads == tc::kRows, "one midpoint per MMA row");
+  using H = Halo<DIR>;
+  extern __shared__ __align__(128) float halo_raw[];
+  // TMA destinations 128-byte aligned (the launch adds 128 bytes for this)
+  float* halo = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(halo_raw) + 127) & ~uintptr_t(127));
+  __shared__ NetTile S;
+  __shared__ unsigned long long tbar;
+  const uint32_t tmem = net_begin(S, blob);
+  if (threadIdx.x == 0) tc::bar_init(tc::smem_u32(&tbar));
+  __syncthreads();
+  uint32_t phase = 0, tphase = 0;
+  const int64_t n0 = g.n[0], nd_ = g.n[DIR];
+  const int64_t f0 = n0 + (DIR == 0), f1 = g.n[1] + (DIR == 1), f2 = g.n[2] + (DIR == 2);
+  const int64_t tpr = (f0 + kGateThreads - 1) / kGateThreads;  // tiles per row of the midpoint grid
+  const int64_t ntiles = tpr * f1 * f2;
+  const int i = threadIdx.x;
+  // the trip count is the same for every thread of the CTA (all take part in the MMAs)
+  for (int64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
+    const int64_t r = T / tpr, x0 = (T % tpr) * kGateThreads;
+    const int64_t i1 = r % f1, i2 = r / f1, i0 = x0 + i;
+    const bool ok = i0 < f0;
+    const int64_t t = r * f0 + i0;
+    const int64_t fp = DIR == 0 ? i0 : (DIR == 1 ? i1 : i2);
+    const bool inner = ok && fp >= 3 && fp <= nd_ - 3;  // nodes fp-3 .. fp+2 all interior
+    // some midpoint of the tile reads the halo (the same for the whole CTA)
+    const bool any = DIR == 0 ? (x0 <= n0 - 3 && x0 + kGateThreads - 1 >= 3) : (fp >= 3 && fp <= nd_ - 3);
+    if (any) {
+      const uint32_t bar = tc::smem_u32(&tbar);
+      if (threadIdx.x == 0) {
+        constexpr uint32_t kLoads = N < 3 ? 2 * kQuant - 2 : 2 * kQuant;
+        tc::bar_expect(bar, kLoads * (uint32_t)(sizeof(float) * H::kW * H::kH));
+        const int c0 = (int)(DIR == 0 ? x0 - 4 : x0);
+        const int c1 = (int)(DIR == 1 ? i1 - 3 : i1);
+        const int c2 = (int)(DIR == 2 ? i2 - 3 : i2);
+#pragma unroll
+        for (int q = 0; q < kQuant; ++q) {
+          if (q == 1 && N < 3) continue;
+          tc::tma_load_4d(tc::smem_u32(halo + (2 * q) * H::kSlot), &tP, c0, c1, c2, val_plane<N, D, DIR>(q), bar);
+          tc::tma_load_4d(tc::smem_u32(halo + (2 * q + 1) * H::kSlot), q < 2 ? &tP : &tR, c0, c1, c2,
+                          res_plane<N, D, DIR>(q), bar);
+        }
+      }
+      if (!tc::bar_wait(bar, tphase) && waits) atomicAdd(waits, 1ull);
+      tphase ^= 1u;
+    }
+    float x[kIn];
+    if (inner) {
+      auto at = [&](int sl, int j) -> float {
+        return DIR == 0 ? halo[sl * H::kSlot + i + 1 + j] : halo[sl * H::kSlot + j * H::kW + i];
+      };
+      features_from<N>([&](int q, int j) { return at(2 * q, j); }, [&](int q, int j) { return at(2 * q + 1, j); },
+                       x);
+    } else if (ok) {
+      Nodes6 nd;
+      face_nodes<DIR>(g, t, nd);
+      stencil_features<N, D, DIR>(nd, P32, R32, g.ncells, x);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kIn; ++k) x[k] = 0.f;
+    }
+    const float z = net_logit(S, x, tmem, phase, waits);
+    if (ok) gate[t] = z > zthr ? 1 : 0;
+  }
+  net_end(tmem);
+}
+
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point query).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// 4-D tensor map (x, y, z, plane) of `planes` FP32 planes of g.ncells cells
+// (interior cells x fastest, then any boundary slices), box of the halo of DIR.
+// False where TMA cannot address it: row or plane strides not multiples of 16
+// bytes, or the address not 16-byte aligned.
+template <int DIR>
+bool halo_map(CUtensorMap* m, const float* base, const DevGrid& g, int planes) {
+  const auto fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(base) & 15u) || g.n[0] % 4 != 0 || g.ncells % 4 != 0) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2], (cuuint64_t)planes};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.n[0] * 4, (cuuint64_t)(g.n[0] * g.n[1]) * 4, (cuuint64_t)g.ncells * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)Halo<DIR>::kW, DIR == 1 ? 6u : 1u, DIR == 2 ? 6u : 1u, 1u};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int N, int D, int DIR>
+void gate_dir(const float* P32, const float* R32, const DevGrid& g, const GateBlob* blob, float zthr, uint8_t* gate,
+              unsigned long long* waits, int max_blocks, cudaStream_t s) {
+  CUtensorMap tP, tR;
+  if (halo_map<DIR>(&tP, P32, g, P32Lay<N, D>::PLANES) && halo_map<DIR>(&tR, R32, g, D + 2)) {
+    const int64_t f0 = g.n[0] + (DIR == 0);
+    const int64_t nt = (f0 + kGateThreads - 1) / kGateThreads * (face_total(g, DIR) / f0);
+    const int64_t nb = nt < max_blocks ? (nt > 0 ? nt : 1) : max_blocks;
+    k_gate_tma<N, D, DIR><<<(unsigned)nb, kGateThreads, Halo<DIR>::kBytes + 128, s>>>(tP, tR, P32, R32, g, blob, zthr,
+                                                                                gate, waits);
+    return;
+  }
+  const int64_t nf = face_total(g, DIR);
   int64_t nb = (nf + kGateThreads - 1) / kGateThreads;
   if (nb > max_blocks) nb = max_blocks;
   if (nb < 1) nb = 1;
-  if (dir == 0) k_gate<N, D, 0><<<(unsigned)nb, kGateThreads, 0, s>>>(P32, R32, g, blob, zthr, gate, waits);
+  k_gate<N, D, DIR><<<(unsigned)nb, kGateThreads, 0, s>>>(P32, R32, g, blob, zthr, gate, waits);
+}
+
+template <int N, int D>
+void gate_nd(int dir, const float* P32, const float* R32, const DevGrid& g, const GateBlob* blob, float zthr,
+             uint8_t* gate, unsigned long long* waits, int max_blocks, cudaStream_t s) {
+  if (dir == 0) gate_dir<N, D, 0>(P32, R32, g, blob, zthr, gate, waits, max_blocks, s);
   if constexpr (D > 1)
-    if (dir == 1) k_gate<N, D, 1><<<(unsigned)nb, kGateThreads, 0, s>>>(P32, R32, g, blob, zthr, gate, waits);
+    if (dir == 1) gate_dir<N, D, 1>(P32, R32, g, blob, zthr, gate, waits, max_blocks, s);
   if constexpr (D > 2)
-    if (dir == 2) k_gate<N, D, 2><<<(unsigned)nb, kGateThreads, 0, s>>>(P32, R32, g, blob, zthr, gate, waits);
+    if (dir == 2) gate_dir<N, D, 2>(P32, R32, g, blob, zthr, gate, waits, max_blocks, s);
 }
 
 // Logits of dataset rows [first, first + n): bf16 tensor-core path (as the

@@ -158,40 +158,55 @@ __device__ __forceinline__ void normalise6(const float (&d)[6], float* x) {
   for (int j = 0; j < 6; ++j) x[j] = (d[j] - mean) * inv;
 }
 
-// The 30 normalised features of a midpoint from the FP32 planes of the
-// precision form: every difference q_j - q_i is formed from the FP32 value
-// and its rounding residue (the volume fractions' from P32, those of rho,
-// u_DIR and p from R32), so that variations far below FP32 resolution keep
-// their shape.
+// Stencil quantities of the features: 0, 1 = alpha_1, alpha_2 (the second
+// absent for N = 2), 2 = rho, 3 = u_DIR, 4 = p.
+constexpr int kQuant = 5;
+
+// The 30 normalised features from a node loader: val(s, j) and res(s, j) are
+// the FP32 value and its FP32 rounding residue of quantity s at stencil node j
+// (i-2 .. i+3). Every difference q_j - q_i is formed from both, so that
+// variations far below FP32 resolution keep their shape.
+template <int N, typename Val, typename Res>
+__device__ __forceinline__ void features_from(Val val, Res res, float (&x)[kIn]) {
+  float d[6];
+#pragma unroll
+  for (int s = 0; s < kQuant; ++s) {
+    if (s == 1 && N < 3) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) x[6 + j] = 0.f;
+      continue;
+    }
+    const float c2 = val(s, 2), r2 = res(s, 2);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) d[j] = (val(s, j) - c2) + (res(s, j) - r2);
+    normalise6(d, x + 6 * s);
+  }
+}
+
+// FP32 planes holding quantity s (values in P32; residues of the volume
+// fractions in P32, those of rho, u_DIR and p in R32).
+template <int N, int D, int DIR>
+__host__ __device__ constexpr int val_plane(int s) {
+  using L = Lay<N, D>;
+  using Q = P32Lay<N, D>;
+  return s < 2 ? L::AL + s : (s == 2 ? Q::RHO : (s == 3 ? L::MOM + DIR : L::EN));
+}
+template <int N, int D, int DIR>
+__host__ __device__ constexpr int res_plane(int s) {
+  using Q = P32Lay<N, D>;
+  return s < 2 ? Q::ALO + s : (s == 2 ? 0 : (s == 3 ? 1 + DIR : 1 + D));
+}
+
+// The features of a midpoint read straight from the FP32 planes at its six
+// nodes (nd: cell indices after the boundary mapping).
 template <int N, int D, int DIR>
 __device__ __forceinline__ void stencil_features(const Nodes6& nd, const float* __restrict__ P32,
                                                  const float* __restrict__ R32, int64_t nc, float (&x)[kIn]) {
-  using L = Lay<N, D>;
-  using Q = P32Lay<N, D>;
-  auto ld = [&](int plane, int j) -> float { return P32[(int64_t)plane * nc + nd.c[j]]; };
-  float d[6];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    if (k < N - 1) {
-      const float h2 = ld(L::AL + k, 2), l2 = ld(Q::ALO + k, 2);
-#pragma unroll
-      for (int j = 0; j < 6; ++j) d[j] = (ld(L::AL + k, j) - h2) + (ld(Q::ALO + k, j) - l2);
-      normalise6(d, x + 6 * k);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 6; ++j) x[6 * k + j] = 0.f;
-    }
-  }
-  const int planes[3] = {Q::RHO, L::MOM + DIR, L::EN};
-  const int rplanes[3] = {0, 1 + DIR, 1 + D};
-  auto lr = [&](int plane, int j) -> float { return R32[(int64_t)plane * nc + nd.c[j]]; };
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float c2 = ld(planes[a], 2), r2 = lr(rplanes[a], 2);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) d[j] = (ld(planes[a], j) - c2) + (lr(rplanes[a], j) - r2);
-    normalise6(d, x + 12 + 6 * a);
-  }
+  auto val = [&](int s, int j) -> float { return P32[(int64_t)val_plane<N, D, DIR>(s) * nc + nd.c[j]]; };
+  auto res = [&](int s, int j) -> float {
+    return (s < 2 ? P32 : R32)[(int64_t)res_plane<N, D, DIR>(s) * nc + nd.c[j]];
+  };
+  features_from<N>(val, res, x);
 }
 
 }  // namespace mlp

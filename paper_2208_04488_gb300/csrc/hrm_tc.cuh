@@ -1,7 +1,8 @@
 // Fifth-generation tensor-core primitives (tcgen05, sm_103a) as inline PTX:
 // tensor-memory allocation, the single-thread kind::f16 MMA with operands in
 // shared memory and the accumulator in tensor memory, its completion through an
-// mbarrier, the warp-wide tensor-memory load, and the fences between them.
+// mbarrier, the warp-wide tensor-memory load, and the fences between them; and
+// the TMA tiled tensor load that stages halo tiles in shared memory.
 //
 // Operand layout used here (A and B both K-major, no swizzle): core matrices of
 // 8 rows x 16 bytes, element (row r, column k) of a 32-column bf16 tile at byte
@@ -10,7 +11,7 @@
 // next 8-row group 512 bytes on (stride byte offset); the second K = 16 slice
 // starts 256 bytes in.
 //
-// Every wait on an MMA completion barrier is bounded (poll count and elapsed
+// Every wait on a completion barrier (MMA or TMA) is bounded (poll count and elapsed
 // %globaltimer); the caller counts a wait that ran out, and the host turns the
 // count into HRM_E_TIMEOUT.
 #pragma once
@@ -94,6 +95,24 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
     if ((it & 255u) == 255u && global_ns() - t0 > 200000000ull) break;
   }
   return false;
+}
+
+// Arm the barrier for one phase: one arrival (this thread) plus `bytes` of
+// asynchronous transfers that complete on it.
+__device__ __forceinline__ void bar_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// TMA tiled load of one box of a 4-D tensor map into shared memory, completing
+// on `bar`. The innermost coordinate times the element size must be a multiple
+// of 16 bytes; coordinates may lie outside the tensor (zero fill).
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(dst),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
 }
 
 // D[tmem] (+)= A B for one K = 16 slice, issued by one thread.
