@@ -242,17 +242,21 @@ def test_logits_match_oracle(hrm):
     np.testing.assert_array_equal(det.logits(17, 45, bf16=True), z16[17:62])
 
 
-TC_GATE_PROBLEMS = [P.shock_tube_1d_baseline(64), P.shock_water_column_2d(48, 26), P.interface_3d(12)]
+# 48 x 26 and the others: stencil planes staged by TMA (rows a multiple of 16
+# bytes); 50 x 26: the direct-load path of the same kernel
+TC_GATE_PROBLEMS = [P.shock_tube_1d_baseline(64), P.shock_water_column_2d(48, 26), P.shock_water_column_2d(50, 26),
+                    P.interface_3d(12)]
 
 
-@pytest.mark.parametrize("pr", TC_GATE_PROBLEMS, ids=[p.name for p in TC_GATE_PROBLEMS])
+@pytest.mark.parametrize("pr", TC_GATE_PROBLEMS, ids=[f"{p.name}_{p.n[0]}" for p in TC_GATE_PROBLEMS])
 def test_gate_kernel_matches_oracle(hrm, orc, pr):
     """Gate bytes of the tensor-core gate kernel against the oracle's features
     through the oracle's bfloat16 network, at a threshold that gates about half
     of the non-uniform midpoints: equal wherever the oracle's logit is not
     within rounding distance of the threshold and the stencil's variation is not
     at rounding level; and the learned RHS equals the RHS with those bytes as a
-    fixed gate. 1D (two species, one partial 128-midpoint tile), 2D and 3D."""
+    fixed gate. 1D (two species, one partial 128-midpoint tile), 2D and 3D;
+    stencil planes staged by TMA and read directly."""
     import torch
     f, g, W = oracle_state(orc, pr, 2)
     theta, _, _ = _random_set(8)
