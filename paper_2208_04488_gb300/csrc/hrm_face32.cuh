@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(kFaceThreads, 5)
     k_face32_fast(const double* __restrict__ W, const float* __restrict__ P32, double* __restrict__ out, DevGrid g,
                   DevFluid f, DevParams pr, const StepState* __restrict__ st, const uint8_t* __restrict__ gate,
                   uint32_t* __restrict__ list, uint32_t* __restrict__ count) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = patch_midpoint<DIR>(g);
   Nodes6 nd;
   bool need = false;
   if (face_nodes<DIR>(g, t, nd)) {
@@ -759,7 +759,7 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
     k_face32(const double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ AUX,
              const float* __restrict__ P32, double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr,
              const StepState* __restrict__ st, const uint8_t* __restrict__ gate) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = patch_midpoint<DIR>(g);
   Nodes6 nd;
   if (!face_nodes<DIR>(g, t, nd)) return;
   const bool lin = gate != nullptr && gate[t] != 0;

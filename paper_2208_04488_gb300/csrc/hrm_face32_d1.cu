@@ -12,17 +12,16 @@ template <int N, int DIR>
 void launch(const double* W, const double* V, const double* AUX, const float* P32, double* out, const DevGrid& g,
             const DevFluid& f, const DevParams& p, const StepState* st, const GateArgs& gate, cudaStream_t s) {
   if constexpr (DIR < kD) {
-    const long long nf = (g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
     if (gate.defer_list) {
       cudaMemsetAsync(gate.defer_count, 0, sizeof(uint32_t), s);
-      k_face32_fast<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(
+      k_face32_fast<N, kD, DIR><<<patch_grid(g, DIR), kFaceThreads, 0, s>>>(
           W, P32, out, g, f, p, st, gate.fixed, gate.defer_list, gate.defer_count);
       const cudaStream_t sf = fix_stream(gate, s);
       k_face32_fix<N, kD, DIR><<<kFixBlocks, kFixThreads, 0, sf>>>(W, P32, out, g, f, p, st, gate.fixed,
                                                                     gate.defer_list, gate.defer_count);
       fix_done(gate);
     } else {
-      k_face32<N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, P32, out, g, f, p, st,
+      k_face32<N, kD, DIR><<<patch_grid(g, DIR), kFaceThreads, 0, s>>>(W, V, AUX, P32, out, g, f, p, st,
                                                                                 gate.fixed);
     }
   }
