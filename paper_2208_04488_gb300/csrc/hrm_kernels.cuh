@@ -305,15 +305,13 @@ struct Nodes6 {
 };
 
 // Midpoint of this thread in a sweep launched over patch_grid blocks of
-// kFaceThreads: x midpoints linearly; y and z midpoints in patches of 32 along x
-// by 4 along the sweep direction (one warp per row), so that the four warps of
-// a block share 9 rows of nodes in L1 instead of reading 24. Past the end of a
-// row or of the grid: the midpoint count (no midpoint).
+// kFaceThreads: linear, or patched as above. Past the end of a row or of the
+// grid: the midpoint count (no midpoint).
 template <int DIR>
 __device__ __forceinline__ int64_t patch_midpoint(const DevGrid& g) {
   static_assert(kFaceThreads == 128, "four warps per patch");
   const int64_t f0 = g.n[0] + (DIR == 0), f1 = g.n[1] + (DIR == 1), f2 = g.n[2] + (DIR == 2);
-  if (DIR == 0) return (int64_t)blockIdx.x * kFaceThreads + threadIdx.x;
+  if (!patched(g, DIR)) return (int64_t)blockIdx.x * kFaceThreads + threadIdx.x;
   const int64_t nbx = (f0 + 31) / 32, b = blockIdx.x;
   const int64_t bx = b % nbx, rest = b / nbx;
   const int w = threadIdx.x >> 5;

@@ -112,10 +112,10 @@ void launch_set_dt(StepState* st, double dt, cudaStream_t s);
 inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 // Blocks of kFaceThreads covering the midpoints of direction dir in the layout
-// of patch_midpoint (x: linear; y, z: patches of 32 x 4).
+// of patch_midpoint (linear, or patches of 32 x 4 where patched(g, dir)).
 inline unsigned patch_grid(const DevGrid& g, int dir) {
   const long long f0 = g.n[0] + (dir == 0), f1 = g.n[1] + (dir == 1), f2 = g.n[2] + (dir == 2);
-  if (dir == 0) return grid_for(f0 * f1 * f2, 128);
+  if (!patched(g, dir)) return grid_for(f0 * f1 * f2, 128);
   const long long nbx = (f0 + 31) / 32;
   return (unsigned)(dir == 1 ? nbx * ((f1 + 3) / 4) * f2 : nbx * f1 * ((f2 + 3) / 4));
 }
