@@ -707,12 +707,13 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
 }
 
 // Screened sweep without the FP64 fallbacks (about a third of the full body's
-// code and at most 96 registers, so five blocks per SM, with a few spilled
-// values): midpoints whose screens fail are appended to `list`
-// (warp-aggregated; order not significant) for k_face32_fix. *count must be 0
-// at launch; list holds one entry per midpoint.
+// code and at most 80 registers, so six blocks per SM, with some values
+// spilled; seven or more blocks changed the compiler's FP32 contraction):
+// midpoints whose screens fail are appended to `list` (warp-aggregated; order
+// not significant) for k_face32_fix. *count must be 0 at launch; list holds one
+// entry per midpoint.
 template <int N, int D, int DIR>
-__global__ void __launch_bounds__(kFaceThreads, 5)
+__global__ void __launch_bounds__(kFaceThreads, 6)
     k_face32_fast(const double* __restrict__ W, const float* __restrict__ P32, double* __restrict__ out, DevGrid g,
                   DevFluid f, DevParams pr, const StepState* __restrict__ st, const uint8_t* __restrict__ gate,
                   uint32_t* __restrict__ list, uint32_t* __restrict__ count) {
