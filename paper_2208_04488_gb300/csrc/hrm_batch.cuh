@@ -132,8 +132,10 @@ __global__ void __launch_bounds__(kBatchFace32Threads, 3)
 // count), the body as k_face32_fast's: midpoints whose screens fail are
 // appended to `list` as (instance << 40 | midpoint) for k_batch_face32_fix.
 // *count must be 0 at launch; list holds one entry per midpoint of the tiles.
+// Six blocks per SM, as the single-context sweep (1.6 % shorter batched step
+// than five; the same results).
 template <int D, int DIR, int N>
-__global__ void __launch_bounds__(kBatchFace32Threads, 5)
+__global__ void __launch_bounds__(kBatchFace32Threads, 6)
     k_batch_face32_tiles(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ tiles, int src,
                          DevParams pr, unsigned long long* __restrict__ list, uint32_t* __restrict__ count) {
   const WorkItem w = tiles[blockIdx.x];
