@@ -243,9 +243,10 @@ def test_logits_match_oracle(hrm):
 
 
 # 48 x 26 and the others: stencil planes staged by TMA (rows a multiple of 16
-# bytes); 50 x 26: the direct-load path of the same kernel
+# bytes); 50 x 26: the direct-load path of the same kernel; the jet: two
+# species in 2D with a Dirichlet side (boundary slices after the interior cells)
 TC_GATE_PROBLEMS = [P.shock_tube_1d_baseline(64), P.shock_water_column_2d(48, 26), P.shock_water_column_2d(50, 26),
-                    P.interface_3d(12)]
+                    P.interface_3d(12), P.mach100_jet_2d(48, 24)]
 
 
 @pytest.mark.parametrize("pr", TC_GATE_PROBLEMS, ids=[f"{p.name}_{p.n[0]}" for p in TC_GATE_PROBLEMS])
