@@ -247,7 +247,10 @@ enum {
   HRM_KERNEL_FINALIZE = 1,  /* dt, sigma_d, lambda_d */
   HRM_KERNEL_FACE_X = 2,    /* per-midpoint sweep in x (HRM_KERNEL_FACE_X + d for direction d) */
   HRM_KERNEL_UPDATE = 5,    /* flux difference, RK combination, relaxation */
-  HRM_KERNEL_GATE = 6       /* learned smoothness gate of one direction */
+  HRM_KERNEL_GATE = 6,      /* learned smoothness gate of one direction */
+  HRM_KERNEL_SWEEPS = 7     /* all sweeps of one stage, fork to join: in 2D and 3D the directions run
+                               concurrently (direction d > 0 on its own stream of the step graph), so
+                               their own brackets overlap and this one times them together */
 };
 
 /* Tracing: with on != 0 the step graph is (re)captured with a CUDA event pair

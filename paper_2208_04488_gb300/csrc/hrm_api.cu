@@ -19,7 +19,7 @@
 using namespace hrm;
 
 namespace {
-constexpr int kMaxProf = 32;  // kernels of one step: at most 3 stages x (2 + 3 + 1) + 1
+constexpr int kMaxProf = 32;  // brackets of one step: 3 stages x (prim, 3 gates, sweeps, 3 sweeps, update) + finalize
 }
 
 struct hrm_ctx {
@@ -51,6 +51,9 @@ struct hrm_ctx {
   void* alloc_user = nullptr;
   cudaStream_t side[3] = {nullptr, nullptr, nullptr};  // deferred midpoints overlap the next sweep here
   cudaEvent_t ev_fast[3] = {}, ev_fix[3] = {};
+  // in 2D and 3D the sweeps of one stage run concurrently: direction d > 0 on par[d]
+  cudaStream_t par[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[3] = {};
   int gate_set[3] = {0, 0, 0};     // fixed gate provided (hrm_set_gate)
   int gate_blocks = 0;             // persistent blocks of the gate kernel
   const CellKernels* ck = nullptr;
@@ -172,19 +175,22 @@ void drop_graph(hrm_ctx* c) {
   c->graph_kernels = 0;
 }
 
-// Launch one kernel of the step; while profiling, bracket it with an event pair
-// (captured as event-record nodes) and remember its kind (HRM_KERNEL_*).
+// Launch one kernel of the step (or a group of launches, such as the
+// concurrent sweeps of a stage); while profiling, bracket it with an event pair
+// on s (captured as event-record nodes) and remember its kind (HRM_KERNEL_*).
+// The slot is taken before launching, so brackets may nest.
 template <typename F>
 void traced(hrm_ctx* c, cudaStream_t s, int kind, F&& launch) {
-  const bool on = c->profiling && c->nprof < kMaxProf;
+  const int i = c->nprof;
+  const bool on = c->profiling && i < kMaxProf;
   // external event-record nodes: recorded each time the graph runs
-  if (on) cudaEventRecordWithFlags(c->prof_ev[2 * c->nprof], s, cudaEventRecordExternal);
-  launch();
   if (on) {
-    cudaEventRecordWithFlags(c->prof_ev[2 * c->nprof + 1], s, cudaEventRecordExternal);
-    c->prof_kind[c->nprof] = kind;
     ++c->nprof;
+    c->prof_kind[i] = kind;
+    cudaEventRecordWithFlags(c->prof_ev[2 * i], s, cudaEventRecordExternal);
   }
+  launch();
+  if (on) cudaEventRecordWithFlags(c->prof_ev[2 * i + 1], s, cudaEventRecordExternal);
 }
 
 float gate_logit_threshold(const hrm_ctx* c) {
@@ -245,26 +251,42 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
     traced(c, s, HRM_KERNEL_FINALIZE, [&] { launch_finalize(c->st, c->dg, c->D, c->params.cfl, 0, s); });
     ++k;
   }
-  for (int d = 0; d < c->D; ++d) {
-    if (separate_gate(c)) {
+  if (separate_gate(c))
+    for (int d = 0; d < c->D; ++d) {
       traced(c, s, HRM_KERNEL_GATE, [&] {
         launch_gate(c->N, c->D, d, c->P32, c->R32, c->dg, c->blob, gate_logit_threshold(c), c->gate[d],
                     &c->st->waits, c->gate_blocks, s);
       });
       ++k;
     }
-    GateArgs ga = gate_of(c, d);
-    if (ga.defer_list) {  // the deferred midpoints run beside the next sweep
-      ga.side = c->side[d];
-      ga.ev_fast = c->ev_fast[d];
-      ga.ev_fix = c->ev_fix[d];
+  // the sweeps: independent (each reads the primitives and writes its own flux
+  // planes), so directions d > 0 run on their own streams beside direction 0
+  const bool fork = c->D > 1 && c->par[1];
+  traced(c, s, HRM_KERNEL_SWEEPS, [&] {
+    if (fork) {
+      cudaEventRecord(c->ev_fork, s);
+      for (int d = 1; d < c->D; ++d) cudaStreamWaitEvent(c->par[d], c->ev_fork, 0);
     }
-    traced(c, s, HRM_KERNEL_FACE_X + d, [&] {
-      c->fk->face[d](c->params.precision, Wsrc, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st, ga,
-                     s);
-    });
-    k += sweep_kernels(c);
-  }
+    for (int d = 0; d < c->D; ++d) {
+      const cudaStream_t sd = (fork && d > 0) ? c->par[d] : s;
+      GateArgs ga = gate_of(c, d);
+      if (ga.defer_list) {  // the deferred midpoints run beside the next sweep
+        ga.side = c->side[d];
+        ga.ev_fast = c->ev_fast[d];
+        ga.ev_fix = c->ev_fix[d];
+      }
+      traced(c, sd, HRM_KERNEL_FACE_X + d, [&] {
+        c->fk->face[d](c->params.precision, Wsrc, c->V, c->AUX, c->P32, c->F[d], c->dg, c->fl, c->dp, c->st, ga,
+                       sd);
+      });
+      k += sweep_kernels(c);
+    }
+    if (fork)
+      for (int d = 1; d < c->D; ++d) {
+        cudaEventRecord(c->ev_join[d], c->par[d]);
+        cudaStreamWaitEvent(s, c->ev_join[d], 0);
+      }
+  });
   if (defer_sweep(c))
     for (int d = 0; d < c->D; ++d) cudaStreamWaitEvent(s, c->ev_fix[d], 0);
   traced(c, s, HRM_KERNEL_UPDATE, [&] {
@@ -522,6 +544,15 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
   } else {
     c->defer_cap = 0;
   }
+  if (D > 1) {
+    if ((s = cuda_check(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event"))) return bail(s);
+    for (int d = 1; d < D; ++d) {
+      if ((s = cuda_check(c, cudaStreamCreateWithFlags(&c->par[d], cudaStreamNonBlocking), "sweep stream")))
+        return bail(s);
+      if ((s = cuda_check(c, cudaEventCreateWithFlags(&c->ev_join[d], cudaEventDisableTiming), "event")))
+        return bail(s);
+    }
+  }
   if ((s = cuda_check(c, ctx_malloc(c, &c->st, sizeof(StepState)), "alloc step state"))) return bail(s);
 #ifdef HRM_BOUNDS_CHECK
   if ((s = cuda_check(c, ctx_malloc(c, &c->dg.oob, sizeof(unsigned long long)), "alloc bounds counter")))
@@ -555,10 +586,13 @@ void hrm_destroy(hrm_ctx* c) {
     if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
   if (c->cap) cudaStreamDestroy(c->cap);
   for (int d = 0; d < 3; ++d) {
+    if (c->par[d]) cudaStreamDestroy(c->par[d]);
+    if (c->ev_join[d]) cudaEventDestroy(c->ev_join[d]);
     if (c->side[d]) cudaStreamDestroy(c->side[d]);
     if (c->ev_fast[d]) cudaEventDestroy(c->ev_fast[d]);
     if (c->ev_fix[d]) cudaEventDestroy(c->ev_fix[d]);
   }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
 }
 

@@ -29,7 +29,9 @@ RK3, EULER, RK2 = 0, 1, 2
 RELAX_OFF, RELAX_STAGE, RELAX_STEP = 0, 1, 2
 KERNEL_PRIM, KERNEL_FINALIZE, KERNEL_FACE_X, KERNEL_FACE_Y, KERNEL_FACE_Z, KERNEL_UPDATE = 0, 1, 2, 3, 4, 5
 KERNEL_GATE = 6
-KERNEL_NAMES = {0: "prim", 1: "finalize", 2: "face_x", 3: "face_y", 4: "face_z", 5: "update", 6: "gate"}
+KERNEL_NAMES = {0: "prim", 1: "finalize", 2: "face_x", 3: "face_y", 4: "face_z", 5: "update", 6: "gate",
+                7: "sweeps"}
+KERNEL_SWEEPS = 7
 LEARNED_OFF, LEARNED_GATE, LEARNED_FIXED = 0, 1, 2
 BC_TRANSMISSIVE, BC_PERIODIC, BC_DIRICHLET = 0, 1, 2
 DETECTOR_PARAMS, DETECTOR_INPUTS = 2081, 30

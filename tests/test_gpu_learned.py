@@ -357,7 +357,8 @@ def _run(hrm, pr, precision, learned_mode, det, dt, steps, threshold=0.5):
     s.set_profiling(True)
     s.step(dt, steps)
     prof = s.profile_read()
-    face_ms = sum(ms for k, ms in prof if k in (2, 3, 4))
+    # the sweeps of a stage run concurrently: their common bracket (kind 7)
+    face_ms = sum(ms for k, ms in prof if k == hrm.KERNEL_SWEEPS)
     gate_ms = sum(ms for k, ms in prof if k == 6)
     frac = None
     if learned_mode:
