@@ -36,6 +36,10 @@ struct hrm_batch {
   DevParams dp{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
+  // the sweeps of a stage (two directions x two species groups) run
+  // concurrently: all but the first on their own streams, fork/join events
+  cudaStream_t par[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[4] = {};
   std::vector<BatchInst> host;   // per-instance description (device pointers)
   std::vector<int> N;
   BatchInst* d_insts = nullptr;
@@ -145,24 +149,39 @@ int enqueue_stage(hrm_batch* b, cudaStream_t s, int src, int dst, double a, doub
     batch_finalize(b->d_insts, b->ninst, b->D, b->params.cfl, s);
     ++k;
   }
+  // the sweeps are independent (each reads the primitives and writes its own
+  // flux planes): sweep j > 0 on par[j], forked after the primitives and
+  // joined before the update
+  if (b->ev_fork) cudaEventRecord(b->ev_fork, s);
+  int j = 0;
   for (int d = 0; d < 2; ++d)
     for (int gN = 0; gN < 2; ++gN) {
       if (!b->n_face[d][gN]) continue;
+      cudaStream_t sj = s;
+      if (j > 0 && b->par[j]) {
+        sj = b->par[j];
+        cudaStreamWaitEvent(sj, b->ev_fork, 0);
+      }
+      ++j;
       const WorkItem* it = b->d_items + b->off_face[d][gN];
       if (fp32 && b->params.screen && b->d_tiles) {
         batch_face32_tiles_d2(2 + gN, d, b->d_insts, b->d_tiles + b->off_tile[d][gN], b->n_tile[d][gN], src, b->dp,
-                              b->defer_list[d][gN], b->defer_count + d * 2 + gN, s);
+                              b->defer_list[d][gN], b->defer_count + d * 2 + gN, sj);
         k += 2;
-        continue;
+      } else {
+        if (fp32)
+          batch_face32_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, sj);
+        else if (b->d_tiles)
+          batch_face64_tiles_d2(2 + gN, d, b->d_insts, b->d_tiles + b->off_tile[d][gN], b->n_tile[d][gN], src,
+                                b->dp, sj);
+        else
+          batch_face64_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, sj);
+        ++k;
       }
-      if (fp32)
-        batch_face32_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, s);
-      else if (b->d_tiles)
-        batch_face64_tiles_d2(2 + gN, d, b->d_insts, b->d_tiles + b->off_tile[d][gN], b->n_tile[d][gN], src, b->dp,
-                              s);
-      else
-        batch_face64_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, s);
-      ++k;
+      if (sj != s) {
+        cudaEventRecord(b->ev_join[j - 1], sj);
+        cudaStreamWaitEvent(s, b->ev_join[j - 1], 0);
+      }
     }
   for (int gN = 0; gN < 2; ++gN) {
     if (!b->n_cell[gN]) continue;
@@ -229,6 +248,11 @@ void hrm_batch_destroy(hrm_batch* b) {
     for (int gN = 0; gN < 2; ++gN) cudaFree(b->defer_list[d][gN]);
   cudaFree(b->defer_count);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int j = 0; j < 4; ++j) {
+    if (b->par[j]) cudaStreamDestroy(b->par[j]);
+    if (b->ev_join[j]) cudaEventDestroy(b->ev_join[j]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   delete b;
 }
 
@@ -273,6 +297,12 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
   b->stream = (cudaStream_t)cuda_stream;
   hrm_status s;
   if ((s = bcuda(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "stream create"))) return bail(s);
+  if ((s = bcuda(b, cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event create"))) return bail(s);
+  for (int j = 1; j < 4; ++j) {
+    if ((s = bcuda(b, cudaStreamCreateWithFlags(&b->par[j], cudaStreamNonBlocking), "stream create"))) return bail(s);
+    if ((s = bcuda(b, cudaEventCreateWithFlags(&b->ev_join[j], cudaEventDisableTiming), "event create")))
+      return bail(s);
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
