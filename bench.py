@@ -575,6 +575,41 @@ def main():
     torch.cuda.synchronize()
     adm = s.admissibility()
     W_fp64 = s.get(hrm.FIELD_W)
+    from paper_2208_04488_gb300.replicas import whole_job_rate
+    value, t_max = whole_job_rate(pr.ncells * args.steps, t_dev, dist, device="cuda")
+
+    # end-to-end through the public API with host buffers, on every rank: per
+    # step the state is uploaded from pinned host memory, advanced one step and
+    # read back.
+    Wh = torch.from_numpy(W_fp64.copy()).pin_memory()
+    Wout = torch.empty_like(Wh).pin_memory()
+    Wdev = torch.empty(Wh.shape, dtype=torch.float64, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    K_e2e = max(3, args.steps // 2)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K_e2e):
+        Wdev.copy_(Wh, non_blocking=True)
+        s.set(Wdev)
+        s.step(0.0, 1)
+        s.get(hrm.FIELD_W, out=Wdev)
+        Wout.copy_(Wdev, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    t_e2e = e0.elapsed_time(e1) * 1e-3
+    bytes_step = Wh.numel() * 8
+    e2e_value, _ = whole_job_rate(pr.ncells * K_e2e, t_e2e, dist, device="cuda")
+    s.set(W_fp64)  # back to the state after the timed steps (the fixed dt below comes from it)
+    if dist is not None:
+        # the other replicas are done: rank 0 measures the rest alone, with no
+        # collective after this point
+        dist.barrier()
+        if rank != 0:
+            dist.destroy_process_group()
+            return
     # precision form on the same workload: timed the same way, and its relative
     # L1 error against FP64 after the same number of equal fixed-size steps
     s32 = make(hrm.FP32)
@@ -610,28 +645,6 @@ def main():
     final = (final_time_errors(hrm, pr, det, stream, args.final_steps)
              if rank == 0 and args.final_steps > 0 else None)
 
-    from paper_2208_04488_gb300.replicas import whole_job_rate
-    value, t_max = whole_job_rate(pr.ncells * args.steps, t_dev, dist, device="cuda")
-
-    # end-to-end through the public API with host buffers: per step the state is
-    # uploaded from pinned host memory, advanced one step and read back.
-    Wh = torch.from_numpy(W_fp64.copy()).pin_memory()
-    Wout = torch.empty_like(Wh).pin_memory()
-    Wdev = torch.empty(Wh.shape, dtype=torch.float64, device="cuda")
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    K_e2e = max(3, args.steps // 2)
-    e0.record(stream)
-    for _ in range(K_e2e):
-        Wdev.copy_(Wh, non_blocking=True)
-        s.set(Wdev)
-        s.step(0.0, 1)
-        s.get(hrm.FIELD_W, out=Wdev)
-        Wout.copy_(Wdev, non_blocking=True)
-    e1.record(stream)
-    e1.synchronize()
-    t_e2e = e0.elapsed_time(e1) * 1e-3
-    bytes_step = Wh.numel() * 8
 
     line = None
     if rank == 0:
@@ -678,7 +691,7 @@ def main():
                          "launch_timing": "the x and y sweeps of a stage run concurrently: their common "
                                           "fork-to-join time, divided by the launches in it",
                          "kernel_time_share": share},
-            "e2e": {"value": pr.ncells * K_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
                     "d2h_bytes_per_step": bytes_step},
             "forms": {
                 "fp32": {"value": pr.ncells * args.steps / t32, "unit": UNIT,
@@ -718,8 +731,6 @@ def main():
                     "selects the linear "
                     "WENO weights where it predicts every weight within 0.01 of d_k; limiters always on; "
                     f"fixed dt = {dt0:.6g} s, errors after {args.steps} steps against plain FP64")
-    if dist is not None:
-        dist.barrier()
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(pr)
