@@ -254,12 +254,13 @@ enum {
 };
 
 /* Tracing: with on != 0 the step graph is (re)captured with a CUDA event pair
- * around every kernel. Costs one event-record node per kernel boundary. */
+ * around every kernel and one around the sweeps of each stage
+ * (HRM_KERNEL_SWEEPS). Costs one event-record node per bracket boundary. */
 hrm_status hrm_set_profiling(hrm_ctx* ctx, int32_t on);
 
 /* After a step with tracing on: synchronises the stream and writes, for the
- * kernels of the last step in launch order, their device time in ms and their
- * kind (HRM_KERNEL_*). Returns how many were written (at most max). */
+ * brackets of the last step in the order they open, their device time in ms
+ * and their kind (HRM_KERNEL_*). Returns how many were written (at most max). */
 int32_t hrm_profile_read(hrm_ctx* ctx, int32_t max, float* ms, int32_t* kind);
 
 /* ------------------------------------------------------------------------
