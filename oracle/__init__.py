@@ -110,6 +110,12 @@ def lib(count: bool = False):
         L.or_sensor.restype = ctypes.c_double
         L.or_face.argtypes = [P(Fluid), P(Params), ctypes.c_int, ctypes.c_double, _DP, _DP, _DP, _DP]
         L.or_rhs.argtypes = [P(Fluid), P(Params), P(Grid), _DP, _DP, _DP]
+        L.or_interp_limit.argtypes = [P(Fluid), P(Params), _DP, _DP]
+        L.or_interp_limit.restype = ctypes.c_int
+        L.or_flux_limit.argtypes = [P(Fluid), P(Params), ctypes.c_int, ctypes.c_double, _DP, _DP, _DP, _DP,
+                                    _DP, _DP]
+        L.or_flux_limit.restype = ctypes.c_int
+        L.or_char_matrices.argtypes = [P(Fluid), ctypes.c_int, _DP, _DP, _DP, _DP, _DP]
         _U8 = ctypes.POINTER(ctypes.c_uint8)
         L.or_rhs_gated.argtypes = [P(Fluid), P(Params), P(Grid), _DP, _DP, _U8, _U8, _U8, _DP]
         L.or_step_gated.argtypes = [P(Fluid), P(Params), P(Grid), _DP, ctypes.c_double, ctypes.c_int,
@@ -258,6 +264,39 @@ def face(f: Fluid, p: Params, dir_, lam, W6):
     t = diag[7 * M:]
     d.update(ut=t[0], uH=t[1], uhcs=t[2], sig=t[3], hsL=int(t[4]), hsR=int(t[5]), flux_flags=int(t[6]))
     return Gm, Gp, d
+
+
+def interp_limit(f: Fluid, p: Params, Vt, Wnode):
+    """The interpolation limiter on one biased midpoint state: returns the
+    limited primitive vector and whether the hard switch fired."""
+    V = np.array(Vt, dtype=np.float64)
+    Wn = np.ascontiguousarray(Wnode, dtype=np.float64)
+    hs = lib().or_interp_limit(ctypes.byref(f), ctypes.byref(p), _ptr(V), _ptr(Wn))
+    return V, hs
+
+
+def flux_limit(f: Fluid, p: Params, dir_, lam, Wi, Wj, Gm, Gp, Hm, Hp):
+    """The flux limiter of one midpoint: returns the limited G^-, G^+ and the
+    flag mask (1 first stage, 2 energy stage, 4 hard switch)."""
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    Wi, Wj, Hm, Hp = c(Wi), c(Wj), c(Hm), c(Hp)
+    gm, gp = np.array(Gm, dtype=np.float64), np.array(Gp, dtype=np.float64)
+    flags = lib().or_flux_limit(ctypes.byref(f), ctypes.byref(p), dir_, lam, _ptr(Wi), _ptr(Wj), _ptr(gm),
+                                _ptr(gp), _ptr(Hm), _ptr(Hp))
+    return gm, gp, flags
+
+
+def char_matrices(f: Fluid, dir_, Wi, Wj):
+    """R^{-1} and R of a midpoint as the oracle applies them, and the averaged
+    state (alpha_k rho_k, rho, c) they are built from."""
+    M = 2 * f.N + f.D
+    Wi = np.ascontiguousarray(Wi, dtype=np.float64)
+    Wj = np.ascontiguousarray(Wj, dtype=np.float64)
+    Rinv = np.zeros((M, M))
+    R = np.zeros((M, M))
+    avg = np.zeros(f.N + 2)
+    lib().or_char_matrices(ctypes.byref(f), dir_, _ptr(Wi), _ptr(Wj), _ptr(Rinv), _ptr(R), _ptr(avg))
+    return Rinv, R, avg
 
 
 def _gate_ptrs(g: Grid, gates):

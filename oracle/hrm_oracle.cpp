@@ -630,6 +630,26 @@ static void project_stencil(const FluidK& f, int dir, const Cell* nd, real U[6][
   }
 }
 
+// Back-projection V = R U of one characteristic vector (App. D): the columns of
+// R are built from the same averaged state as R^{-1} in project_stencil; its
+// entries alpha_k rho_k/(2c) and rho c/2.
+static void back_project(const FluidK& f, int dir, const real* arb, real rhob, real cb, const real* Ut,
+                         real* Vt) {
+  const int M = f.M, N = f.N, D = f.D;
+  const int un = sMOM(f, dir), sp = sE(f);
+  int tang[2], nt = 0;
+  for (int d = 0; d < D; ++d)
+    if (d != dir) tang[nt++] = d;
+  real ark_2c[OR_MAXN];
+  for (int k = 0; k < N; ++k) ark_2c[k] = arb[k] / (real(2.0) * cb);
+  const real rc_2 = rhob * cb / real(2.0);
+  for (int k = 0; k < N; ++k) Vt[k] = (-ark_2c[k]) * Ut[0] + Ut[1 + k] + ark_2c[k] * Ut[M - 1];
+  Vt[un] = real(0.5) * Ut[0] + real(0.5) * Ut[M - 1];
+  for (int t = 0; t < nt; ++t) Vt[sMOM(f, tang[t])] = Ut[N + 1 + t];
+  Vt[sp] = (-rc_2) * Ut[0] + rc_2 * Ut[M - 1];
+  for (int k = 0; k < N - 1; ++k) Vt[sAL(f, k)] = Ut[N + D + k];
+}
+
 // ---------------------------------------------------------------------------
 // One midpoint x_{i+1/2} in direction `dir` from the six node cells
 // nd[0..5] = i-2 .. i+3. Produces the quasi-conservative fluxes
@@ -639,7 +659,7 @@ static void project_stencil(const FluidK& f, int dir, const Cell* nd, real U[6][
 // linear weight d_k; everything else is unchanged.
 static void face_flux(const FluidK& f, const or_params* P, int dir, real lam, const Cell* nd,
                       real* Gm, real* Gp, FaceDiag* dg, int lin = 0) {
-  const int M = f.M, N = f.N, D = f.D;
+  const int M = f.M, N = f.N;
   const Cell& ci = nd[2];
   const Cell& cj = nd[3];
   const int un = sMOM(f, dir), sp = sE(f);
@@ -657,10 +677,6 @@ static void face_flux(const FluidK& f, const or_params* P, int dir, real lam, co
     real arb[OR_MAXN], rhob, cb;
     real U[6][OR_MAXM];
     project_stencil(f, dir, nd, U, arb, rhob, cb);
-    // tangential directions in increasing order
-    int tang[2], nt = 0;
-    for (int d = 0; d < D; ++d)
-      if (d != dir) tang[nt++] = d;
     // ---- WENO-IS left- and right-biased interpolation of each field (App. C)
     real UL[OR_MAXM], UR[OR_MAXM];
     for (int m = 0; m < M; ++m) {
@@ -675,20 +691,9 @@ static void face_flux(const FluidK& f, const or_params* P, int dir, real lam, co
       }
     }
     // ---- back to primitive variables: V~ = R U~ (App. D)
-    // entries of R: alpha_k rho_k/(2c) and rho c/2 of the averaged state
-    real ark_2c[OR_MAXN];
-    for (int k = 0; k < N; ++k) ark_2c[k] = arb[k] / (real(2.0) * cb);
-    const real rc_2 = rhob * cb / real(2.0);
     real VL[OR_MAXM], VR[OR_MAXM];
-    for (int side = 0; side < 2; ++side) {
-      const real* Ut = side == 0 ? UL : UR;
-      real* Vt = side == 0 ? VL : VR;
-      for (int k = 0; k < N; ++k) Vt[k] = (-ark_2c[k]) * Ut[0] + Ut[1 + k] + ark_2c[k] * Ut[M - 1];
-      Vt[un] = real(0.5) * Ut[0] + real(0.5) * Ut[M - 1];
-      for (int t = 0; t < nt; ++t) Vt[sMOM(f, tang[t])] = Ut[N + 1 + t];
-      Vt[sp] = (-rc_2) * Ut[0] + rc_2 * Ut[M - 1];
-      for (int k = 0; k < N - 1; ++k) Vt[sAL(f, k)] = Ut[N + D + k];
-    }
+    back_project(f, dir, arb, rhob, cb, UL, VL);
+    back_project(f, dir, arb, rhob, cb, UR, VR);
     if (dg)
       for (int m = 0; m < M; ++m) {
         dg->VL_weno[m] = VL[m];
@@ -1167,6 +1172,92 @@ void or_face(const or_fluid* fl, const or_params* P, int dir, double lam, const 
     t[5] = dg.hsR;
     t[6] = dg.flux_flags;
   }
+}
+
+// Interpolation limiter of one biased midpoint state (Sec. 4.3.2, the two
+// interpolation algorithms and the hard switch): Vt (M, in/out) is the
+// interpolated primitive vector, Wn the conservative vector of its node (W_i
+// for the left-biased, W_{i+1} for the right-biased state). Returns 1 when the
+// hard switch fired.
+int or_interp_limit(const or_fluid* fl, const or_params* P, double* Vt, const double* Wn) {
+  FluidK f = make_fluid(fl);
+  real w[OR_MAXM], v[OR_MAXM];
+  for (int m = 0; m < f.M; ++m) {
+    w[m] = Wn[m];
+    v[m] = Vt[m];
+  }
+  Cell c;
+  cell_from_W(f, w, c);
+  int hs = interp_limit(f, P, v, c);
+  for (int m = 0; m < f.M; ++m) Vt[m] = val(v[m]);
+  return hs;
+}
+
+// Flux limiter of one midpoint (Sec. 4.3.2, the two flux algorithms and the
+// hard switch): W_i, W_{i+1}, the high-order G^-_{i+1/2}, G^+_{i+1/2} (in/out)
+// and the first-order G^{HLLC,-}, G^{HLLC,+}; F_i and F_{i+1} (direction dir)
+// are evaluated from W_i and W_{i+1}. Returns flux_limit's flag mask.
+int or_flux_limit(const or_fluid* fl, const or_params* P, int dir, double lam, const double* Wi,
+                  const double* Wj, double* Gm, double* Gp, const double* Hm, const double* Hp) {
+  FluidK f = make_fluid(fl);
+  real wi[OR_MAXM], wj[OR_MAXM], gm[OR_MAXM], gp[OR_MAXM], hm[OR_MAXM], hp[OR_MAXM];
+  for (int m = 0; m < f.M; ++m) {
+    wi[m] = Wi[m];
+    wj[m] = Wj[m];
+    gm[m] = Gm[m];
+    gp[m] = Gp[m];
+    hm[m] = Hm[m];
+    hp[m] = Hp[m];
+  }
+  Cell ci, cj;
+  cell_from_W(f, wi, ci);
+  cell_from_W(f, wj, cj);
+  real Fi[OR_MAXM], Fj[OR_MAXM];
+  flux_F(f, dir, ci.V, ci.W, Fi);
+  flux_F(f, dir, cj.V, cj.W, Fj);
+  int flags = flux_limit(f, P, real(lam), ci.W, cj.W, Fi, Fj, gm, gp, hm, hp);
+  for (int m = 0; m < f.M; ++m) {
+    Gm[m] = val(gm[m]);
+    Gp[m] = val(gp[m]);
+  }
+  return flags;
+}
+
+// The projection matrices of a midpoint in direction dir from its nodes W_i,
+// W_{i+1} (App. D), as the face computation applies them: column m of Rinv is
+// the characteristic vector project_stencil makes of the unit primitive vector
+// e_m, column m of R the primitive vector back_project makes of the unit
+// characteristic vector e_m (both M*M, row-major). avg receives the averaged
+// state the matrices use: alpha_k rho_k (N), rho, c.
+void or_char_matrices(const or_fluid* fl, int dir, const double* Wi, const double* Wj, double* Rinv,
+                      double* R, double* avg) {
+  FluidK f = make_fluid(fl);
+  const int M = f.M;
+  real wi[OR_MAXM], wj[OR_MAXM];
+  for (int m = 0; m < M; ++m) {
+    wi[m] = Wi[m];
+    wj[m] = Wj[m];
+  }
+  Cell nd[6];
+  cell_from_W(f, wi, nd[2]);
+  cell_from_W(f, wj, nd[3]);
+  nd[0] = nd[1] = nd[4] = nd[5] = nd[2];
+  real arb[OR_MAXN], rhob = 0.0, cb = 0.0;
+  for (int col = 0; col < M; ++col) {
+    for (int m = 0; m < M; ++m) nd[0].V[m] = real(m == col ? 1.0 : 0.0);
+    real U[6][OR_MAXM];
+    project_stencil(f, dir, nd, U, arb, rhob, cb);
+    for (int m = 0; m < M; ++m) Rinv[m * M + col] = val(U[0][m]);
+  }
+  for (int col = 0; col < M; ++col) {
+    real e[OR_MAXM], v[OR_MAXM];
+    for (int m = 0; m < M; ++m) e[m] = real(m == col ? 1.0 : 0.0);
+    back_project(f, dir, arb, rhob, cb, e, v);
+    for (int m = 0; m < M; ++m) R[m * M + col] = val(v[m]);
+  }
+  for (int k = 0; k < f.N; ++k) avg[k] = val(arb[k]);
+  avg[f.N] = val(rhob);
+  avg[f.N + 1] = val(cb);
 }
 
 void or_rhs_gated(const or_fluid* fl, const or_params* P, const or_grid* g, const double* W,
