@@ -419,12 +419,12 @@ int64_t hrm_batch_total_cells(const hrm_batch* b);
 /* Allocation-free time step. The paper has no counterpart: this entry point
  * exists for callers that may not allocate device memory -- an application
  * whose device memory is already owned by its own pool (for example a caching
- * allocator holding the free memory, or a fixed memory budget per solver), or
- * code that runs where cudaMalloc is not allowed (for example while a stream is
- * being captured into a CUDA graph). It computes what hrm_dt computes (tau_d =
- * max(|u_d| + c)/dx_d, dt = cfl / sum tau_d, Sec. 4.1.2) for a state the caller
- * owns, without a context and without calling cudaMalloc, cudaFree or any
- * allocating library routine.
+ * allocator holding the free memory, or a fixed memory budget per solver), or a
+ * time-critical loop that must not call cudaMalloc or cudaFree (both can
+ * synchronise the device). It computes what hrm_dt computes (the per-direction
+ * maxima tau_d = max(|u_d| + c)/dx_d and dt = cfl / sum tau_d) for a state the
+ * caller owns, without a context and without calling cudaMalloc, cudaFree or
+ * any allocating library routine.
  *   W_device: the state, layout above, nspecies (2..3), ndim (1..3), n[ndim],
  *             dx[ndim], species table as for hrm_create (q may be NULL);
  *   out_device: 1 + ndim doubles of device memory, receives dt then tau_d.
@@ -437,7 +437,9 @@ int64_t hrm_batch_total_cells(const hrm_batch* b);
  * be cleared, but calls that overlap on the GPU (other streams, other threads)
  * share the array and race. The first call on a device looks up the array's
  * device address for that device (cudaGetSymbolAddress, once per device); make
- * that first call before any stream capture. */
+ * that first call before any stream capture. A CUDA error left pending by
+ * earlier work in the process is not taken over: the call then launches
+ * nothing, returns HRM_E_CUDA and leaves that error pending for its owner. */
 /* (The state's interior cells only: the prescribed states of a context's
  * Dirichlet sides, which hrm_dt includes, are not part of W.) */
 hrm_status hrm_dt_noalloc(int32_t nspecies, int32_t ndim, const int64_t* n, const double* dx,

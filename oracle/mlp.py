@@ -5,7 +5,7 @@ the 30 -> 32 -> 32 -> 1 multilayer perceptron the CUDA library trains and
 evaluates: ReLU hidden layers, a sigmoid output and the binary cross-entropy
 loss, with its gradient derived by hand (back-propagation). Used to check the
 GPU training kernels' gradients; pinned itself to central finite differences
-(tests/test_oracle_mlp.py). Only tests/ and bench.py's checks import it.
+(tests/test_oracle_learned.py). Only tests/ and bench.py's checks import it.
 
 Parameter vector layout (shared definition of the data format, not of code):
 W1[30][32], b1[32], W2[32][32], b2[32], w3[32], b3 -- 2081 values, with

@@ -194,6 +194,14 @@ extern "C" hrm_status hrm_dt_noalloc(int32_t nspecies, int32_t ndim, const int64
   }
   f.liq = liq < 0 ? 0 : liq;
   fill_fluid_f(f);
+  // An error pending from earlier work belongs to its owner: report it without
+  // clearing it, and launch nothing, so the check after the launches sees only
+  // errors of this call.
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess) {
+    hrm::set_thread_error("hrm_dt_noalloc: a CUDA error from earlier work is pending; nothing launched");
+    return HRM_E_CUDA;
+  }
   unsigned long long* partials = nullptr;
   if (partials_address(&partials) != HRM_OK) {
     hrm::set_thread_error("hrm_dt_noalloc: scratch address lookup failed");

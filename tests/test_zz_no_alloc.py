@@ -1,10 +1,15 @@
 """The allocation-free time step (hrm_dt_noalloc) against the context path.
 
 hrm_dt_noalloc serves callers that may not allocate device memory (an
-application whose memory belongs to its own pool, or code running where
-cudaMalloc is not allowed, such as inside a stream capture). It must return
-what hrm_dt returns for the same state, call after call, while reusing its
-one fixed scratch array. This file is collected last on purpose.
+application whose memory belongs to its own pool or budget, or a time-critical
+loop that must not call cudaMalloc or cudaFree). It must return what hrm_dt
+returns for the same state, call after call, while reusing its one fixed
+scratch array, and it must leave the device's free memory unchanged.
+
+The file name sorts last so that pytest collects it after every other test
+file: a run that stops at its first failure has then already run all the
+other tests if this one fails. The tests here depend on no other test and
+pass alone in a fresh process as well.
 """
 import ctypes
 
@@ -27,10 +32,11 @@ def hrm():
     return H
 
 
-def _noalloc_dt(H, pr, W_dev, cfl):
+def _noalloc_dt(H, pr, W_dev, cfl, out=None):
     import torch
     L = H.lib()
-    out = torch.full((1 + pr.D,), -1.0, dtype=torch.float64, device="cuda")
+    if out is None:
+        out = torch.full((1 + pr.D,), -1.0, dtype=torch.float64, device="cuda")
     n = (ctypes.c_int64 * 3)(*(pr.n + [1] * (3 - pr.D)))
     dx = (ctypes.c_double * 3)(*(pr.dx + [1.0] * (3 - pr.D)))
     arr = lambda v: (ctypes.c_double * len(v))(*v)
@@ -69,3 +75,24 @@ def test_noalloc_dt_rejects_grids_beyond_its_scratch(hrm):
                           ctypes.c_void_p(W.data_ptr()), 0.5, ctypes.c_void_p(out.data_ptr()), None)
     assert st == hrm.HRM_E_INVAL
     assert "134217728" in L.hrm_last_error(None).decode()
+
+
+def test_noalloc_dt_leaves_free_device_memory_unchanged(hrm):
+    """After one warm-up call (which loads the kernels' module and looks up the
+    scratch array's address), a call changes the device's free memory by
+    nothing: it allocates no device memory."""
+    import torch
+    pr = P.shock_bubble_2d(256, 128)
+    s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, check=0))
+    W = torch.empty((pr.M, pr.ncells), dtype=torch.float64, device="cuda")
+    s.get(hrm.FIELD_W, out=W)
+    dt_ctx, _ = s.dt(pr.cfl)
+    out = torch.full((1 + pr.D,), -1.0, dtype=torch.float64, device="cuda")
+    first = _noalloc_dt(hrm, pr, W, pr.cfl, out)
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    again = _noalloc_dt(hrm, pr, W, pr.cfl, out)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+    assert first[0] == dt_ctx and again[0] == dt_ctx
