@@ -236,17 +236,22 @@ bool separate_gate(const hrm_ctx* c) { return c->params.learned == 1; }
 int tau_mode(const hrm_ctx* c) { return c->params.cfl_sound ? 2 : 1; }
 
 // One RK stage: primitives of Wsrc, (gates,) midpoint fluxes, update into Wout.
+// Precision form: the update of every stage but the last also writes the next
+// stage's FP32 planes (k_update32p, fuse_next), and a stage whose planes were
+// written so (prim_done) skips its primitive kernel.
 int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, double a, double b, int relax,
-                  int count, bool first) {
+                  int count, bool first, bool prim_done = false, bool fuse_next = false) {
   int k = 0;
   float* p32 = p32_target(c);
-  traced(c, s, HRM_KERNEL_PRIM, [&] {
-    if (c->params.precision == HRM_FP32)
-      launch_prim32(c->N, c->D, Wsrc, c->P32, r32_target(c), c->dg, c->fl, c->st, first ? tau_mode(c) : 0, s);
-    else
-      c->ck->prim(Wsrc, c->V, c->AUX, p32, r32_target(c), c->dg, c->fl, c->st, first ? tau_mode(c) : 0, s);
-  });
-  ++k;
+  if (!prim_done) {
+    traced(c, s, HRM_KERNEL_PRIM, [&] {
+      if (c->params.precision == HRM_FP32)
+        launch_prim32(c->N, c->D, Wsrc, c->P32, r32_target(c), c->dg, c->fl, c->st, first ? tau_mode(c) : 0, s);
+      else
+        c->ck->prim(Wsrc, c->V, c->AUX, p32, r32_target(c), c->dg, c->fl, c->st, first ? tau_mode(c) : 0, s);
+    });
+    ++k;
+  }
   if (first) {
     traced(c, s, HRM_KERNEL_FINALIZE, [&] { launch_finalize(c->st, c->dg, c->D, c->params.cfl, 0, s); });
     ++k;
@@ -290,8 +295,12 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
   if (defer_sweep(c))
     for (int d = 0; d < c->D; ++d) cudaStreamWaitEvent(s, c->ev_fix[d], 0);
   traced(c, s, HRM_KERNEL_UPDATE, [&] {
-    c->fk->update(0, c->params.precision == HRM_FP32, c->Wn, Wsrc, Wout, c->F[0], c->F[1], c->F[2], c->dg, c->fl,
-                  c->st, a, b, relax, count, s);
+    if (fuse_next)
+      launch_update32p(c->N, c->D, c->Wn, Wsrc, Wout, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, a, b, relax,
+                       count, c->P32, r32_target(c), s);
+    else
+      c->fk->update(0, c->params.precision == HRM_FP32, c->Wn, Wsrc, Wout, c->F[0], c->F[1], c->F[2], c->dg,
+                    c->fl, c->st, a, b, relax, count, s);
   });
   ++k;
   return k;
@@ -303,19 +312,20 @@ int enqueue_step(hrm_ctx* c, cudaStream_t s) {
   const int rs = c->params.relax_mode == HRM_RELAX_STAGE;
   const int rf = c->params.relax_mode != HRM_RELAX_OFF;
   const int ck = c->params.check ? 1 : 0;  // admissibility counters, read only with params.check
+  const bool fp32 = c->params.precision == HRM_FP32;  // stages after the first take fused planes
   int k = 0;
   switch (c->params.integrator) {
     case HRM_EULER:
       k += enqueue_stage(c, s, c->Wn, c->Wn, 0.0, 1.0, rf, ck, true);
       break;
     case HRM_RK2:
-      k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true);
-      k += enqueue_stage(c, s, c->Ws, c->Wn, 0.5, 0.5, rf, ck, false);
+      k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true, false, fp32);
+      k += enqueue_stage(c, s, c->Ws, c->Wn, 0.5, 0.5, rf, ck, false, fp32);
       break;
     default:
-      k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true);
-      k += enqueue_stage(c, s, c->Ws, c->Ws, 0.75, 0.25, rs, 0, false);
-      k += enqueue_stage(c, s, c->Ws, c->Wn, 1.0 / 3.0, 2.0 / 3.0, rf, ck, false);
+      k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true, false, fp32);
+      k += enqueue_stage(c, s, c->Ws, c->Ws, 0.75, 0.25, rs, 0, false, fp32, fp32);
+      k += enqueue_stage(c, s, c->Ws, c->Wn, 1.0 / 3.0, 2.0 / 3.0, rf, ck, false, fp32);
       break;
   }
   return k;

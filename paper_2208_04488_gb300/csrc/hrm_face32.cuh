@@ -298,43 +298,37 @@ __device__ __forceinline__ bool flux_screen32(const float* __restrict__ P32, int
 // division by S, the velocities, rho c^2 and c in FP32 (their FP32 values are
 // all the midpoint kernel uses). The node states the FP64 limiters need where a
 // screen fails are evaluated from W there.
+// FP32 planes of one cell from its FP64 state w (M values), its density rho
+// and R_e = rho (rho e~) = rho (E - sum alpha_k rho_k q_k) - |rho u|^2 / 2. The
+// pressure numerator rho (rho e~ - P) = R_e - rho P is formed in FP64 (it
+// cancels where p_inf ~ 1e9 Pa meets the ambient pressure), then
+// p = (R_e - rho P) / (rho S) in FP32; no FP64 division. Returns u_d and c.
 template <int N, int D>
-__device__ __forceinline__ void prim32_body(int64_t c, const double* __restrict__ W, float* __restrict__ P32,
-                                            float* __restrict__ R32, const DevGrid& g, const DevFluid& f,
-                                            double* s, bool c4 = false) {
+__device__ __forceinline__ void prim32_store(int64_t c, const double* w, double rho, double Re,
+                                             float* __restrict__ P32, float* __restrict__ R32, int64_t nc,
+                                             const DevFluid& f, float* u, float& cs) {
   using L = Lay<N, D>;
   using Q = P32Lay<N, D>;
-  constexpr int M = L::M;
-  const int64_t nc = g.ncells;
-  double w[M];
-#pragma unroll
-  for (int m = 0; m < M; ++m) w[m] = W[m * nc + c];
-  double rho = 0.0, sa = 0.0;
-#pragma unroll
-  for (int k = 0; k < N; ++k) rho += w[k];
+  double sa = 0.0;
 #pragma unroll
   for (int k = 0; k < N - 1; ++k) sa += w[L::AL + k];
   const double aN = 1.0 - sa;
-  double S = 0.0, P = 0.0, rq = 0.0;
+  double S = 0.0, P = 0.0;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const double a = k < N - 1 ? w[L::AL + k] : aN;
     S += a * f.inv_gm1[k];
     P += a * f.gpinf_gm1[k];
-    rq += w[k] * f.q[k];
   }
-  const double irho = 1.0 / rho;
-  double m2 = 0.0;
-#pragma unroll
-  for (int d = 0; d < D; ++d) m2 += w[L::MOM + d] * w[L::MOM + d];
-  const double num = ((w[L::EN] - rq) - 0.5 * m2 * irho) - P;  // rho e~ - P
-  const float rho32 = (float)rho, irho32 = (float)irho;
+  const double num = Re - rho * P;  // rho (rho e~ - P)
+  const double rS = rho * S;
+  const float rho32 = (float)rho, irho32 = 1.f / rho32;
   const float S32 = (float)S, iS = 1.f / S32;
-  const float p = (float)num * iS;
+  const float irS = 1.f / (float)rS;
+  const float p = (float)num * irS;
   const float Pf = (float)P;
   const float rc2 = (1.f + iS) * p + Pf * iS;
-  const float cs = sqrtf(rc2 * irho32);
-  float u[D];
+  cs = sqrtf(rc2 * irho32);
 #pragma unroll
   for (int d = 0; d < D; ++d) u[d] = (float)w[L::MOM + d] * irho32;
 #pragma unroll
@@ -357,12 +351,45 @@ __device__ __forceinline__ void prim32_body(int64_t c, const double* __restrict_
     P32[(Q::ALO + k) * nc + c] = (float)(a - (double)ah);
   }
   if (R32) {
-    // residues: rho exactly; u_d and p from the FP64 remainders of m - u rho and num - p S
+    // residues: rho exactly; u_d and p from the FP64 remainders of m - u rho and
+    // (R_e - rho P) - p rho S
     R32[c] = (float)(rho - (double)rho32);
 #pragma unroll
     for (int d = 0; d < D; ++d) R32[(1 + d) * nc + c] = (float)(w[L::MOM + d] - (double)u[d] * rho) * irho32;
-    R32[(1 + D) * nc + c] = (float)(num - (double)p * S) * iS;
+    R32[(1 + D) * nc + c] = (float)(num - (double)p * rS) * irS;
   }
+}
+
+// rho and R_e of a conservative state (the inputs of prim32_store).
+template <int N, int D>
+__device__ __forceinline__ void rho_Re(const double* w, const DevFluid& f, double& rho, double& Re) {
+  using L = Lay<N, D>;
+  double rq = 0.0, m2 = 0.0;
+  rho = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    rho += w[k];
+    rq += w[k] * f.q[k];
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) m2 += w[L::MOM + d] * w[L::MOM + d];
+  Re = rho * (w[L::EN] - rq) - 0.5 * m2;
+}
+
+template <int N, int D>
+__device__ __forceinline__ void prim32_body(int64_t c, const double* __restrict__ W, float* __restrict__ P32,
+                                            float* __restrict__ R32, const DevGrid& g, const DevFluid& f,
+                                            double* s, bool c4 = false) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+  const int64_t nc = g.ncells;
+  double w[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) w[m] = W[m * nc + c];
+  double rho, Re;
+  rho_Re<N, D>(w, f, rho, Re);
+  float u[D], cs;
+  prim32_store<N, D>(c, w, rho, Re, P32, R32, nc, f, u, cs);
   if (c4) {
     const double cw = c4_of_cell<N, D>(w, f);  // four-equation HRM c (FP64)
 #pragma unroll
@@ -384,6 +411,40 @@ __global__ void __launch_bounds__(kCellThreads)
   if (c < g.ncells) prim32_body<N, D>(c, W, P32, R32, g, f, s, tau == 2);
   if (!tau) return;
   block_tau_max<D>(s, st->tau_bits);
+}
+
+// Precision-form update of one RK stage with the next stage's primitives fused
+// in: the flux difference and SSP-RK combination (fast_combine), the
+// relaxation (relax_fast), the admissibility count, the store of W_out, then
+// the FP32 planes of W_out (prim32_store) that the next stage's sweeps read --
+// in place of a separate k_prim32 pass over W_out. Interior cells only: the
+// planes of Dirichlet slices keep what the stage's first primitive pass wrote
+// (their states do not change).
+template <int N, int D>
+__global__ void __launch_bounds__(kCellThreads)
+    k_update32p(const double* Wn, const double* Wsrc, double* Wout, const double* __restrict__ F0,
+                const double* __restrict__ F1, const double* __restrict__ F2, DevGrid g, DevFluid f,
+                StepState* st, double a, double b, int relax, int count, float* __restrict__ P32,
+                float* __restrict__ R32) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.nint) return;
+  const int64_t nc = g.ncells;
+  double Ws[M], Wo[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) Ws[m] = Wsrc[m * nc + c];
+  fast_combine<N, D>(c, Wn, Ws, F0, F1, F2, g, st->dt, a, b, Wo);
+  double rho, Re;
+  if (relax)
+    relax_fast<N, D>(Wo, f, rho, Re);
+  else
+    rho_Re<N, D>(Wo, f, rho, Re);
+  if (count) count_bits(st, admissibility_bits<N, D>(Wo, f));
+#pragma unroll
+  for (int m = 0; m < M; ++m) Wout[m * nc + c] = Wo[m];
+  float u[D], cs;
+  prim32_store<N, D>(c, Wo, rho, Re, P32, R32, nc, f, u, cs);
 }
 
 // DEFER: where a screen fails (or for the first-order scheme) return false

@@ -596,33 +596,76 @@ __global__ void __launch_bounds__(kFaceThreads)
 
 // ---------------------------------------------------------------- thermal relaxation (Sec. 4.2)
 
+// Precision-form relaxation (FP64 throughout): the same root p* and T* as
+// relax_cell, with the quadratic A_p p^2 + B_p p + C_p = 0 multiplied by rho^2
+// so that its coefficients need no division:
+//   rho^2 A_p = rho C_v,  rho^2 B_p = -(R_e R_m - p_inf,1 rho (C_v + rho_1' R_1)),
+//   rho^2 C_p = -R_e p_inf,1 (R_m - rho_1' R_1),
+// with C_v = sum alpha_k rho_k c_v,k, R_m = sum alpha_k rho_k (c_p,k - c_v,k),
+// rho_1' = alpha_1 rho_1 (species `liq`) and R_e = rho (rho e~) =
+// rho (E - sum alpha_k rho_k q_k) - |rho u|^2 / 2. With
+// Y = rho_1' (p* + gamma_1 p_inf,1) c_v,1 + (C_v - rho_1' c_v,1)(p* + p_inf,1),
+// Eq. T_relax_e gives T* = R_e (p* + p_inf,1) / (rho Y), and the relaxed volume
+// fractions alpha_k = alpha_k rho_k R_k T* / (p* + p_inf,k) share one division
+// z = R_e / (rho Y p*). Two divisions and one square root per cell. Returns rho
+// and R_e for a primitive evaluation that follows.
+template <int N, int D>
+__device__ __forceinline__ void relax_fast(double* W, const DevFluid& f, double& rho_out, double& Re_out,
+                                           double* pT = nullptr) {
+  using L = Lay<N, D>;
+  const int l = f.liq;
+  double rho = 0.0, Cv = 0.0, Rm = 0.0, rq = 0.0, m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    rho += W[k];
+    Cv += W[k] * f.cv[k];
+    Rm += W[k] * f.Rg[k];
+    rq += W[k] * f.q[k];
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) m2 += W[L::MOM + d] * W[L::MOM + d];
+  const double Re = rho * (W[L::EN] - rq) - 0.5 * m2;
+  const double pinf1 = f.pinf[l], Wl = W[l], WlR1 = Wl * f.Rg[l];
+  const double A = rho * Cv;
+  const double B = -(Re * Rm - pinf1 * rho * (Cv + WlR1));
+  const double C = -(Re * pinf1 * (Rm - WlR1));
+  const double sq = sqrt(B * B - 4.0 * A * C);
+  const double ps = (B > 0.0) ? (-2.0 * C) / (B + sq) : (sq - B) / (2.0 * A);
+  const double ppl = ps + pinf1;
+  const double Y = Wl * (ps + f.gamma[l] * pinf1) * f.cv[l] + (Cv - Wl * f.cv[l]) * ppl;
+  const double z = Re / (rho * Y * ps);
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k)  // alpha_k = rho_k' R_k T* / (p* + p_inf,k), one stiffened gas at most
+    W[L::AL + k] = W[k] * f.Rg[k] * (k == l ? ps : ppl) * z;
+  if (pT) {
+    pT[0] = ps;
+    pT[1] = z * ps * ppl;
+  }
+  rho_out = rho;
+  Re_out = Re;
+}
+
 // Infinite-rate thermal relaxation of one cell: keeps alpha_k rho_k, rho u, E and
 // replaces the stored alpha_k by rho Y_k / rho_k(p*, T*). p* is the positive root of
 // A_p p^2 + B_p p + C_p = 0 (Eqs. Ap_Bp_Cp_1-3, p_relax) in the cancellation-free
 // form, T* from Eq. T_relax_e. Species `liq` is the stiffened gas.
+// FAST (precision form): relax_fast.
 template <int N, int D, bool FAST = false>
 __device__ __forceinline__ void relax_cell(double* W, const DevFluid& f, double* pT = nullptr) {
+  if constexpr (FAST) {
+    double rho, Re;
+    relax_fast<N, D>(W, f, rho, Re, pT);
+    return;
+  }
   using L = Lay<N, D>;
   const int l = f.liq;
   double rho = 0.0;
 #pragma unroll
   for (int k = 0; k < N; ++k) rho += W[k];
   double Y[N];
-  const double inv_rho = FAST ? 1.0 / rho : 0.0;
 #pragma unroll
-  for (int k = 0; k < N; ++k) Y[k] = FAST ? W[k] * inv_rho : W[k] / rho;
-  double re;
-  if (FAST) {
-    // rho e~ with the reciprocal of rho (rhoe_tilde divides)
-    double kin = 0.0, rq = 0.0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) kin += W[L::MOM + d] * W[L::MOM + d];
-#pragma unroll
-    for (int k = 0; k < N; ++k) rq += W[k] * f.q[k];
-    re = W[L::EN] - 0.5 * kin * inv_rho - rq;
-  } else {
-    re = rhoe_tilde<N, D>(W, f);
-  }
+  for (int k = 0; k < N; ++k) Y[k] = W[k] / rho;
+  const double re = rhoe_tilde<N, D>(W, f);
   double cvb = 0.0, cpb = 0.0;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
@@ -635,21 +678,6 @@ __device__ __forceinline__ void relax_cell(double* W, const DevFluid& f, double*
   const double Cp = -(re * pinf1 * ((cpb - cvb) - Yl * R1));
   const double sq = sqrt(Bp * Bp - 4.0 * Ap * Cp);
   const double ps = (Bp > 0.0) ? (-2.0 * Cp) / (Bp + sq) : (sq - Bp) / (2.0 * Ap);
-  if (FAST) {
-    // 1/(p* + p_inf,1) and 1/p* from one reciprocal of their product
-    const double r2 = 1.0 / (ps * (ps + pinf1));
-    const double inv_pl = ps * r2, inv_p = (ps + pinf1) * r2;
-    const double den = Yl * (ps + f.gamma[l] * pinf1) * f.cv[l] * inv_pl + cvb - Yl * f.cv[l];
-    const double Ts = re * inv_rho / den;
-#pragma unroll
-    for (int k = 0; k < N - 1; ++k)  // alpha_k = rho Y_k / rho_k(p*, T*)
-      W[L::AL + k] = W[k] * (f.Rg[k] * Ts) * (k == l ? inv_pl : (f.pinf[k] == 0.0 ? inv_p : 1.0 / (ps + f.pinf[k])));
-    if (pT) {
-      pT[0] = ps;
-      pT[1] = Ts;
-    }
-    return;
-  }
   const double den = Yl * (ps + f.gamma[l] * pinf1) * f.cv[l] / (ps + pinf1) + cvb - Yl * f.cv[l];
   const double Ts = (re / rho) / den;
 #pragma unroll
@@ -695,6 +723,51 @@ __device__ __forceinline__ void count_bits(StepState* st, int b) {
 
 // ---------------------------------------------------------------- per-cell update
 
+// Precision form: W_out = a W^n + b (W_src + dt RHS) of one interior cell c,
+// with W_src + dt RHS accumulated directly and dt/dx_d folded into one
+// coefficient per direction (one multiply-add per slot and direction). Ws: the
+// cell's W_src, already loaded.
+template <int N, int D>
+__device__ __forceinline__ void fast_combine(int64_t c, const double* Wn, const double* Ws,
+                                             const double* __restrict__ F0, const double* __restrict__ F1,
+                                             const double* __restrict__ F2, const DevGrid& g, double dt, double a,
+                                             double b, double* Wo) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+  const int64_t nc = g.ncells;
+  const int64_t i0 = c % g.n[0];
+  const int64_t r = c / g.n[0];
+  const int64_t i1 = r % g.n[1], i2 = r / g.n[1];
+  double acc[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) acc[m] = Ws[m];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double* F = d == 0 ? F0 : (d == 1 ? F1 : F2);
+    const int64_t f0 = g.n[0] + (d == 0), f1 = g.n[1] + (d == 1), f2 = g.n[2] + (d == 2);
+    const int64_t nf = f0 * f1 * f2;
+    const int64_t fl = HRM_IDX(g, (i2 * f1 + i1) * f0 + i0, nf);
+    const int64_t fr = HRM_IDX(g, fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1)), nf);
+    const double cd = -dt * g.inv_dx[d];
+    // G^-_{i+1/2} - G^+_{i-1/2}: the alpha slots of the right face use alpha_i
+    // (planes AL..), those of the left face alpha_i as its right neighbour (planes M..)
+#pragma unroll
+    for (int m = 0; m < L::NC; ++m) acc[m] += cd * (F[m * nf + fr] - F[m * nf + fl]);
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+      const int m = L::AL + k;
+      acc[m] += cd * (F[m * nf + fr] - F[(M + k) * nf + fl]);
+    }
+  }
+  if (a == 0.0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) Wo[m] = b * acc[m];
+  } else {
+#pragma unroll
+    for (int m = 0; m < M; ++m) Wo[m] = a * Wn[m * nc + c] + b * acc[m];
+  }
+}
+
 // RHS_i = -sum_d (G^{d,-}_{i+1/2} - G^{d,+}_{i-1/2}) / dx_d (Eq. semi_W_G_pm_eqn),
 // then W_out = a W^n + b (W_src + dt RHS) (SSP-RK stage in Shu-Osher form),
 // optionally followed by the thermal relaxation and the admissibility count.
@@ -717,35 +790,8 @@ __device__ __forceinline__ void update_body(int64_t c, const double* Wn, const d
 #pragma unroll
   for (int m = 0; m < M; ++m) Ws[m] = Wsrc[m * nc + c];
   if constexpr (FAST && MODE == 0) {
-    // precision form: W_src + dt RHS accumulated directly, dt/dx_d folded into
-    // one coefficient per direction (one multiply-add per slot and direction)
-    double acc[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) acc[m] = Ws[m];
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const double* F = d == 0 ? F0 : (d == 1 ? F1 : F2);
-      const int64_t f0 = g.n[0] + (d == 0), f1 = g.n[1] + (d == 1), f2 = g.n[2] + (d == 2);
-      const int64_t nf = f0 * f1 * f2;
-      const int64_t fl = HRM_IDX(g, (i2 * f1 + i1) * f0 + i0, nf);
-      const int64_t fr = HRM_IDX(g, fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1)), nf);
-      const double cd = -dt * g.inv_dx[d];
-#pragma unroll
-      for (int m = 0; m < L::NC; ++m) acc[m] += cd * (F[m * nf + fr] - F[m * nf + fl]);
-#pragma unroll
-      for (int k = 0; k < N - 1; ++k) {
-        const int m = L::AL + k;
-        acc[m] += cd * (F[m * nf + fr] - F[(M + k) * nf + fl]);
-      }
-    }
     double Wo[M];
-    if (a == 0.0) {
-#pragma unroll
-      for (int m = 0; m < M; ++m) Wo[m] = b * acc[m];
-    } else {
-#pragma unroll
-      for (int m = 0; m < M; ++m) Wo[m] = a * Wn[m * nc + c] + b * acc[m];
-    }
+    fast_combine<N, D>(c, Wn, Ws, F0, F1, F2, g, dt, a, b, Wo);
     if (relax) relax_cell<N, D, FAST>(Wo, f);
     if (count) count_bits(st, admissibility_bits<N, D>(Wo, f));
 #pragma unroll
