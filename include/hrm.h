@@ -360,6 +360,15 @@ hrm_status hrm_probe_fma_peak(int32_t precision, int32_t iters, void* stream, do
  * the number of waits that ran out (128); the device stays usable. Synchronises
  * `stream`. */
 hrm_status hrm_probe_wait_timeout(void* stream, int64_t* expired);
+/* Diagnostic (not a step of the method): the precision form converts between
+ * FP32 and FP64 with integer operations on the IEEE-754 encodings (FP64
+ * instructions, conversions included, are scarce on this GPU). For n elements of
+ * device arrays: narrowed[i] = in_d[i] rounded to the nearest float (ties to
+ * even), widened[i] = in_f[i] as a double -- which must equal the hardware
+ * conversions bit for bit. Enqueued on `stream`; no synchronisation;
+ * HRM_E_INVAL for n < 0 or a NULL array with n > 0. */
+hrm_status hrm_probe_convert(const double* in_d, const float* in_f, int64_t n, float* narrowed, double* widened,
+                             void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent 2D problems of uneven size (each its own grid

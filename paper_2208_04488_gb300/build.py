@@ -1,9 +1,10 @@
 """Build the in-tree CUDA library ``_build/libhrm.so`` for sm_103a with nvcc.
 
-Each translation unit compiles in parallel. The per-cell unit and the FP64
-per-midpoint units are built without FMA contraction, so the FP64 path
-evaluates every expression in the order written with IEEE rounding; the FP32
-units keep contraction.
+Each translation unit compiles in parallel. The per-cell unit, the FP64
+per-midpoint units and the precision form's units are built without FMA
+contraction: the FP64 path evaluates every expression in the order written with
+IEEE rounding, and the precision form's FP32 expressions round the same way in
+every kernel that inlines them (its FMAs are explicit fma()/fmaf() calls).
 """
 from __future__ import annotations
 
@@ -28,14 +29,14 @@ UNITS = {
     "hrm_face64_d1.cu": ["--fmad=false"],
     "hrm_face64_d2.cu": ["--fmad=false"],
     "hrm_face64_d3.cu": ["--fmad=false"],
-    "hrm_face32_d1.cu": [],
-    "hrm_face32_d2.cu": [],
-    "hrm_face32_d3.cu": [],
+    "hrm_face32_d1.cu": ["--fmad=false"],
+    "hrm_face32_d2.cu": ["--fmad=false"],
+    "hrm_face32_d3.cu": ["--fmad=false"],
     "hrm_api.cu": [],
     "hrm_probe.cu": [],
     "hrm_noalloc.cu": ["--fmad=false"],
     "hrm_batch64_d2.cu": ["--fmad=false"],
-    "hrm_batch32_d2.cu": [],
+    "hrm_batch32_d2.cu": ["--fmad=false"],
     "hrm_batch_api.cu": [],
     "hrm_learned.cu": [],
     "hrm_learned_data.cu": ["--fmad=false"],

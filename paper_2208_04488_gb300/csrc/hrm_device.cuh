@@ -18,7 +18,7 @@ namespace hrm {
 // Species constants, derived once on the host from gamma, p_inf, c_v, q (Sec. 2).
 struct DevFluid {
   int32_t liq;  // index of the stiffened gas (Sec. 4.2 calls it species 1)
-  int32_t pad;
+  int32_t has_q;  // 1 when some q_k != 0 (the precision form skips sum alpha_k rho_k q_k otherwise)
   double inv_gm1[HRM_MAXN];    // 1/(gamma_k - 1)
   double gpinf_gm1[HRM_MAXN];  // gamma_k p_inf_k / (gamma_k - 1)
   double cv[HRM_MAXN], cp[HRM_MAXN], Rg[HRM_MAXN];  // c_v, c_p, c_p - c_v
@@ -29,7 +29,9 @@ struct DevFluid {
 
 // Fill the FP32 copies of the species constants (host).
 inline void fill_fluid_f(DevFluid& f) {
+  f.has_q = 0;
   for (int k = 0; k < HRM_MAXN; ++k) {
+    if (f.q[k] != 0.0) f.has_q = 1;
     f.inv_gm1_f[k] = (float)f.inv_gm1[k];
     f.gpinf_gm1_f[k] = (float)f.gpinf_gm1[k];
     f.q_f[k] = (float)f.q[k];
@@ -78,7 +80,48 @@ struct DevParams {
   // the thresholds rounded up to FP32
   int32_t screen, pad_;
   float eps_ar_f, eps_rhoe_f, hs_rc2_f, eps_a_mf;  // eps_a_mf: eps_a + 1e-13 (float-float margin)
+  float weno_eps_f, Cs_f;                          // FP32 roundings of weno_eps and Cs
 };
+
+// ---------------------------------------------------------------- FP32 <-> FP64 on the integer pipes
+// GB300 executes FP64 instructions, the FP32 <-> FP64 conversions included, at
+// 1/64 of the FP32 rate. The precision form converts tens of values per cell and
+// per midpoint, so these two build the converted encodings from the IEEE-754
+// formats with integer operations instead; each gives exactly the hardware
+// conversion's result (the GPU tests compare them bit for bit).
+
+// float -> double, exact: sign kept, exponent rebiased by 1023 - 127 = 896,
+// mantissa moved up by 52 - 23 = 29 bits. Zeros are built here; subnormal,
+// infinite and NaN inputs use the hardware conversion.
+__device__ __forceinline__ double widen_f32(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t mag = u & 0x7fffffffu;
+  if (mag - 0x00800000u >= 0x7f000000u) {  // not a normal number
+    if (mag == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)x;
+  }
+  const uint32_t hi = (u & 0x80000000u) | ((mag >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// double -> float, rounded to nearest with ties to even: the 52-bit mantissa
+// keeps its top 23 bits and the 29 dropped bits decide the rounding (a carry
+// may move into the exponent, up to infinity past the largest float). Done
+// here for results with a normal float exponent (1..254) and for zeros; other
+// inputs (subnormal or overflowing results, infinities, NaN) use the hardware
+// conversion.
+__device__ __forceinline__ float narrow_f64(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  if (e - 897u >= 254u) {
+    if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+    return (float)x;
+  }
+  const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t r = lo & 0x1fffffffu;
+  const uint32_t f = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
+  return __uint_as_float(f + ((r > 0x10000000u || (r == 0x10000000u && (m & 1u))) ? 1u : 0u));
+}
 
 // Per-step scalars kept on the device so that a captured graph needs no host input.
 struct StepState {

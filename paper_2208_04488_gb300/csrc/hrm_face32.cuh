@@ -35,19 +35,53 @@ __device__ __forceinline__ float lin_increment(float a, float b, float d, float 
   return (3.f * a - 20.f * b + 60.f * d - 5.f * e) * (1.f / 128.f);
 }
 
+// WENO-IS (App. C) of the precision form on differences from the central node
+// (a, b, d, e = u_{i-2}, u_{i-1}, u_{i+1}, u_{i+2} minus u_i, scaled to unit
+// range): the same sub-stencil values, smoothness indicators, tau_5 and weights
+// as weno_is, with the multiply-adds written as fmaf and the five weight
+// divisions as approximate reciprocals (__fdividef, within 2 ulp; every
+// denominator lies in [1e-15, 1e3]).
+__device__ __forceinline__ float weno_is_f32(float a, float b, float d, float e, float eps) {
+  const float s0 = 0.5f * d;
+  const float s1 = -0.5f * b;
+  const float s2 = 0.125f * fmaf(6.f, d, -e);
+  const float s3 = 0.125f * fmaf(3.f, a, -10.f * b);
+  const float c13_12 = 13.f / 12.f;
+  const float b0 = d * d;
+  const float b1 = b * b;
+  float t = b + d, tt = b - d;
+  const float b01 = fmaf(c13_12 * t, t, 0.25f * tt * tt);
+  t = fmaf(-2.f, d, e);
+  tt = fmaf(-4.f, d, e);
+  const float b2 = fmaf(c13_12 * t, t, 0.25f * tt * tt);
+  t = fmaf(-2.f, b, a);
+  tt = fmaf(-4.f, b, a);
+  const float b3 = fmaf(c13_12 * t, t, 0.25f * tt * tt);
+  t = fmaf(-4.f, d + b, e + a);
+  tt = fmaf(2.f, b - d, e - a);
+  const float tau5 = fmaf(c13_12 * t, t, 0.25f * tt * tt);
+  const float q01 = __fdividef(tau5, b01 + eps);
+  const float e0 = (15.f / 32.f) * fmaf(__fdividef(tau5, b0 + eps), q01, 1.f);
+  const float e1 = (5.f / 32.f) * fmaf(__fdividef(tau5, b1 + eps), q01, 1.f);
+  const float e2 = (5.f / 16.f) * (1.f + __fdividef(tau5, b2 + eps));
+  const float e3 = (1.f / 16.f) * (1.f + __fdividef(tau5, b3 + eps));
+  const float es = (e0 + e1) + (e2 + e3);
+  return __fdividef(fmaf(e0, s0, fmaf(e1, s1, fmaf(e2, s2, e3 * s3))), es);
+}
+
 __device__ __forceinline__ float weno_is_scaled(float um2, float um1, float u0, float up1, float up2, float eps,
                                                 bool lin = false) {
   float a = um2 - u0, b = um1 - u0, d = up1 - u0, e = up2 - u0;
   if (lin) return u0 + lin_increment(a, b, d, e);
   const float s = fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(d), fabsf(e)));
   if (!(s > kTinyRange)) return u0;
-  const float inv = 1.f / s;
+  const float inv = __frcp_rn(s);
   a *= inv;
   b *= inv;
   d *= inv;
   e *= inv;
   const float eps_s = fmaxf(eps * inv * inv, 1e-15f);
-  return u0 + s * weno_is<float>(a, b, 0.f, d, e, eps_s);
+  return fmaf(s, weno_is_f32(a, b, d, e, eps_s), u0);
 }
 
 // WENO-IS increment from already-formed differences (u_j - u_0) of a stencil
@@ -56,9 +90,9 @@ __device__ __forceinline__ float weno_increment(float a, float b, float d, float
   if (lin) return lin_increment(a, b, d, e);
   const float s = fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(d), fabsf(e)));
   if (!(s > kTinyRange)) return 0.f;
-  const float inv = 1.f / s;
+  const float inv = __frcp_rn(s);
   const float eps_s = fmaxf(eps * inv * inv, 1e-15f);
-  return s * weno_is<float>(a * inv, b * inv, 0.f, d * inv, e * inv, eps_s);
+  return s * weno_is_f32(a * inv, b * inv, d * inv, e * inv, eps_s);
 }
 
 // Interpolation limiter of the precision form: partial densities from FP32,
@@ -163,10 +197,10 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
   return ff_sum(p.hi, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo)));
 }
 __device__ __forceinline__ ff ff_of(double x) {
-  const float h = (float)x;
-  return {h, (float)(x - (double)h)};
+  const float h = narrow_f64(x);
+  return {h, narrow_f64(x - widen_f32(h))};
 }
-__device__ __forceinline__ double ff_d(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double ff_d(ff a) { return widen_f32(a.hi) + widen_f32(a.lo); }
 __device__ __forceinline__ float ff_f(ff a) { return a.hi + a.lo; }
 #define HRM_FF(c) ff{(float)(c), (float)((c) - (double)(float)(c))}
 
@@ -302,7 +336,9 @@ __device__ __forceinline__ bool flux_screen32(const float* __restrict__ P32, int
 // and R_e = rho (rho e~) = rho (E - sum alpha_k rho_k q_k) - |rho u|^2 / 2. The
 // pressure numerator rho (rho e~ - P) = R_e - rho P is formed in FP64 (it
 // cancels where p_inf ~ 1e9 Pa meets the ambient pressure), then
-// p = (R_e - rho P) / (rho S) in FP32; no FP64 division. Returns u_d and c.
+// p = (R_e - rho P) / (rho S) in FP32; no FP64 division. S = 1/(gbar - 1) and
+// the P of the FP32 sound speed come from the FP32 volume fractions (all their
+// terms are positive). Returns u_d and c.
 template <int N, int D>
 __device__ __forceinline__ void prim32_store(int64_t c, const double* w, double rho, double Re,
                                              float* __restrict__ P32, float* __restrict__ R32, int64_t nc,
@@ -313,50 +349,56 @@ __device__ __forceinline__ void prim32_store(int64_t c, const double* w, double 
 #pragma unroll
   for (int k = 0; k < N - 1; ++k) sa += w[L::AL + k];
   const double aN = 1.0 - sa;
-  double S = 0.0, P = 0.0;
+  double P = 0.0;
+  float S32 = 0.f, Pf = 0.f;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const double a = k < N - 1 ? w[L::AL + k] : aN;
-    S += a * f.inv_gm1[k];
-    P += a * f.gpinf_gm1[k];
+    const float a32 = narrow_f64(a);
+    S32 += a32 * f.inv_gm1_f[k];
+    if (f.pinf[k] != 0.0) {  // one stiffened gas at most: P has one term
+      P = fma(a, f.gpinf_gm1[k], P);
+      Pf += a32 * f.gpinf_gm1_f[k];
+    }
   }
-  const double num = Re - rho * P;  // rho (rho e~ - P)
-  const double rS = rho * S;
-  const float rho32 = (float)rho, irho32 = 1.f / rho32;
-  const float S32 = (float)S, iS = 1.f / S32;
-  const float irS = 1.f / (float)rS;
-  const float p = (float)num * irS;
-  const float Pf = (float)P;
+  const double num = fma(-rho, P, Re);  // rho (rho e~ - P)
+  const float rho32 = narrow_f64(rho), irho32 = 1.f / rho32;
+  const float iS = 1.f / S32;
+  const float rS32 = rho32 * S32, irS = 1.f / rS32;
+  const float p = narrow_f64(num) * irS;
   const float rc2 = (1.f + iS) * p + Pf * iS;
   cs = sqrtf(rc2 * irho32);
 #pragma unroll
-  for (int d = 0; d < D; ++d) u[d] = (float)w[L::MOM + d] * irho32;
+  for (int d = 0; d < D; ++d) u[d] = narrow_f64(w[L::MOM + d]) * irho32;
 #pragma unroll
-  for (int k = 0; k < N; ++k) P32[k * nc + c] = (float)w[k];
+  for (int k = 0; k < N; ++k) P32[k * nc + c] = narrow_f64(w[k]);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     P32[(L::MOM + d) * nc + c] = u[d];
-    P32[(Q::MOM + d) * nc + c] = (float)w[L::MOM + d];
+    P32[(Q::MOM + d) * nc + c] = narrow_f64(w[L::MOM + d]);
   }
   P32[L::EN * nc + c] = p;
   P32[Q::C * nc + c] = cs;
   P32[Q::RHO * nc + c] = rho32;
   P32[Q::RC2 * nc + c] = rc2;
-  P32[Q::E * nc + c] = (float)w[L::EN];
+  P32[Q::E * nc + c] = narrow_f64(w[L::EN]);
 #pragma unroll
   for (int k = 0; k < N - 1; ++k) {
     const double a = w[L::AL + k];
-    const float ah = (float)a;
+    const float ah = narrow_f64(a);
     P32[(L::AL + k) * nc + c] = ah;
-    P32[(Q::ALO + k) * nc + c] = (float)(a - (double)ah);
+    P32[(Q::ALO + k) * nc + c] = narrow_f64(a - widen_f32(ah));
   }
   if (R32) {
     // residues: rho exactly; u_d and p from the FP64 remainders of m - u rho and
-    // (R_e - rho P) - p rho S
-    R32[c] = (float)(rho - (double)rho32);
+    // (R_e - rho P) - p rho S (rho S in FP64 here)
+    R32[c] = narrow_f64(rho - widen_f32(rho32));
 #pragma unroll
-    for (int d = 0; d < D; ++d) R32[(1 + d) * nc + c] = (float)(w[L::MOM + d] - (double)u[d] * rho) * irho32;
-    R32[(1 + D) * nc + c] = (float)(num - (double)p * rS) * irS;
+    for (int d = 0; d < D; ++d) R32[(1 + d) * nc + c] = narrow_f64(w[L::MOM + d] - widen_f32(u[d]) * rho) * irho32;
+    double S = 0.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) S = fma(k < N - 1 ? w[L::AL + k] : aN, f.inv_gm1[k], S);
+    R32[(1 + D) * nc + c] = narrow_f64(num - widen_f32(p) * (rho * S)) * irS;
   }
 }
 
@@ -367,13 +409,14 @@ __device__ __forceinline__ void rho_Re(const double* w, const DevFluid& f, doubl
   double rq = 0.0, m2 = 0.0;
   rho = 0.0;
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    rho += w[k];
-    rq += w[k] * f.q[k];
+  for (int k = 0; k < N; ++k) rho += w[k];
+  if (f.has_q) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) rq = fma(w[k], f.q[k], rq);
   }
 #pragma unroll
-  for (int d = 0; d < D; ++d) m2 += w[L::MOM + d] * w[L::MOM + d];
-  Re = rho * (w[L::EN] - rq) - 0.5 * m2;
+  for (int d = 0; d < D; ++d) m2 = fma(w[L::MOM + d], w[L::MOM + d], m2);
+  Re = fma(rho, w[L::EN] - rq, -0.5 * m2);
 }
 
 template <int N, int D>
@@ -397,7 +440,7 @@ __device__ __forceinline__ void prim32_body(int64_t c, const double* __restrict_
     return;
   }
 #pragma unroll
-  for (int d = 0; d < D; ++d) s[d] = (double)((fabsf(u[d]) + cs) * (float)g.inv_dx[d]);
+  for (int d = 0; d < D; ++d) s[d] = widen_f32((fabsf(u[d]) + cs) * narrow_f64(g.inv_dx[d]));
 }
 
 template <int N, int D>
@@ -513,7 +556,7 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
     const float cb = 0.5f * (ld(Q::C, 2) + ld(Q::C, 3));
     const float inv_rc = 1.f / (rhob * cb);
     const float rc2b = rhob * cb * cb;
-    const float eps = (float)pr.weno_eps;
+    const float eps = pr.weno_eps_f;
     // The N + D + 1 characteristic fields other than the volume fractions in one
     // loop, so that the WENO-IS code exists once (the sweep is bound by
     // instruction fetch when it is unrolled): field fi = 0 is u - p/(rho c)
@@ -694,7 +737,7 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
       const float prod = sr_ * sp_;
       float pw = prod;
       for (int e = 1; e < pr.qexp; ++e) pw = pw * prod;
-      sig = tanhf((float)pr.Cs * pw);
+      sig = tanhf(pr.Cs_f * pw);
     }
     const float one_m = 1.f - sig;
     const float uhcs = psi * ut - a1 * (u6[2] + u6[3]) + a2 * (u6[1] + u6[4]) - a3 * (u6[0] + u6[5]);
@@ -717,7 +760,7 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
       }
       const float ghcs = psi * Gt[m] - a1 * (Gn[2] + Gn[3]) + a2 * (Gn[1] + Gn[4]) - a3 * (Gn[0] + Gn[5]);
       g32[m] = sig * Gt[m] + one_m * ghcs;
-      G.Gc[m] = (double)g32[m];
+      G.Gc[m] = widen_f32(g32[m]);
     }
     // alpha slots, quasi-conservative form (Eq. G_pm): with alpha_j = alpha_i +
     // dA_j, the blended HCS alpha flux is alpha_i u^ + Rh, where u^ is the blended

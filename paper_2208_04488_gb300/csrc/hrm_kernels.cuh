@@ -618,21 +618,24 @@ __device__ __forceinline__ void relax_fast(double* W, const DevFluid& f, double&
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     rho += W[k];
-    Cv += W[k] * f.cv[k];
-    Rm += W[k] * f.Rg[k];
-    rq += W[k] * f.q[k];
+    Cv = fma(W[k], f.cv[k], Cv);
+    Rm = fma(W[k], f.Rg[k], Rm);
+  }
+  if (f.has_q) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) rq = fma(W[k], f.q[k], rq);
   }
 #pragma unroll
-  for (int d = 0; d < D; ++d) m2 += W[L::MOM + d] * W[L::MOM + d];
-  const double Re = rho * (W[L::EN] - rq) - 0.5 * m2;
+  for (int d = 0; d < D; ++d) m2 = fma(W[L::MOM + d], W[L::MOM + d], m2);
+  const double Re = fma(rho, W[L::EN] - rq, -0.5 * m2);
   const double pinf1 = f.pinf[l], Wl = W[l], WlR1 = Wl * f.Rg[l];
   const double A = rho * Cv;
-  const double B = -(Re * Rm - pinf1 * rho * (Cv + WlR1));
+  const double B = fma(pinf1 * rho, Cv + WlR1, -(Re * Rm));
   const double C = -(Re * pinf1 * (Rm - WlR1));
-  const double sq = sqrt(B * B - 4.0 * A * C);
+  const double sq = sqrt(fma(B, B, -4.0 * A * C));
   const double ps = (B > 0.0) ? (-2.0 * C) / (B + sq) : (sq - B) / (2.0 * A);
   const double ppl = ps + pinf1;
-  const double Y = Wl * (ps + f.gamma[l] * pinf1) * f.cv[l] + (Cv - Wl * f.cv[l]) * ppl;
+  const double Y = fma(Wl * fma(f.gamma[l], pinf1, ps), f.cv[l], fma(-Wl, f.cv[l], Cv) * ppl);
   const double z = Re / (rho * Y * ps);
 #pragma unroll
   for (int k = 0; k < N - 1; ++k)  // alpha_k = rho_k' R_k T* / (p* + p_inf,k), one stiffened gas at most
@@ -723,6 +726,9 @@ __device__ __forceinline__ void count_bits(StepState* st, int b) {
 
 // ---------------------------------------------------------------- per-cell update
 
+// The precision form's FP64 arithmetic writes its multiply-adds as explicit
+// fma(): its translation units are built without FMA contraction, so that every
+// FP32 expression rounds as written whichever kernel it is inlined into.
 // Precision form: W_out = a W^n + b (W_src + dt RHS) of one interior cell c,
 // with W_src + dt RHS accumulated directly and dt/dx_d folded into one
 // coefficient per direction (one multiply-add per slot and direction). Ws: the
@@ -752,19 +758,22 @@ __device__ __forceinline__ void fast_combine(int64_t c, const double* Wn, const 
     // G^-_{i+1/2} - G^+_{i-1/2}: the alpha slots of the right face use alpha_i
     // (planes AL..), those of the left face alpha_i as its right neighbour (planes M..)
 #pragma unroll
-    for (int m = 0; m < L::NC; ++m) acc[m] += cd * (F[m * nf + fr] - F[m * nf + fl]);
+    for (int m = 0; m < L::NC; ++m) acc[m] = fma(cd, F[m * nf + fr] - F[m * nf + fl], acc[m]);
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) {
       const int m = L::AL + k;
-      acc[m] += cd * (F[m * nf + fr] - F[(M + k) * nf + fl]);
+      acc[m] = fma(cd, F[m * nf + fr] - F[(M + k) * nf + fl], acc[m]);
     }
   }
-  if (a == 0.0) {
+  if (a == 0.0 && b == 1.0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) Wo[m] = acc[m];
+  } else if (a == 0.0) {
 #pragma unroll
     for (int m = 0; m < M; ++m) Wo[m] = b * acc[m];
   } else {
 #pragma unroll
-    for (int m = 0; m < M; ++m) Wo[m] = a * Wn[m * nc + c] + b * acc[m];
+    for (int m = 0; m < M; ++m) Wo[m] = fma(a, Wn[m * nc + c], b * acc[m]);
   }
 }
 

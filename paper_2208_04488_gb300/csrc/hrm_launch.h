@@ -155,6 +155,8 @@ inline void fill_screen(DevParams& d, int requested) {
   d.eps_rhoe_f = float_up(d.eps_rhoe);
   d.hs_rc2_f = float_up(d.hs_rc2);
   d.eps_a_mf = float_up(d.eps_a + 1e-13);
+  d.weno_eps_f = (float)d.weno_eps;
+  d.Cs_f = (float)d.Cs;
   d.pad_ = 0;
 }
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/hrm.h"
+#include "hrm_device.cuh"
 #include "hrm_tc.cuh"
 
 namespace {
@@ -64,7 +65,24 @@ __global__ void __launch_bounds__(128) k_wait_probe(unsigned long long* expired)
   if (!hrm::tc::bar_wait(hrm::tc::smem_u32(&bar), 0u)) atomicAdd(expired, 1ull);
 }
 
+// The integer-pipe conversions of the precision form, element by element.
+__global__ void k_convert(const double* in_d, const float* in_f, int64_t n, float* narrowed, double* widened) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  narrowed[i] = hrm::narrow_f64(in_d[i]);
+  widened[i] = hrm::widen_f32(in_f[i]);
+}
+
 }  // namespace
+
+extern "C" hrm_status hrm_probe_convert(const double* in_d, const float* in_f, int64_t n, float* narrowed,
+                                        double* widened, void* stream) {
+  if (n < 0 || (n > 0 && (!in_d || !in_f || !narrowed || !widened))) return HRM_E_INVAL;
+  if (n == 0) return HRM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_convert<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in_d, in_f, n, narrowed, widened);
+  return cudaGetLastError() == cudaSuccess ? HRM_OK : HRM_E_CUDA;
+}
 
 extern "C" hrm_status hrm_probe_wait_timeout(void* stream, int64_t* expired) {
   if (!expired) return HRM_E_INVAL;

@@ -174,6 +174,8 @@ def lib():
     L.hrm_probe_fma_peak.restype = ctypes.c_int
     L.hrm_probe_wait_timeout.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64)]
     L.hrm_probe_wait_timeout.restype = ctypes.c_int
+    L.hrm_probe_convert.argtypes = [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]
+    L.hrm_probe_convert.restype = ctypes.c_int
     for name in ("hrm_create", "hrm_set_params", "hrm_set", "hrm_set_primitive", "hrm_dt", "hrm_step",
                  "hrm_relax", "hrm_rhs", "hrm_get", "hrm_time", "hrm_admissibility"):
         getattr(L, name).restype = ctypes.c_int
@@ -195,6 +197,21 @@ def probe_wait_timeout(stream=None):
     n = ctypes.c_int64()
     st = lib().hrm_probe_wait_timeout(_VP(_stream_handle(stream)), ctypes.byref(n))
     return st, n.value
+
+
+def probe_convert(in_d, in_f, stream=None):
+    """The library's integer-pipe FP64 -> FP32 (nearest) and FP32 -> FP64
+    conversions of two device tensors of equal length: (narrowed, widened)."""
+    import torch
+    assert in_d.dtype == torch.float64 and in_f.dtype == torch.float32 and in_d.numel() == in_f.numel()
+    in_d, in_f = in_d.contiguous(), in_f.contiguous()
+    narrowed = torch.empty_like(in_f)
+    widened = torch.empty_like(in_d)
+    st = lib().hrm_probe_convert(_VP(in_d.data_ptr()), _VP(in_f.data_ptr()), in_d.numel(),
+                                 _VP(narrowed.data_ptr()), _VP(widened.data_ptr()), _VP(_stream_handle(stream)))
+    if st != HRM_OK:
+        raise HrmError(st, "conversion probe failed")
+    return narrowed, widened
 
 
 def params_default(**overrides) -> HrmParams:
