@@ -190,6 +190,41 @@ hrm_status hrm_dt(hrm_ctx* ctx, double cfl, double* dt_out, double* tau_out);
  * ran out (its gate bytes are then unreliable). */
 hrm_status hrm_step(hrm_ctx* ctx, double dt, int32_t nsteps);
 
+/* The same step taken one RK stage at a time, so that a caller can exchange
+ * halo layers between stages and reduce the CFL maxima over several contexts
+ * (domain decomposition: one context per subdomain, each holding its layers
+ * plus 3 ghost layers per inner side; the stencil of a midpoint spans nodes
+ * i-2..i+3 and the HCS flux difference nodes i-3..i+3, Sec. 4.3.1). A step is
+ * hrm_begin_step, then hrm_stage(0) .. hrm_stage(hrm_stages() - 1); with the
+ * step state given, the results equal hrm_step's bit for bit.
+ *
+ * hrm_step_tau: the maxima tau_d = max(|u_d| + c) / dx_d of the step state as a
+ * step computes them (Sec. 4.1.2; the form's sound speed and precision), over
+ * every cell the context holds; D values. Synchronises.
+ * hrm_begin_step: start a step from maxima tau_d (e.g. the maxima over all
+ * subdomains): dt = cfl / sum_d tau_d unless dt > 0 is given, sigma_d =
+ * tau_d / sum tau, lambda_d = dt / (sigma_d dx_d); advances the time and step
+ * counters. HRM_E_INVAL for a negative or NaN tau_d, or when dt <= 0 and every
+ * tau_d is 0. Synchronises.
+ * hrm_stage: RK stage `stage` (0-based; 3 stages for SSP-RK3, 2 for SSP-RK2,
+ * 1 for forward Euler): primitives of the stage's input state, the sweeps, the
+ * update with the relaxation of params.relax_mode; the last stage writes the
+ * step state. Launches without a graph and without the admissibility count
+ * (use hrm_admissibility). Does not synchronise.
+ * hrm_layers: copy `count` whole layers of cells along the slowest direction
+ * (z in 3D, y in 2D, x in 1D), starting at layer `first`, between `buf`
+ * (M planes of count x layer cells, layer = cells of one layer; caller-owned,
+ * device memory when on_device) and the state stage `stage` reads (stage 0:
+ * the step state; later stages: the RK stage state): set = 0 copies out, set =
+ * 1 copies in. HRM_E_INVAL for layers outside the grid. Synchronises for host
+ * buffers. */
+hrm_status hrm_step_tau(hrm_ctx* ctx, double* tau);
+hrm_status hrm_begin_step(hrm_ctx* ctx, const double* tau, double dt);
+int32_t hrm_stages(const hrm_ctx* ctx);
+hrm_status hrm_stage(hrm_ctx* ctx, int32_t stage);
+hrm_status hrm_layers(hrm_ctx* ctx, int32_t stage, int32_t set, int64_t first, int64_t count, double* buf,
+                      int32_t on_device);
+
 /* Apply the thermal relaxation (Sec. 4.2) to the current state in place. */
 hrm_status hrm_relax(hrm_ctx* ctx);
 

@@ -751,6 +751,112 @@ hrm_status hrm_step(hrm_ctx* c, double dt, int32_t nsteps) {
   return HRM_OK;
 }
 
+// ---------------------------------------------------------------- stepwise stages (domain decomposition)
+
+hrm_status hrm_step_tau(hrm_ctx* c, double* tau) {
+  Range range("hrm_step_tau");
+  if (!c || !tau) return c ? fail(c, HRM_E_INVAL, "null tau") : HRM_E_INVAL;
+  hrm_status s;
+  if ((s = check_boundaries(c))) return s;
+  // the primitive kernel of a step's first stage, with its CFL maxima
+  if (c->params.precision == HRM_FP32)
+    launch_prim32(c->N, c->D, c->Wn, c->P32, r32_target(c), c->dg, c->fl, c->st, tau_mode(c), c->stream);
+  else
+    c->ck->prim(c->Wn, c->V, c->AUX, p32_target(c), r32_target(c), c->dg, c->fl, c->st, tau_mode(c), c->stream);
+  ++c->launches;
+  unsigned long long bits[3] = {0ull, 0ull, 0ull};
+  if ((s = cuda_check(c, cudaMemcpyAsync(bits, c->st->tau_bits, sizeof bits, cudaMemcpyDeviceToHost, c->stream),
+                      "read tau")))
+    return s;
+  if ((s = cuda_check(c, cudaMemsetAsync(c->st->tau_bits, 0, sizeof bits, c->stream), "clear tau"))) return s;
+  if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "tau sync"))) return s;
+  for (int d = 0; d < c->D; ++d) std::memcpy(&tau[d], &bits[d], sizeof(double));
+  return HRM_OK;
+}
+
+hrm_status hrm_begin_step(hrm_ctx* c, const double* tau, double dt) {
+  Range range("hrm_begin_step");
+  if (!c || !tau) return c ? fail(c, HRM_E_INVAL, "null tau") : HRM_E_INVAL;
+  unsigned long long bits[3] = {0ull, 0ull, 0ull};
+  double sum = 0.0;
+  for (int d = 0; d < c->D; ++d) {
+    if (!(tau[d] >= 0.0)) return fail(c, HRM_E_INVAL, "tau[%d] must be a non-negative number", d);
+    std::memcpy(&bits[d], &tau[d], sizeof(double));
+    sum += tau[d];
+  }
+  if (!(dt > 0.0) && !(sum > 0.0)) return fail(c, HRM_E_INVAL, "no step: dt <= 0 and all tau_d are 0");
+  hrm_status s;
+  if ((s = cuda_check(c, cudaMemcpyAsync(c->st->tau_bits, bits, sizeof bits, cudaMemcpyHostToDevice, c->stream),
+                      "set tau")))
+    return s;
+  launch_set_dt(c->st, dt > 0.0 ? dt : 0.0, c->stream);
+  launch_finalize(c->st, c->dg, c->D, c->params.cfl, 0, c->stream);
+  c->launches += 2;
+  if ((s = last_launch(c, "begin step"))) return s;
+  // host values: the copy above reads the caller's array
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "begin step sync");
+}
+
+int32_t hrm_stages(const hrm_ctx* c) {
+  if (!c) return 0;
+  return c->params.integrator == HRM_EULER ? 1 : (c->params.integrator == HRM_RK2 ? 2 : 3);
+}
+
+hrm_status hrm_stage(hrm_ctx* c, int32_t stage) {
+  Range range("hrm_stage");
+  if (!c) return HRM_E_INVAL;
+  const int ns = hrm_stages(c);
+  if (stage < 0 || stage >= ns) return fail(c, HRM_E_INVAL, "stage %d outside 0..%d", stage, ns - 1);
+  hrm_status s;
+  if ((s = check_boundaries(c))) return s;
+  const int rs = c->params.relax_mode == HRM_RELAX_STAGE;
+  const int rf = c->params.relax_mode != HRM_RELAX_OFF;
+  const bool last = stage == ns - 1;
+  const double* src = stage == 0 ? c->Wn : c->Ws;
+  double* dst = last ? c->Wn : c->Ws;
+  double a = 0.0, b = 1.0;
+  if (c->params.integrator == HRM_RK2 && stage == 1) a = b = 0.5;
+  if (c->params.integrator == HRM_RK3 && stage == 1) {
+    a = 0.75;
+    b = 0.25;
+  }
+  if (c->params.integrator == HRM_RK3 && stage == 2) {
+    a = 1.0 / 3.0;
+    b = 2.0 / 3.0;
+  }
+  const int prof = c->profiling;
+  c->profiling = 0;  // event brackets belong to the captured step graph
+  c->launches += enqueue_stage(c, c->stream, src, dst, a, b, last ? rf : rs, 0, false);
+  c->profiling = prof;
+  return last_launch(c, "stage");
+}
+
+hrm_status hrm_layers(hrm_ctx* c, int32_t stage, int32_t set, int64_t first, int64_t count, double* buf,
+                      int32_t on_device) {
+  Range range("hrm_layers");
+  if (!c || (!buf && count > 0)) return c ? fail(c, HRM_E_INVAL, "null buffer") : HRM_E_INVAL;
+  if (stage < 0 || stage >= hrm_stages(c)) return fail(c, HRM_E_INVAL, "stage %d out of range", stage);
+  const int ds = c->D - 1;  // slowest direction
+  int64_t layer = 1;
+  for (int d = 0; d < ds; ++d) layer *= c->dg.n[d];
+  if (first < 0 || count < 0 || first + count > c->dg.n[ds])
+    return fail(c, HRM_E_INVAL, "layers %lld..%lld outside 0..%lld", (long long)first, (long long)(first + count),
+                (long long)c->dg.n[ds]);
+  if (count == 0) return HRM_OK;
+  double* state = stage == 0 ? c->Wn : c->Ws;
+  const int64_t cells = count * layer, off = first * layer;
+  hrm_status s;
+  if (set)
+    s = copy_planes(c, state + off, c->nc, buf, cells, cells, c->M,
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, "set layers");
+  else
+    s = copy_planes(c, buf, cells, state + off, c->nc, cells, c->M,
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, "get layers");
+  if (s) return s;
+  if (!on_device) return cuda_check(c, cudaStreamSynchronize(c->stream), "layers sync");
+  return HRM_OK;
+}
+
 hrm_status hrm_relax(hrm_ctx* c) {
   Range range("hrm_relax");
   if (!c) return HRM_E_INVAL;

@@ -176,6 +176,15 @@ def lib():
     L.hrm_probe_wait_timeout.restype = ctypes.c_int
     L.hrm_probe_convert.argtypes = [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]
     L.hrm_probe_convert.restype = ctypes.c_int
+    L.hrm_step_tau.argtypes = [_VP, _DP]
+    L.hrm_begin_step.argtypes = [_VP, _DP, ctypes.c_double]
+    L.hrm_stages.argtypes = [_VP]
+    L.hrm_stages.restype = ctypes.c_int32
+    L.hrm_stage.argtypes = [_VP, ctypes.c_int32]
+    L.hrm_layers.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _VP,
+                             ctypes.c_int32]
+    for name in ("hrm_step_tau", "hrm_begin_step", "hrm_stage", "hrm_layers"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("hrm_create", "hrm_set_params", "hrm_set", "hrm_set_primitive", "hrm_dt", "hrm_step",
                  "hrm_relax", "hrm_rhs", "hrm_get", "hrm_time", "hrm_admissibility"):
         getattr(L, name).restype = ctypes.c_int
@@ -388,6 +397,40 @@ class Solver:
 
     def step(self, dt=0.0, nsteps=1):
         return self._check(lib().hrm_step(self.h, float(dt), int(nsteps)))
+
+    # -- one stage at a time (domain decomposition)
+    def step_tau(self):
+        """tau_d of the step state as a step computes them (D values)."""
+        tau = (ctypes.c_double * 3)()
+        self._check(lib().hrm_step_tau(self.h, tau))
+        return np.array(tau[:self.D])
+
+    def begin_step(self, tau, dt=0.0):
+        t3 = (ctypes.c_double * 3)(*[float(v) for v in tau])
+        self._check(lib().hrm_begin_step(self.h, t3, float(dt)))
+
+    def stages(self) -> int:
+        return int(lib().hrm_stages(self.h))
+
+    def stage(self, k):
+        self._check(lib().hrm_stage(self.h, int(k)))
+
+    def layer_cells(self) -> int:
+        """Cells of one layer along the slowest direction."""
+        return int(np.prod(self.n[:-1])) if self.D > 1 else 1
+
+    def get_layers(self, stage, first, count, out=None):
+        """Layers first..first+count-1 (slowest direction) of the state stage
+        `stage` reads: (M, count x layer) numpy array or the given tensor."""
+        if out is None:
+            out = np.empty((self.M, count * self.layer_cells()))
+        ptr, dev = self._ptr(out)
+        self._check(lib().hrm_layers(self.h, int(stage), 0, int(first), int(count), _VP(ptr), dev))
+        return out
+
+    def set_layers(self, stage, first, count, buf):
+        ptr, dev = self._ptr(buf)
+        self._check(lib().hrm_layers(self.h, int(stage), 1, int(first), int(count), _VP(ptr), dev))
 
     def try_step(self, dt=0.0, nsteps=1):
         """hrm_step returning the status instead of raising."""

@@ -38,7 +38,7 @@ def _doubles(rng, n):
     fmax = float(np.finfo(np.float32).max)
     tiny = float(np.finfo(np.float32).tiny)
     edges = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, fmax, -fmax, np.nextafter(fmax, np.inf),
-                      fmax + 0.5 * float(np.spacing(np.float32(fmax))), 2.0 ** 128, tiny, -tiny,
+                      fmax + 2.0 ** 103, 2.0 ** 128, tiny, -tiny,  # fmax + half its ulp: the tie that rounds to infinity
                       np.nextafter(tiny, 0.0), tiny * (1 - 2.0 ** -25), tiny * 0.5, 1e-45, 5e-324, 1.0, -1.0,
                       1.0 - 2.0 ** -25, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24])
     return np.concatenate([uniform_bits, signed, near, edges])
