@@ -366,6 +366,44 @@ def measure_3d(torch, hrm, problems, stream, flush, args):
     return out
 
 
+def measure_decomposed(torch, hrm, problems, dist, rank, ws, stream):
+    """The 256^3 3D configuration split over the ranks (one GPU each) into
+    slabs along z with 3 ghost layers per inner side: halo layers exchanged
+    with NCCL before every RK stage, the CFL maxima max-reduced per step
+    (paper_2208_04488_gb300.decomp). All ranks take part; the whole grid's
+    cell-updates over the slowest rank's time (CUDA events on the library's
+    stream, after a barrier)."""
+    from paper_2208_04488_gb300 import decomp
+    from paper_2208_04488_gb300.replicas import whole_job_rate
+    pr = problems.interface_3d(256)
+    slab = decomp.partition(pr.n[-1], ws, periodic=True)[rank]
+    loc = decomp.local_problem(pr, slab)
+    out = {"workload": "3D perturbed interface, 256^3 cells, Mach 1.5 shock, water + air + helium, SSP-RK3, "
+                       f"split into {ws} slabs along z (periodic), 3 ghost layers per inner side",
+           "cells": pr.ncells, "ranks": ws, "owned_layers": slab.count, "exchange": "NCCL send/recv per stage",
+           "scaling": "strong"}
+    for name, prec, K in (("fp32", hrm.FP32, 6), ("fp64", hrm.FP64, 2)):
+        s = hrm.Solver.from_problem(loc, params=hrm.params_default(cfl=pr.cfl, check=0, precision=prec),
+                                    stream=stream)
+        run = decomp.Decomposed(s, slab, decomp.TorchComm(dist, device="cuda"), device_buffers=True)
+        run.step(1)
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        b0 = run.exchanged_bytes
+        e0.record(stream)
+        run.step(K)
+        e1.record(stream)
+        e1.synchronize()
+        el = e0.elapsed_time(e1) * 1e-3
+        rate, t_max = whole_job_rate(pr.ncells * K, el, dist, device="cuda")
+        out[name] = {"value": rate, "unit": UNIT, "ms_per_step": 1e3 * t_max / K, "steps": K,
+                     "halo_bytes_sent_per_step_per_rank": (run.exchanged_bytes - b0) / K}
+        s.close()
+    return out
+
+
 def gated_face_flops(problem, cfl):
     """Algorithmic flops per midpoint with every midpoint gated to the linear
     WENO weights (oracle counting build), per direction."""
@@ -603,6 +641,8 @@ def main():
     bytes_step = Wh.numel() * 8
     e2e_value, _ = whole_job_rate(pr.ncells * K_e2e, t_e2e, dist, device="cuda")
     s.set(W_fp64)  # back to the state after the timed steps (the fixed dt below comes from it)
+    # more than one GPU: the 3D configuration decomposed over all of them
+    decomposed = measure_decomposed(torch, hrm, problems, dist, rank, ws, stream) if dist is not None else None
     if dist is not None:
         # the other replicas are done: rank 0 measures the rest alone, with no
         # collective after this point
@@ -675,7 +715,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": pr.ncells, "species": pr.N,
                        "l2": "working set ~190 MB > L2 and L2 flushed (256 MB write) before every timed step",
-                       "parallelism": f"{ws} independent replica(s)" if ws > 1 else "single GPU"},
+                       "parallelism": (f"{ws} independent replica(s); decomposed_3d: the 256^3 case split over {ws} GPUs"
+                                       if ws > 1 else "single GPU")},
             "roofline": {"bound": "alu", "kernel": "k_face (per-midpoint, FP64)",
                          "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
                          "frac": frac, "traffic": TRAFFIC_BYTES["k_face_fp64"],
@@ -712,6 +753,7 @@ def main():
             },
             "batched": batched,
             "interface_3d": three_d,
+            "decomposed_3d": decomposed,
             "tube_400": tube,
             "final_time": final,
             "learned": learned_block,

@@ -103,3 +103,74 @@ def test_two_ranks_equal_one_context(hrm, tmp_path, name, precision):
     got = np.load(tmp_path / "W.npy")
     ref, _ = _single(hrm, _problem(name), prec, nsteps)
     np.testing.assert_array_equal(got, ref)
+
+
+class _ThreadComm:
+    """Two ranks as threads of one process: CUDA tensors pass through a mailbox
+    (the exchange path NCCL takes, device buffers included). Every wait has a
+    time limit, so a failing rank cannot leave the other blocked."""
+
+    def __init__(self, rank, world, box):
+        self.rank, self.world, self.box = rank, world, box
+
+    def allreduce_max(self, values):
+        b = self.box
+        b["tau"][self.rank] = np.asarray(values, dtype=np.float64)
+        b["bar"].wait()
+        out = np.max(np.stack(b["tau"]), axis=0)
+        b["bar"].wait()
+        return out
+
+    def exchange(self, sends, recvs):
+        import torch
+        b = self.box
+        torch.cuda.current_stream().synchronize()
+        with b["cv"]:
+            for peer, tag, t in sends:
+                b["mail"].setdefault((self.rank, peer, tag), []).append(t.clone())
+            b["cv"].notify_all()
+        for peer, tag, t in recvs:
+            with b["cv"]:
+                if not b["cv"].wait_for(lambda: b["mail"].get((peer, self.rank, tag)), timeout=120):
+                    raise TimeoutError("halo message did not arrive")
+                src = b["mail"][(peer, self.rank, tag)].pop(0)
+            t.copy_(src)
+        torch.cuda.synchronize()
+
+
+def test_device_buffer_exchange_two_threads(hrm):
+    """The decomposed driver with device-resident halo buffers (as with NCCL):
+    two rank threads, each with its own context and stream, equal one context."""
+    import threading
+    import torch
+    from paper_2208_04488_gb300 import decomp as dc
+    pr = P.interface_3d(24)
+    slabs = dc.partition(pr.n[-1], 2, True)
+    box = {"cv": threading.Condition(), "bar": threading.Barrier(2, timeout=120), "tau": [None, None], "mail": {}}
+    result, errors = {}, []
+
+    def rank_main(r):
+        try:
+            torch.cuda.set_device(0)
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                loc = hrm.Solver.from_problem(dc.local_problem(pr, slabs[r]),
+                                              params=hrm.params_default(cfl=pr.cfl, check=0, precision=hrm.FP32),
+                                              stream=stream)
+                run = dc.Decomposed(loc, slabs[r], _ThreadComm(r, 2, box), device_buffers=True)
+                run.step(4)
+                result[r] = run.owned_state()
+                loc.close()
+        except Exception as e:  # reported by the main thread
+            errors.append(e)
+            box["bar"].abort()
+
+    th = [threading.Thread(target=rank_main, args=(r,)) for r in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=300)
+    assert not errors, errors
+    got = np.concatenate([result[0], result[1]], axis=1)
+    ref, _ = _single(hrm, pr, hrm.FP32, 4)
+    np.testing.assert_array_equal(got, ref)
