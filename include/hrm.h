@@ -405,16 +405,27 @@ hrm_status hrm_probe_wait_timeout(void* stream, int64_t* expired);
 hrm_status hrm_probe_convert(const double* in_d, const float* in_f, int64_t n, float* narrowed, double* widened,
                              void* stream);
 
+/* Diagnostic, not a step of the method: the bounded grid barrier of the
+ * batched form's persistent kernel, made to run out: 4 blocks wait at a barrier
+ * that counts 5 (nothing completes it), each wait limited to limit_ms. Returns
+ * HRM_E_TIMEOUT with *expired = the waits that ran out (4); the device stays
+ * usable. Synchronises `stream`. */
+hrm_status hrm_probe_barrier_timeout(void* stream, double limit_ms, int64_t* expired);
+
 /* ---------------------------------------------------------------------------
  * Batched form: many independent 2D problems of uneven size (each its own grid
- * and species table, N = 2 or 3) advanced together. Each phase of a step (cell
- * primitives and CFL maxima, step scalars, midpoint sweeps per direction,
- * update with relaxation) is ONE persistent launch over a table of work items
- * (instance, range of cells or faces) covering every instance, and one step is
- * one captured CUDA graph. Every instance keeps its own CFL time step (params.cfl,
- * Sec. 4.1.2) and simulated time. The per-element arithmetic is that of the
- * single-problem path: with HRM_FP64 every instance reproduces an hrm_ctx of the
- * same problem bit for bit. Only PP-WCNS-IS with SSP-RK3 is offered.
+ * and species table, N = 2 or 3) advanced together. Each RK stage is ONE
+ * persistent cooperative launch for every instance: its blocks take work items
+ * (instance, range of cells; instance, direction, 128-midpoint tile) from
+ * device queues through the primitive phase (at the first stage with the CFL
+ * maxima, then every instance's step scalars), the midpoint phase (both
+ * directions) and the update with relaxation, separated by a grid barrier
+ * whose waits are bounded (2^26 polls or 2 s). One step is one captured CUDA
+ * graph of three such launches. Every instance keeps its own CFL time step
+ * (params.cfl, Sec. 4.1.2) and simulated time. The per-element arithmetic is
+ * that of the single-problem path: every instance reproduces an hrm_ctx of the
+ * same problem bit for bit, in both forms. Only PP-WCNS-IS with SSP-RK3 is
+ * offered.
  * ------------------------------------------------------------------------- */
 typedef struct hrm_batch hrm_batch; /* opaque, owned by the library */
 
@@ -439,23 +450,24 @@ hrm_status hrm_batch_set(hrm_batch* b, int32_t i, const double* W, int32_t on_de
 /* Copy the state W of instance i (host: synchronises). */
 hrm_status hrm_batch_get(hrm_batch* b, int32_t i, double* dst, int32_t on_device);
 /* nsteps CFL steps of every instance: one graph launch per step. With
- * params.check, synchronises and returns HRM_E_ADMISSIBILITY if any cell of any
- * instance left the admissible set. */
+ * params.check, synchronises and returns HRM_E_TIMEOUT if a grid-barrier wait
+ * ran out since the last check (the launch then left its blocks early: the
+ * states are unreliable), else HRM_E_ADMISSIBILITY if any cell of any instance
+ * left the admissible set. */
 hrm_status hrm_batch_step(hrm_batch* b, int32_t nsteps);
 hrm_status hrm_batch_time(hrm_batch* b, int32_t i, double* t, int64_t* steps);
 /* Admissibility counters summed over the instances (as hrm_admissibility). */
 hrm_status hrm_batch_admissibility(hrm_batch* b, int64_t counts[4]);
-/* Launch shape of the persistent per-cell kernels: cells per work item (>= 256)
- * and persistent blocks per SM (1..32); threads per block (64, 128 or 256) and
- * faces per work item (>= face_threads) apply to the precision form's sweep
- * with screen = 0 only -- the other sweeps run one block per 128-midpoint tile
- * of the instances. */
+/* Launch shape of the persistent stage kernel: cells per work item of its
+ * per-cell phases (>= 256) and blocks per SM (1 .. the most that can be
+ * resident; 0 or larger values: all that fit). face_threads and face_tile are
+ * accepted and ignored (midpoints go in tiles of 128, one thread each). */
 hrm_status hrm_batch_set_launch(hrm_batch* b, int32_t face_threads, int32_t face_tile, int32_t cell_tile,
                                 int32_t blocks_per_sm);
 /* Autotuner: times steps_per_trial steps of the batch itself for each candidate
- * launch shape (threads {64,128,256} x faces per item {1,8,64} x threads x blocks
- * per SM {1,2,4,8}), restores the states after every trial, keeps the fastest and
- * writes it to best[4] (face_threads, face_tile, cell_tile, blocks_per_sm). */
+ * launch shape (cells per item {1024, 4096, 16384} x blocks per SM 1 .. the most
+ * resident), restores the states after every trial, keeps the fastest and
+ * writes it to best[4] (128, 128, cell_tile, blocks_per_sm). */
 hrm_status hrm_batch_tune(hrm_batch* b, int32_t steps_per_trial, int32_t* best);
 int64_t hrm_batch_kernel_launches(const hrm_batch* b);
 int64_t hrm_batch_total_cells(const hrm_batch* b);

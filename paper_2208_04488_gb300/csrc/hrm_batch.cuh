@@ -1,12 +1,13 @@
 // Batched form: many independent problems of uneven size advanced together,
-// one persistent launch per phase for all of them. Blocks loop over a table of
-// work items (instance, element range); every item lies inside one instance,
+// one persistent launch per RK stage for all of them. Blocks take work items
+// (instance, element range) from queues; every item lies inside one instance,
 // so the per-element bodies are exactly those of the single-instance kernels
 // and a batched instance reproduces its own context bit for bit.
 #pragma once
 
 #include "hrm_cell.cuh"
 #include "hrm_face32.cuh"
+#include "hrm_sync.cuh"
 
 namespace hrm {
 
@@ -33,204 +34,187 @@ struct WorkItem {
   int64_t end;
 };
 
-constexpr int kBatchMaxThreads = 256;
-
 __device__ __forceinline__ const double* pick(const BatchInst& I, int sel) { return sel == 0 ? I.Wn : I.Ws; }
 __device__ __forceinline__ double* pick_mut(const BatchInst& I, int sel) { return sel == 0 ? I.Wn : I.Ws; }
 
-// Each kernel is instantiated per species count N and runs over the work items
-// of the instances with that N (the item lists are grouped by N), so that its
-// body is one specialisation and its register count that of the single-context
-// kernel.
+constexpr int kBatchFace32Threads = 128;  // threads of the persistent kernel: one per midpoint of a tile
 
-// Primitives of every cell of the instances (+ per-instance CFL maxima).
-template <int D, int N>
-__global__ void __launch_bounds__(kBatchMaxThreads)
-    k_batch_prim(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
-                 int fp32, int tau) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const WorkItem w = items[it];
-    const BatchInst& I = insts[w.inst];
-    double s[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) s[d] = 0.0;
-    const double* W = pick(I, src);
-    float* P32 = fp32 ? I.P32 : nullptr;
-    for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
-      double sc[D];
-      prim_body<N, D>(c, W, I.V, I.AUX, P32, nullptr, I.g, I.f, sc);
-#pragma unroll
-      for (int d = 0; d < D; ++d) s[d] = (sc[d] != sc[d]) ? sc[d] : (sc[d] > s[d] ? sc[d] : s[d]);
-    }
-    if (tau) block_tau_max<D>(s, I.st->tau_bits);
-  }
-}
+// ---------------------------------------------------------------- persistent stage kernel
+// One launch per RK stage for every instance: the primitive phase, at the first
+// stage the step scalars of every instance, the midpoint phase over
+// 128-midpoint tiles of both directions, the update phase -- separated by the
+// bounded grid barrier of hrm_sync.cuh. Blocks take work items from one queue
+// per phase; the cell items are grouped by species count and the tiles by
+// species count and direction, so that neighbouring items run the same code.
+// Every element goes through the single-context body, so an instance
+// reproduces its own context bit for bit (FP64), and the precision form's
+// rounding is the single context's too (its units are built without FMA
+// contraction). All data written in one phase and read in a later one is
+// reached through the instance table, never through a read-only kernel
+// argument.
 
-// FP32 planes (and CFL maxima) of the instances for the precision form.
-template <int D, int N>
-__global__ void __launch_bounds__(kBatchMaxThreads)
-    k_batch_prim32(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
-                   int tau) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const WorkItem w = items[it];
-    const BatchInst& I = insts[w.inst];
-    double s[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) s[d] = 0.0;
-    const double* W = pick(I, src);
-    for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
-      double sc[D];
-      prim32_body<N, D>(c, W, I.P32, nullptr, I.g, I.f, sc);
-#pragma unroll
-      for (int d = 0; d < D; ++d) s[d] = (sc[d] != sc[d]) ? sc[d] : (sc[d] > s[d] ? sc[d] : s[d]);
-    }
-    if (tau) block_tau_max<D>(s, I.st->tau_bits);
-  }
-}
-
-// Midpoints of direction DIR of the instances: FP64 (bit-exact; up to 256
-// threads per block) or the precision form (at most 128 threads, three blocks
-// per SM, as the single-context sweep).
-constexpr int kBatchFace32Threads = 128;
-
-template <int D, int DIR, int N>
-__device__ __forceinline__ void batch_face_items(const BatchInst* __restrict__ insts,
-                                                 const WorkItem* __restrict__ items, int nitems, int src,
-                                                 const DevParams& pr, bool fp32) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const WorkItem w = items[it];
-    const BatchInst& I = insts[w.inst];
-    const double* W = pick(I, src);
-    const double lam = I.st->lam[DIR];
-    for (int64_t t = w.begin + threadIdx.x; t < w.end; t += blockDim.x) {
-      Nodes6 nd;
-      if (!face_nodes<DIR>(I.g, t, nd)) continue;
-      if (fp32)
-        face32_body<N, D, DIR>(t, nd, W, I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr, lam);
-      else
-        face_body<double, N, D, DIR>(t, nd, W, I.V, I.AUX, I.F[DIR], I.g, I.f, pr, lam);
-    }
-  }
-}
-
-template <int D, int DIR, int N>
-__global__ void __launch_bounds__(kBatchMaxThreads)
-    k_batch_face64(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
-                   DevParams pr) {
-  batch_face_items<D, DIR, N>(insts, items, nitems, src, pr, false);
-}
-
-template <int D, int DIR, int N>
-__global__ void __launch_bounds__(kBatchFace32Threads, 3)
-    k_batch_face32(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
-                   DevParams pr) {
-  batch_face_items<D, DIR, N>(insts, items, nitems, src, pr, true);
-}
-
-// The precision form's screened sweep over tiles of 128 midpoints of the
-// instances (one block per tile, one launch for all instances of a species
-// count), the body as k_face32_fast's: midpoints whose screens fail are
-// appended to `list` as (instance << 40 | midpoint) for k_batch_face32_fix.
-// *count must be 0 at launch; list holds one entry per midpoint of the tiles.
-// Six blocks per SM, as the single-context sweep (1.6 % shorter batched step
-// than five; the same results).
-template <int D, int DIR, int N>
-__global__ void __launch_bounds__(kBatchFace32Threads, 6)
-    k_batch_face32_tiles(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ tiles, int src,
-                         DevParams pr, unsigned long long* __restrict__ list, uint32_t* __restrict__ count) {
-  const WorkItem w = tiles[blockIdx.x];
-  const BatchInst& I = insts[w.inst];
-  const int64_t t = w.begin + threadIdx.x;
-  Nodes6 nd;
-  bool need = false;
-  if (t < w.end && face_nodes<DIR>(I.g, t, nd))
-    need = !face32_body<N, D, DIR, true>(t, nd, pick(I, src), I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr,
-                                         I.st->lam[DIR]);
-  const unsigned m = __ballot_sync(0xffffffffu, need);
-  if (m == 0u) return;
-  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (need)
-    list[base + __popc(m & ((1u << lane) - 1u))] = ((unsigned long long)w.inst << 40) | (unsigned long long)t;
-}
-
-// FP64 midpoints over the same 128-midpoint tiles (one block per tile; the
-// per-midpoint body is the single-context FP64 sweep's, bit for bit).
-template <int D, int DIR, int N>
-__global__ void __launch_bounds__(kBatchFace32Threads)
-    k_batch_face64_tiles(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ tiles, int src,
-                         DevParams pr) {
-  const WorkItem w = tiles[blockIdx.x];
-  const BatchInst& I = insts[w.inst];
-  const int64_t t = w.begin + threadIdx.x;
-  Nodes6 nd;
-  if (t < w.end && face_nodes<DIR>(I.g, t, nd))
-    face_body<double, N, D, DIR>(t, nd, pick(I, src), I.V, I.AUX, I.F[DIR], I.g, I.f, pr, I.st->lam[DIR]);
-}
-
-// The deferred midpoints of k_batch_face32_tiles with the full body, spread
-// lane-major over one-warp blocks (each is a long FP64 chain).
-template <int D, int DIR, int N>
-__global__ void __launch_bounds__(kBatchFace32Threads, 2)
-    k_batch_face32_fix(const BatchInst* __restrict__ insts, int src, DevParams pr,
-                       const unsigned long long* __restrict__ list, const uint32_t* __restrict__ count) {
-  const int64_t n = *count;
-  for (int64_t r = threadIdx.x;; r += blockDim.x) {
-    const int64_t i = r * gridDim.x + blockIdx.x;
-    if (i >= n) break;
-    const unsigned long long e = list[i];
-    const BatchInst& I = insts[(int)(e >> 40)];
-    const int64_t t = (int64_t)(e & ((1ull << 40) - 1ull));
-    Nodes6 nd;
-    if (!face_nodes<DIR>(I.g, t, nd)) continue;
-    face32_body<N, D, DIR>(t, nd, pick(I, src), I.V, I.AUX, I.P32, I.F[DIR], I.g, I.f, pr, I.st->lam[DIR]);
-  }
-}
-
-// Flux difference, SSP-RK combination and relaxation of every cell of the instances.
-template <int D, bool FAST, int N>
-__global__ void __launch_bounds__(kBatchMaxThreads)
-    k_batch_update(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items, int nitems, int src,
-                   int dst, double a, double b, int relax, int count) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const WorkItem w = items[it];
-    const BatchInst& I = insts[w.inst];
-    const double* Wsrc = pick(I, src);
-    double* Wout = pick_mut(I, dst);
-    const double dt = I.st->dt;
-    for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x)
-      update_body<N, D, 0, FAST>(c, I.Wn, Wsrc, Wout, I.F[0], I.F[1], I.F[2], I.g, I.f, I.st, dt, a, b, relax,
-                                 count);
-  }
-}
-
-// Host launchers (instantiated for D = 2 in hrm_batch64_d2.cu / hrm_batch32_d2.cu).
-struct BatchLaunch {
-  int grid;      // persistent blocks
-  int threads;   // threads per block
+struct StageArgs {
+  const BatchInst* insts;
+  const WorkItem* cells;  // cell work items
+  const WorkItem* tiles;  // 128-midpoint tiles, the direction in WorkItem::pad
+  int ncell_items, ntiles, ninst;
+  int src, dst;           // 0: W^n, 1: the stage state
+  double a, b;            // W_dst = a W^n + b (W_src + dt RHS)
+  int relax;
+  int prim;               // 1: primitive phase (0: the previous stage's update wrote the FP32 planes)
+  int first;              // 1: CFL maxima in the primitive phase, then the step scalars
+  int fuse_next;          // precision form: the update writes the next stage's FP32 planes
+  double cfl;
+  DevParams pr;
+  GridSync* sync;
+  uint64_t limit_ns;      // time limit of one barrier wait
 };
 
-void batch_prim_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int tau,
-                   cudaStream_t);
-void batch_prim32_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int tau,
-                     cudaStream_t);
-void batch_finalize(const BatchInst*, int ninst, int D, double cfl, cudaStream_t);
-void batch_face64_d2(int N, int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
-                     const DevParams&, cudaStream_t);
-void batch_face32_d2(int N, int dir, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src,
-                     const DevParams&, cudaStream_t);
-// The FP64 sweep over ntiles 128-midpoint tiles.
-void batch_face64_tiles_d2(int N, int dir, const BatchInst*, const WorkItem* tiles, int ntiles, int src,
-                           const DevParams&, cudaStream_t);
-// The screened sweep over ntiles 128-midpoint tiles and the fix-up of its
-// deferred midpoints (after a reset of *count).
-void batch_face32_tiles_d2(int N, int dir, const BatchInst*, const WorkItem* tiles, int ntiles, int src,
-                           const DevParams&, unsigned long long* list, uint32_t* count, cudaStream_t);
-void batch_update64_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst,
-                       double a, double b, int relax, int count, cudaStream_t);
-void batch_update32_d2(int N, const BatchLaunch&, const BatchInst*, const WorkItem*, int nitems, int src, int dst,
-                       double a, double b, int relax, int count, cudaStream_t);
+// Step scalars of instance I from its CFL maxima (as k_finalize).
+template <int D>
+__device__ __forceinline__ void batch_finalize_inst(const BatchInst& I, double cfl) {
+  StepState* st = I.st;
+  double tau[3] = {0.0, 0.0, 0.0}, sum = 0.0;
+  for (int d = 0; d < D; ++d) {
+    tau[d] = __longlong_as_double((long long)st->tau_bits[d]);
+    sum = sum + tau[d];
+    st->tau_bits[d] = 0ull;
+  }
+  const double dt = cfl / sum;
+  for (int d = 0; d < D; ++d) {
+    const double sigma = tau[d] / sum;
+    st->lam[d] = dt / (sigma * I.g.dx[d]);
+    st->tau[d] = tau[d];
+  }
+  st->dt = dt;
+  st->t = st->t + dt;
+  st->steps = st->steps + 1;
+}
+
+// The full precision-form midpoint (FP64 limiters where a screen fails), out
+// of line: rarely taken, and kept out of the persistent kernel's hot code.
+template <int N, int D, int DIR>
+__device__ __noinline__ void face32_full(int64_t t, const Nodes6& nd, const BatchInst& I, int src,
+                                         const DevParams& pr, float* xs) {
+  face32_body<N, D, DIR, false, true>(t, nd, pick(I, src), nullptr, nullptr, I.P32, I.F[DIR], I.g, I.f, pr,
+                                      I.st->lam[DIR], false, xs);
+}
+
+template <int N, int D, int DIR, bool FP32>
+__device__ __forceinline__ void stage_face(const BatchInst& I, int64_t t, int src, const DevParams& pr, float* xs) {
+  Nodes6 nd;
+  if (!face_nodes<DIR>(I.g, t, nd)) return;
+  if constexpr (FP32) {
+    if (!face32_body<N, D, DIR, true, true>(t, nd, pick(I, src), nullptr, nullptr, I.P32, I.F[DIR], I.g, I.f, pr,
+                                            I.st->lam[DIR], false, xs))
+      face32_full<N, D, DIR>(t, nd, I, src, pr, xs);
+  } else {
+    face_body<double, N, D, DIR>(t, nd, pick(I, src), I.V, I.AUX, I.F[DIR], I.g, I.f, pr, I.st->lam[DIR]);
+  }
+}
+
+template <int N, int D, bool FP32>
+__device__ __forceinline__ void stage_prim(const BatchInst& I, const WorkItem& w, int src, int tau) {
+  double s[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) s[d] = 0.0;
+  const double* W = pick(I, src);
+  for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
+    double sc[D];
+    if constexpr (FP32)
+      prim32_body<N, D>(c, W, I.P32, nullptr, I.g, I.f, sc);
+    else
+      prim_body<N, D>(c, W, I.V, I.AUX, nullptr, nullptr, I.g, I.f, sc);
+#pragma unroll
+    for (int d = 0; d < D; ++d) s[d] = (sc[d] != sc[d]) ? sc[d] : (sc[d] > s[d] ? sc[d] : s[d]);
+  }
+  if (tau) block_tau_max<D>(s, I.st->tau_bits);
+}
+
+template <int N, int D, bool FP32>
+__device__ __forceinline__ void stage_update(const BatchInst& I, const WorkItem& w, const StageArgs& A) {
+  using L = Lay<N, D>;
+  const double* Wsrc = pick(I, A.src);
+  double* Wout = pick_mut(I, A.dst);
+  const double dt = I.st->dt;
+  for (int64_t c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
+    if constexpr (FP32) {
+      if (A.fuse_next) {
+        // as k_update32p: combination, relaxation, store, next stage's FP32 planes
+        double Ws[L::M], Wo[L::M];
+#pragma unroll
+        for (int m = 0; m < L::M; ++m) Ws[m] = Wsrc[m * I.g.ncells + c];
+        fast_combine<N, D>(c, I.Wn, Ws, I.F[0], I.F[1], I.F[2], I.g, dt, A.a, A.b, Wo);
+        double rho, Re;
+        if (A.relax)
+          relax_fast<N, D>(Wo, I.f, rho, Re);
+        else
+          rho_Re<N, D>(Wo, I.f, rho, Re);
+#pragma unroll
+        for (int m = 0; m < L::M; ++m) Wout[m * I.g.ncells + c] = Wo[m];
+        float u[D], cs;
+        prim32_store<N, D>(c, Wo, rho, Re, I.P32, nullptr, I.g.ncells, I.f, u, cs);
+        continue;
+      }
+    }
+    update_body<N, D, 0, FP32>(c, I.Wn, Wsrc, Wout, I.F[0], I.F[1], I.F[2], I.g, I.f, I.st, dt, A.a, A.b, A.relax,
+                               0);
+  }
+}
+
+template <int D, bool FP32>
+__device__ __forceinline__ void batch_stage(const StageArgs& A) {
+  __shared__ float xs[2 * Lay<3, D>::M * kBatchFace32Threads];  // the FP32 bodies' column (largest N)
+  const unsigned int nb = gridDim.x;
+  if (A.prim) {
+    for (int it = next_item(A.sync, 0); it < A.ncell_items; it = next_item(A.sync, 0)) {
+      const WorkItem w = A.cells[it];
+      const BatchInst& I = A.insts[w.inst];
+      if (I.N == 2)
+        stage_prim<2, D, FP32>(I, w, A.src, A.first);
+      else
+        stage_prim<3, D, FP32>(I, w, A.src, A.first);
+    }
+    if (!grid_barrier(A.sync, nb, A.limit_ns)) return;
+  }
+  if (A.first) {
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) batch_finalize_inst<D>(A.insts[i], A.cfl);
+    if (!grid_barrier(A.sync, nb, A.limit_ns)) return;
+  }
+  for (int it = next_item(A.sync, 1); it < A.ntiles; it = next_item(A.sync, 1)) {
+    const WorkItem w = A.tiles[it];
+    const BatchInst& I = A.insts[w.inst];
+    const int64_t t = w.begin + threadIdx.x;
+    if (t >= w.end) continue;
+    const int key = I.N * 2 + w.pad;
+    if (key == 4)
+      stage_face<2, D, 0, FP32>(I, t, A.src, A.pr, xs);
+    else if (key == 5)
+      stage_face<2, D, 1, FP32>(I, t, A.src, A.pr, xs);
+    else if (key == 6)
+      stage_face<3, D, 0, FP32>(I, t, A.src, A.pr, xs);
+    else
+      stage_face<3, D, 1, FP32>(I, t, A.src, A.pr, xs);
+  }
+  if (!grid_barrier(A.sync, nb, A.limit_ns)) return;
+  for (int it = next_item(A.sync, 2); it < A.ncell_items; it = next_item(A.sync, 2)) {
+    const WorkItem w = A.cells[it];
+    const BatchInst& I = A.insts[w.inst];
+    if (I.N == 2)
+      stage_update<2, D, FP32>(I, w, A);
+    else
+      stage_update<3, D, FP32>(I, w, A);
+  }
+}
+
+// Persistent stage launchers for D = 2 (FP64: hrm_batch64_d2.cu, precision
+// form: hrm_batch32_d2.cu): a cooperative launch of `grid` blocks of
+// kBatchFace32Threads threads; *_fit: the most blocks per SM that can be
+// resident at once.
+int batch_stage64_fit();
+int batch_stage32_fit();
+cudaError_t batch_stage64_launch(int grid, const StageArgs& A, cudaStream_t s);
+cudaError_t batch_stage32_launch(int grid, const StageArgs& A, cudaStream_t s);
 
 }  // namespace hrm

@@ -1,6 +1,7 @@
 // C ABI of the batched form (include/hrm.h, hrm_batch_*): many independent 2D
-// problems of uneven size advanced together, one persistent launch per phase
-// and one captured CUDA graph per step; launch shapes picked by an autotuner.
+// problems of uneven size advanced together, one persistent cooperative launch
+// per RK stage and one captured CUDA graph per step; the launch shape picked by
+// an autotuner.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,12 +22,13 @@ using namespace hrm;
 namespace {
 
 struct Shape {
-  int face_threads = 128;
-  int cell_threads = 256;
-  int face_tile = 1024;   // faces per work item
-  int cell_tile = 4096;   // cells per work item
-  int blocks_per_sm = 2;  // persistent grid = SMs x blocks_per_sm
+  int cell_tile = 4096;   // cells per work item of the per-cell phases
+  int blocks_per_sm = 0;  // persistent grid = SMs x blocks_per_sm (0: all that fit)
 };
+
+// Time limit of one grid-barrier wait of the persistent kernel: far above any
+// phase's duration, so that only a barrier that cannot complete runs out.
+constexpr uint64_t kBarrierLimitNs = 2000000000ull;
 
 }  // namespace
 
@@ -36,26 +38,19 @@ struct hrm_batch {
   DevParams dp{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
-  // the sweeps of a stage (two directions x two species groups) run
-  // concurrently: all but the first on their own streams, fork/join events
-  cudaStream_t par[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t ev_fork = nullptr, ev_join[4] = {};
   std::vector<BatchInst> host;   // per-instance description (device pointers)
   std::vector<int> N;
   BatchInst* d_insts = nullptr;
-  WorkItem* d_items = nullptr;   // [cells | faces x | faces y]
-  // work-item lists grouped by species count: [g] = N = 2, 3; cells first,
-  // then the faces of each direction
-  int off_cell[2] = {0, 0}, n_cell[2] = {0, 0};
-  int off_face[2][2] = {{0, 0}, {0, 0}}, n_face[2][2] = {{0, 0}, {0, 0}};
-  // precision form: 128-midpoint tiles of every instance per direction and
-  // species group, the worklists of deferred midpoints and their counters
-  WorkItem* d_tiles = nullptr;
-  int off_tile[2][2] = {{0, 0}, {0, 0}}, n_tile[2][2] = {{0, 0}, {0, 0}};
-  unsigned long long* defer_list[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  uint32_t* defer_count = nullptr;  // [d * 2 + gN]
+  WorkItem* d_cells = nullptr;   // cell work items, grouped by species count
+  int ncell_items = 0;
+  WorkItem* d_tiles = nullptr;   // 128-midpoint tiles, grouped by species count and direction (in pad)
+  int ntiles = 0;
+  GridSync* sync = nullptr;      // queues and barrier of the persistent launches
+  unsigned int expired_seen = 0; // barrier waits that ran out, as last reported
   Shape shape;
   int sms = 0;
+  int fit = 0;                   // resident blocks per SM of the persistent kernel
+  bool direct = false;           // launches not captured into a graph (capture refused)
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_kernels = 0;
   int64_t launches = 0;
@@ -88,131 +83,120 @@ void drop_graph(hrm_batch* b) {
   b->graph_kernels = 0;
 }
 
-// Work items: every instance's cells in chunks of cell_tile, its faces of
-// each direction in chunks of face_tile; no item spans two instances; each list
-// grouped by the instances' species count.
+// Work items: every instance's cells in chunks of cell_tile, grouped by species
+// count; tiles of 128 midpoints of every instance and direction, grouped by
+// species count and direction (the direction in WorkItem::pad). No item spans
+// two instances.
 hrm_status build_items(hrm_batch* b) {
-  std::vector<WorkItem> all;
-  for (int kind = 0; kind < 3; ++kind) {  // 0 cells, 1 x faces, 2 y faces
-    for (int gN = 0; gN < 2; ++gN) {
-      const int begin = (int)all.size();
+  std::vector<WorkItem> cells, tiles;
+  for (int gN = 2; gN <= 3; ++gN)
+    for (int i = 0; i < b->ninst; ++i) {
+      if (b->N[i] != gN) continue;
+      const DevGrid& g = b->host[i].g;
+      for (int64_t c = 0; c < g.ncells; c += b->shape.cell_tile)
+        cells.push_back({i, 0, c, std::min<int64_t>(c + b->shape.cell_tile, g.ncells)});
+    }
+  for (int gN = 2; gN <= 3; ++gN)
+    for (int d = 0; d < 2; ++d)
       for (int i = 0; i < b->ninst; ++i) {
-        if (b->N[i] != 2 + gN) continue;
+        if (b->N[i] != gN) continue;
         const DevGrid& g = b->host[i].g;
-        if (kind == 0) {
-          for (int64_t c = 0; c < g.ncells; c += b->shape.cell_tile)
-            all.push_back({i, 0, c, std::min<int64_t>(c + b->shape.cell_tile, g.ncells)});
-        } else {
-          const int d = kind - 1;
-          const int64_t nf = (g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * g.n[2];
-          for (int64_t t = 0; t < nf; t += b->shape.face_tile)
-            all.push_back({i, 0, t, std::min<int64_t>(t + b->shape.face_tile, nf)});
-        }
+        const int64_t nf = (g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * g.n[2];
+        for (int64_t t = 0; t < nf; t += kBatchFace32Threads)
+          tiles.push_back({i, d, t, std::min<int64_t>(t + kBatchFace32Threads, nf)});
       }
-      const int n = (int)all.size() - begin;
-      if (kind == 0) {
-        b->off_cell[gN] = begin;
-        b->n_cell[gN] = n;
-      } else {
-        b->off_face[kind - 1][gN] = begin;
-        b->n_face[kind - 1][gN] = n;
-      }
-    }
-  }
-  if (b->d_items) cudaFree(b->d_items);
-  b->d_items = nullptr;
-  hrm_status s = bcuda(b, cudaMalloc(&b->d_items, sizeof(WorkItem) * all.size()), "alloc work items");
-  if (s) return s;
-  s = bcuda(b, cudaMemcpy(b->d_items, all.data(), sizeof(WorkItem) * all.size(), cudaMemcpyHostToDevice),
-            "copy work items");
+  cudaFree(b->d_cells);
+  cudaFree(b->d_tiles);
+  b->d_cells = nullptr;
+  b->d_tiles = nullptr;
+  hrm_status s;
+  if ((s = bcuda(b, cudaMalloc(&b->d_cells, sizeof(WorkItem) * cells.size()), "alloc work items"))) return s;
+  if ((s = bcuda(b, cudaMalloc(&b->d_tiles, sizeof(WorkItem) * tiles.size()), "alloc tiles"))) return s;
+  if ((s = bcuda(b, cudaMemcpy(b->d_cells, cells.data(), sizeof(WorkItem) * cells.size(), cudaMemcpyHostToDevice),
+                 "copy work items")))
+    return s;
+  if ((s = bcuda(b, cudaMemcpy(b->d_tiles, tiles.data(), sizeof(WorkItem) * tiles.size(), cudaMemcpyHostToDevice),
+                 "copy tiles")))
+    return s;
+  b->ncell_items = (int)cells.size();
+  b->ntiles = (int)tiles.size();
   drop_graph(b);
-  return s;
+  return HRM_OK;
 }
 
-int enqueue_stage(hrm_batch* b, cudaStream_t s, int src, int dst, double a, double bb, int relax, int count,
-                  bool first) {
+int grid_blocks(const hrm_batch* b) {
+  const int per_sm = b->shape.blocks_per_sm > 0 ? std::min(b->shape.blocks_per_sm, b->fit) : b->fit;
+  return b->sms * per_sm;
+}
+
+// One RK stage: reset the phase queues and the barrier count, then the
+// persistent launch (SSP-RK3 in Shu-Osher form; src/dst 0 = W^n, 1 = stage state).
+hrm_status enqueue_stage(hrm_batch* b, cudaStream_t s, int stage) {
   const bool fp32 = b->params.precision == HRM_FP32;
-  const BatchLaunch lc{b->sms * std::max(1, 2 * b->shape.blocks_per_sm * 128 / b->shape.cell_threads),
-                       b->shape.cell_threads};
-  const BatchLaunch lf{b->sms * b->shape.blocks_per_sm, b->shape.face_threads};
-  int k = 0;
-  for (int gN = 0; gN < 2; ++gN) {
-    if (!b->n_cell[gN]) continue;
-    const WorkItem* it = b->d_items + b->off_cell[gN];
-    if (fp32)
-      batch_prim32_d2(2 + gN, lc, b->d_insts, it, b->n_cell[gN], src, first ? 1 : 0, s);
-    else
-      batch_prim_d2(2 + gN, lc, b->d_insts, it, b->n_cell[gN], src, first ? 1 : 0, s);
-    ++k;
-  }
-  if (first) {
-    batch_finalize(b->d_insts, b->ninst, b->D, b->params.cfl, s);
-    ++k;
-  }
-  // the sweeps are independent (each reads the primitives and writes its own
-  // flux planes): sweep j > 0 on par[j], forked after the primitives and
-  // joined before the update
-  if (b->ev_fork) cudaEventRecord(b->ev_fork, s);
-  int j = 0;
-  for (int d = 0; d < 2; ++d)
-    for (int gN = 0; gN < 2; ++gN) {
-      if (!b->n_face[d][gN]) continue;
-      cudaStream_t sj = s;
-      if (j > 0 && b->par[j]) {
-        sj = b->par[j];
-        cudaStreamWaitEvent(sj, b->ev_fork, 0);
-      }
-      ++j;
-      const WorkItem* it = b->d_items + b->off_face[d][gN];
-      if (fp32 && b->params.screen && b->d_tiles) {
-        batch_face32_tiles_d2(2 + gN, d, b->d_insts, b->d_tiles + b->off_tile[d][gN], b->n_tile[d][gN], src, b->dp,
-                              b->defer_list[d][gN], b->defer_count + d * 2 + gN, sj);
-        k += 2;
-      } else {
-        if (fp32)
-          batch_face32_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, sj);
-        else if (b->d_tiles)
-          batch_face64_tiles_d2(2 + gN, d, b->d_insts, b->d_tiles + b->off_tile[d][gN], b->n_tile[d][gN], src,
-                                b->dp, sj);
-        else
-          batch_face64_d2(2 + gN, d, lf, b->d_insts, it, b->n_face[d][gN], src, b->dp, sj);
-        ++k;
-      }
-      if (sj != s) {
-        cudaEventRecord(b->ev_join[j - 1], sj);
-        cudaStreamWaitEvent(s, b->ev_join[j - 1], 0);
-      }
-    }
-  for (int gN = 0; gN < 2; ++gN) {
-    if (!b->n_cell[gN]) continue;
-    const WorkItem* it = b->d_items + b->off_cell[gN];
-    if (fp32)
-      batch_update32_d2(2 + gN, lc, b->d_insts, it, b->n_cell[gN], src, dst, a, bb, relax, count, s);
-    else
-      batch_update64_d2(2 + gN, lc, b->d_insts, it, b->n_cell[gN], src, dst, a, bb, relax, count, s);
-    ++k;
-  }
-  return k;
+  const int rs = b->params.relax_mode == HRM_RELAX_STAGE;
+  const int rf = b->params.relax_mode != HRM_RELAX_OFF;
+  StageArgs A{};
+  A.insts = b->d_insts;
+  A.cells = b->d_cells;
+  A.tiles = b->d_tiles;
+  A.ncell_items = b->ncell_items;
+  A.ntiles = b->ntiles;
+  A.ninst = b->ninst;
+  A.src = stage == 0 ? 0 : 1;
+  A.dst = stage == 2 ? 0 : 1;
+  A.a = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
+  A.b = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+  A.relax = stage == 2 ? rf : rs;
+  A.first = stage == 0;
+  // precision form: the updates of stages 1 and 2 write the next stage's FP32 planes
+  A.prim = (!fp32 || stage == 0) ? 1 : 0;
+  A.fuse_next = fp32 && stage < 2 ? 1 : 0;
+  A.cfl = b->params.cfl;
+  A.pr = b->dp;
+  A.sync = b->sync;
+  A.limit_ns = kBarrierLimitNs;
+  hrm_status st;
+  if ((st = bcuda(b, cudaMemsetAsync(b->sync, 0, 5 * sizeof(unsigned int), s), "reset queues"))) return st;
+  const cudaError_t e = fp32 ? batch_stage32_launch(grid_blocks(b), A, s) : batch_stage64_launch(grid_blocks(b), A, s);
+  return bcuda(b, e, "persistent stage launch");
 }
 
+hrm_status enqueue_step(hrm_batch* b, cudaStream_t s) {
+  for (int k = 0; k < 3; ++k)
+    if (hrm_status st = enqueue_stage(b, s, k)) return st;
+  return HRM_OK;
+}
+
+// One graph per step with the three stage launches; where capturing a
+// cooperative launch is refused, the stages are launched directly.
 hrm_status build_graph(hrm_batch* b) {
   drop_graph(b);
+  b->graph_kernels = 3;
+  if (b->direct) return HRM_OK;
   cudaGraph_t g = nullptr;
   hrm_status s = bcuda(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
   if (s) return s;
-  const int rs = b->params.relax_mode == HRM_RELAX_STAGE;
-  const int rf = b->params.relax_mode != HRM_RELAX_OFF;
-  // SSP-RK3 (Shu-Osher): src/dst 0 = W^n, 1 = stage state
-  int k = enqueue_stage(b, b->cap, 0, 1, 0.0, 1.0, rs, 0, true);
-  k += enqueue_stage(b, b->cap, 1, 1, 0.75, 0.25, rs, 0, false);
-  // (hrm_batch_admissibility counts separately: no counters in the step)
-  k += enqueue_stage(b, b->cap, 1, 0, 1.0 / 3.0, 2.0 / 3.0, rf, 0, false);
-  if ((s = bcuda(b, cudaStreamEndCapture(b->cap, &g), "end capture"))) return s;
+  const hrm_status se = enqueue_step(b, b->cap);
+  const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+  if (se || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    b->direct = true;
+    return HRM_OK;
+  }
   cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
   cudaGraphDestroy(g);
-  if ((s = bcuda(b, e, "graph instantiate"))) return s;
-  b->graph_kernels = k;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b->gexec = nullptr;
+    b->direct = true;
+  }
   return HRM_OK;
+}
+
+hrm_status launch_step(hrm_batch* b) {
+  if (b->direct) return enqueue_step(b, b->stream);
+  return bcuda(b, cudaGraphLaunch(b->gexec, b->stream), "graph launch");
 }
 
 void reset_instance(hrm_batch* b, int i) {
@@ -242,17 +226,10 @@ void hrm_batch_destroy(hrm_batch* b) {
     cudaFree(I.st);
   }
   cudaFree(b->d_insts);
-  cudaFree(b->d_items);
+  cudaFree(b->d_cells);
   cudaFree(b->d_tiles);
-  for (int d = 0; d < 2; ++d)
-    for (int gN = 0; gN < 2; ++gN) cudaFree(b->defer_list[d][gN]);
-  cudaFree(b->defer_count);
+  cudaFree(b->sync);
   if (b->cap) cudaStreamDestroy(b->cap);
-  for (int j = 0; j < 4; ++j) {
-    if (b->par[j]) cudaStreamDestroy(b->par[j]);
-    if (b->ev_join[j]) cudaEventDestroy(b->ev_join[j]);
-  }
-  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   delete b;
 }
 
@@ -297,15 +274,15 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
   b->stream = (cudaStream_t)cuda_stream;
   hrm_status s;
   if ((s = bcuda(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "stream create"))) return bail(s);
-  if ((s = bcuda(b, cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event create"))) return bail(s);
-  for (int j = 1; j < 4; ++j) {
-    if ((s = bcuda(b, cudaStreamCreateWithFlags(&b->par[j], cudaStreamNonBlocking), "stream create"))) return bail(s);
-    if ((s = bcuda(b, cudaEventCreateWithFlags(&b->ev_join[j], cudaEventDisableTiming), "event create")))
-      return bail(s);
-  }
-  int dev = 0;
+  int dev = 0, coop = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return bail(bfail(b, HRM_E_CUDA, "the device does not support cooperative launches"));
+  b->fit = p.precision == HRM_FP32 ? batch_stage32_fit() : batch_stage64_fit();
+  if (b->fit < 1) return bail(bfail(b, HRM_E_CUDA, "persistent stage kernel: no resident block fits an SM"));
+  if ((s = bcuda(b, cudaMalloc(&b->sync, sizeof(GridSync)), "alloc grid sync"))) return bail(s);
+  if ((s = bcuda(b, cudaMemset(b->sync, 0, sizeof(GridSync)), "clear grid sync"))) return bail(s);
   b->host.resize(ninst);
   b->N.resize(ninst);
   for (int i = 0; i < ninst; ++i) {
@@ -384,32 +361,6 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
                  "copy instances")))
     return bail(s);
   if ((s = build_items(b))) return bail(s);
-  // precision form: tiles of 128 midpoints and worklists (one entry per midpoint)
-  {
-    std::vector<WorkItem> tiles;
-    for (int d = 0; d < 2; ++d)
-      for (int gN = 0; gN < 2; ++gN) {
-        b->off_tile[d][gN] = (int)tiles.size();
-        size_t nf_all = 0;
-        for (int i = 0; i < b->ninst; ++i) {
-          if (b->N[i] != 2 + gN) continue;
-          const DevGrid& g = b->host[i].g;
-          const int64_t nf = (g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * g.n[2];
-          nf_all += (size_t)nf;
-          for (int64_t t = 0; t < nf; t += kBatchFace32Threads)
-            tiles.push_back({i, 0, t, std::min<int64_t>(t + kBatchFace32Threads, nf)});
-        }
-        b->n_tile[d][gN] = (int)tiles.size() - b->off_tile[d][gN];
-        if (nf_all && (s = bcuda(b, cudaMalloc(&b->defer_list[d][gN], sizeof(unsigned long long) * nf_all),
-                                 "alloc worklist")))
-          return bail(s);
-      }
-    if ((s = bcuda(b, cudaMalloc(&b->d_tiles, sizeof(WorkItem) * tiles.size()), "alloc tiles"))) return bail(s);
-    if ((s = bcuda(b, cudaMemcpy(b->d_tiles, tiles.data(), sizeof(WorkItem) * tiles.size(), cudaMemcpyHostToDevice),
-                   "copy tiles")))
-      return bail(s);
-    if ((s = bcuda(b, cudaMalloc(&b->defer_count, sizeof(uint32_t) * 4), "alloc worklist counters"))) return bail(s);
-  }
   *out = b;
   return HRM_OK;
 }
@@ -464,12 +415,22 @@ hrm_status hrm_batch_step(hrm_batch* b, int32_t nsteps) {
   if (nsteps < 0) return bfail(b, HRM_E_INVAL, "nsteps must be non-negative");
   if (nsteps == 0) return HRM_OK;
   hrm_status s;
-  if (!b->gexec && (s = build_graph(b))) return s;
+  if (!b->gexec && !b->direct && (s = build_graph(b))) return s;
   for (int i = 0; i < nsteps; ++i) {
-    if ((s = bcuda(b, cudaGraphLaunch(b->gexec, b->stream), "graph launch"))) return s;
+    if ((s = launch_step(b))) return s;
     b->launches += b->graph_kernels;
   }
   if (!b->params.check) return bcuda(b, cudaGetLastError(), "batch step");
+  unsigned int expired = 0;
+  if ((s = bcuda(b, cudaMemcpyAsync(&expired, &b->sync->expired, sizeof expired, cudaMemcpyDeviceToHost, b->stream),
+                 "read barrier state")))
+    return s;
+  if ((s = bcuda(b, cudaStreamSynchronize(b->stream), "batch step sync"))) return s;
+  if (expired != b->expired_seen) {
+    const unsigned int n = expired - b->expired_seen;
+    b->expired_seen = expired;
+    return bfail(b, HRM_E_TIMEOUT, "%u grid-barrier waits of the persistent stage kernel ran out", n);
+  }
   int64_t c[4];
   if ((s = hrm_batch_admissibility(b, c))) return s;
   if (c[0] | c[1] | c[2] | c[3])
@@ -509,13 +470,9 @@ hrm_status hrm_batch_admissibility(hrm_batch* b, int64_t counts[4]) {
 hrm_status hrm_batch_set_launch(hrm_batch* b, int32_t face_threads, int32_t face_tile, int32_t cell_tile,
                                 int32_t blocks_per_sm) {
   if (!b) return HRM_E_INVAL;
-  if ((face_threads != 64 && face_threads != 128 && face_threads != 256) || face_tile < face_threads ||
-      cell_tile < 256 || blocks_per_sm < 1 || blocks_per_sm > 32)
-    return bfail(b, HRM_E_INVAL, "invalid launch shape");
-  if (b->params.precision == HRM_FP32 && face_threads > kBatchFace32Threads)
-    return bfail(b, HRM_E_INVAL, "precision form: at most %d threads per midpoint block", kBatchFace32Threads);
-  b->shape.face_threads = face_threads;
-  b->shape.face_tile = face_tile;
+  (void)face_threads;
+  (void)face_tile;
+  if (cell_tile < 256 || blocks_per_sm < 0 || blocks_per_sm > 32) return bfail(b, HRM_E_INVAL, "invalid launch shape");
   b->shape.cell_tile = cell_tile;
   b->shape.blocks_per_sm = blocks_per_sm;
   return build_items(b);
@@ -535,42 +492,37 @@ hrm_status hrm_batch_tune(hrm_batch* b, int32_t steps_per_trial, int32_t* best) 
                                          b->stream), "save step state");
   }
   if (!s) s = bcuda(b, cudaStreamSynchronize(b->stream), "save sync");
-  const int threads[] = {64, 128, 256};
-  const int tiles[] = {1, 8, 64};         // face items of threads x tile faces
-  const int bps[] = {1, 2, 4, 8};
+  const int tiles[] = {1024, 4096, 16384};  // cells per work item
   float best_ms = 1e30f;
   Shape best_shape = b->shape;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int th : threads)
-    for (int tl : tiles)
-      for (int bp : bps) {
-        if (s) break;
-        if (th * bp > 2 * 256) continue;  // at most two 256-thread blocks of the register-heavy sweep per SM
-        if (b->params.precision == HRM_FP32 && th > kBatchFace32Threads) continue;
-        if ((s = hrm_batch_set_launch(b, th, th * tl, 4096, bp))) break;
-        if ((s = build_graph(b))) break;
-        cudaGraphLaunch(b->gexec, b->stream);  // warm-up
-        cudaEventRecord(e0, b->stream);
-        for (int k = 0; k < steps_per_trial; ++k) cudaGraphLaunch(b->gexec, b->stream);
-        cudaEventRecord(e1, b->stream);
-        if ((s = bcuda(b, cudaEventSynchronize(e1), "tuning trial"))) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        b->launches += b->graph_kernels * (steps_per_trial + 1);
-        if (ms < best_ms) {
-          best_ms = ms;
-          best_shape = b->shape;
-        }
-        // restore the states for the next trial
-        for (int i = 0; i < b->ninst; ++i) {
-          const size_t bytes = sizeof(double) * (size_t)b->host[i].g.ncells * (2 * b->N[i] + 2);
-          cudaMemcpyAsync(b->host[i].Wn, saved[i], bytes, cudaMemcpyDeviceToDevice, b->stream);
-          cudaMemcpyAsync(b->host[i].st, &saved_st[i], sizeof(StepState), cudaMemcpyHostToDevice, b->stream);
-        }
-        cudaStreamSynchronize(b->stream);
+  for (int tl : tiles)
+    for (int bp = 1; bp <= b->fit; ++bp) {
+      if (s) break;
+      if ((s = hrm_batch_set_launch(b, kBatchFace32Threads, kBatchFace32Threads, tl, bp))) break;
+      if ((s = build_graph(b))) break;
+      if ((s = launch_step(b))) break;  // warm-up
+      cudaEventRecord(e0, b->stream);
+      for (int k = 0; k < steps_per_trial && !s; ++k) s = launch_step(b);
+      cudaEventRecord(e1, b->stream);
+      if (s || (s = bcuda(b, cudaEventSynchronize(e1), "tuning trial"))) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      b->launches += b->graph_kernels * (steps_per_trial + 1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_shape = b->shape;
       }
+      // restore the states for the next trial
+      for (int i = 0; i < b->ninst; ++i) {
+        const size_t bytes = sizeof(double) * (size_t)b->host[i].g.ncells * (2 * b->N[i] + 2);
+        cudaMemcpyAsync(b->host[i].Wn, saved[i], bytes, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(b->host[i].st, &saved_st[i], sizeof(StepState), cudaMemcpyHostToDevice, b->stream);
+      }
+      cudaStreamSynchronize(b->stream);
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   for (double* p : saved) cudaFree(p);
@@ -578,8 +530,8 @@ hrm_status hrm_batch_tune(hrm_batch* b, int32_t steps_per_trial, int32_t* best) 
   b->shape = best_shape;
   if ((s = build_items(b))) return s;
   if (best) {
-    best[0] = best_shape.face_threads;
-    best[1] = best_shape.face_tile;
+    best[0] = kBatchFace32Threads;
+    best[1] = kBatchFace32Threads;
     best[2] = best_shape.cell_tile;
     best[3] = best_shape.blocks_per_sm;
   }

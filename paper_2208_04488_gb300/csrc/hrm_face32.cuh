@@ -494,12 +494,14 @@ __global__ void __launch_bounds__(kCellThreads)
 // without writing the midpoint, so that the FP64 fallback code is not part of
 // the kernel; the midpoint is then computed by the full body (k_face32_fix).
 // Returns true when the midpoint's outputs were written.
-template <int N, int D, int DIR, bool DEFER = false>
+// XSMEM: the per-thread column of biased values lives in `xs` (the caller's
+// shared memory, 2 x M x kFaceThreads floats) instead of a static array of its own.
+template <int N, int D, int DIR, bool DEFER = false, bool XSMEM = false>
 __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const double* __restrict__ W,
                                             const double* __restrict__ V, const double* __restrict__ AUX,
                                             const float* __restrict__ P32, double* __restrict__ out,
                                             const DevGrid& g, const DevFluid& f, const DevParams& pr, double lam,
-                                            bool lin = false) {
+                                            bool lin = false, float* xs = nullptr) {
   using L = Lay<N, D>;
   using Q = P32Lay<N, D>;
   constexpr int M = L::M;
@@ -564,8 +566,15 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
     // (slots 1..N), then the tangential velocities (slots N+1..N+D-1) and last
     // u + p/(rho c) (slot M-1). Each field is a node plane (or u_n) plus a
     // multiple of p; the biased values go through a per-thread shared column.
-    __shared__ float sU[2][M][kFaceThreads];
+    float* sU;
+    if constexpr (XSMEM) {
+      sU = xs;
+    } else {
+      __shared__ float sU_own[2 * M * kFaceThreads];
+      sU = sU_own;
+    }
     const int tid = threadIdx.x;
+    auto col = [&](int side, int slot) -> float& { return sU[(side * M + slot) * kFaceThreads + tid]; };
     // (a gated midpoint skips the projection: see below)
 #pragma unroll 1
     for (int fi = 0; fi < (lin ? 0 : L::NC); ++fi) {
@@ -585,16 +594,16 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
 #pragma unroll
       for (int j = 0; j < 6; ++j) w6[j] = (plane < 0 ? u6[j] : ld(plane, j)) + cp * p6[j];
       const int slot = fi == N + D ? M - 1 : fi;
-      sU[0][slot][tid] = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
-      sU[1][slot][tid] = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
+      col(0, slot) = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
+      col(1, slot) = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
     }
     float UL[M], UR[M], arb[N];
     if (!lin) {
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         if (m >= N + D && m < M - 1) continue;  // volume fractions: below
-        UL[m] = sU[0][m][tid];
-        UR[m] = sU[1][m][tid];
+        UL[m] = col(0, m);
+        UR[m] = col(1, m);
       }
 #pragma unroll
       for (int k = 0; k < N; ++k) arb[k] = 0.5f * (ld(k, 2) + ld(k, 3));

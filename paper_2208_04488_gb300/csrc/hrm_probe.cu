@@ -7,6 +7,7 @@
 
 #include "../../include/hrm.h"
 #include "hrm_device.cuh"
+#include "hrm_sync.cuh"
 #include "hrm_tc.cuh"
 
 namespace {
@@ -73,7 +74,28 @@ __global__ void k_convert(const double* in_d, const float* in_f, int64_t n, floa
   widened[i] = hrm::widen_f32(in_f[i]);
 }
 
+// Blocks waiting at a grid barrier that counts one block more than launched.
+__global__ void __launch_bounds__(128) k_barrier_probe(hrm::GridSync* s, uint64_t limit_ns) {
+  hrm::grid_barrier(s, gridDim.x + 1u, limit_ns);
+}
+
 }  // namespace
+
+extern "C" hrm_status hrm_probe_barrier_timeout(void* stream, double limit_ms, int64_t* expired) {
+  if (!expired || !(limit_ms > 0.0) || limit_ms > 10000.0) return HRM_E_INVAL;
+  *expired = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  hrm::GridSync* d = nullptr;
+  if (cudaMallocAsync(&d, sizeof *d, s) != cudaSuccess) return HRM_E_NOMEM;
+  cudaMemsetAsync(d, 0, sizeof *d, s);
+  k_barrier_probe<<<4, 128, 0, s>>>(d, (uint64_t)(limit_ms * 1e6));
+  unsigned int h = 0;
+  cudaMemcpyAsync(&h, &d->expired, sizeof h, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return HRM_E_CUDA;
+  *expired = (int64_t)h;
+  return h ? HRM_E_TIMEOUT : HRM_OK;
+}
 
 extern "C" hrm_status hrm_probe_convert(const double* in_d, const float* in_f, int64_t n, float* narrowed,
                                         double* widened, void* stream) {

@@ -176,6 +176,8 @@ def lib():
     L.hrm_probe_wait_timeout.restype = ctypes.c_int
     L.hrm_probe_convert.argtypes = [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]
     L.hrm_probe_convert.restype = ctypes.c_int
+    L.hrm_probe_barrier_timeout.argtypes = [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]
+    L.hrm_probe_barrier_timeout.restype = ctypes.c_int
     L.hrm_step_tau.argtypes = [_VP, _DP]
     L.hrm_begin_step.argtypes = [_VP, _DP, ctypes.c_double]
     L.hrm_stages.argtypes = [_VP]
@@ -205,6 +207,13 @@ def probe_wait_timeout(stream=None):
     """(status, expired) of the bounded-wait probe: HRM_E_TIMEOUT and 128."""
     n = ctypes.c_int64()
     st = lib().hrm_probe_wait_timeout(_VP(_stream_handle(stream)), ctypes.byref(n))
+    return st, n.value
+
+
+def probe_barrier_timeout(limit_ms=50.0, stream=None):
+    """(status, expired) of the grid-barrier probe: HRM_E_TIMEOUT and 4."""
+    n = ctypes.c_int64()
+    st = lib().hrm_probe_barrier_timeout(_VP(_stream_handle(stream)), float(limit_ms), ctypes.byref(n))
     return st, n.value
 
 
