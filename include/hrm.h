@@ -190,6 +190,23 @@ hrm_status hrm_dt(hrm_ctx* ctx, double cfl, double* dt_out, double* tau_out);
  * ran out (its gate bytes are then unreliable). */
 hrm_status hrm_step(hrm_ctx* ctx, double dt, int32_t nsteps);
 
+/* How hrm_step runs a step. path 0 (the default): the captured graph of
+ * per-phase kernels. path 1: where the context is in the precision form in 2D
+ * with PP-WCNS-IS, SSP-RK3, the five-equation CFL speed, no Dirichlet side and
+ * no learned gate, as three persistent cooperative launches of the batched
+ * form's stage kernel over this one context (one per RK stage, every phase in
+ * it; work items from device queues, phases separated by a bounded grid
+ * barrier; with params.check a barrier wait that ran out is returned as
+ * HRM_E_TIMEOUT); otherwise as path 0. Both give the same state bit for bit
+ * (path 1 is the slower one on a single large grid: its FP64-bound update runs
+ * under the midpoint body's register budget). With profiling on,
+ * hrm_profile_read reports the persistent step's phases (primitives, step
+ * scalars, midpoints of both directions, update) from %globaltimer stamps.
+ * hrm_step_launches: kernel launches per step of the current step graph (0
+ * before the first step). */
+hrm_status hrm_set_step_path(hrm_ctx* ctx, int32_t path);
+int32_t hrm_step_launches(const hrm_ctx* ctx);
+
 /* The same step taken one RK stage at a time, so that a caller can exchange
  * halo layers between stages and reduce the CFL maxima over several contexts
  * (domain decomposition: one context per subdomain, each holding its layers

@@ -2,6 +2,7 @@
 // graph and dispatch to the kernel tables.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -9,10 +10,12 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/hrm.h"
+#include "hrm_batch.cuh"
 #include "hrm_launch.h"
 #include "hrm_learned.h"
 
@@ -61,6 +64,17 @@ struct hrm_ctx {
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_kernels = 0;
   int64_t launches = 0;
+  // precision form in 2D: the step as three persistent stage launches (the
+  // batched form's kernel over this one context), else the per-phase graph
+  int step_path = 0;               // hrm_set_step_path: 1 persistent where eligible, 0 per-phase kernels
+  bool persist = false;            // the current graph is the persistent one
+  bool persist_refused = false;    // capturing the persistent launches failed once: per-phase graph
+  BatchInst* p_inst = nullptr;     // this context as a one-instance batch
+  WorkItem* p_cells = nullptr;
+  WorkItem* p_tiles = nullptr;
+  int p_ncell = 0, p_ntiles = 0, p_grid = 0;
+  GridSync* p_sync = nullptr;
+  unsigned int p_expired_seen = 0;
   // tracing: event pairs around every kernel of the captured step
   int profiling = 0;
   int nprof = 0;
@@ -331,9 +345,134 @@ int enqueue_step(hrm_ctx* c, cudaStream_t s) {
   return k;
 }
 
+// The persistent step applies to the precision form in 2D with PP-WCNS-IS,
+// SSP-RK3, the five-equation CFL speed, no Dirichlet sides and no learned gate.
+bool persistent_eligible(const hrm_ctx* c) {
+  const hrm_params& p = c->params;
+  return c->step_path == 1 && !c->persist_refused && p.precision == HRM_FP32 && c->D == 2 && c->nint == c->nc &&
+         !p.learned && p.scheme == HRM_SCHEME_WCNS && p.integrator == HRM_RK3 && !p.cfl_sound &&
+         (c->N == 2 || c->N == 3);
+}
+
+// Device tables of the persistent step: this context as one instance, its
+// cells in items of 1024, its midpoints of both directions in tiles of 128.
+hrm_status setup_persistent(hrm_ctx* c) {
+  if (c->p_inst) return HRM_OK;
+  BatchInst I;
+  std::memset(&I, 0, sizeof I);
+  I.g = c->dg;
+  I.f = c->fl;
+  I.N = c->N;
+  I.Wn = c->Wn;
+  I.Ws = c->Ws;
+  I.V = c->V;
+  I.AUX = c->AUX;
+  for (int d = 0; d < 3; ++d) I.F[d] = c->F[d];
+  I.P32 = c->P32;
+  I.st = c->st;
+  std::vector<WorkItem> cells, tiles;
+  constexpr int64_t kCellItem = 1024;
+  for (int64_t x = 0; x < c->nint; x += kCellItem) cells.push_back({0, 0, x, std::min<int64_t>(x + kCellItem, c->nint)});
+  for (int d = 0; d < 2; ++d) {
+    const int64_t nf = (c->dg.n[0] + (d == 0)) * (c->dg.n[1] + (d == 1));
+    for (int64_t t = 0; t < nf; t += kBatchFace32Threads)
+      tiles.push_back({0, d, t, std::min<int64_t>(t + kBatchFace32Threads, nf)});
+  }
+  hrm_status s;
+  if ((s = cuda_check(c, ctx_malloc(c, &c->p_inst, sizeof I), "alloc instance"))) return s;
+  if ((s = cuda_check(c, ctx_malloc(c, &c->p_cells, sizeof(WorkItem) * cells.size()), "alloc items"))) return s;
+  if ((s = cuda_check(c, ctx_malloc(c, &c->p_tiles, sizeof(WorkItem) * tiles.size()), "alloc tiles"))) return s;
+  if ((s = cuda_check(c, ctx_malloc(c, &c->p_sync, sizeof(GridSync)), "alloc grid sync"))) return s;
+  if ((s = cuda_check(c, cudaMemcpyAsync(c->p_inst, &I, sizeof I, cudaMemcpyHostToDevice, c->stream), "copy instance")))
+    return s;
+  if ((s = cuda_check(c, cudaMemcpyAsync(c->p_cells, cells.data(), sizeof(WorkItem) * cells.size(),
+                                         cudaMemcpyHostToDevice, c->stream), "copy items")))
+    return s;
+  if ((s = cuda_check(c, cudaMemcpyAsync(c->p_tiles, tiles.data(), sizeof(WorkItem) * tiles.size(),
+                                         cudaMemcpyHostToDevice, c->stream), "copy tiles")))
+    return s;
+  if ((s = cuda_check(c, cudaMemsetAsync(c->p_sync, 0, sizeof(GridSync), c->stream), "clear grid sync"))) return s;
+  if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "persistent set-up"))) return s;
+  c->p_ncell = (int)cells.size();
+  c->p_ntiles = (int)tiles.size();
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  c->p_grid = sms * batch_stage32_fit();
+  return c->p_grid > 0 ? HRM_OK : fail(c, HRM_E_CUDA, "persistent stage kernel: no resident block fits an SM");
+}
+
+// The three stage launches of one persistent step (SSP-RK3, Shu-Osher form).
+hrm_status enqueue_persistent_step(hrm_ctx* c, cudaStream_t s) {
+  const int rs = c->params.relax_mode == HRM_RELAX_STAGE;
+  const int rf = c->params.relax_mode != HRM_RELAX_OFF;
+  for (int k = 0; k < 3; ++k) {
+    StageArgs A{};
+    A.insts = c->p_inst;
+    A.cells = c->p_cells;
+    A.tiles = c->p_tiles;
+    A.ncell_items = c->p_ncell;
+    A.ntiles = c->p_ntiles;
+    A.ninst = 1;
+    A.src = k == 0 ? 0 : 1;
+    A.dst = k == 2 ? 0 : 1;
+    A.a = k == 0 ? 0.0 : (k == 1 ? 0.75 : 1.0 / 3.0);
+    A.b = k == 0 ? 1.0 : (k == 1 ? 0.25 : 2.0 / 3.0);
+    A.relax = k == 2 ? rf : rs;
+    A.first = k == 0;
+    A.prim = k == 0;
+    A.fuse_next = k < 2;
+    A.cfl = c->params.cfl;
+    A.pr = c->dp;
+    A.sync = c->p_sync;
+    A.limit_ns = 2000000000ull;
+    A.stage = k;
+    A.update = 1;
+    hrm_status st;
+    if ((st = cuda_check(c, cudaMemsetAsync(c->p_sync, 0, kResetWords * sizeof(unsigned int), s), "reset queues")))
+      return st;
+    if ((st = cuda_check(c, batch_stage32_launch(c->p_grid, A, s), "persistent stage launch"))) return st;
+  }
+  return HRM_OK;
+}
+
+// Capture the persistent step; false when the capture or instantiation was
+// refused (the per-phase graph is used from then on).
+bool build_persistent_graph(hrm_ctx* c) {
+  if (setup_persistent(c)) return false;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const hrm_status se = enqueue_persistent_step(c, c->cap);
+  const cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
+  if (se || ee != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  const cudaError_t e = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->gexec = nullptr;
+    return false;
+  }
+  c->graph_kernels = 3;
+  c->persist = true;
+  return true;
+}
+
 hrm_status build_graph(hrm_ctx* c) {
   drop_graph(c);
   c->nprof = 0;
+  c->persist = false;
+  if (persistent_eligible(c)) {
+    if (build_persistent_graph(c)) return HRM_OK;
+    c->persist_refused = true;
+    c->err.clear();
+  }
   cudaGraph_t g = nullptr;
   hrm_status s = cuda_check(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
   if (s) return s;
@@ -592,6 +731,10 @@ void hrm_destroy(hrm_ctx* c) {
   ctx_free(c, c->dg.oob);
   ctx_free(c, c->blob);
   for (int d = 0; d < 3; ++d) ctx_free(c, c->gate[d]);
+  ctx_free(c, c->p_inst);
+  ctx_free(c, c->p_cells);
+  ctx_free(c, c->p_tiles);
+  ctx_free(c, c->p_sync);
   for (int i = 0; i < 2 * kMaxProf; ++i)
     if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -604,6 +747,18 @@ void hrm_destroy(hrm_ctx* c) {
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
+}
+
+hrm_status hrm_set_step_path(hrm_ctx* c, int32_t path) {
+  if (!c || (path != 0 && path != 1)) return c ? fail(c, HRM_E_INVAL, "step path must be 0 or 1") : HRM_E_INVAL;
+  if (path != c->step_path) drop_graph(c);
+  c->step_path = path;
+  return HRM_OK;
+}
+
+int32_t hrm_step_launches(const hrm_ctx* c) {
+  if (!c) return 0;
+  return c->gexec ? (int32_t)c->graph_kernels : 0;
 }
 
 hrm_status hrm_set_profiling(hrm_ctx* c, int32_t on) {
@@ -622,6 +777,33 @@ hrm_status hrm_set_profiling(hrm_ctx* c, int32_t on) {
 int32_t hrm_profile_read(hrm_ctx* c, int32_t max, float* ms, int32_t* kind) {
   if (!c || !c->profiling || !c->gexec) return 0;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return 0;
+  if (c->persist) {
+    // phase brackets of the three stage launches from their %globaltimer stamps
+    unsigned long long st[3][5];
+    if (cudaMemcpy(st, c->p_sync->stamp, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    int n = 0;
+    auto put = [&](int k, unsigned long long a, unsigned long long b) {
+      if (n >= max) return;
+      if (ms) ms[n] = b > a ? (float)((double)(b - a) * 1e-6) : 0.f;
+      if (kind) kind[n] = k;
+      ++n;
+    };
+    for (int k = 0; k < 3; ++k) {
+      if (k == 0) {
+        put(HRM_KERNEL_PRIM, st[k][0], st[k][1]);
+        put(HRM_KERNEL_FINALIZE, st[k][1], st[k][2]);
+      }
+      // both directions' midpoints run in one phase
+      put(HRM_KERNEL_SWEEPS, st[k][2], st[k][3]);
+      put(HRM_KERNEL_FACE_X, st[k][2], st[k][3]);
+      put(HRM_KERNEL_FACE_X + 1, st[k][2], st[k][3]);
+      put(HRM_KERNEL_UPDATE, st[k][3], st[k][4]);
+    }
+    return n;
+  }
   const int n = c->nprof < max ? c->nprof : max;
   for (int i = 0; i < n; ++i) {
     float t = 0.f;
@@ -734,6 +916,22 @@ hrm_status hrm_step(hrm_ctx* c, double dt, int32_t nsteps) {
     c->launches += c->graph_kernels;
   }
   if (!c->params.check) return last_launch(c, "step");
+  if (c->persist) {
+    // the persistent step counts nothing itself: the final state's admissibility,
+    // and the grid-barrier waits that ran out
+    c->ck->admiss(c->Wn, c->dg, c->fl, c->st, c->stream);
+    ++c->launches;
+    unsigned int expired = 0;
+    if ((s = cuda_check(c, cudaMemcpyAsync(&expired, &c->p_sync->expired, sizeof expired, cudaMemcpyDeviceToHost,
+                                           c->stream), "read barrier state")))
+      return s;
+    if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "step sync"))) return s;
+    if (expired != c->p_expired_seen) {
+      const unsigned int n = expired - c->p_expired_seen;
+      c->p_expired_seen = expired;
+      return fail(c, HRM_E_TIMEOUT, "%u grid-barrier waits of the persistent step ran out", n);
+    }
+  }
   unsigned long long cnt[5];
   static_assert(offsetof(StepState, waits) == offsetof(StepState, counts) + 4 * sizeof(unsigned long long),
                 "wait counter follows the admissibility counters");

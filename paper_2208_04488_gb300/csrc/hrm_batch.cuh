@@ -68,9 +68,12 @@ struct StageArgs {
   DevParams pr;
   GridSync* sync;
   uint64_t limit_ns;      // time limit of one barrier wait
+  int stage;              // 0..2: slot of the phase stamps
+  int update;             // 1: the update phase runs in this launch (0: the caller runs it after)
 };
 
-// Step scalars of instance I from its CFL maxima (as k_finalize).
+// Step scalars of instance I from its CFL maxima (as k_finalize: a requested
+// step dt_req > 0 is taken as it is).
 template <int D>
 __device__ __forceinline__ void batch_finalize_inst(const BatchInst& I, double cfl) {
   StepState* st = I.st;
@@ -80,7 +83,7 @@ __device__ __forceinline__ void batch_finalize_inst(const BatchInst& I, double c
     sum = sum + tau[d];
     st->tau_bits[d] = 0ull;
   }
-  const double dt = cfl / sum;
+  const double dt = st->dt_req > 0.0 ? st->dt_req : cfl / sum;
   for (int d = 0; d < D; ++d) {
     const double sigma = tau[d] / sum;
     st->lam[d] = dt / (sigma * I.g.dx[d]);
@@ -166,6 +169,9 @@ template <int D, bool FP32>
 __device__ __forceinline__ void batch_stage(const StageArgs& A) {
   __shared__ float xs[2 * Lay<3, D>::M * kBatchFace32Threads];  // the FP32 bodies' column (largest N)
   const unsigned int nb = gridDim.x;
+  const bool stamper = blockIdx.x == 0 && threadIdx.x == 0;
+  unsigned long long* stamp = A.sync->stamp[A.stage];
+  if (stamper) stamp[0] = tc::global_ns();
   if (A.prim) {
     for (int it = next_item(A.sync, 0); it < A.ncell_items; it = next_item(A.sync, 0)) {
       const WorkItem w = A.cells[it];
@@ -177,11 +183,13 @@ __device__ __forceinline__ void batch_stage(const StageArgs& A) {
     }
     if (!grid_barrier(A.sync, nb, A.limit_ns)) return;
   }
+  if (stamper) stamp[1] = tc::global_ns();
   if (A.first) {
     if (blockIdx.x == 0)
       for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) batch_finalize_inst<D>(A.insts[i], A.cfl);
     if (!grid_barrier(A.sync, nb, A.limit_ns)) return;
   }
+  if (stamper) stamp[2] = tc::global_ns();
   for (int it = next_item(A.sync, 1); it < A.ntiles; it = next_item(A.sync, 1)) {
     const WorkItem w = A.tiles[it];
     const BatchInst& I = A.insts[w.inst];
@@ -197,14 +205,23 @@ __device__ __forceinline__ void batch_stage(const StageArgs& A) {
     else
       stage_face<3, D, 1, FP32>(I, t, A.src, A.pr, xs);
   }
-  if (!grid_barrier(A.sync, nb, A.limit_ns)) return;
-  for (int it = next_item(A.sync, 2); it < A.ncell_items; it = next_item(A.sync, 2)) {
-    const WorkItem w = A.cells[it];
-    const BatchInst& I = A.insts[w.inst];
-    if (I.N == 2)
-      stage_update<2, D, FP32>(I, w, A);
-    else
-      stage_update<3, D, FP32>(I, w, A);
+  if (A.update) {
+    if (!grid_barrier(A.sync, nb, A.limit_ns)) return;
+    if (stamper) stamp[3] = tc::global_ns();
+    for (int it = next_item(A.sync, 2); it < A.ncell_items; it = next_item(A.sync, 2)) {
+      const WorkItem w = A.cells[it];
+      const BatchInst& I = A.insts[w.inst];
+      if (I.N == 2)
+        stage_update<2, D, FP32>(I, w, A);
+      else
+        stage_update<3, D, FP32>(I, w, A);
+    }
+  }
+  // the last block to finish stamps the end of the launch
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&A.sync->done, 1u) == nb - 1u) stamp[4] = tc::global_ns();
   }
 }
 

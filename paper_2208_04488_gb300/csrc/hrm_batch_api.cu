@@ -155,8 +155,10 @@ hrm_status enqueue_stage(hrm_batch* b, cudaStream_t s, int stage) {
   A.pr = b->dp;
   A.sync = b->sync;
   A.limit_ns = kBarrierLimitNs;
+  A.stage = stage;
+  A.update = 1;
   hrm_status st;
-  if ((st = bcuda(b, cudaMemsetAsync(b->sync, 0, 5 * sizeof(unsigned int), s), "reset queues"))) return st;
+  if ((st = bcuda(b, cudaMemsetAsync(b->sync, 0, kResetWords * sizeof(unsigned int), s), "reset queues"))) return st;
   const cudaError_t e = fp32 ? batch_stage32_launch(grid_blocks(b), A, s) : batch_stage64_launch(grid_blocks(b), A, s);
   return bcuda(b, e, "persistent stage launch");
 }

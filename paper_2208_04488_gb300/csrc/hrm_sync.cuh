@@ -13,15 +13,19 @@
 
 namespace hrm {
 
-// Device state of one persistent launch; `queue` and `arrived` must be 0 at
-// launch (a memset node before each launch), `generation` may hold anything.
+// Device state of one persistent launch; the first kResetWords words (`queue`,
+// `arrived`, `done`) must be 0 at launch (a memset node before each launch),
+// `generation` may hold anything. `stamp` receives %globaltimer at the phase
+// boundaries of each stage's launch (profiling).
 struct GridSync {
   unsigned int queue[4];    // next work item of each phase
   unsigned int arrived;     // blocks at the current barrier
+  unsigned int done;        // blocks that finished the launch
   unsigned int generation;  // completed barriers
   unsigned int expired;     // barrier waits that ran out (accumulates over launches)
-  unsigned int pad;
+  unsigned long long stamp[3][5];  // per stage: start, after prim, after finalize, after midpoints, end
 };
+constexpr int kResetWords = 6;
 
 // Barrier of all `nblocks` blocks of the grid: every thread's earlier global
 // writes are visible to every thread after it (fence, arrival count, release by

@@ -185,7 +185,10 @@ def lib():
     L.hrm_stage.argtypes = [_VP, ctypes.c_int32]
     L.hrm_layers.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _VP,
                              ctypes.c_int32]
-    for name in ("hrm_step_tau", "hrm_begin_step", "hrm_stage", "hrm_layers"):
+    L.hrm_set_step_path.argtypes = [_VP, ctypes.c_int32]
+    L.hrm_step_launches.argtypes = [_VP]
+    L.hrm_step_launches.restype = ctypes.c_int32
+    for name in ("hrm_step_tau", "hrm_begin_step", "hrm_stage", "hrm_layers", "hrm_set_step_path"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("hrm_create", "hrm_set_params", "hrm_set", "hrm_set_primitive", "hrm_dt", "hrm_step",
                  "hrm_relax", "hrm_rhs", "hrm_get", "hrm_time", "hrm_admissibility"):
@@ -406,6 +409,13 @@ class Solver:
 
     def step(self, dt=0.0, nsteps=1):
         return self._check(lib().hrm_step(self.h, float(dt), int(nsteps)))
+
+    def set_step_path(self, path):
+        """1: persistent stage launches where eligible (default); 0: per-phase kernels."""
+        self._check(lib().hrm_set_step_path(self.h, int(path)))
+
+    def step_launches(self) -> int:
+        return int(lib().hrm_step_launches(self.h))
 
     # -- one stage at a time (domain decomposition)
     def step_tau(self):

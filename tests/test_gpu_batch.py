@@ -1,4 +1,4 @@
-"""Batched form: many uneven 2D instances in one persistent launch per RK stage.
+"""Batched form: many uneven 2D instances, one persistent launch per RK stage.
 
 Each batched instance must reproduce the single-problem context of the same
 problem bit for bit, in FP64 and in the precision form (same per-element
