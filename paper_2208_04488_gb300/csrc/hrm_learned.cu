@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(kGateThreads)
   __shared__ NetTile S;
   const uint32_t tmem = net_begin(S, blob);
   uint32_t phase = 0;
+  const float z0 = net_zero_logit(S, tmem, phase, waits);
   const int64_t nf = face_total(g, DIR);
   // the trip count is the same for every thread of the CTA (all take part in the MMAs)
   for (int64_t base = (int64_t)blockIdx.x * kGateThreads; base < nf; base += (int64_t)gridDim.x * kGateThreads) {
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(kGateThreads)
 #pragma unroll
       for (int k = 0; k < kIn; ++k) x[k] = 0.f;
     }
-    const float z = net_logit(S, x, tmem, phase, waits);
+    const float z = net_logit_or_zero(S, x, z0, tmem, phase, waits);
     if (ok) gate[t] = z > zthr ? 1 : 0;
   }
   net_end(tmem);
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(kGateThreads)
   if (threadIdx.x == 0) tc::bar_init(tc::smem_u32(&tbar));
   __syncthreads();
   uint32_t phase = 0, tphase = 0;
+  const float z0 = net_zero_logit(S, tmem, phase, waits);
   const int64_t n0 = g.n[0], nd_ = g.n[DIR];
   const int64_t f0 = n0 + (DIR == 0), f1 = g.n[1] + (DIR == 1), f2 = g.n[2] + (DIR == 2);
   const int64_t tpr = (f0 + kGateThreads - 1) / kGateThreads;  // tiles per row of the midpoint grid
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(kGateThreads)
 #pragma unroll
       for (int k = 0; k < kIn; ++k) x[k] = 0.f;
     }
-    const float z = net_logit(S, x, tmem, phase, waits);
+    const float z = net_logit_or_zero(S, x, z0, tmem, phase, waits);
     if (ok) gate[t] = z > zthr ? 1 : 0;
   }
   net_end(tmem);

@@ -143,6 +143,28 @@ __device__ __forceinline__ float net_logit(NetTile& S, const float (&x)[kIn], ui
   return z + S.w.b3;
 }
 
+// Logit of every thread's row, skipping the network for a tile of uniform
+// stencils: a uniform stencil has exactly zero features, and an MMA row depends
+// only on its own A row, so its logit is the zero-feature logit z0 the CTA
+// computed once through the same path. CTA-wide (the same trip count for all).
+__device__ __forceinline__ float net_logit_or_zero(NetTile& S, const float (&x)[kIn], float z0, uint32_t tmem,
+                                                   uint32_t& phase, unsigned long long* waits) {
+  int nz = 0;
+#pragma unroll
+  for (int k = 0; k < kIn; ++k) nz |= x[k] != 0.f;
+  if (!__syncthreads_or(nz)) return z0;
+  return net_logit(S, x, tmem, phase, waits);
+}
+
+// The zero-feature logit (every row zero), once per CTA.
+__device__ __forceinline__ float net_zero_logit(NetTile& S, uint32_t tmem, uint32_t& phase,
+                                                unsigned long long* waits) {
+  float x0[kIn];
+#pragma unroll
+  for (int k = 0; k < kIn; ++k) x0[k] = 0.f;
+  return net_logit(S, x0, tmem, phase, waits);
+}
+
 // Normalise six differences (d[2] = 0) into x[0..5].
 __device__ __forceinline__ void normalise6(const float (&d)[6], float* x) {
   float s = 0.f, lo = 0.f, hi = 0.f;
