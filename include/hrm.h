@@ -92,7 +92,7 @@ typedef struct {
   int32_t check;       /* 1: hrm_step synchronises and reports admissibility */
   double eps_ar, eps_a, eps_rhoe;      /* limiter thresholds 1e-10, 1e-10, 1e-8 */
   double hs_ar, hs_a, hs_rc2, hs_rhoe; /* hard switches 1e-11, 1e-11, 1e-9, 1e-9 */
-  double weno_eps;                     /* 1e-15 (App. C) */
+  double weno_eps;                     /* 1e-15 (App. C); (0, 1e50] */
   double Cs, q_sensor;                 /* shock sensor 1e12 and 2 (Sec. 4.3.1) */
   double learned_threshold;            /* gate probability in (0, 1) above which d_k are used */
   int32_t screen;      /* precision form: 1 (default) first certifies in FP32, with rounding

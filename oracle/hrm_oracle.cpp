@@ -391,11 +391,20 @@ static real weno_is_left(const real* u, double eps, real* omega_out) {
   real t5a = up2 - real(4.0) * up1 + real(6.0) * u0 - real(4.0) * um1 + um2;
   real t5b = up2 - real(2.0) * up1 + real(2.0) * um1 - um2;
   real tau5 = real(13.0 / 12.0) * t5a * t5a + real(0.25) * t5b * t5b;
-  // nonlinear weights
-  real e0 = real(d0) * (real(1.0) + (tau5 / (b0 + real(eps))) * (tau5 / (b01 + real(eps))));
-  real e1 = real(d1) * (real(1.0) + (tau5 / (b1 + real(eps))) * (tau5 / (b01 + real(eps))));
-  real e2 = real(d2) * (real(1.0) + tau5 / (b2 + real(eps)));
-  real e3 = real(d3) * (real(1.0) + tau5 / (b3 + real(eps)));
+  // nonlinear weights omega_k = eta_k / sum_s eta_s, with every eta_k multiplied
+  // by the same positive factor (beta_0 + eps)(beta_1 + eps)(beta_01 + eps)
+  // (beta_2 + eps)(beta_3 + eps), which leaves omega_k as it is and clears the
+  // denominators of eta_k: eta_0 = d_0 (1 + tau_5^2 / ((beta_0 + eps)(beta_01 + eps)))
+  // becomes d_0 ((beta_0 + eps)(beta_01 + eps) + tau_5^2)(beta_1 + eps)(beta_2 + eps)(beta_3 + eps), etc.
+  const real a = b0 + real(eps), b = b1 + real(eps), c = b01 + real(eps);
+  const real g2 = b2 + real(eps), g3 = b3 + real(eps);
+  const real t2 = tau5 * tau5;
+  const real g23 = g2 * g3;
+  const real abc = (a * b) * c;
+  real e0 = real(d0) * ((a * c + t2) * (b * g23));
+  real e1 = real(d1) * ((b * c + t2) * (a * g23));
+  real e2 = real(d2) * ((g2 + tau5) * (abc * g3));
+  real e3 = real(d3) * ((g3 + tau5) * (abc * g2));
   real esum = e0 + e1 + e2 + e3;
   if (omega_out) {  // omega_k = e_k / sum of e
     omega_out[0] = e0 / esum;

@@ -161,6 +161,9 @@ hrm_status check_params(hrm_ctx* c, const hrm_params* p) {
   if (p->q_sensor < 1.0 || p->q_sensor != std::floor(p->q_sensor))
     return fail(c, HRM_E_INVAL, "q_sensor must be a positive integer");
   if (p->cfl_sound < 0 || p->cfl_sound > 1) return fail(c, HRM_E_INVAL, "unknown cfl_sound %d", p->cfl_sound);
+  // the WENO-IS weights are formed as products of five (beta + eps) (App. C,
+  // scaled by a common factor): eps well inside the FP64 range
+  if (!(p->weno_eps > 0.0 && p->weno_eps <= 1e50)) return fail(c, HRM_E_INVAL, "weno_eps must lie in (0, 1e50]");
   return HRM_OK;
 }
 

@@ -252,6 +252,7 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
   else
     hrm_params_default(&b->params);
   const hrm_params& p = b->params;
+  if (!(p.weno_eps > 0.0 && p.weno_eps <= 1e50)) return bail(bfail(b, HRM_E_INVAL, "weno_eps must lie in (0, 1e50]"));
   if (p.cfl <= 0.0 || (p.limiters && p.cfl > 0.5))
     return bail(bfail(b, HRM_E_INVAL, "cfl must be in (0, 0.5] with the limiters on (Sec. 4.1.2)"));
   if (p.scheme != HRM_SCHEME_WCNS || p.integrator != HRM_RK3 || p.learned || p.precision < 0 || p.precision > 1 ||

@@ -238,6 +238,24 @@ __device__ __forceinline__ R rho_c2(R S, R P, R p) {
 
 // Left-biased incremental-stencil WENO value at x_{i+1/2} from
 // (u_{i-2}, u_{i-1}, u_i, u_{i+1}, u_{i+2}).
+// The incremental-stencil weights eta_k (App. C) scaled by the common positive
+// factor (beta_0 + eps)(beta_1 + eps)(beta_01 + eps)(beta_2 + eps)(beta_3 + eps):
+// omega_k = eta_k / sum_s eta_s is unchanged, and no division is left, e.g.
+// eta_0 (...) = d_0 [(beta_0 + eps)(beta_01 + eps) + tau_5^2] (beta_1 + eps)(beta_2 + eps)(beta_3 + eps).
+// The operation order is the oracle's (bit-identical FP64 path).
+template <typename R>
+__device__ __forceinline__ void weno_eta(R b0, R b1, R b01, R b2, R b3, R tau5, R eps, R& e0, R& e1, R& e2,
+                                         R& e3) {
+  const R a = b0 + eps, b = b1 + eps, c = b01 + eps, g2 = b2 + eps, g3 = b3 + eps;
+  const R t2 = tau5 * tau5;
+  const R g23 = g2 * g3;
+  const R abc = (a * b) * c;
+  e0 = R(15.0 / 32.0) * ((a * c + t2) * (b * g23));
+  e1 = R(5.0 / 32.0) * ((b * c + t2) * (a * g23));
+  e2 = R(5.0 / 16.0) * ((g2 + tau5) * (abc * g3));
+  e3 = R(1.0 / 16.0) * ((g3 + tau5) * (abc * g2));
+}
+
 template <typename R>
 __device__ __forceinline__ R weno_is(R um2, R um1, R u0, R up1, R up2, R eps) {
   const R s0 = R(0.5) * (u0 + up1);
@@ -260,11 +278,8 @@ __device__ __forceinline__ R weno_is(R um2, R um1, R u0, R up1, R up2, R eps) {
   t = up2 - R(4) * up1 + R(6) * u0 - R(4) * um1 + um2;
   tt = up2 - R(2) * up1 + R(2) * um1 - um2;
   const R tau5 = c13_12 * t * t + R(0.25) * tt * tt;
-  const R q01 = tau5 / (b01 + eps);
-  const R e0 = R(15.0 / 32.0) * (R(1) + (tau5 / (b0 + eps)) * q01);
-  const R e1 = R(5.0 / 32.0) * (R(1) + (tau5 / (b1 + eps)) * q01);
-  const R e2 = R(5.0 / 16.0) * (R(1) + tau5 / (b2 + eps));
-  const R e3 = R(1.0 / 16.0) * (R(1) + tau5 / (b3 + eps));
+  R e0, e1, e2, e3;
+  weno_eta<R>(b0, b1, b01, b2, b3, tau5, eps, e0, e1, e2, e3);
   const R es = e0 + e1 + e2 + e3;
   // sum_k omega_k S_k with omega_k = e_k / es: the normalisation applied once
   return (e0 * s0 + e1 * s1 + e2 * s2 + e3 * s3) / es;
@@ -307,11 +322,8 @@ __device__ __forceinline__ R weno_dev(R um2, R um1, R u0, R up1, R up2, R eps) {
   t = up2 - R(4) * up1 + R(6) * u0 - R(4) * um1 + um2;
   tt = up2 - R(2) * up1 + R(2) * um1 - um2;
   const R tau5 = c13_12 * t * t + R(0.25) * tt * tt;
-  const R q01 = tau5 / (b01 + eps);
-  const R e0 = R(15.0 / 32.0) * (R(1) + (tau5 / (b0 + eps)) * q01);
-  const R e1 = R(5.0 / 32.0) * (R(1) + (tau5 / (b1 + eps)) * q01);
-  const R e2 = R(5.0 / 16.0) * (R(1) + tau5 / (b2 + eps));
-  const R e3 = R(1.0 / 16.0) * (R(1) + tau5 / (b3 + eps));
+  R e0, e1, e2, e3;
+  weno_eta<R>(b0, b1, b01, b2, b3, tau5, eps, e0, e1, e2, e3);
   const R es = e0 + e1 + e2 + e3;
   const R dv[4] = {e0 / es - R(15.0 / 32.0), e1 / es - R(5.0 / 32.0), e2 / es - R(5.0 / 16.0),
                    e3 / es - R(1.0 / 16.0)};

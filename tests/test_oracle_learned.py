@@ -177,7 +177,9 @@ def test_features_two_species_and_boundaries(orc):
     # midpoint 6 lies at the jump: nodes 3..8 -> p = 2e5 x3, 1e5 x3
     np.testing.assert_allclose(F[6, 4], [0.5, 0.5, 0.5, -0.5, -0.5, -0.5], atol=1e-15)
     assert dev[6] > 0.3                   # a jump drives the weights far from d_k
-    assert dev[0] == 0.0 and np.all(F[0] == 0.0)  # transmissive: uniform ghost stencil
+    # transmissive: uniform ghost stencil; its weights are d_k up to the rounding of
+    # the common factor the weights are scaled by (App. C normalisation)
+    assert dev[0] <= 1e-15 and np.all(F[0] == 0.0)
     gp = orc.make_grid([n], [0.1], [1, 1])
     Fp = orc.stencil_sample(f, prm, gp, W, 0, np.array([0]))[0].reshape(5, 6)
     # periodic midpoint 0: nodes n-3, n-2, n-1, 0, 1, 2 -> p = 1e5 x3, 2e5 x3
