@@ -1,7 +1,8 @@
 """Command-line runner: advance one of the built-in workloads on the GPU.
 
     python -m paper_2208_04488_gb300.run --workload shock_bubble --nx 1024 --ny 512 \
-        --steps 10 [--precision fp64|fp32] [--dt 0] [--gate none|all|learned]
+        --steps 10 [--precision fp64|fp32] [--dt 0] [--gate none|all|learned] [--step-path 0|1]
+    python -m paper_2208_04488_gb300.run --workload batch --steps 2 [--precision fp64|fp32]
 
 Prints the wall time per step (CUDA events), the simulated time and the
 admissibility counters. Used for profiling captures of single kernels.
@@ -16,7 +17,7 @@ import sys
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 WORKLOADS = ("shock_bubble", "shock_tube", "interface_3d", "water_column", "advection_2d", "mach100_jet",
-             "undex")
+             "undex", "batch")
 
 
 def make_problem(name, nx, ny, nz):
@@ -50,13 +51,30 @@ def main(argv=None):
     ap.add_argument("--gate", default="none", choices=["none", "all", "learned"],
                     help="all: every midpoint gated (fixed gate); learned: a detector trained on the small "
                          "training set")
+    ap.add_argument("--step-path", type=int, default=0, choices=[0, 1],
+                    help="1: the persistent stage kernel where the context allows it (hrm_set_step_path)")
     a = ap.parse_args(argv)
     import torch
     from paper_2208_04488_gb300 import build, hrm
     build.build()
-    pr = make_problem(a.workload, a.nx, a.ny, a.nz)
     prec = hrm.FP64 if a.precision == "fp64" else hrm.FP32
+    if a.workload == "batch":
+        # the 64 seeded uneven 2D instances of the batched form, one persistent launch per stage
+        from paper_2208_04488_gb300 import problems as P
+        ps = P.batch_instances(64, seed=4242)
+        b = hrm.BatchSolver(ps, params=hrm.params_default(cfl=0.4, precision=prec, check=0))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.step(a.steps)
+        e1.record()
+        e1.synchronize()
+        print(json.dumps({"workload": "batch_64", "cells": b.total_cells(),
+                          "ms_per_step": e0.elapsed_time(e1) / max(a.steps, 1), "admissibility": b.admissibility()}))
+        return
+    pr = make_problem(a.workload, a.nx, a.ny, a.nz)
     s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, precision=prec, check=0))
+    s.set_step_path(a.step_path)
     if a.gate == "all":
         import numpy as np
         for d in range(pr.D):
