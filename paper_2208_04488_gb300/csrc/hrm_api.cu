@@ -76,6 +76,12 @@ struct hrm_ctx {
   GridSync* p_sync = nullptr;
   unsigned int p_expired_seen = 0;
   // tracing: event pairs around every kernel of the captured step
+  // precision form: W^n's interior cells all came out of relax_fast (a step
+  // that relaxed at its last stage, and no state written since); the stage
+  // updates leave out cells they return unchanged only then. Mirrored into
+  // StepState::wn_relaxed (wn_relaxed_dev: the value last written there).
+  bool wn_relaxed = false;
+  int wn_relaxed_dev = 0;
   int profiling = 0;
   int nprof = 0;
   cudaEvent_t prof_ev[2 * kMaxProf] = {};
@@ -530,6 +536,22 @@ void reset_step_state(hrm_ctx* c) {
   z.cfl = c->params.cfl;
   cudaMemcpyAsync(c->st, &z, sizeof z, cudaMemcpyHostToDevice, c->stream);
   cudaStreamSynchronize(c->stream);
+  c->wn_relaxed = false;
+  c->wn_relaxed_dev = 0;
+}
+
+// The relaxed-state flag of W^n as the next kernels on the stream must see it.
+void sync_relaxed(hrm_ctx* c) {
+  const int v = c->wn_relaxed ? 1 : 0;
+  if (v == c->wn_relaxed_dev) return;
+  cudaMemsetAsync(&c->st->wn_relaxed, v, sizeof(int), c->stream);  // bytes 0x01: nonzero
+  c->wn_relaxed_dev = v;
+}
+
+// After a full step: W^n came out of relax_fast when the precision form relaxed
+// at the step's last stage.
+bool step_leaves_relaxed(const hrm_ctx* c) {
+  return c->params.precision == HRM_FP32 && c->params.relax_mode != HRM_RELAX_OFF;
 }
 
 }  // namespace
@@ -826,6 +848,7 @@ hrm_status hrm_set_params(hrm_ctx* c, const hrm_params* p) {
   c->params = *p;
   fill_dev_params(c);
   drop_graph(c);
+  c->wn_relaxed = false;
   StepState* st = c->st;
   double cfl = p->cfl;
   cudaMemcpyAsync(&st->cfl, &cfl, sizeof cfl, cudaMemcpyHostToDevice, c->stream);
@@ -915,8 +938,10 @@ hrm_status hrm_step(hrm_ctx* c, double dt, int32_t nsteps) {
   // admissibility counters and the tensor-core wait counter that follows them
   if (c->params.check) cudaMemsetAsync(&c->st->counts, 0, 5 * sizeof(unsigned long long), c->stream);
   for (int i = 0; i < nsteps; ++i) {
+    sync_relaxed(c);
     if ((s = cuda_check(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch"))) return s;
     c->launches += c->graph_kernels;
+    c->wn_relaxed = step_leaves_relaxed(c);
   }
   if (!c->params.check) return last_launch(c, "step");
   if (c->persist) {
@@ -1027,8 +1052,10 @@ hrm_status hrm_stage(hrm_ctx* c, int32_t stage) {
   }
   const int prof = c->profiling;
   c->profiling = 0;  // event brackets belong to the captured step graph
+  sync_relaxed(c);
   c->launches += enqueue_stage(c, c->stream, src, dst, a, b, last ? rf : rs, 0, false);
   c->profiling = prof;
+  if (last) c->wn_relaxed = step_leaves_relaxed(c);
   return last_launch(c, "stage");
 }
 
@@ -1047,6 +1074,7 @@ hrm_status hrm_layers(hrm_ctx* c, int32_t stage, int32_t set, int64_t first, int
   double* state = stage == 0 ? c->Wn : c->Ws;
   const int64_t cells = count * layer, off = first * layer;
   hrm_status s;
+  if (set) c->wn_relaxed = false;  // the written cells need not be relax_fast output
   if (set)
     s = copy_planes(c, state + off, c->nc, buf, cells, cells, c->M,
                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, "set layers");
@@ -1063,6 +1091,7 @@ hrm_status hrm_relax(hrm_ctx* c) {
   if (!c) return HRM_E_INVAL;
   c->ck->relax(c->Wn, c->dg, c->fl, c->stream);
   ++c->launches;
+  c->wn_relaxed = false;  // the FP64 relaxation, not relax_fast
   return last_launch(c, "relax");
 }
 

@@ -477,6 +477,16 @@ __global__ void __launch_bounds__(kCellThreads)
   double Ws[M], Wo[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) Ws[m] = Wsrc[m * nc + c];
+  const bool with_wn = a != 0.0;
+  if ((!relax || st->wn_relaxed) && stage_keeps_cell<N, D>(c, Wn, Ws, F0, F1, F2, g, with_wn)) {
+    // W_out = W_src exactly, and the planes already hold those of W_src
+    if (Wout != Wsrc && !(with_wn && Wout == Wn)) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) Wout[m * nc + c] = Ws[m];
+    }
+    if (count) count_bits(st, admissibility_bits<N, D>(Ws, f));
+    return;
+  }
   fast_combine<N, D>(c, Wn, Ws, F0, F1, F2, g, st->dt, a, b, Wo);
   double rho, Re;
   if (relax)

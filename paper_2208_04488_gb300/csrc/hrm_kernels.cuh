@@ -732,7 +732,9 @@ __device__ __forceinline__ void count_bits(StepState* st, int b) {
 // Precision form: W_out = a W^n + b (W_src + dt RHS) of one interior cell c,
 // with W_src + dt RHS accumulated directly and dt/dx_d folded into one
 // coefficient per direction (one multiply-add per slot and direction). Ws: the
-// cell's W_src, already loaded.
+// cell's W_src, already loaded. The SSP-RK stages that combine with W^n have
+// b = 1 - a, so their combination is formed as acc + a (W^n - acc): two
+// operations as before, and exactly acc when W^n equals acc.
 template <int N, int D>
 __device__ __forceinline__ void fast_combine(int64_t c, const double* Wn, const double* Ws,
                                              const double* __restrict__ F0, const double* __restrict__ F1,
@@ -773,8 +775,55 @@ __device__ __forceinline__ void fast_combine(int64_t c, const double* Wn, const 
     for (int m = 0; m < M; ++m) Wo[m] = b * acc[m];
   } else {
 #pragma unroll
-    for (int m = 0; m < M; ++m) Wo[m] = fma(a, Wn[m * nc + c], b * acc[m]);
+    for (int m = 0; m < M; ++m) Wo[m] = fma(a, Wn[m * nc + c] - acc[m], acc[m]);
   }
+}
+
+// Precision form: whether a stage returns cell c exactly as it is, so that its
+// arithmetic can be left out. Every flux difference G^-_{i+1/2} - G^+_{i-1/2}
+// is exactly zero when the two faces' values are bit-equal and finite; a stage
+// that combines with W^n (with_wn) also needs W_src bit-equal to W^n. Then
+// fast_combine returns W_src exactly (its weights sum to one), except that a
+// component -0 would come back +0, so those are left to the arithmetic; and
+// relax_fast, which recomputes the volume fractions from the conserved
+// variables alone, returns the cell unchanged if it came out of relax_fast
+// before -- the caller's condition. Only integer compares: no FP64 work.
+template <int N, int D>
+__device__ __forceinline__ bool stage_keeps_cell(int64_t c, const double* Wn, const double* Ws,
+                                                 const double* __restrict__ F0, const double* __restrict__ F1,
+                                                 const double* __restrict__ F2, const DevGrid& g, bool with_wn) {
+  using L = Lay<N, D>;
+  constexpr int M = L::M;
+  const int64_t nc = g.ncells;
+  const int64_t i0 = c % g.n[0];
+  const int64_t r = c / g.n[0];
+  const int64_t i1 = r % g.n[1], i2 = r / g.n[1];
+  auto bits = [](double x) { return (unsigned long long)__double_as_longlong(x); };
+  auto same_finite = [&](double x, double y) {
+    const unsigned long long bx = bits(x);
+    return (bx == bits(y)) & (((bx >> 52) & 0x7ffull) != 0x7ffull);
+  };
+  bool same = true;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double* F = d == 0 ? F0 : (d == 1 ? F1 : F2);
+    const int64_t f0 = g.n[0] + (d == 0), f1 = g.n[1] + (d == 1), f2 = g.n[2] + (d == 2);
+    const int64_t nf = f0 * f1 * f2;
+    const int64_t fl = HRM_IDX(g, (i2 * f1 + i1) * f0 + i0, nf);
+    const int64_t fr = HRM_IDX(g, fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1)), nf);
+#pragma unroll
+    for (int m = 0; m < L::NC; ++m) same = same & same_finite(F[m * nf + fr], F[m * nf + fl]);
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) same = same & same_finite(F[(L::AL + k) * nf + fr], F[(M + k) * nf + fl]);
+  }
+  if (with_wn) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const unsigned long long bs = bits(Ws[m]);
+      same = same & (bs == bits(Wn[m * nc + c])) & (bs != 0x8000000000000000ull);
+    }
+  }
+  return same;
 }
 
 // RHS_i = -sum_d (G^{d,-}_{i+1/2} - G^{d,+}_{i-1/2}) / dx_d (Eq. semi_W_G_pm_eqn),
@@ -799,6 +848,16 @@ __device__ __forceinline__ void update_body(int64_t c, const double* Wn, const d
 #pragma unroll
   for (int m = 0; m < M; ++m) Ws[m] = Wsrc[m * nc + c];
   if constexpr (FAST && MODE == 0) {
+    const bool with_wn = a != 0.0;
+    if ((!relax || st->wn_relaxed) && stage_keeps_cell<N, D>(c, Wn, Ws, F0, F1, F2, g, with_wn)) {
+      // W_out = W_src exactly; already there in place, or (with_wn) in W^n
+      if (Wout != Wsrc && !(with_wn && Wout == Wn)) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) Wout[m * nc + c] = Ws[m];
+      }
+      if (count) count_bits(st, admissibility_bits<N, D>(Ws, f));
+      return;
+    }
     double Wo[M];
     fast_combine<N, D>(c, Wn, Ws, F0, F1, F2, g, dt, a, b, Wo);
     if (relax) relax_cell<N, D, FAST>(Wo, f);
