@@ -447,8 +447,11 @@ def run_form(torch, hrm, pr, precision, det, dt, steps, warmup, flush, stream, t
     t, per = time_steps(torch, s, steps, flush, stream, dt)
     out = {"t": t, "per": per, "launches": s.kernel_launches() - l0, "adm": s.admissibility(),
            "W": s.get(hrm.FIELD_W)}
-    out["gated"] = (float(np.mean(np.concatenate([s.get_gate(d) for d in range(pr.D)]))) if det is not None
-                    else 0.0)
+    # gate bytes: 1 linear weights, 0 full WENO-IS, 2 (precision form) a
+    # uniform stencil, which takes the exact node flux
+    gb = np.concatenate([s.get_gate(d) for d in range(pr.D)]) if det is not None else np.zeros(1, np.uint8)
+    out["gated"] = float(np.mean(gb != 0)) if det is not None else 0.0
+    out["gated_uniform"] = float(np.mean(gb == 2)) if det is not None else 0.0
     s.close()
     return out
 
@@ -517,7 +520,7 @@ def form_summary(hrm, pr, r, ref_W, steps, face_fl, face_fl_gated, peak, peak_na
     gate_t = r["per"].get(hrm.KERNEL_GATE, (0, 0.0))
     l1 = rel_l1_state(r["W"], ref_W, pr.N, pr.D).tolist() if ref_W is not None else None
     return {"value": pr.ncells * steps / r["t"], "unit": UNIT, "ms_per_step": 1e3 * r["t"] / steps,
-            "gated_share": g,
+            "gated_share": g, "gated_share_uniform": r.get("gated_uniform", 0.0),
             "rel_l1_vs_fp64": None if l1 is None else {"max_over_variables": max(l1), "per_variable": l1},
             "admissibility_after": r["adm"],
             "launches_per_step": r["launches"] / steps,

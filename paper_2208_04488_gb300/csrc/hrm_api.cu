@@ -248,11 +248,18 @@ GateArgs gate_of(const hrm_ctx* c, int d) {
     g.defer_count = g.defer_list + c->defer_cap;
   }
   if (c->params.learned) g.fixed = c->gate[d];
+  if (c->params.learned == 1 && defer_sweep(c)) {  // the network inside the sweep
+    g.net = c->blob;
+    g.R32 = c->R32;
+    g.zthr = gate_logit_threshold(c);
+    g.out_gate = c->gate[d];
+  }
   return g;
 }
 
-// With the learned detector, its gate kernel runs before each sweep (both forms).
-bool separate_gate(const hrm_ctx* c) { return c->params.learned == 1; }
+// With the learned detector, its gate kernel runs before each sweep, except in
+// the precision form's screened sweep, which evaluates the network itself.
+bool separate_gate(const hrm_ctx* c) { return c->params.learned == 1 && !defer_sweep(c); }
 
 // CFL maxima of the prim kernels: 1 with the five-equation c, 2 with the
 // four-equation HRM c (params.cfl_sound).

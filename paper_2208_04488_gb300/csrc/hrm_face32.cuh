@@ -456,6 +456,69 @@ __global__ void __launch_bounds__(kCellThreads)
   block_tau_max<D>(s, st->tau_bits);
 }
 
+// True when every FP32 plane holds the same value at the six nodes of a
+// midpoint (a NaN anywhere makes it false). One unrolled pass without
+// branches, so that every load can be in flight at once: measured on the
+// 1024x512 shock-bubble, rounds of four planes with an exit after each, or
+// short-circuit compares (each load waiting for the previous compare), made
+// the check cost as much as the work it saves.
+template <int N, int D>
+__device__ __forceinline__ bool uniform_stencil(const float* __restrict__ P32, int64_t nc, const Nodes6& nd) {
+  bool same = true;
+#pragma unroll
+  for (int q = 0; q < P32Lay<N, D>::PLANES; ++q) {
+    const float* p = P32 + (int64_t)q * nc;
+    float v[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) v[j] = p[nd.c[j]];
+    same = same & (v[0] == v[2]) & (v[1] == v[2]) & (v[3] == v[2]) & (v[4] == v[2]) & (v[5] == v[2]);
+  }
+  return same;
+}
+
+// Midpoint t of a uniform stencil: the node's physical flux from the
+// conservative planes (the HCS node-flux expression at node i), zero alpha slots.
+template <int N, int D, int DIR>
+__device__ __forceinline__ void uniform_flux(int64_t t, const Nodes6& nd, const float* __restrict__ P32,
+                                             double* __restrict__ out, const DevGrid& g) {
+  using L = Lay<N, D>;
+  using Q = P32Lay<N, D>;
+  constexpr int M = L::M;
+  const int64_t nc = g.ncells;
+  const int64_t nf = face_count<DIR>(g);
+  auto ld = [&](int plane) -> float { return P32[(int64_t)plane * nc + nd.c[2]]; };
+  const float un = ld(L::MOM + DIR), pn = ld(L::EN);
+#pragma unroll
+  for (int m = 0; m < L::NC; ++m) {
+    float v;
+    if (m < L::MOM)
+      v = ld(m) * un;
+    else if (m < L::EN)
+      v = ld(Q::MOM + (m - L::MOM)) * un + ((m - L::MOM) == DIR ? pn : 0.f);
+    else
+      v = (ld(Q::E) + pn) * un;
+    out[m * nf + t] = widen_f32(v);
+  }
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) {
+    out[(L::AL + k) * nf + t] = 0.0;
+    out[(M + k) * nf + t] = 0.0;
+  }
+}
+
+// Appends index t to a worklist where `need` (all lanes of the warp call it;
+// warp-aggregated: one atomic per warp; order not significant).
+__device__ __forceinline__ void defer_push(bool need, int64_t t, uint32_t* __restrict__ list,
+                                           uint32_t* __restrict__ count) {
+  const unsigned m = __ballot_sync(0xffffffffu, need);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (need) list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)t;
+}
+
 // Precision-form update of one RK stage with the next stage's primitives fused
 // in: the flux difference and SSP-RK combination (fast_combine), the
 // relaxation (relax_fast), the admissibility count, the store of W_out, then
@@ -464,15 +527,13 @@ __global__ void __launch_bounds__(kCellThreads)
 // planes of Dirichlet slices keep what the stage's first primitive pass wrote
 // (their states do not change).
 template <int N, int D>
-__global__ void __launch_bounds__(kCellThreads)
-    k_update32p(const double* Wn, const double* Wsrc, double* Wout, const double* __restrict__ F0,
-                const double* __restrict__ F1, const double* __restrict__ F2, DevGrid g, DevFluid f,
-                StepState* st, double a, double b, int relax, int count, float* __restrict__ P32,
-                float* __restrict__ R32) {
+__device__ __forceinline__ void update32p_cell(int64_t c, const double* Wn, const double* Wsrc, double* Wout,
+                                               const double* __restrict__ F0, const double* __restrict__ F1,
+                                               const double* __restrict__ F2, const DevGrid& g, const DevFluid& f,
+                                               StepState* st, double a, double b, int relax, int count,
+                                               float* __restrict__ P32, float* __restrict__ R32) {
   using L = Lay<N, D>;
   constexpr int M = L::M;
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.nint) return;
   const int64_t nc = g.ncells;
   double Ws[M], Wo[M];
 #pragma unroll
@@ -500,24 +561,15 @@ __global__ void __launch_bounds__(kCellThreads)
   prim32_store<N, D>(c, Wo, rho, Re, P32, R32, nc, f, u, cs);
 }
 
-// True when every FP32 plane holds the same value at the six nodes of a
-// midpoint (a NaN anywhere makes it false). One unrolled pass without
-// branches, so that every load can be in flight at once: measured on the
-// 1024x512 shock-bubble, rounds of four planes with an exit after each, or
-// short-circuit compares (each load waiting for the previous compare), made
-// the check cost as much as the work it saves.
 template <int N, int D>
-__device__ __forceinline__ bool uniform_stencil(const float* __restrict__ P32, int64_t nc, const Nodes6& nd) {
-  bool same = true;
-#pragma unroll
-  for (int q = 0; q < P32Lay<N, D>::PLANES; ++q) {
-    const float* p = P32 + (int64_t)q * nc;
-    float v[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) v[j] = p[nd.c[j]];
-    same = same & (v[0] == v[2]) & (v[1] == v[2]) & (v[3] == v[2]) & (v[4] == v[2]) & (v[5] == v[2]);
-  }
-  return same;
+__global__ void __launch_bounds__(kCellThreads)
+    k_update32p(const double* Wn, const double* Wsrc, double* Wout, const double* __restrict__ F0,
+                const double* __restrict__ F1, const double* __restrict__ F2, DevGrid g, DevFluid f,
+                StepState* st, double a, double b, int relax, int count, float* __restrict__ P32,
+                float* __restrict__ R32) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.nint) return;
+  update32p_cell<N, D>(c, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32);
 }
 
 // DEFER: where a screen fails (or for the first-order scheme) return false
@@ -526,12 +578,13 @@ __device__ __forceinline__ bool uniform_stencil(const float* __restrict__ P32, i
 // Returns true when the midpoint's outputs were written.
 // XSMEM: the per-thread column of biased values lives in `xs` (the caller's
 // shared memory, 2 x M x kFaceThreads floats) instead of a static array of its own.
+// nonuniform: the caller has found the stencil not uniform (uniform_stencil).
 template <int N, int D, int DIR, bool DEFER = false, bool XSMEM = false>
 __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const double* __restrict__ W,
                                             const double* __restrict__ V, const double* __restrict__ AUX,
                                             const float* __restrict__ P32, double* __restrict__ out,
                                             const DevGrid& g, const DevFluid& f, const DevParams& pr, double lam,
-                                            bool lin = false, float* xs = nullptr) {
+                                            bool lin = false, float* xs = nullptr, bool nonuniform = false) {
   using L = Lay<N, D>;
   using Q = P32Lay<N, D>;
   constexpr int M = L::M;
@@ -590,7 +643,8 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
     // conservative planes, as the HCS term reads it) instead of through rounded
     // steps that would only cancel; every FP32 sweep takes the same exit, so
     // they stay bit-identical to one another.
-    if (uniform_stencil<N, D>(P32, nc, nd)) {
+    if (!nonuniform && uniform_stencil<N, D>(P32, nc, nd)) {
+      // (uniform_flux, written out here: as a call the sweep spills more)
       const float un = ld(L::MOM + DIR, 2), pn = ld(L::EN, 2);
 #pragma unroll
       for (int m = 0; m < L::NC; ++m) {
@@ -899,13 +953,7 @@ __global__ void __launch_bounds__(kFaceThreads, 6)
     const bool lin = gate != nullptr && gate[t] != 0;
     need = !face32_body<N, D, DIR, true>(t, nd, W, nullptr, nullptr, P32, out, g, f, pr, st->lam[DIR], lin);
   }
-  const unsigned m = __ballot_sync(0xffffffffu, need);
-  if (m == 0u) return;
-  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (need) list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)t;
+  defer_push(need, t, list, count);
 }
 
 // The midpoints a k_face32_fast launch deferred, with the full body (FP64

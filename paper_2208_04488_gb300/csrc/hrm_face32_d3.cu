@@ -1,6 +1,7 @@
 // FP32-bulk per-midpoint kernels for D = 3, N = 2..3 species (the precision
 // form: interpolation, Riemann fluxes and HCS in FP32; limiter theta in FP64).
 #include "hrm_face32.cuh"
+#include "hrm_face32_net.cuh"
 #include "hrm_launch.h"
 
 namespace hrm {
@@ -14,8 +15,13 @@ void launch(const double* W, const double* V, const double* AUX, const float* P3
   if constexpr (DIR < kD) {
     if (gate.defer_list) {
       cudaMemsetAsync(gate.defer_count, 0, sizeof(uint32_t), s);
-      k_face32_fast<N, kD, DIR><<<patch_grid(g, DIR), kFaceThreads, 0, s>>>(
-          W, P32, out, g, f, p, st, gate.fixed, gate.defer_list, gate.defer_count);
+      if (gate.net)
+        k_face32_net<N, kD, DIR><<<patch_grid(g, DIR), kFaceThreads, 0, s>>>(
+            W, P32, gate.R32, out, g, f, p, st, static_cast<const mlp::GateBlob*>(gate.net), gate.zthr,
+            gate.out_gate, gate.defer_list, gate.defer_count);
+      else
+        k_face32_fast<N, kD, DIR><<<patch_grid(g, DIR), kFaceThreads, 0, s>>>(
+            W, P32, out, g, f, p, st, gate.fixed, gate.defer_list, gate.defer_count);
       const cudaStream_t sf = fix_stream(gate, s);
       k_face32_fix<N, kD, DIR><<<kFixBlocks, kFixThreads, 0, sf>>>(W, P32, out, g, f, p, st, gate.fixed,
                                                                     gate.defer_list, gate.defer_count);

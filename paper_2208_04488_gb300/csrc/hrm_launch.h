@@ -37,6 +37,15 @@ struct GateArgs {
   // sweep; the caller joins ev_fix before the update
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fast = nullptr, ev_fix = nullptr;
+  // precision form with the learned detector (with a worklist): the sweep
+  // evaluates the network itself (k_face32_net) from the FP32 planes and their
+  // residues R32, with the detector's inference blob (an mlp::GateBlob) and the
+  // logit threshold, and writes its gate bytes to `out_gate` (which the
+  // deferred-midpoint kernel then reads as `fixed`)
+  const void* net = nullptr;
+  const float* R32 = nullptr;
+  float zthr = 0.f;
+  uint8_t* out_gate = nullptr;
 };
 
 // Stream of the deferred-midpoint kernel: gate.side (forked from s after the

@@ -165,6 +165,110 @@ __device__ __forceinline__ float net_zero_logit(NetTile& S, uint32_t tmem, uint3
   return net_logit(S, x0, tmem, phase, waits);
 }
 
+// ---------------------------------------------------------------- one warp, 32 stencils
+// The same network for the 32 stencils of one warp with warp-level MMA
+// (mma.sync m16n8k16, bf16 inputs, FP32 accumulation): what the precision
+// form's midpoint sweep runs in place of the gate kernel, only in warps that
+// hold a non-uniform stencil. The B operands are read from the blob's tcgen05
+// arrangement in global memory (L1-resident): B fragment word (n, k..k+1), k
+// even, is one 32-bit word there.
+__device__ __forceinline__ uint32_t blob_word(const __nv_bfloat16* w, int n, int k) {
+  const char* p = reinterpret_cast<const char*>(w) + (n >> 3) * 512 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+  return __ldg(reinterpret_cast<const unsigned int*>(p));
+}
+
+// D = A B + D: A 16x16 bf16 row-major fragments, B 16x8 bf16 column-major, D FP32.
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Row stride (bf16) of a warp's feature tile in shared memory: 80 bytes, so
+// that the eight rows a fragment load touches fall in distinct banks.
+constexpr int kWarpRow = 40;
+
+// Lane r writes its features as row r of the warp's tile X (bf16, columns
+// kIn..31 zero).
+__device__ __forceinline__ void warp_store_row(__nv_bfloat16 (*X)[kWarpRow], int r, const float (&x)[kIn]) {
+  uint32_t* row = reinterpret_cast<uint32_t*>(X[r]);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) row[k] = pack_bf16(2 * k < kIn ? x[2 * k] : 0.f, 2 * k + 1 < kIn ? x[2 * k + 1] : 0.f);
+}
+
+// Logit of the stencil in row `lane` of X. All 32 lanes call it, after every
+// lane stored its row (and a __syncwarp). Fragment layout of m16n8k16: lane 4 g
+// + q holds A rows g, g + 8 at columns 2q, 2q + 1 (and + 8), B column g at
+// rows 2q, 2q + 1 (and + 8), and D rows g, g + 8 at columns 2q, 2q + 1, so the
+// D tiles of one layer (bias, ReLU, bf16) are the A fragments of the next.
+__device__ __forceinline__ float warp_logit(const GateBlob& W, const __nv_bfloat16 (*X)[kWarpRow], int lane) {
+  const int g = lane >> 2, q = lane & 3;
+  auto ld32 = [](const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); };
+  float zr[2][2];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    float c1[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) c1[nt][0] = c1[nt][1] = c1[nt][2] = c1[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt) {
+      uint32_t a[4];
+      a[0] = ld32(&X[16 * mt + g][16 * kt + 2 * q]);
+      a[1] = ld32(&X[16 * mt + g + 8][16 * kt + 2 * q]);
+      a[2] = ld32(&X[16 * mt + g][16 * kt + 2 * q + 8]);
+      a[3] = ld32(&X[16 * mt + g + 8][16 * kt + 2 * q + 8]);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+        mma_bf16(c1[nt], a, blob_word(W.w1, 8 * nt + g, 16 * kt + 2 * q),
+                 blob_word(W.w1, 8 * nt + g, 16 * kt + 2 * q + 8));
+    }
+    uint32_t h[2][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int col = 8 * nt + 2 * q;
+      const float b0 = __ldg(&W.b1[col]), b1 = __ldg(&W.b1[col + 1]);
+      h[nt >> 1][(nt & 1) * 2 + 0] = pack_bf16(fmaxf(c1[nt][0] + b0, 0.f), fmaxf(c1[nt][1] + b1, 0.f));
+      h[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16(fmaxf(c1[nt][2] + b0, 0.f), fmaxf(c1[nt][3] + b1, 0.f));
+    }
+    float c2[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) c2[nt][0] = c2[nt][1] = c2[nt][2] = c2[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+        mma_bf16(c2[nt], h[kt], blob_word(W.w2, 8 * nt + g, 16 * kt + 2 * q),
+                 blob_word(W.w2, 8 * nt + g, 16 * kt + 2 * q + 8));
+    // output layer in FP32: this lane's columns, then the sum over the quad
+    float sg = 0.f, sg8 = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int col = 8 * nt + 2 * q;
+      const float b0 = __ldg(&W.b2[col]), b1 = __ldg(&W.b2[col + 1]);
+      const float w0 = __ldg(&W.w3[col]), w1 = __ldg(&W.w3[col + 1]);
+      sg += fmaxf(c2[nt][0] + b0, 0.f) * w0 + fmaxf(c2[nt][1] + b1, 0.f) * w1;
+      sg8 += fmaxf(c2[nt][2] + b0, 0.f) * w0 + fmaxf(c2[nt][3] + b1, 0.f) * w1;
+    }
+    sg += __shfl_xor_sync(0xffffffffu, sg, 1);
+    sg += __shfl_xor_sync(0xffffffffu, sg, 2);
+    sg8 += __shfl_xor_sync(0xffffffffu, sg8, 1);
+    sg8 += __shfl_xor_sync(0xffffffffu, sg8, 2);
+    const float b3 = __ldg(&W.b3);
+    zr[mt][0] = sg + b3;
+    zr[mt][1] = sg8 + b3;
+  }
+  // row r = 16 mt + 8 half + g' is held by lanes 4 g' .. 4 g' + 3
+  const int src = 4 * (lane & 7);
+  const float v00 = __shfl_sync(0xffffffffu, zr[0][0], src);
+  const float v01 = __shfl_sync(0xffffffffu, zr[0][1], src);
+  const float v10 = __shfl_sync(0xffffffffu, zr[1][0], src);
+  const float v11 = __shfl_sync(0xffffffffu, zr[1][1], src);
+  const int half = (lane >> 3) & 1;
+  return (lane >> 4) ? (half ? v11 : v10) : (half ? v01 : v00);
+}
+
 // Normalise six differences (d[2] = 0) into x[0..5].
 __device__ __forceinline__ void normalise6(const float (&d)[6], float* x) {
   float s = 0.f, lo = 0.f, hi = 0.f;

@@ -165,6 +165,24 @@ def fp32_sensitive(orc, pr, f, W, d):
     return sens
 
 
+def fp32_level(orc, pr, f, W, d):
+    """Midpoints of direction d where every stencil input (alpha_1, alpha_2,
+    rho, u_d, p) varies by at most 2^-21 of its magnitude (a few FP32 units in
+    the last place) or stays below the smallest normal float (a velocity of
+    1e-51 rounds to 0): the stencils whose FP32 planes can all be equal, which
+    the precision form's sweep takes as uniform (oracle values only)."""
+    Vc = np.stack([orc.prim_cell(f, W[:, c])[0] for c in range(pr.ncells)], axis=1)
+    rho = W[:pr.N].sum(axis=0)
+    cells = _node_cells(pr, d, np.arange(face_counts(pr)[d]))
+    flat = np.ones(cells.shape[0], dtype=bool)
+    alphas = [Vc[pr.N + pr.D + 1 + k] for k in range(min(pr.N - 1, 2))]
+    for q in alphas + [rho, Vc[pr.N + d], Vc[pr.N + pr.D]]:
+        qv = q[cells]
+        mag = np.abs(qv).max(axis=1)
+        flat &= ((qv.max(axis=1) - qv.min(axis=1)) <= 2.0 ** -21 * mag) | (mag < 2.0 ** -126)
+    return flat
+
+
 def _random_set(seed, n=1000):
     rng = np.random.default_rng(seed)
     theta = rng.normal(0.0, 0.3, mlp.NPARAM).astype(np.float32)
@@ -251,13 +269,16 @@ TC_GATE_PROBLEMS = [P.shock_tube_1d_baseline(64), P.shock_water_column_2d(48, 26
 
 @pytest.mark.parametrize("pr", TC_GATE_PROBLEMS, ids=[f"{p.name}_{p.n[0]}" for p in TC_GATE_PROBLEMS])
 def test_gate_kernel_matches_oracle(hrm, orc, pr):
-    """Gate bytes of the tensor-core gate kernel against the oracle's features
-    through the oracle's bfloat16 network, at a threshold that gates about half
-    of the non-uniform midpoints: equal wherever the oracle's logit is not
-    within rounding distance of the threshold and the stencil's variation is not
-    at rounding level; and the learned RHS equals the RHS with those bytes as a
-    fixed gate. 1D (two species, one partial 128-midpoint tile), 2D and 3D;
-    stencil planes staged by TMA and read directly."""
+    """Gate bytes of the network against the oracle's features through the
+    oracle's bfloat16 network, at a threshold that gates about half of the
+    non-uniform midpoints: equal wherever the oracle's logit is not within
+    rounding distance of the threshold and the stencil's variation is not at
+    rounding level; and the learned RHS equals the RHS with those bytes as a
+    fixed gate. FP64: the tensor-core gate kernel (1D with two species and one
+    partial 128-midpoint tile, 2D, 3D; stencil planes staged by TMA and read
+    directly). FP32: the network inside the screened sweep (warp-level MMA),
+    whose uniform stencils (every FP32 plane equal at the six nodes) take byte 2
+    (the exact node flux)."""
     import torch
     f, g, W = oracle_state(orc, pr, 2)
     theta, _, _ = _random_set(8)
@@ -287,12 +308,22 @@ def test_gate_kernel_matches_oracle(hrm, orc, pr):
         for d in range(pr.D):
             gg = s.get_gate(d)
             z = zs[d]
-            firm = (np.abs(z - zthr) > 0.05 * (1 + np.abs(z))) & ~fp32_sensitive(orc, pr, f, W, d)
-            assert firm.mean() > 0.4
+            flat = np.all(feats[d] == 0.0, axis=1)
+            uni = gg == 2
+            if precision == hrm.FP64:
+                assert not uni.any()
+            assert fp32_level(orc, pr, f, W, d)[uni].all()
+            firm = (np.abs(z - zthr) > 0.05 * (1 + np.abs(z))) & ~fp32_sensitive(orc, pr, f, W, d) & ~uni
+            # enough compared midpoints (FP32: among the non-uniform ones, many of
+            # which lie at the threshold or vary at rounding level)
+            if precision == hrm.FP64:
+                assert firm.mean() > 0.4
+            else:
+                assert firm.sum() >= 0.1 * (~uni).sum(), (int(firm.sum()), int((~uni).sum()))
             np.testing.assert_array_equal(gg[firm], (z[firm] > zthr).astype(np.uint8))
-            rough = ~np.all(feats[d] == 0.0, axis=1)
+            rough = ~flat
             if rough.sum() >= 20:
-                assert 0.05 < gg[rough].mean() < 0.95
+                assert 0.05 < (gg[rough] == 1).mean() < 0.95
             gates.append(gg)
         for d in range(pr.D):
             s.set_gate(d, gates[d])
@@ -361,8 +392,8 @@ def _run(hrm, pr, precision, learned_mode, det, dt, steps, threshold=0.5):
     face_ms = sum(ms for k, ms in prof if k == hrm.KERNEL_SWEEPS)
     gate_ms = sum(ms for k, ms in prof if k == 6)
     frac = None
-    if learned_mode:
-        frac = float(np.mean(np.concatenate([s.get_gate(d) for d in range(pr.D)])))
+    if learned_mode:  # gated: linear weights (1) or, in the precision form, a uniform stencil (2)
+        frac = float(np.mean(np.concatenate([s.get_gate(d) for d in range(pr.D)]) != 0))
     W = s.get(hrm.FIELD_W)
     adm = s.admissibility()
     s.close()

@@ -53,8 +53,10 @@ def test_persistent_step_relax_modes_and_profile(hrm):
         W0, _, _ = _run(hrm, pr, 0, 0.0, 4, relax_mode=mode)
         np.testing.assert_array_equal(W1, W0)
     s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, check=0, precision=hrm.FP32))
+    s.set_step_path(1)
     s.set_profiling(True)
     s.step(0.0, 2)
+    assert s.step_launches() == 3
     prof = s.profile_read()
     kinds = [k for k, _ in prof]
     assert kinds.count(hrm.KERNEL_SWEEPS) == 3 and kinds.count(hrm.KERNEL_UPDATE) == 3
