@@ -136,7 +136,6 @@ __device__ __forceinline__ void stage_prim(const BatchInst& I, const WorkItem& w
 
 template <int N, int D, bool FP32>
 __device__ __forceinline__ void stage_update(const BatchInst& I, const WorkItem& w, const StageArgs& A) {
-  using L = Lay<N, D>;
   const double* Wsrc = pick(I, A.src);
   double* Wout = pick_mut(I, A.dst);
   const double dt = I.st->dt;
@@ -144,19 +143,8 @@ __device__ __forceinline__ void stage_update(const BatchInst& I, const WorkItem&
     if constexpr (FP32) {
       if (A.fuse_next) {
         // as k_update32p: combination, relaxation, store, next stage's FP32 planes
-        double Ws[L::M], Wo[L::M];
-#pragma unroll
-        for (int m = 0; m < L::M; ++m) Ws[m] = Wsrc[m * I.g.ncells + c];
-        fast_combine<N, D>(c, I.Wn, Ws, I.F[0], I.F[1], I.F[2], I.g, dt, A.a, A.b, Wo);
-        double rho, Re;
-        if (A.relax)
-          relax_fast<N, D>(Wo, I.f, rho, Re);
-        else
-          rho_Re<N, D>(Wo, I.f, rho, Re);
-#pragma unroll
-        for (int m = 0; m < L::M; ++m) Wout[m * I.g.ncells + c] = Wo[m];
-        float u[D], cs;
-        prim32_store<N, D>(c, Wo, rho, Re, I.P32, nullptr, I.g.ncells, I.f, u, cs);
+        update32p_cell<N, D>(c, I.Wn, Wsrc, Wout, I.F[0], I.F[1], I.F[2], I.g, I.f, I.st, A.a, A.b, A.relax, 0,
+                             I.P32, nullptr);
         continue;
       }
     }

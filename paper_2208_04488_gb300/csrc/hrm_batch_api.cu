@@ -55,6 +55,10 @@ struct hrm_batch {
   int64_t graph_kernels = 0;
   int64_t launches = 0;
   int64_t total_cells = 0;
+  // per instance: W^n came out of relax_fast (StepState::wn_relaxed; the
+  // precision form's updates leave out unchanged cells only then), and the
+  // value last written to the device
+  std::vector<char> relaxed, relaxed_dev;
   std::string err;
 };
 
@@ -206,6 +210,16 @@ void reset_instance(hrm_batch* b, int i) {
   z.cfl = b->params.cfl;
   cudaMemcpyAsync(b->host[i].st, &z, sizeof z, cudaMemcpyHostToDevice, b->stream);
   cudaStreamSynchronize(b->stream);
+  if ((int)b->relaxed.size() > i) b->relaxed[i] = b->relaxed_dev[i] = 0;
+}
+
+// The relaxed-state flags as the next step's kernels must see them.
+void sync_relaxed(hrm_batch* b) {
+  for (int i = 0; i < b->ninst; ++i)
+    if (b->relaxed[i] != b->relaxed_dev[i]) {
+      cudaMemsetAsync(&b->host[i].st->wn_relaxed, b->relaxed[i] ? 1 : 0, sizeof(int), b->stream);
+      b->relaxed_dev[i] = b->relaxed[i];
+    }
 }
 
 }  // namespace
@@ -288,6 +302,8 @@ hrm_status hrm_batch_create(hrm_batch** out, int32_t ninst, const hrm_instance* 
   if ((s = bcuda(b, cudaMemset(b->sync, 0, sizeof(GridSync)), "clear grid sync"))) return bail(s);
   b->host.resize(ninst);
   b->N.resize(ninst);
+  b->relaxed.assign(ninst, 0);
+  b->relaxed_dev.assign(ninst, 0);
   for (int i = 0; i < ninst; ++i) {
     const hrm_instance& in = inst[i];
     BatchInst& I = b->host[i];
@@ -419,9 +435,12 @@ hrm_status hrm_batch_step(hrm_batch* b, int32_t nsteps) {
   if (nsteps == 0) return HRM_OK;
   hrm_status s;
   if (!b->gexec && !b->direct && (s = build_graph(b))) return s;
+  const char after = b->params.precision == HRM_FP32 && b->params.relax_mode != HRM_RELAX_OFF;
   for (int i = 0; i < nsteps; ++i) {
+    sync_relaxed(b);
     if ((s = launch_step(b))) return s;
     b->launches += b->graph_kernels;
+    std::fill(b->relaxed.begin(), b->relaxed.end(), after);
   }
   if (!b->params.check) return bcuda(b, cudaGetLastError(), "batch step");
   unsigned int expired = 0;

@@ -706,12 +706,21 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
         plane = L::MOM + (t_ < DIR ? t_ : t_ + 1);
         cp = 0.f;
       }
-      float w6[6];
+      // The projection is linear with the midpoint's frozen eigenvectors, so the
+      // field is interpolated as increments: d6[j] is the projection of the
+      // primitive differences V_j - V_i (exactly zero where they vanish), the
+      // columns take the WENO-IS increments about node i (left) and node i+1
+      // (right), and the back-projection below adds R times them to the node
+      // values. In exact arithmetic the same as interpolating the projected
+      // values and back-projecting them; in FP32 it keeps the projection's
+      // rounding off a uniform or nearly uniform stencil.
+      float d6[6];
+      const float v2 = plane < 0 ? u6[2] : ld(plane, 2);
 #pragma unroll
-      for (int j = 0; j < 6; ++j) w6[j] = (plane < 0 ? u6[j] : ld(plane, j)) + cp * p6[j];
+      for (int j = 0; j < 6; ++j) d6[j] = ((plane < 0 ? u6[j] : ld(plane, j)) - v2) + cp * (p6[j] - p6[2]);
       const int slot = fi == N + D ? M - 1 : fi;
-      col(0, slot) = weno_is_scaled(w6[0], w6[1], w6[2], w6[3], w6[4], eps, lin);
-      col(1, slot) = weno_is_scaled(w6[5], w6[4], w6[3], w6[2], w6[1], eps, lin);
+      col(0, slot) = weno_increment(d6[0], d6[1], d6[3], d6[4], eps);
+      col(1, slot) = weno_increment(d6[5] - d6[3], d6[4] - d6[3], -d6[3], d6[1] - d6[3], eps);
     }
     float UL[M], UR[M], arb[N];
     if (!lin) {
@@ -783,19 +792,20 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
       const float rc_2 = rhob * cb * 0.5f;
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
-        const float* U = side == 0 ? UL : UR;
+        const float* U = side == 0 ? UL : UR;  // increments (the volume fractions: values)
         float* Vt = side == 0 ? sl.V : sr.V;
+        const int j = 2 + side;                // node i or i+1
 #pragma unroll
-        for (int k = 0; k < N; ++k) Vt[k] = U[1 + k] + h[k] * (U[M - 1] - U[0]);
-        Vt[L::MOM + DIR] = 0.5f * (U[0] + U[M - 1]);
+        for (int k = 0; k < N; ++k) Vt[k] = ld(k, j) + (U[1 + k] + h[k] * (U[M - 1] - U[0]));
+        Vt[L::MOM + DIR] = u6[j] + 0.5f * (U[0] + U[M - 1]);
         int t_ = 0;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
           if (d == DIR) continue;
-          Vt[L::MOM + d] = U[N + 1 + t_];
+          Vt[L::MOM + d] = ld(L::MOM + d, j) + U[N + 1 + t_];
           ++t_;
         }
-        Vt[L::EN] = rc_2 * (U[M - 1] - U[0]);
+        Vt[L::EN] = p6[j] + rc_2 * (U[M - 1] - U[0]);
 #pragma unroll
         for (int k = 0; k < N - 1; ++k) Vt[L::AL + k] = U[N + D + k];
       }
@@ -864,9 +874,18 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
       for (int e = 1; e < pr.qexp; ++e) pw = pw * prod;
       sig = tanhf(pr.Cs_f * pw);
     }
-    const float one_m = 1.f - sig;
-    const float uhcs = psi * ut - a1 * (u6[2] + u6[3]) + a2 * (u6[1] + u6[4]) - a3 * (u6[0] + u6[5]);
-    const float uhat = sig * ut + one_m * uhcs;
+    // HCS and the sensor blend as deviations from r, the mean of the two
+    // nodes' values: the HCS weights sum to one (psi - 2 a1 + 2 a2 - 2 a3 = 1),
+    // so in exact arithmetic this is psi g~ - a1 (g_i + g_i+1) + a2 (...) -
+    // a3 (...) blended as sig g~ + (1 - sig) g_HCS; in FP32 its rounding scales
+    // with the deviations and vanishes where all inputs equal r.
+    auto hcs_blend = [&](float gt, float g0, float g1, float g2, float g3, float g4, float g5) -> float {
+      const float r = 0.5f * (g2 + g3);
+      const float h = r + (psi * (gt - r) - a1 * ((g2 - r) + (g3 - r)) + a2 * ((g1 - r) + (g4 - r)) -
+                           a3 * ((g0 - r) + (g5 - r)));
+      return h + sig * (gt - h);
+    };
+    const float uhat = hcs_blend(ut, u6[0], u6[1], u6[2], u6[3], u6[4], u6[5]);
     float g32[L::NC];
 #pragma unroll
     for (int m = 0; m < L::NC; ++m) {
@@ -883,8 +902,7 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
           v = (ld(Q::E, j) + p6[j]) * un;
         Gn[j] = v;
       }
-      const float ghcs = psi * Gt[m] - a1 * (Gn[2] + Gn[3]) + a2 * (Gn[1] + Gn[4]) - a3 * (Gn[0] + Gn[5]);
-      g32[m] = sig * Gt[m] + one_m * ghcs;
+      g32[m] = hcs_blend(Gt[m], Gn[0], Gn[1], Gn[2], Gn[3], Gn[4], Gn[5]);
       G.Gc[m] = widen_f32(g32[m]);
     }
     // alpha slots, quasi-conservative form (Eq. G_pm): with alpha_j = alpha_i +
