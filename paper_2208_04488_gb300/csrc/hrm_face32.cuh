@@ -457,15 +457,19 @@ __global__ void __launch_bounds__(kCellThreads)
 }
 
 // True when every FP32 plane holds the same value at the six nodes of a
-// midpoint (a NaN anywhere makes it false). One unrolled pass without
-// branches, so that every load can be in flight at once: measured on the
-// 1024x512 shock-bubble, rounds of four planes with an exit after each, or
+// midpoint (a NaN anywhere makes it false). One pass without branches, so
+// that many loads are in flight at once: measured on the 1024x512
+// shock-bubble, rounds of four planes with an exit after each, or
 // short-circuit compares (each load waiting for the previous compare), made
-// the check cost as much as the work it saves.
-template <int N, int D>
+// the check cost as much as the work it saves. PARTIAL: four planes per loop
+// trip instead of all of them unrolled, for the batched stage kernel, whose
+// register budget is shared with every phase (fully unrolled there, the
+// check's loads spilled: 16.6 against 11.8 ms per batched step). The result
+// is the same either way.
+template <int N, int D, bool PARTIAL = false>
 __device__ __forceinline__ bool uniform_stencil(const float* __restrict__ P32, int64_t nc, const Nodes6& nd) {
   bool same = true;
-#pragma unroll
+#pragma unroll(PARTIAL ? 4 : P32Lay<N, D>::PLANES)
   for (int q = 0; q < P32Lay<N, D>::PLANES; ++q) {
     const float* p = P32 + (int64_t)q * nc;
     float v[6];
@@ -643,7 +647,7 @@ __device__ __forceinline__ bool face32_body(int64_t t, const Nodes6& nd, const d
     // conservative planes, as the HCS term reads it) instead of through rounded
     // steps that would only cancel; every FP32 sweep takes the same exit, so
     // they stay bit-identical to one another.
-    if (!nonuniform && uniform_stencil<N, D>(P32, nc, nd)) {
+    if (!nonuniform && uniform_stencil<N, D, XSMEM>(P32, nc, nd)) {
       // (uniform_flux, written out here: as a call the sweep spills more)
       const float un = ld(L::MOM + DIR, 2), pn = ld(L::EN, 2);
 #pragma unroll
