@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 # DRAM traffic per launch of the dominant kernels, dram__bytes_read.sum + dram__bytes_write.sum from one
 # ncu --set full capture on this workload (profiles/k_face_fp64_shock_bubble_1024x512.md and
 # profiles/k_face32_shock_bubble_1024x512.md); to be re-taken whenever those kernels change.
-TRAFFIC_BYTES = {"k_face_fp64": 99.22e6, "k_face32": 43.43e6}
+TRAFFIC_BYTES = {"k_face_fp64": 99.22e6, "k_face32": 73.09e6}
 # FP64-pipe activity of the FP64 sweep in the same ncu capture (fraction of peak sustained)
 FP64_PIPE_ACTIVE = {"k_face_fp64": 0.858}
 METRIC = "cell-updates/s (FP64 plain vs FP32+learned) at stated L1 err; % of roofline"
@@ -702,6 +702,14 @@ def main():
         n32, tf32 = sweep_time(hrm, per32, pr.D)
         ach32 = fl_launch / (tf32 / n32)
         share32 = time_shares(hrm, per32, pr.D)
+        # the precision form's sweep finishes a uniform stencil exactly (the node
+        # flux) without the method's arithmetic: the share of such midpoints, as
+        # the learned form's sweep reports it in its gate bytes (byte 2) at the
+        # end of the same steps, and the sweep's compulsory bytes per launch (the
+        # FP32 planes of the cells read once, the FP64 flux planes written once)
+        uni = (learned_runs["fp32_learned"].get("gated_uniform") if learned_runs is not None else None)
+        nfx = (pr.n[0] + 1) * int(np.prod(pr.n[1:]))
+        bytes32 = 4 * (pr.M + 4 + pr.D + pr.N - 1) * pr.ncells + 8 * (pr.M + pr.N - 1) * nfx
         learned_block = None
         if learned_runs is not None:
             faces_g = gated_face_flops(pr, pr.cfl)
@@ -749,7 +757,19 @@ def main():
                                       "peak_fp32": fp32_peak / 1e12, "frac_of_fp32_peak": ach32 / fp32_peak,
                                       "peak_fp64": fp64_peak / 1e12,
                                       "avg_launch_ms": 1e3 * tf32 / n32, "kernel_time_share": share32,
-                                      "traffic": TRAFFIC_BYTES["k_face32"]}},
+                                      "traffic": TRAFFIC_BYTES["k_face32"],
+                                      "flops_counted": "the method as written at every midpoint, including "
+                                                       "the uniform stencils the sweep finishes exactly "
+                                                       "without that arithmetic: not a measure of pipe use "
+                                                       "(ncu: FMA pipe 13-14 %)",
+                                      "uniform_share": uni,
+                                      "frac_of_fp32_peak_nonuniform_midpoints": (
+                                          None if uni is None else ach32 * (1.0 - uni) / fp32_peak),
+                                      "hbm": {"compulsory_bytes_per_launch": bytes32,
+                                              "achieved_gbs": bytes32 / (tf32 / n32) / 1e9,
+                                              "peak_gbs": pk.get("hbm_gbs"),
+                                              "frac": (bytes32 / (tf32 / n32) / 1e9 / pk["hbm_gbs"]
+                                                       if pk.get("hbm_gbs") else None)}}},
             },
             "batched": batched,
             "interface_3d": three_d,
