@@ -656,6 +656,15 @@ class BatchSolver:
     def step(self, nsteps=1):
         return self._check(lib().hrm_batch_step(self.h, int(nsteps)))
 
+    def set(self, i, W):
+        """Instance i's conservative state, (M, cells) FP64 host array."""
+        self._check(lib().hrm_batch_set(self.h, int(i), _VP(np.ascontiguousarray(W, dtype=np.float64).ctypes.data), 0))
+
+    def set_primitive(self, i, prim):
+        """Instance i's state from primitives, (N + D + 1, cells) FP64 host array."""
+        self._check(lib().hrm_batch_set_primitive(self.h, int(i),
+                                                  _VP(np.ascontiguousarray(prim, dtype=np.float64).ctypes.data), 0))
+
     def get(self, i):
         pr = self.problems[i]
         out = np.empty((pr.M, pr.ncells))
