@@ -328,9 +328,14 @@ int32_t hrm_profile_read(hrm_ctx* ctx, int32_t max, float* ms, int32_t* kind);
  * field use the linear weights d_k instead of the WENO-IS weights; the
  * characteristic projection (App. D), both positivity limiters (Sec. 4.3.2),
  * the Riemann solves, HCS and blending are unchanged. Inference: bfloat16
- * inputs and weights, FP32 accumulation on the fifth-generation tensor cores
- * (tcgen05: one 128-row tile of midpoints per CTA, accumulators in tensor
- * memory), in a gate kernel that runs before each sweep in both forms.
+ * inputs and weights, FP32 accumulation, on the tensor cores: in the FP64
+ * form (and the precision form with params.screen = 0) a gate kernel runs
+ * before each sweep (tcgen05: one 128-row tile of midpoints per CTA,
+ * accumulators in tensor memory); in the precision form's screened sweep the
+ * sweep runs the network itself with warp-level MMA, only in warps that hold a
+ * stencil that is not uniform (a uniform stencil -- every FP32 plane equal at
+ * the six nodes -- takes the exact node flux, which the interpolation weights
+ * do not affect).
  *
  * Training data come from states the method produces: the label of a midpoint
  * is 1 when every WENO-IS weight of every characteristic field and both biases
@@ -389,15 +394,17 @@ hrm_status hrm_detector_evaluate(hrm_detector* det, double threshold, int32_t bf
 
 /* Copy det's current inference weights into ctx (a snapshot; det may be
  * destroyed afterwards) and allocate its gate buffers; then params.learned = 1
- * is accepted. The gate kernel runs once per direction and stage, before the
- * sweep, on the FP32 planes (and their rounding residues) that the primitive
- * kernel writes. */
+ * is accepted. The network runs once per direction and stage (in a gate kernel
+ * before the sweep, or inside the precision form's screened sweep) on the FP32
+ * planes (and their rounding residues) that the primitive kernel writes. */
 hrm_status hrm_set_detector(hrm_ctx* ctx, const hrm_detector* det);
 /* Fixed gate of direction dir (host, one byte per midpoint over the midpoint
  * grid of dir: n_d + 1 along d, x fastest; nonzero = gated), used at every
  * stage while params.learned = 2. */
 hrm_status hrm_set_gate(hrm_ctx* ctx, int32_t dir, const uint8_t* gate);
-/* The gate bytes last used in direction dir (host, same layout). */
+/* The gate bytes last used in direction dir (host, same layout): 1 gated, 0
+ * not gated; after a precision-form sweep that evaluated the network itself,
+ * 2 marks a uniform stencil (exact node flux, no gate needed). */
 hrm_status hrm_get_gate(hrm_ctx* ctx, int32_t dir, uint8_t* gate);
 
 /* Diagnostic, not a step of the method: measured FMA-pipe throughput of the
