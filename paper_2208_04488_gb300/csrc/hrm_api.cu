@@ -76,10 +76,12 @@ struct hrm_ctx {
   GridSync* p_sync = nullptr;
   unsigned int p_expired_seen = 0;
   // tracing: event pairs around every kernel of the captured step
-  // precision form: W^n's interior cells all came out of relax_fast (a step
-  // that relaxed at its last stage, and no state written since); the stage
-  // updates leave out cells they return unchanged only then. Mirrored into
-  // StepState::wn_relaxed (wn_relaxed_dev: the value last written there).
+  // W^n's interior cells all came out of this form's relaxation (relax_fast in
+  // the precision form, relax_cell in FP64: a step that relaxed at its last
+  // stage, and no state or parameter written since); the stage updates take
+  // the relaxation's result from W^n for cells it would return unchanged only
+  // then. Mirrored into StepState::wn_relaxed (wn_relaxed_dev: the value last
+  // written there).
   bool wn_relaxed = false;
   int wn_relaxed_dev = 0;
   int profiling = 0;
@@ -555,11 +557,9 @@ void sync_relaxed(hrm_ctx* c) {
   c->wn_relaxed_dev = v;
 }
 
-// After a full step: W^n came out of relax_fast when the precision form relaxed
-// at the step's last stage.
-bool step_leaves_relaxed(const hrm_ctx* c) {
-  return c->params.precision == HRM_FP32 && c->params.relax_mode != HRM_RELAX_OFF;
-}
+// After a full step: W^n came out of the form's relaxation when the step
+// relaxed at its last stage.
+bool step_leaves_relaxed(const hrm_ctx* c) { return c->params.relax_mode != HRM_RELAX_OFF; }
 
 }  // namespace
 
@@ -1098,7 +1098,7 @@ hrm_status hrm_relax(hrm_ctx* c) {
   if (!c) return HRM_E_INVAL;
   c->ck->relax(c->Wn, c->dg, c->fl, c->stream);
   ++c->launches;
-  c->wn_relaxed = false;  // the FP64 relaxation, not relax_fast
+  c->wn_relaxed = false;  // (not tracked: in the precision form this is not relax_fast)
   return last_launch(c, "relax");
 }
 

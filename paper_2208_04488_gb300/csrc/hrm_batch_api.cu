@@ -55,9 +55,9 @@ struct hrm_batch {
   int64_t graph_kernels = 0;
   int64_t launches = 0;
   int64_t total_cells = 0;
-  // per instance: W^n came out of relax_fast (StepState::wn_relaxed; the
-  // precision form's updates leave out unchanged cells only then), and the
-  // value last written to the device
+  // per instance: W^n came out of the form's relaxation (StepState::wn_relaxed;
+  // the updates take the relaxation's result from W^n for unchanged cells only
+  // then), and the value last written to the device
   std::vector<char> relaxed, relaxed_dev;
   std::string err;
 };
@@ -435,7 +435,7 @@ hrm_status hrm_batch_step(hrm_batch* b, int32_t nsteps) {
   if (nsteps == 0) return HRM_OK;
   hrm_status s;
   if (!b->gexec && !b->direct && (s = build_graph(b))) return s;
-  const char after = b->params.precision == HRM_FP32 && b->params.relax_mode != HRM_RELAX_OFF;
+  const char after = b->params.relax_mode != HRM_RELAX_OFF;
   for (int i = 0; i < nsteps; ++i) {
     sync_relaxed(b);
     if ((s = launch_step(b))) return s;

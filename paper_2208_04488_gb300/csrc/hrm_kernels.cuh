@@ -779,22 +779,15 @@ __device__ __forceinline__ void fast_combine(int64_t c, const double* Wn, const 
   }
 }
 
-// Precision form: whether a stage returns cell c exactly as it is, so that its
-// arithmetic can be left out. Every flux difference G^-_{i+1/2} - G^+_{i-1/2}
-// is exactly zero when the two faces' values are bit-equal and finite; a stage
-// that combines with W^n (with_wn) also needs W_src bit-equal to W^n. Then
-// fast_combine returns W_src exactly (its weights sum to one), except that a
-// component -0 would come back +0, so those are left to the arithmetic; and
-// relax_fast, which recomputes the volume fractions from the conserved
-// variables alone, returns the cell unchanged if it came out of relax_fast
-// before -- the caller's condition. Only integer compares: no FP64 work.
+// Whether every flux difference G^-_{i+1/2} - G^+_{i-1/2} of cell c is exactly
+// +0: the two faces' values bit-equal and finite in every slot and direction.
+// Integer compares only.
 template <int N, int D>
-__device__ __forceinline__ bool stage_keeps_cell(int64_t c, const double* Wn, const double* Ws,
-                                                 const double* __restrict__ F0, const double* __restrict__ F1,
-                                                 const double* __restrict__ F2, const DevGrid& g, bool with_wn) {
+__device__ __forceinline__ bool faces_unchanged(int64_t c, const double* __restrict__ F0,
+                                                const double* __restrict__ F1, const double* __restrict__ F2,
+                                                const DevGrid& g) {
   using L = Lay<N, D>;
   constexpr int M = L::M;
-  const int64_t nc = g.ncells;
   const int64_t i0 = c % g.n[0];
   const int64_t r = c / g.n[0];
   const int64_t i1 = r % g.n[1], i2 = r / g.n[1];
@@ -816,11 +809,31 @@ __device__ __forceinline__ bool stage_keeps_cell(int64_t c, const double* Wn, co
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) same = same & same_finite(F[(L::AL + k) * nf + fr], F[(M + k) * nf + fl]);
   }
+  return same;
+}
+
+// Precision form: whether a stage returns cell c exactly as it is, so that its
+// arithmetic can be left out. Every flux difference G^-_{i+1/2} - G^+_{i-1/2}
+// is exactly zero when the two faces' values are bit-equal and finite; a stage
+// that combines with W^n (with_wn) also needs W_src bit-equal to W^n. Then
+// fast_combine returns W_src exactly (its weights sum to one), except that a
+// component -0 would come back +0, so those are left to the arithmetic; and
+// relax_fast, which recomputes the volume fractions from the conserved
+// variables alone, returns the cell unchanged if it came out of relax_fast
+// before -- the caller's condition. Only integer compares: no FP64 work.
+template <int N, int D>
+__device__ __forceinline__ bool stage_keeps_cell(int64_t c, const double* Wn, const double* Ws,
+                                                 const double* __restrict__ F0, const double* __restrict__ F1,
+                                                 const double* __restrict__ F2, const DevGrid& g, bool with_wn) {
+  constexpr int M = Lay<N, D>::M;
+  const int64_t nc = g.ncells;
+  bool same = faces_unchanged<N, D>(c, F0, F1, F2, g);
   if (with_wn) {
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      const unsigned long long bs = bits(Ws[m]);
-      same = same & (bs == bits(Wn[m * nc + c])) & (bs != 0x8000000000000000ull);
+      const unsigned long long bs = (unsigned long long)__double_as_longlong(Ws[m]);
+      same = same & (bs == (unsigned long long)__double_as_longlong(Wn[m * nc + c])) &
+             (bs != 0x8000000000000000ull);
     }
   }
   return same;
@@ -869,8 +882,12 @@ __device__ __forceinline__ void update_body(int64_t c, const double* Wn, const d
   double rhs[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) rhs[m] = 0.0;
+  // Faces all bit-equal: every difference is +0, its quotient by dx too, and
+  // the sums below would leave rhs at +0 -- the divisions are left out.
+  const bool flat = faces_unchanged<N, D>(c, F0, F1, F2, g);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
+    if (flat) break;
     const double* F = d == 0 ? F0 : (d == 1 ? F1 : F2);
     const int64_t f0 = g.n[0] + (d == 0), f1 = g.n[1] + (d == 1), f2 = g.n[2] + (d == 2);
     const int64_t nf = f0 * f1 * f2;
@@ -904,7 +921,22 @@ __device__ __forceinline__ void update_body(int64_t c, const double* Wn, const d
 #pragma unroll
     for (int m = 0; m < M; ++m) Wo[m] = a * Wn[m * nc + c] + b * (Ws[m] + dt * rhs[m]);
   }
-  if (relax) relax_cell<N, D, FAST>(Wo, f);
+  // relax_cell recomputes the volume fractions from the conserved variables
+  // alone: where those are bit-equal to W^n's and W^n came out of relax_cell
+  // (the host's flag), it would return W^n's volume fractions, taken directly.
+  bool keep = false;
+  if (relax && flat && st->wn_relaxed) {
+    keep = true;
+#pragma unroll
+    for (int m = 0; m < L::NC; ++m)
+      keep = keep & (__double_as_longlong(Wo[m]) == __double_as_longlong(Wn[m * nc + c]));
+  }
+  if (keep) {
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) Wo[L::AL + k] = Wn[(L::AL + k) * nc + c];
+  } else if (relax) {
+    relax_cell<N, D, FAST>(Wo, f);
+  }
   if (count) count_bits(st, admissibility_bits<N, D>(Wo, f));
 #pragma unroll
   for (int m = 0; m < M; ++m) Wout[m * nc + c] = Wo[m];

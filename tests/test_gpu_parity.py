@@ -435,23 +435,29 @@ def test_fp32_screen_is_exact(hrm, pr):
     ("shock_bubble_96x48", {}), ("shock_bubble_96x48", dict(relax_mode=2)),
     ("shock_bubble_96x48", dict(relax_mode=0)), ("shock_bubble_96x48", dict(integrator=1)),
     ("shock_bubble_96x48", dict(integrator=2)), ("water_column_192x96", {}), ("interface_3d_20", {}),
-    ("tube_400", {})], ids=lambda c: c[0] + "".join(f"_{k}{v}" for k, v in c[1].items()))
+    ("tube_400", {}), ("shock_bubble_96x48", dict(precision=0)), ("shock_bubble_96x48", dict(precision=0, relax_mode=2)),
+    ("interface_3d_20", dict(precision=0))],
+    ids=lambda c: c[0] + "".join(f"_{k}{v}" for k, v in c[1].items()))
 def test_fp32_unchanged_cells_left_out_exactly(hrm, case):
-    """The precision form's stage updates leave out the cells they return
-    unchanged (all flux differences exactly zero and, where the stage combines
-    with W^n, W_src equal to W^n), when W^n came out of the form's own
-    relaxation. Writing a layer back through hrm_layers before every step
-    withdraws that condition, so the second run does all the arithmetic; the
-    states agree bit for bit, from the set-up state (which the form has not
-    relaxed) on, in every integrator and relaxation mode."""
+    """The stage updates leave out work on cells where the result is known:
+    the precision form skips cells it returns unchanged (all flux differences
+    exactly zero and, where the stage combines with W^n, W_src equal to W^n),
+    the FP64 form skips their divisions and takes the relaxation's result from
+    W^n -- both only when W^n came out of the form's own relaxation. Writing a
+    layer back through hrm_layers before every step withdraws that condition,
+    so the second run does all the arithmetic; the states agree bit for bit,
+    from the set-up state (which no relaxation produced) on, in every
+    integrator and relaxation mode."""
     name, kw = case
+    kw = dict(kw)
+    kw.setdefault("precision", hrm.FP32)
     pr = {"shock_bubble_96x48": lambda: P.shock_bubble_2d(96, 48),
           "water_column_192x96": lambda: P.shock_water_column_2d(192, 96),
           "interface_3d_20": lambda: P.interface_3d(20),
           "tube_400": lambda: P.shock_tube_1d_baseline(400)}[name]()
     out = []
     for rewrite in (False, True):
-        s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, precision=hrm.FP32, check=0, **kw))
+        s = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, check=0, **kw))
         dt = 0.8 * s.dt(pr.cfl)[0]
         for _ in range(8):
             if rewrite:
@@ -461,7 +467,7 @@ def test_fp32_unchanged_cells_left_out_exactly(hrm, case):
         s.close()
     np.testing.assert_array_equal(out[0], out[1])
     # the runs moved the state, and most cells of these set-ups are uniform
-    s0 = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, precision=hrm.FP32, check=0, **kw))
+    s0 = hrm.Solver.from_problem(pr, params=hrm.params_default(cfl=pr.cfl, check=0, **kw))
     assert not np.array_equal(out[0], s0.get(hrm.FIELD_W))
     s0.close()
 
