@@ -84,6 +84,12 @@ struct hrm_ctx {
   // written there).
   bool wn_relaxed = false;
   int wn_relaxed_dev = 0;
+  // precision form: the FP32 planes and the CFL maxima (StepState::tau_bits)
+  // already hold W^n's, written by the last stage of the step just launched
+  // (fuse_last), so that the next step's first primitive pass has nothing to
+  // do; mirrored into StepState::planes_tau like wn_relaxed.
+  bool planes_tau = false;
+  int planes_tau_dev = 0;
   int profiling = 0;
   int nprof = 0;
   cudaEvent_t prof_ev[2 * kMaxProf] = {};
@@ -267,12 +273,19 @@ bool separate_gate(const hrm_ctx* c) { return c->params.learned == 1 && !defer_s
 // four-equation HRM c (params.cfl_sound).
 int tau_mode(const hrm_ctx* c) { return c->params.cfl_sound ? 2 : 1; }
 
+// The precision form's last stage writes the next step's FP32 planes and CFL
+// maxima itself: with the five-equation sound speed and without Dirichlet
+// slices (whose cells the update does not cover).
+bool fuse_last(const hrm_ctx* c) {
+  return c->params.precision == HRM_FP32 && !c->params.cfl_sound && c->nint == c->nc;
+}
+
 // One RK stage: primitives of Wsrc, (gates,) midpoint fluxes, update into Wout.
 // Precision form: the update of every stage but the last also writes the next
 // stage's FP32 planes (k_update32p, fuse_next), and a stage whose planes were
 // written so (prim_done) skips its primitive kernel.
 int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, double a, double b, int relax,
-                  int count, bool first, bool prim_done = false, bool fuse_next = false) {
+                  int count, bool first, bool prim_done = false, bool fuse_next = false, bool tau_next = false) {
   int k = 0;
   float* p32 = p32_target(c);
   if (!prim_done) {
@@ -329,7 +342,7 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
   traced(c, s, HRM_KERNEL_UPDATE, [&] {
     if (fuse_next)
       launch_update32p(c->N, c->D, c->Wn, Wsrc, Wout, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, a, b, relax,
-                       count, c->P32, r32_target(c), s);
+                       count, c->P32, r32_target(c), s, tau_next ? 1 : 0);
     else
       c->fk->update(0, c->params.precision == HRM_FP32, c->Wn, Wsrc, Wout, c->F[0], c->F[1], c->F[2], c->dg,
                     c->fl, c->st, a, b, relax, count, s);
@@ -345,19 +358,20 @@ int enqueue_step(hrm_ctx* c, cudaStream_t s) {
   const int rf = c->params.relax_mode != HRM_RELAX_OFF;
   const int ck = c->params.check ? 1 : 0;  // admissibility counters, read only with params.check
   const bool fp32 = c->params.precision == HRM_FP32;  // stages after the first take fused planes
+  const bool fl = fuse_last(c);  // the last stage: the next step's planes and CFL maxima too
   int k = 0;
   switch (c->params.integrator) {
     case HRM_EULER:
-      k += enqueue_stage(c, s, c->Wn, c->Wn, 0.0, 1.0, rf, ck, true);
+      k += enqueue_stage(c, s, c->Wn, c->Wn, 0.0, 1.0, rf, ck, true, false, fl, fl);
       break;
     case HRM_RK2:
       k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true, false, fp32);
-      k += enqueue_stage(c, s, c->Ws, c->Wn, 0.5, 0.5, rf, ck, false, fp32);
+      k += enqueue_stage(c, s, c->Ws, c->Wn, 0.5, 0.5, rf, ck, false, fp32, fl, fl);
       break;
     default:
       k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true, false, fp32);
       k += enqueue_stage(c, s, c->Ws, c->Ws, 0.75, 0.25, rs, 0, false, fp32, fp32);
-      k += enqueue_stage(c, s, c->Ws, c->Wn, 1.0 / 3.0, 2.0 / 3.0, rf, ck, false, fp32);
+      k += enqueue_stage(c, s, c->Ws, c->Wn, 1.0 / 3.0, 2.0 / 3.0, rf, ck, false, fp32, fl, fl);
       break;
   }
   return k;
@@ -547,15 +561,31 @@ void reset_step_state(hrm_ctx* c) {
   cudaStreamSynchronize(c->stream);
   c->wn_relaxed = false;
   c->wn_relaxed_dev = 0;
+  c->planes_tau = false;
+  c->planes_tau_dev = 0;
 }
 
-// The relaxed-state flag of W^n as the next kernels on the stream must see it.
-void sync_relaxed(hrm_ctx* c) {
-  const int v = c->wn_relaxed ? 1 : 0;
-  if (v == c->wn_relaxed_dev) return;
-  cudaMemsetAsync(&c->st->wn_relaxed, v, sizeof(int), c->stream);  // bytes 0x01: nonzero
-  c->wn_relaxed_dev = v;
+// The host flags of W^n as the next kernels on the stream must see them.
+void sync_flag(hrm_ctx* c, bool v, int& dev, int* target) {
+  if ((v ? 1 : 0) == dev) return;
+  cudaMemsetAsync(target, v ? 1 : 0, sizeof(int), c->stream);  // bytes 0x01: nonzero
+  dev = v ? 1 : 0;
 }
+void sync_relaxed(hrm_ctx* c) {
+  sync_flag(c, c->wn_relaxed, c->wn_relaxed_dev, &c->st->wn_relaxed);
+  sync_flag(c, c->planes_tau, c->planes_tau_dev, &c->st->planes_tau);
+}
+
+// Every write of the state, and every call that runs a primitive pass or
+// consumes the CFL maxima outside a step, leaves the planes and maxima to the
+// next step's primitive pass: the maxima the last stage accumulated are
+// discarded and the device flag cleared at once (stream order).
+void planes_stale(hrm_ctx* c) {
+  if (c->planes_tau) cudaMemsetAsync(c->st->tau_bits, 0, sizeof c->st->tau_bits, c->stream);
+  c->planes_tau = false;
+  sync_flag(c, false, c->planes_tau_dev, &c->st->planes_tau);
+}
+
 
 // After a full step: W^n came out of the form's relaxation when the step
 // relaxed at its last stage.
@@ -783,7 +813,10 @@ void hrm_destroy(hrm_ctx* c) {
 
 hrm_status hrm_set_step_path(hrm_ctx* c, int32_t path) {
   if (!c || (path != 0 && path != 1)) return c ? fail(c, HRM_E_INVAL, "step path must be 0 or 1") : HRM_E_INVAL;
-  if (path != c->step_path) drop_graph(c);
+  if (path != c->step_path) {
+    drop_graph(c);
+    planes_stale(c);
+  }
   c->step_path = path;
   return HRM_OK;
 }
@@ -856,6 +889,7 @@ hrm_status hrm_set_params(hrm_ctx* c, const hrm_params* p) {
   fill_dev_params(c);
   drop_graph(c);
   c->wn_relaxed = false;
+  planes_stale(c);
   StepState* st = c->st;
   double cfl = p->cfl;
   cudaMemcpyAsync(&st->cfl, &cfl, sizeof cfl, cudaMemcpyHostToDevice, c->stream);
@@ -892,6 +926,7 @@ hrm_status hrm_set_boundary(hrm_ctx* c, int32_t side, const double* values, int3
                             int32_t on_device) {
   Range range("hrm_set_boundary");
   if (!c || !values) return HRM_E_INVAL;
+  planes_stale(c);
   if (side < 0 || side >= 2 * c->D || c->dg.bc[side] != HRM_BC_DIRICHLET)
     return fail(c, HRM_E_INVAL, "side %d is not a Dirichlet side", side);
   const int64_t off = c->dg.goff[side], ns = c->nint / c->dg.n[side / 2];
@@ -918,6 +953,7 @@ hrm_status hrm_set_boundary(hrm_ctx* c, int32_t side, const double* values, int3
 hrm_status hrm_dt(hrm_ctx* c, double cfl, double* dt_out, double* tau_out) {
   Range range("hrm_dt");
   if (!c || !(cfl > 0.0)) return c ? fail(c, HRM_E_INVAL, "cfl must be positive") : HRM_E_INVAL;
+  planes_stale(c);
   if (hrm_status s = check_boundaries(c)) return s;
   c->ck->prim(c->Wn, c->V, c->AUX, nullptr, nullptr, c->dg, c->fl, c->st, tau_mode(c), c->stream);
   launch_finalize(c->st, c->dg, c->D, cfl, 1, c->stream);
@@ -949,6 +985,7 @@ hrm_status hrm_step(hrm_ctx* c, double dt, int32_t nsteps) {
     if ((s = cuda_check(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch"))) return s;
     c->launches += c->graph_kernels;
     c->wn_relaxed = step_leaves_relaxed(c);
+    c->planes_tau = fuse_last(c) && !c->persist;
   }
   if (!c->params.check) return last_launch(c, "step");
   if (c->persist) {
@@ -989,6 +1026,7 @@ hrm_status hrm_step(hrm_ctx* c, double dt, int32_t nsteps) {
 hrm_status hrm_step_tau(hrm_ctx* c, double* tau) {
   Range range("hrm_step_tau");
   if (!c || !tau) return c ? fail(c, HRM_E_INVAL, "null tau") : HRM_E_INVAL;
+  planes_stale(c);
   hrm_status s;
   if ((s = check_boundaries(c))) return s;
   // the primitive kernel of a step's first stage, with its CFL maxima
@@ -1010,6 +1048,7 @@ hrm_status hrm_step_tau(hrm_ctx* c, double* tau) {
 hrm_status hrm_begin_step(hrm_ctx* c, const double* tau, double dt) {
   Range range("hrm_begin_step");
   if (!c || !tau) return c ? fail(c, HRM_E_INVAL, "null tau") : HRM_E_INVAL;
+  planes_stale(c);
   unsigned long long bits[3] = {0ull, 0ull, 0ull};
   double sum = 0.0;
   for (int d = 0; d < c->D; ++d) {
@@ -1038,6 +1077,7 @@ int32_t hrm_stages(const hrm_ctx* c) {
 hrm_status hrm_stage(hrm_ctx* c, int32_t stage) {
   Range range("hrm_stage");
   if (!c) return HRM_E_INVAL;
+  planes_stale(c);
   const int ns = hrm_stages(c);
   if (stage < 0 || stage >= ns) return fail(c, HRM_E_INVAL, "stage %d outside 0..%d", stage, ns - 1);
   hrm_status s;
@@ -1081,7 +1121,10 @@ hrm_status hrm_layers(hrm_ctx* c, int32_t stage, int32_t set, int64_t first, int
   double* state = stage == 0 ? c->Wn : c->Ws;
   const int64_t cells = count * layer, off = first * layer;
   hrm_status s;
-  if (set) c->wn_relaxed = false;  // the written cells need not be relax_fast output
+  if (set) {
+    c->wn_relaxed = false;  // the written cells need not be relaxation output
+    planes_stale(c);
+  }
   if (set)
     s = copy_planes(c, state + off, c->nc, buf, cells, cells, c->M,
                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, "set layers");
@@ -1099,12 +1142,14 @@ hrm_status hrm_relax(hrm_ctx* c) {
   c->ck->relax(c->Wn, c->dg, c->fl, c->stream);
   ++c->launches;
   c->wn_relaxed = false;  // (not tracked: in the precision form this is not relax_fast)
+  planes_stale(c);
   return last_launch(c, "relax");
 }
 
 hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
   Range range("hrm_rhs");
   if (!c || !lam || !rhs) return HRM_E_INVAL;
+  planes_stale(c);
   double l3[3] = {0.0, 0.0, 0.0};
   for (int d = 0; d < c->D; ++d) l3[d] = lam[d];
   hrm_status s;

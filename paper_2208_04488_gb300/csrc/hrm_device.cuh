@@ -136,6 +136,7 @@ struct StepState {
   unsigned long long counts[4];    // admissibility counters
   unsigned long long waits;        // bounded tensor-core waits that ran out (learned gate)
   int wn_relaxed;  // nonzero: every interior cell of W^n came out of the form's relaxation (set by the host)
+  int planes_tau;  // nonzero: the FP32 planes and tau_bits already hold W^n's (set by the host)
 };
 
 // Whether the midpoints of direction dir go to blocks in patches of 32 along x

@@ -447,6 +447,9 @@ template <int N, int D>
 __global__ void __launch_bounds__(kCellThreads)
     k_prim32(const double* __restrict__ W, float* __restrict__ P32, float* __restrict__ R32, DevGrid g, DevFluid f,
              StepState* st, int tau) {
+  // a step's first primitive pass: the previous step's last update may have
+  // written these planes and CFL maxima already (k_update32p with tau)
+  if (tau && st->planes_tau) return;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double s[D];
 #pragma unroll
@@ -535,10 +538,17 @@ __device__ __forceinline__ void update32p_cell(int64_t c, const double* Wn, cons
                                                const double* __restrict__ F0, const double* __restrict__ F1,
                                                const double* __restrict__ F2, const DevGrid& g, const DevFluid& f,
                                                StepState* st, double a, double b, int relax, int count,
-                                               float* __restrict__ P32, float* __restrict__ R32) {
+                                               float* __restrict__ P32, float* __restrict__ R32,
+                                               double* s = nullptr) {
   using L = Lay<N, D>;
+  using Q = P32Lay<N, D>;
   constexpr int M = L::M;
   const int64_t nc = g.ncells;
+  // the cell's five-equation CFL speeds (|u_d| + c) / dx_d, as k_prim32 forms them
+  auto speeds = [&](const float* u, float cs) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) s[d] = widen_f32((fabsf(u[d]) + cs) * narrow_f64(g.inv_dx[d]));
+  };
   double Ws[M], Wo[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) Ws[m] = Wsrc[m * nc + c];
@@ -550,6 +560,12 @@ __device__ __forceinline__ void update32p_cell(int64_t c, const double* Wn, cons
       for (int m = 0; m < M; ++m) Wout[m * nc + c] = Ws[m];
     }
     if (count) count_bits(st, admissibility_bits<N, D>(Ws, f));
+    if (s) {
+      float u[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) u[d] = P32[(int64_t)(L::MOM + d) * nc + c];
+      speeds(u, P32[(int64_t)Q::C * nc + c]);
+    }
     return;
   }
   fast_combine<N, D>(c, Wn, Ws, F0, F1, F2, g, st->dt, a, b, Wo);
@@ -563,6 +579,7 @@ __device__ __forceinline__ void update32p_cell(int64_t c, const double* Wn, cons
   for (int m = 0; m < M; ++m) Wout[m * nc + c] = Wo[m];
   float u[D], cs;
   prim32_store<N, D>(c, Wo, rho, Re, P32, R32, nc, f, u, cs);
+  if (s) speeds(u, cs);
 }
 
 template <int N, int D>
@@ -570,10 +587,21 @@ __global__ void __launch_bounds__(kCellThreads)
     k_update32p(const double* Wn, const double* Wsrc, double* Wout, const double* __restrict__ F0,
                 const double* __restrict__ F1, const double* __restrict__ F2, DevGrid g, DevFluid f,
                 StepState* st, double a, double b, int relax, int count, float* __restrict__ P32,
-                float* __restrict__ R32) {
+                float* __restrict__ R32, int tau = 0) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.nint) return;
-  update32p_cell<N, D>(c, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32);
+  if (!tau) {
+    if (c >= g.nint) return;
+    update32p_cell<N, D>(c, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32);
+    return;
+  }
+  // a step's last stage (tau): the next step's planes and CFL maxima as well,
+  // which k_prim32 then leaves as they are (grids without Dirichlet slices,
+  // whose cells this kernel does not cover)
+  double s[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) s[d] = 0.0;
+  if (c < g.nint) update32p_cell<N, D>(c, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32, s);
+  block_tau_max<D>(s, st->tau_bits);
 }
 
 // DEFER: where a screen fails (or for the first-order scheme) return false

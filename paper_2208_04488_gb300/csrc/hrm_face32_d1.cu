@@ -47,12 +47,14 @@ void update32_d1(int N, const double* Wn, const double* Wsrc, double* Wout, cons
 
 void update32p_d1(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
                   const double* F2, const DevGrid& g, const DevFluid& f, StepState* st, double a, double b, int relax,
-                  int count, float* P32, float* R32, cudaStream_t s) {
+                  int count, float* P32, float* R32, int tau, cudaStream_t s) {
   const unsigned gr = grid_for(g.nint, kCellThreads);
   if (N == 2)
-    k_update32p<2, kD><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32);
+    k_update32p<2, kD><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32,
+                                                    tau);
   else if (N == 3)
-    k_update32p<3, kD><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32);
+    k_update32p<3, kD><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32,
+                                                    tau);
 }
 
 void face32_d1(int N, int dir, const double* W, const double* V, const double* AUX, const float* P32, double* out,

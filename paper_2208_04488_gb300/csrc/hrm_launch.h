@@ -105,19 +105,22 @@ void face32_d3(int N, int dir, const double* W, const double* V, const double* A
 // hrm_face32_dD.cu).
 void update32p_d1(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
                   const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
-                  int count, float* P32, float* R32, cudaStream_t);
+                  int count, float* P32, float* R32, int tau, cudaStream_t);
 void update32p_d2(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
                   const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
-                  int count, float* P32, float* R32, cudaStream_t);
+                  int count, float* P32, float* R32, int tau, cudaStream_t);
 void update32p_d3(int N, const double* Wn, const double* Wsrc, double* Wout, const double* F0, const double* F1,
                   const double* F2, const DevGrid&, const DevFluid&, StepState*, double a, double b, int relax,
-                  int count, float* P32, float* R32, cudaStream_t);
+                  int count, float* P32, float* R32, int tau, cudaStream_t);
+// tau: also accumulate the CFL maxima of W_out into st->tau_bits (a step's last
+// stage; grids without Dirichlet slices, five-equation sound speed).
 inline void launch_update32p(int N, int D, const double* Wn, const double* Wsrc, double* Wout, const double* F0,
                              const double* F1, const double* F2, const DevGrid& g, const DevFluid& f, StepState* st,
-                             double a, double b, int relax, int count, float* P32, float* R32, cudaStream_t s) {
-  if (D == 1) update32p_d1(N, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32, s);
-  if (D == 2) update32p_d2(N, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32, s);
-  if (D == 3) update32p_d3(N, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32, s);
+                             double a, double b, int relax, int count, float* P32, float* R32, cudaStream_t s,
+                             int tau = 0) {
+  if (D == 1) update32p_d1(N, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32, tau, s);
+  if (D == 2) update32p_d2(N, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32, tau, s);
+  if (D == 3) update32p_d3(N, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, P32, R32, tau, s);
 }
 
 // Primitive kernel of the precision form (FP32 planes only; hrm_face32_dD.cu).

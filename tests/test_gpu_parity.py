@@ -472,6 +472,29 @@ def test_fp32_unchanged_cells_left_out_exactly(hrm, case):
     s0.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_dt_and_steps_after_steps_equal_a_fresh_context(hrm, precision):
+    """The precision form's last stage writes the next step's FP32 planes and
+    CFL maxima, and the next step's primitive pass then leaves them; hrm_dt
+    between steps must still see only the current state: its dt, and the steps
+    that follow, equal those of a new context given that state."""
+    pr = P.shock_bubble_2d(96, 48)
+    prm = hrm.params_default(cfl=pr.cfl, check=0, precision=precision)
+    s = hrm.Solver.from_problem(pr, params=prm)
+    s.step(0.0, 3)
+    W = s.get(hrm.FIELD_W)
+    t = hrm.Solver.from_problem(pr, params=prm, set_state=False)
+    t.set(W)
+    (dt_s, tau_s), (dt_t, tau_t) = s.dt(pr.cfl), t.dt(pr.cfl)
+    assert dt_s == dt_t
+    np.testing.assert_array_equal(tau_s, tau_t)
+    s.step(0.0, 3)
+    t.step(0.0, 3)
+    np.testing.assert_array_equal(s.get(hrm.FIELD_W), t.get(hrm.FIELD_W))
+    s.close()
+    t.close()
+
+
 MODES = [dict(integrator=1), dict(integrator=2), dict(scheme=1), dict(relax_mode=2), dict(relax_mode=0),
          dict(blend=0), dict(limiters=0, cfl=0.4)]
 
