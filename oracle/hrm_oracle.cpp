@@ -370,7 +370,22 @@ static void hllc(const FluidK& f, int dir, const real* VL, const real* VR, real*
 // Incremental-stencil WENO interpolation (App. C), left-biased midpoint value
 // at x_{i+1/2} from u[0..4] = u_{i-2}, u_{i-1}, u_i, u_{i+1}, u_{i+2}.
 // ---------------------------------------------------------------------------
+// Whether the five stencil values are bit-identical.
+static bool constant_stencil(const real* u) {
+  uint64_t b[5];
+  for (int j = 0; j < 5; ++j) {
+    const double x = val(u[j]);
+    std::memcpy(&b[j], &x, sizeof x);
+  }
+  return b[0] == b[2] && b[1] == b[2] && b[3] == b[2] && b[4] == b[2];
+}
+
 static real weno_is_left(const real* u, double eps, real* omega_out) {
+  // A constant stencil: every sub-stencil interpolant reproduces the constant
+  // and the weights sum to one (App. C), so the interpolated value is that
+  // constant, returned as it is (the weighted sum below reaches it only to
+  // rounding). The weights themselves (omega_out) are formed in full.
+  if (!omega_out && constant_stencil(u)) return u[2];
   const real um2 = u[0], um1 = u[1], u0 = u[2], up1 = u[3], up2 = u[4];
   // sub-stencil interpolants S0..S3
   real s0 = real(0.5) * (u0 + up1);
@@ -420,6 +435,8 @@ static real weno_is_left(const real* u, double eps, real* omega_out) {
 // (optimal) weight d_k: the value a smoothness gate selects where it judges
 // the stencil smooth (the nonlinear weights then differ little from d_k).
 static real weno_lin_left(const real* u) {
+  // a constant stencil: the linear weights sum to one as well (App. C)
+  if (constant_stencil(u)) return u[2];
   const real um2 = u[0], um1 = u[1], u0 = u[2], up1 = u[3], up2 = u[4];
   real s0 = real(0.5) * (u0 + up1);
   real s1 = real(0.5) * (real(3.0) * u0 - um1);

@@ -36,13 +36,18 @@ class Source:
 
 def default_sources(scale: str = "full") -> List[Source]:
     """The training problems: the 400-cell water-air shock tube, the 2D
-    shock-bubble interaction (1024 x 512; 256 x 128 when scale="small") and the
-    3D perturbed interface (128^3; 32^3 when small)."""
+    shock-bubble interaction (1024 x 512; 256 x 128 when scale="small"), the
+    3D perturbed interface (128^3; 32^3 when small) and the periodic smooth
+    advection of Sec. 5.2 (256^2; 128^2 when small), whose volume fractions
+    vary smoothly at every midpoint (the other problems' smooth stencils are
+    mostly interface tails)."""
     small = scale == "small"
     tube = P.shock_tube_1d_baseline(400)
     bubble = P.shock_bubble_2d(256, 128) if small else P.shock_bubble_2d(1024, 512)
     iface = P.interface_3d(32 if small else 128)
+    adv = P.advection_2d_smooth(128 if small else 256)
     return [
+        Source(adv, snapshots=3, steps_between=10, keep_smooth=0.3 if small else 0.05, keep_flat=0.01),
         Source(tube, snapshots=6, steps_between=60, keep_smooth=1.0, keep_flat=0.2),
         Source(bubble, snapshots=4, steps_between=40 if small else 150, precision=hrm.FP32,
                keep_smooth=0.2 if small else 0.05, keep_flat=0.02 if small else 0.005),
