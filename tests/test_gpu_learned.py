@@ -362,7 +362,7 @@ def trained(hrm):
 
 def test_training_on_method_stencils(hrm, trained):
     """Trained on stencils of the method's own runs (shock tube, shock-bubble,
-    3D interface): the loss falls, the set holds both classes, and the
+    3D interface, smooth periodic advection): the loss falls, the set holds both classes, and the
     tensor-core inference classifies the training midpoints with few
     smooth-predictions on rough stencils."""
     det, rep = trained
