@@ -98,12 +98,13 @@ def dist_env():
     return ws, rank, local
 
 
-def algorithmic_face_flops(problem, cfl):
-    """Algorithmic flops per midpoint of each direction on the initial state,
-    from the oracle's operation-counting build (add, mul, div, sqrt, tanh each
-    one flop)."""
+def algorithmic_face_flops(problem, cfl, W=None):
+    """Algorithmic flops per midpoint of each direction on the state W (default:
+    the initial state), from the oracle's operation-counting build (add, mul,
+    div, sqrt, tanh each one flop)."""
     import oracle
-    f, g, W = oracle.setup(problem)
+    f, g, W0 = oracle.setup(problem)
+    W = W0 if W is None else np.ascontiguousarray(W, dtype=np.float64)
     dt, _ = oracle.dt(f, g, W, cfl)
     lam = oracle.lambdas(f, g, W, dt)
     out = []
@@ -111,6 +112,16 @@ def algorithmic_face_flops(problem, cfl):
         c, nf = oracle.faces_flops(f, oracle.make_params(), g, W, lam, d)
         out.append((sum(c.values()) / nf, nf, c))
     return out
+
+
+def run_face_flops(problem, cfl, W_end):
+    """Flops per midpoint of each direction over a run from the initial state to
+    W_end: the mean of the counts on the two states. A uniform stencil (six
+    bit-identical node states) costs only the node flux, and the share of such
+    midpoints falls as the waves spread, so the initial state alone undercounts."""
+    a = algorithmic_face_flops(problem, cfl)
+    b = algorithmic_face_flops(problem, cfl, W_end)
+    return [(0.5 * (x[0] + y[0]), x[1], {"first": round(x[0], 1), "last": round(y[0], 1)}) for x, y in zip(a, b)]
 
 
 def first_order_face_flops(problem, cfl, d):
@@ -401,15 +412,27 @@ def measure_decomposed(torch, hrm, problems, dist, rank, ws, stream):
     return out
 
 
-def gated_face_flops(problem, cfl):
+def gated_face_flops(problem, cfl, W_end=None):
     """Algorithmic flops per midpoint with every midpoint gated to the linear
-    WENO weights (oracle counting build), per direction."""
+    WENO weights (oracle counting build), per direction; with W_end, the mean of
+    the counts on the initial state and on W_end."""
     import oracle
-    f, g, W = oracle.setup(problem)
-    dt, _ = oracle.dt(f, g, W, cfl)
-    lam = oracle.lambdas(f, g, W, dt)
-    return [sum(oracle.faces_flops(f, oracle.make_params(), g, W, lam, d, gated=True)[0].values())
-            / oracle.faces_flops(f, oracle.make_params(), g, W, lam, d, gated=True)[1] for d in range(problem.D)]
+    f, g, W0 = oracle.setup(problem)
+
+    def count(W):
+        dt, _ = oracle.dt(f, g, W, cfl)
+        lam = oracle.lambdas(f, g, W, dt)
+        out = []
+        for d in range(problem.D):
+            c, nf = oracle.faces_flops(f, oracle.make_params(), g, W, lam, d, gated=True)
+            out.append(sum(c.values()) / nf)
+        return out
+
+    a = count(W0)
+    if W_end is None:
+        return a
+    b = count(np.ascontiguousarray(W_end, dtype=np.float64))
+    return [0.5 * (x + y) for x, y in zip(a, b)]
 
 
 def train_detector(hrm, stream):
@@ -541,9 +564,9 @@ def measure_learned_workload(torch, hrm, problems, det, stream, flush, args, fp6
     s0.close()
     dt = 0.8 * dt0
     K = max(4, args.steps // 2)
-    faces = algorithmic_face_flops(pr, pr.cfl)
-    faces_g = gated_face_flops(pr, pr.cfl)
     ref = run_form(torch, hrm, pr, hrm.FP64, None, dt, K, args.warmup, flush, stream)
+    faces = run_face_flops(pr, pr.cfl, ref["W"])
+    faces_g = gated_face_flops(pr, pr.cfl, ref["W"])
     out = {"workload": "2D shock-water column + SF6 bubble, 2048x1024, Mach 1.47, paper fluids, CFL 0.5 "
                        "(0.8 x the initial CFL step, fixed)", "cells": pr.ncells, "steps": K, "dt": dt,
            "validation_on_this_workload": learned.validation(det, problems.shock_water_column_2d(1024, 512), 100,
@@ -691,7 +714,9 @@ def main():
         pk, pk_src = peaks()
         fp64_peak = hrm.probe_fma_peak(hrm.FP64)
         fp32_peak = hrm.probe_fma_peak(hrm.FP32)
-        faces = algorithmic_face_flops(pr, pr.cfl)
+        # flops of the method per midpoint over the timed steps (they start from
+        # the initial state and end at W_fp64)
+        faces = run_face_flops(pr, pr.cfl, W_fp64)
         # dominant kernels: the per-midpoint sweeps (one launch per direction and
         # stage); algorithmic flops per launch / average launch duration
         fl_launch = sum(faces[d][0] * faces[d][1] for d in range(pr.D)) / pr.D
@@ -712,7 +737,7 @@ def main():
         bytes32 = 4 * (pr.M + 4 + pr.D + pr.N - 1) * pr.ncells + 8 * (pr.M + pr.N - 1) * nfx
         learned_block = None
         if learned_runs is not None:
-            faces_g = gated_face_flops(pr, pr.cfl)
+            faces_g = gated_face_flops(pr, pr.cfl, W_fp64)
             learned_block = {"detector": train_rep,
                              "threshold": 0.5,
                              "shock_water_column": measure_learned_workload(torch, hrm, problems, det, stream, flush,
@@ -732,10 +757,13 @@ def main():
                          "fp64_pipe_active_ncu": FP64_PIPE_ACTIVE["k_face_fp64"],
                          "peak_source": "measured FP64 FMA-chain probe on this GPU (hrm_probe_fma_peak)",
                          "algorithmic_flops_per_face": [round(x[0], 1) for x in faces],
-                         "of_which_first_order_flux": round(first_order_face_flops(pr, pr.cfl, 0), 1),
+                         "flops_per_face_first_last_state": [x[2] for x in faces],
+                         "first_order_flux_flops_per_nonuniform_midpoint": round(first_order_face_flops(pr, pr.cfl, 0), 1),
                          "flop_count": "the oracle's count of the method as written (add, mul, div, sqrt, "
-                                       "tanh one flop each); it includes the first-order HLLC flux at every "
-                                       "midpoint, which the sweep evaluates only where the flux limiter can act",
+                                       "tanh one flop each), the mean of its counts on the first and the last "
+                                       "state of the timed steps; it includes the first-order HLLC flux at every "
+                                       "non-uniform midpoint, which the sweep evaluates only where the flux "
+                                       "limiter can act, and only the node flux at uniform stencils",
                          "avg_launch_ms": 1e3 * t_face / n_face, "launches_timed": n_face,
                          "launch_timing": "the x and y sweeps of a stage run concurrently: their common "
                                           "fork-to-join time, divided by the launches in it",

@@ -676,6 +676,20 @@ static void back_project(const FluidK& f, int dir, const real* arb, real rhob, r
   for (int k = 0; k < N - 1; ++k) Vt[sAL(f, k)] = Ut[N + D + k];
 }
 
+// Whether the six node states of a midpoint are bit-identical.
+static bool uniform_nodes(const FluidK& f, const Cell* nd) {
+  for (int m = 0; m < f.M; ++m) {
+    uint64_t b[6];
+    for (int j = 0; j < 6; ++j) {
+      const double x = val(nd[j].W[m]);
+      std::memcpy(&b[j], &x, sizeof x);
+    }
+    for (int j = 0; j < 6; ++j)
+      if (b[j] != b[2]) return false;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // One midpoint x_{i+1/2} in direction `dir` from the six node cells
 // nd[0..5] = i-2 .. i+3. Produces the quasi-conservative fluxes
@@ -689,6 +703,22 @@ static void face_flux(const FluidK& f, const or_params* P, int dir, real lam, co
   const Cell& ci = nd[2];
   const Cell& cj = nd[3];
   const int un = sMOM(f, dir), sp = sE(f);
+
+  // A uniform stencil (six bit-identical node states) of the high-order scheme
+  // takes the node's physical flux F^d with zero alpha slots: in exact arithmetic
+  // that is what every step below returns. The WENO-IS and linear interpolations
+  // reproduce a constant (App. C), so V~_L = V~_R = V; the HLLC flux of two equal
+  // states is their physical flux (Sec. 4.1.1); the HCS weights sum to one
+  // (psi - 2 a1 + 2 a2 - 2 a3 = 1), so G^HCS = G~ and any sensor blend of the two
+  // returns it, with u^ the node velocity; the quasi-conservative alpha slots are
+  // then alpha u - u alpha = 0 (Eq. G_pm); and the node state is each positivity
+  // limiter's own first-order candidate, so neither limiter changes the result
+  // (Sec. 4.3.2). The diagnostic path (dg) evaluates every step.
+  if (!dg && P->scheme == 0 && uniform_nodes(f, nd)) {
+    flux_F(f, dir, ci.V, ci.W, Gm);
+    for (int m = 0; m < M; ++m) Gp[m] = Gm[m];
+    return;
+  }
 
   // First-order HLLC flux G^{HLLC} and u_* from the node states (Sec. 4.1.1).
   real GH[OR_MAXM], uH;

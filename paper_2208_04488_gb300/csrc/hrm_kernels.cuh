@@ -365,6 +365,20 @@ __device__ __forceinline__ void node_flux(const double* W, const double* V, doub
   F[L::EN] = (W[L::EN] + p) * un;
 }
 
+// Whether the six node states of a midpoint are bit-identical (every plane of W).
+template <int N, int D>
+__device__ __forceinline__ bool uniform_nodes(const double* __restrict__ W, int64_t nc, const Nodes6& nd) {
+  bool same = true;
+#pragma unroll
+  for (int m = 0; m < Lay<N, D>::M; ++m) {
+    const long long b = __double_as_longlong(W[m * nc + nd.c[2]]);
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      if (j != 2) same &= __double_as_longlong(W[m * nc + nd.c[j]]) == b;
+  }
+  return same;
+}
+
 // Outputs of a midpoint: M + N - 1 planes over the face grid of the direction --
 // the NC conservative flux slots, the N-1 alpha slots of G^-_{i+1/2} (planes
 // AL..M-1) and the N-1 alpha slots of G^+_{i+1/2} (planes M..M+N-2).
@@ -419,6 +433,24 @@ __device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const dou
   if (pr.scheme == 1) {
     first_order();
     G = H;
+  } else if (uniform_nodes<N, D>(W, nc, nd)) {
+    // six bit-identical node states: in exact arithmetic every step below returns
+    // the node's physical flux with zero alpha slots -- constants are reproduced
+    // by the interpolation (App. C), the HLLC flux of equal states is their flux
+    // (Sec. 4.1.1), the HCS weights sum to one, alpha u - u alpha = 0 (Eq. G_pm),
+    // and the node state is the limiters' own candidate (Sec. 4.3.2)
+    const double un = Vi[L::MOM + DIR], p = Vi[L::EN];
+#pragma unroll
+    for (int k = 0; k < N; ++k) G.Gc[k] = Wi[k] * un;
+#pragma unroll
+    for (int d = 0; d < D; ++d) G.Gc[L::MOM + d] = Wi[L::MOM + d] * un;
+    G.Gc[L::MOM + DIR] = G.Gc[L::MOM + DIR] + p;
+    G.Gc[L::EN] = (Wi[L::EN] + p) * un;
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+      G.gm[k] = 0.0;
+      G.gp[k] = 0.0;
+    }
   } else {
     R p6[6], u6[6];
 #pragma unroll

@@ -85,7 +85,9 @@ def test_fixed_gate_scheme_bit_exact(hrm, orc, pr):
 
 
 def _node_cells(pr, d, t):
-    """Cell indices of the six stencil nodes of midpoints t of direction d."""
+    """Cell indices of the six stencil nodes of midpoints t of direction d
+    (periodic or clamped; a Dirichlet node keeps the clamped cell here and is
+    replaced by its boundary slice in _stencil_inputs)."""
     ext = list(pr.n) + [1] * (3 - pr.D)
     fe = [ext[e] + (e == d) for e in range(3)]
     q = [t % fe[0], (t // fe[0]) % fe[1], t // (fe[0] * fe[1])]
@@ -100,6 +102,41 @@ def _node_cells(pr, d, t):
         r[d] = jj
         out.append((r[2] * ext[1] + r[1]) * ext[0] + r[0])
     return np.stack(out, axis=1)
+
+
+def _stencil_inputs(orc, pr, f, W, d):
+    """The gate's five inputs (alpha_1, alpha_2, rho, u_d, p) at the six nodes of
+    every midpoint of direction d, (n_faces, 6) each (None for an absent volume
+    fraction): interior cells, and for a node beyond a Dirichlet side the cell of
+    that side's boundary slice continuing the line (oracle values only)."""
+    def per_cell(Wc):
+        V = np.stack([orc.prim_cell(f, Wc[:, c])[0] for c in range(Wc.shape[1])], axis=1)
+        al = [V[pr.N + pr.D + 1 + k] if pr.N > 1 + k else None for k in range(2)]
+        return al + [Wc[:pr.N].sum(axis=0), V[pr.N + d], V[pr.N + pr.D]]
+    inner = per_cell(W)
+    bnd = {b: per_cell(orc.ic_from_prim(f, prim)) for b, prim in getattr(pr, "boundary", {}).items()}
+    t = np.arange(face_counts(pr)[d])
+    cells = _node_cells(pr, d, t)
+    ext = list(pr.n) + [1] * (3 - pr.D)
+    fe = [ext[e] + (e == d) for e in range(3)]
+    q = [t % fe[0], (t // fe[0]) % fe[1], t // (fe[0] * fe[1])]
+    sl, stride = np.zeros_like(t), 1  # slice cell: the other indices, lowest fastest
+    for e in range(pr.D):
+        if e != d:
+            sl, stride = sl + q[e] * stride, stride * ext[e]
+    out = []
+    for a, arr in enumerate(inner):
+        if arr is None:
+            out.append(None)
+            continue
+        v = arr[cells]
+        for j in range(6):
+            jj = q[d] - 3 + j
+            for side, beyond in ((0, jj < 0), (1, jj >= ext[d])):
+                if pr.bc[2 * d + side] == 2 and beyond.any():
+                    v[beyond, j] = bnd[2 * d + side][a][sl[beyond]]
+        out.append(v)
+    return out
 
 
 COLLECT_PROBLEMS = [P.shock_tube_1d_baseline(64), P.shock_bubble_2d(40, 21), P.interface_3d(12)]
@@ -118,9 +155,6 @@ def test_collect_matches_oracle(hrm, orc, pr):
     assert added == sum(face_counts(pr)) == det.size()
     X, y, dv = det.samples()
     op = orc.make_params()
-    # per-cell quantities (alpha_1, alpha_2, rho, u_d, p) for the tolerance
-    Vc = np.stack([orc.prim_cell(f, W[:, c])[0] for c in range(pr.ncells)], axis=1)
-    rho = W[:pr.N].sum(axis=0)
     off = 0
     for d, nf in enumerate(face_counts(pr)):
         idx = np.arange(nf)
@@ -129,16 +163,15 @@ def test_collect_matches_oracle(hrm, orc, pr):
         np.testing.assert_allclose(dv[sl], dev_or.astype(np.float32), rtol=1e-6, atol=1e-30)
         clear = np.abs(dev_or - 0.01) > 1e-9
         np.testing.assert_array_equal(y[sl][clear], (dev_or < 0.01)[clear].astype(np.float32))
-        cells = _node_cells(pr, d, idx)
-        qs = [Vc[pr.N + pr.D + 1] if pr.N > 1 else None, Vc[pr.N + pr.D + 2] if pr.N > 2 else None,
-              rho, Vc[pr.N + d], Vc[pr.N + pr.D]]
+        # node values of the gate's inputs (alpha_1, alpha_2, rho, u_d, p) for the tolerance
+        qs = _stencil_inputs(orc, pr, f, W, d)
         for a in range(5):
             got = X[sl, 6 * a:6 * a + 6].astype(np.float64)
             ref = F_or[:, 6 * a:6 * a + 6]
             if qs[a] is None:
                 assert np.all(got == 0.0)
                 continue
-            qv = qs[a][cells]
+            qv = qs[a]
             rng_ = qv.max(axis=1) - qv.min(axis=1)
             mag = np.abs(qv).max(axis=1)
             # every input carries its FP32 rounding residue: ~2^-48 of its magnitude
@@ -153,13 +186,10 @@ def fp32_sensitive(orc, pr, f, W, d):
     u_d, p) varies by less than 1e-10 of its magnitude: there even the
     residue-carrying FP32 inputs of the gate (2^-48 of the magnitude) visibly
     round the normalised features (oracle values only)."""
-    Vc = np.stack([orc.prim_cell(f, W[:, c])[0] for c in range(pr.ncells)], axis=1)
-    rho = W[:pr.N].sum(axis=0)
-    cells = _node_cells(pr, d, np.arange(face_counts(pr)[d]))
-    sens = np.zeros(cells.shape[0], dtype=bool)
-    alphas = [Vc[pr.N + pr.D + 1 + k] for k in range(min(pr.N - 1, 2))]
-    for q in alphas + [rho, Vc[pr.N + d], Vc[pr.N + pr.D]]:
-        qv = q[cells]
+    sens = np.zeros(face_counts(pr)[d], dtype=bool)
+    for qv in _stencil_inputs(orc, pr, f, W, d):
+        if qv is None:
+            continue
         r = qv.max(axis=1) - qv.min(axis=1)
         sens |= (r > 0) & (r < 1e-10 * np.abs(qv).max(axis=1))
     return sens
@@ -171,13 +201,10 @@ def fp32_level(orc, pr, f, W, d):
     the last place) or stays below the smallest normal float (a velocity of
     1e-51 rounds to 0): the stencils whose FP32 planes can all be equal, which
     the precision form's sweep takes as uniform (oracle values only)."""
-    Vc = np.stack([orc.prim_cell(f, W[:, c])[0] for c in range(pr.ncells)], axis=1)
-    rho = W[:pr.N].sum(axis=0)
-    cells = _node_cells(pr, d, np.arange(face_counts(pr)[d]))
-    flat = np.ones(cells.shape[0], dtype=bool)
-    alphas = [Vc[pr.N + pr.D + 1 + k] for k in range(min(pr.N - 1, 2))]
-    for q in alphas + [rho, Vc[pr.N + d], Vc[pr.N + pr.D]]:
-        qv = q[cells]
+    flat = np.ones(face_counts(pr)[d], dtype=bool)
+    for qv in _stencil_inputs(orc, pr, f, W, d):
+        if qv is None:
+            continue
         mag = np.abs(qv).max(axis=1)
         flat &= ((qv.max(axis=1) - qv.min(axis=1)) <= 2.0 ** -21 * mag) | (mag < 2.0 ** -126)
     return flat

@@ -224,6 +224,77 @@ def test_hllc_equal_states_give_physical_flux(orc):
         assert s == pytest.approx(un, rel=1e-13)
 
 
+def test_uniform_stencil_face_is_the_physical_flux(orc):
+    """App. C, Sec. 4.1.1, Eqs. reconstructed_G and G_pm, Sec. 4.3.2: a midpoint whose
+    six node states are equal, evaluated step by step (projection, WENO-IS, both
+    positivity limiters, two HLLC solves, HCS, sensor blend and flux limiter -- the
+    single-face entry point always evaluates them all), returns the node's physical
+    flux F^d in the conservative slots and zero in the alpha slots of both G^- and
+    G^+, to rounding. The grid sweeps take that flux directly at bit-identical
+    stencils; this pins the shortcut to the full evaluation."""
+    params = orc.make_params()
+    for fl, D, seed in (([P.BENCH_WATER, P.BENCH_AIR, P.BENCH_HELIUM], 2, 5),
+                        ([P.PAPER_WATER, P.PAPER_AIR], 3, 6)):
+        N = len(fl)
+        f = _fluid(orc, fl, D=D)
+        prim, _ = P.random_admissible_states(N, D, 24, seed=seed, fluids=fl)
+        W = orc.ic_from_prim(f, prim)
+        worst = 0.0
+        for c in range(W.shape[1]):
+            Wn = W[:, c]
+            V, o = orc.prim_cell(f, Wn)
+            p = V[N + D]
+            for d in range(D):
+                un = V[N + d]
+                a = abs(un) + o["c"]
+                lam = 0.4 / a
+                Gm, Gp, _ = orc.face(f, params, d, lam, np.stack([Wn] * 6))
+                F = np.zeros_like(Wn)
+                F[:N + D + 1] = Wn[:N + D + 1] * un
+                F[N + d] += p
+                F[N + D] += p * un
+                rho = Wn[:N].sum()
+                scale = np.concatenate([Wn[:N] * a, np.full(D, rho * a * a + p),
+                                        [(abs(Wn[N + D]) + p) * a], np.full(N - 1, a)])
+                for G in (Gm, Gp):
+                    err = np.abs(G - F) / scale
+                    worst = max(worst, err.max())
+        assert worst < 1e-12, worst
+
+
+def test_grid_sweep_matches_the_full_face_evaluation(orc):
+    """Eq. semi_W_G_pm_eqn: the grid right-hand side, whose sweep takes the physical
+    flux directly at bit-identical stencils, equals -(G^-_{i+1/2} - G^+_{i-1/2}) / dx
+    assembled from the single-face entry point (every step evaluated) to rounding.
+    On the gas/liquid shock tube after a step the uniform regions on both sides of
+    the waves meet non-uniform stencils, so cells with one face of each kind are
+    checked too."""
+    pr = P.shock_tube_1d_paper(120)
+    f, g, W = orc.setup(pr)
+    p = orc.make_params()
+    dt, _ = orc.dt(f, g, W, 0.4)
+    W = orc.step(f, p, g, W, dt, 1)
+    lam = dt / g.dx[0]
+    R = orc.rhs(f, p, g, W, [lam])
+    n, N, D = W.shape[1], f.N, 1
+    Gm, Gp, uni = {}, {}, {}
+    for fc in range(3, n - 2):  # face fc lies between cells fc-1 and fc
+        W6 = np.ascontiguousarray(W[:, fc - 3:fc + 3].T)
+        Gm[fc], Gp[fc], _ = orc.face(f, p, 0, lam, W6)
+        uni[fc] = bool((W6 == W6[2]).all())
+    mixed = 0
+    for i in range(3, n - 3):
+        Rf = -(Gm[i + 1] - Gp[i]) / g.dx[0]
+        Vc, o = orc.prim_cell(f, W[:, i])
+        a = abs(Vc[N]) + o["c"]
+        pc, rho = Vc[N + D], W[:N, i].sum()
+        scale = np.concatenate([np.full(N, rho * a), np.full(D, rho * a * a + pc),
+                                [(abs(W[N + D, i]) + pc) * a], np.full(N - 1, a)]) / g.dx[0]
+        assert (np.abs(R[:, i] - Rf) <= 1e-12 * scale).all(), (i, (R[:, i] - Rf) / scale)
+        mixed += uni[i] != uni[i + 1]
+    assert sum(uni.values()) > 20 and mixed >= 2, (sum(uni.values()), mixed)
+
+
 def test_hllc_resolves_isolated_contact(orc):
     """Equal p and u, different composition: HLLC is exact for a contact, so
     s_* = u and the flux is the upwind (left) physical flux."""
