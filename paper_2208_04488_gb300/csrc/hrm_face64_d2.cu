@@ -18,8 +18,8 @@ void face_l(int precision, const double* W, const double* V, const double* AUX, 
       face32_d2(N, DIR, W, V, AUX, P32, out, g, f, p, st, gate, s);
       return;
     }
-    const long long nf = (g.n[0] + (DIR == 0)) * (g.n[1] + (DIR == 1)) * (g.n[2] + (DIR == 2));
-    k_face<double, N, kD, DIR><<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(W, V, AUX, out, g, f, p, st, gate.fixed);
+    k_face<double, N, kD, DIR><<<lane_patch_grid(g, DIR), kFaceThreads, 0, s>>>(W, V, AUX, out, g, f, p, st,
+                                                                                gate.fixed);
   }
 }
 

@@ -614,12 +614,33 @@ __device__ __forceinline__ void face_body(int64_t t, const Nodes6& nd, const dou
   }
 }
 
+// Midpoint of this thread in a sweep of a 2D or 3D grid launched over
+// lane_patch_grid blocks: a block takes 32 x 4 midpoints (along x, then y; z
+// from the block index) and each warp an 8 x 4 patch of them. Uniform and
+// non-uniform stencils come in bands a few midpoints wide along the material
+// interfaces and wave fronts; a warp of 32 midpoints along one row crossing such
+// a band holds a few non-uniform lanes, which run the whole midpoint body, and
+// an 8 x 4 patch holds more of the band and fewer idle lanes. Past the end of
+// the grid: the midpoint count (no midpoint).
+template <int DIR>
+__device__ __forceinline__ int64_t lane_patch_midpoint(const DevGrid& g) {
+  static_assert(kFaceThreads == 128, "four warps per block");
+  const int64_t f0 = g.n[0] + (DIR == 0), f1 = g.n[1] + (DIR == 1), f2 = g.n[2] + (DIR == 2);
+  const int64_t nbx = (f0 + 31) / 32, nby = (f1 + 3) / 4, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i0 = (b % nbx) * 32 + w * 8 + (lane & 7);
+  const int64_t i1 = ((b / nbx) % nby) * 4 + (lane >> 3);
+  const int64_t i2 = b / (nbx * nby);
+  if (i0 >= f0 || i1 >= f1 || i2 >= f2) return f0 * f1 * f2;
+  return (i2 * f1 + i1) * f0 + i0;
+}
+
 template <typename R, int N, int D, int DIR>
 __global__ void __launch_bounds__(kFaceThreads)
     k_face(const double* __restrict__ W, const double* __restrict__ V, const double* __restrict__ AUX,
            double* __restrict__ out, DevGrid g, DevFluid f, DevParams pr, const StepState* __restrict__ st,
            const uint8_t* __restrict__ gate) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = D >= 2 ? lane_patch_midpoint<DIR>(g) : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Nodes6 nd;
   if (!face_nodes<DIR>(g, t, nd)) return;
   const bool lin = gate != nullptr && gate[t] != 0;

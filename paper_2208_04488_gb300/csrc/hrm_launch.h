@@ -151,6 +151,13 @@ inline unsigned patch_grid(const DevGrid& g, int dir) {
   return (unsigned)(dir == 1 ? nbx * ((f1 + 3) / 4) * f2 : nbx * f1 * ((f2 + 3) / 4));
 }
 
+// Blocks of kFaceThreads covering the midpoints of direction dir of a 2D or 3D
+// grid in the layout of lane_patch_midpoint (32 x 4 midpoints per block).
+inline unsigned lane_patch_grid(const DevGrid& g, int dir) {
+  const long long f0 = g.n[0] + (dir == 0), f1 = g.n[1] + (dir == 1), f2 = g.n[2] + (dir == 2);
+  return (unsigned)(((f0 + 31) / 32) * ((f1 + 3) / 4) * f2);
+}
+
 // Smallest float not below x (thresholds of the FP32 screens).
 inline float float_up(double x) {
   float f = (float)x;
