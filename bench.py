@@ -786,13 +786,13 @@ def main():
                                       "peak_fp64": fp64_peak / 1e12,
                                       "avg_launch_ms": 1e3 * tf32 / n32, "kernel_time_share": share32,
                                       "traffic": TRAFFIC_BYTES["k_face32"],
-                                      "flops_counted": "the method as written at every midpoint, including "
-                                                       "the uniform stencils the sweep finishes exactly "
-                                                       "without that arithmetic: not a measure of pipe use "
-                                                       "(ncu: FMA pipe 13-14 %)",
+                                      "flops_counted": "the oracle's count over the timed states, as for the "
+                                                       "FP64 sweep: the method's arithmetic at non-uniform "
+                                                       "midpoints, the node flux at uniform ones (the sweep "
+                                                       "takes that flux where its FP32 planes are uniform); "
+                                                       "the sweep is bound by the latency of its non-uniform "
+                                                       "warps, not by the FP32 pipe (ncu: FMA pipe 13-14 %)",
                                       "uniform_share": uni,
-                                      "frac_of_fp32_peak_nonuniform_midpoints": (
-                                          None if uni is None else ach32 * (1.0 - uni) / fp32_peak),
                                       "hbm": {"compulsory_bytes_per_launch": bytes32,
                                               "achieved_gbs": bytes32 / (tf32 / n32) / 1e9,
                                               "peak_gbs": pk.get("hbm_gbs"),
