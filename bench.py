@@ -639,15 +639,16 @@ def main():
     from paper_2208_04488_gb300.replicas import whole_job_rate
     value, t_max = whole_job_rate(pr.ncells * args.steps, t_dev, dist, device="cuda")
 
-    # end-to-end through the public API with host buffers, on every rank: per
-    # step the state is uploaded from pinned host memory, advanced one step and
-    # read back.
-    Wh = torch.from_numpy(W_fp64.copy()).pin_memory()
-    Wout = torch.empty_like(Wh).pin_memory()
+    # end-to-end through the public API with host buffers, on every rank: the
+    # same steps from the initial condition, the state living in pinned host
+    # memory; per step it is uploaded, advanced one step and read back into the
+    # host state the next step uploads.
+    s.set_primitive(pr.prim)
+    Wh = torch.from_numpy(s.get(hrm.FIELD_W)).pin_memory()
     Wdev = torch.empty(Wh.shape, dtype=torch.float64, device="cuda")
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    K_e2e = max(3, args.steps // 2)
+    K_e2e = args.steps
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -657,7 +658,7 @@ def main():
         s.set(Wdev)
         s.step(0.0, 1)
         s.get(hrm.FIELD_W, out=Wdev)
-        Wout.copy_(Wdev, non_blocking=True)
+        Wh.copy_(Wdev, non_blocking=True)
     e1.record(stream)
     e1.synchronize()
     t_e2e = e0.elapsed_time(e1) * 1e-3
