@@ -47,6 +47,7 @@ struct hrm_ctx {
   StepState* st = nullptr;
   mlp::GateBlob* blob = nullptr;   // learned gate weights (hrm_set_detector)
   uint8_t* gate[3] = {nullptr, nullptr, nullptr};  // gate bytes per direction (midpoint grids)
+  uint8_t* same = nullptr;         // FP64 form: per cell, the last update left W bit for bit as its source
   uint32_t* defer = nullptr;       // precision form: per direction, a worklist of deferred midpoints and its counter
   int64_t defer_cap = 0;           // worklist entries (the largest midpoint grid; 0: no worklist)
   hrm_alloc_fn alloc = nullptr;    // device memory source (hrm_set_allocator at creation; NULL: cudaMalloc)
@@ -284,8 +285,13 @@ bool fuse_last(const hrm_ctx* c) {
 // Precision form: the update of every stage but the last also writes the next
 // stage's FP32 planes (k_update32p, fuse_next), and a stage whose planes were
 // written so (prim_done) skips its primitive kernel.
+// FP64 form within one step: same_out, the update marks the cells whose state it
+// leaves bit for bit as in Wsrc; same_in, the primitive pass keeps those cells'
+// primitives (the previous stage's update marked them, nothing wrote W since).
 int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, double a, double b, int relax,
-                  int count, bool first, bool prim_done = false, bool fuse_next = false, bool tau_next = false) {
+                  int count, bool first, bool prim_done = false, bool fuse_next = false, bool tau_next = false,
+                  bool same_in = false, bool same_out = false) {
+  uint8_t* same = c->params.precision == HRM_FP64 ? c->same : nullptr;
   int k = 0;
   float* p32 = p32_target(c);
   if (!prim_done) {
@@ -293,7 +299,8 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
       if (c->params.precision == HRM_FP32)
         launch_prim32(c->N, c->D, Wsrc, c->P32, r32_target(c), c->dg, c->fl, c->st, first ? tau_mode(c) : 0, s);
       else
-        c->ck->prim(Wsrc, c->V, c->AUX, p32, r32_target(c), c->dg, c->fl, c->st, first ? tau_mode(c) : 0, s);
+        c->ck->prim(Wsrc, c->V, c->AUX, p32, r32_target(c), c->dg, c->fl, c->st, first ? tau_mode(c) : 0,
+                    same_in && !first ? same : nullptr, s);
     });
     ++k;
   }
@@ -345,7 +352,7 @@ int enqueue_stage(hrm_ctx* c, cudaStream_t s, const double* Wsrc, double* Wout, 
                        count, c->P32, r32_target(c), s, tau_next ? 1 : 0);
     else
       c->fk->update(0, c->params.precision == HRM_FP32, c->Wn, Wsrc, Wout, c->F[0], c->F[1], c->F[2], c->dg,
-                    c->fl, c->st, a, b, relax, count, s);
+                    c->fl, c->st, a, b, relax, count, same_out ? same : nullptr, s);
   });
   ++k;
   return k;
@@ -365,13 +372,13 @@ int enqueue_step(hrm_ctx* c, cudaStream_t s) {
       k += enqueue_stage(c, s, c->Wn, c->Wn, 0.0, 1.0, rf, ck, true, false, fl, fl);
       break;
     case HRM_RK2:
-      k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true, false, fp32);
-      k += enqueue_stage(c, s, c->Ws, c->Wn, 0.5, 0.5, rf, ck, false, fp32, fl, fl);
+      k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true, false, fp32, false, false, true);
+      k += enqueue_stage(c, s, c->Ws, c->Wn, 0.5, 0.5, rf, ck, false, fp32, fl, fl, true, false);
       break;
     default:
-      k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true, false, fp32);
-      k += enqueue_stage(c, s, c->Ws, c->Ws, 0.75, 0.25, rs, 0, false, fp32, fp32);
-      k += enqueue_stage(c, s, c->Ws, c->Wn, 1.0 / 3.0, 2.0 / 3.0, rf, ck, false, fp32, fl, fl);
+      k += enqueue_stage(c, s, c->Wn, c->Ws, 0.0, 1.0, rs, 0, true, false, fp32, false, false, true);
+      k += enqueue_stage(c, s, c->Ws, c->Ws, 0.75, 0.25, rs, 0, false, fp32, fp32, false, true, true);
+      k += enqueue_stage(c, s, c->Ws, c->Wn, 1.0 / 3.0, 2.0 / 3.0, rf, ck, false, fp32, fl, fl, true, false);
       break;
   }
   return k;
@@ -738,6 +745,7 @@ hrm_status hrm_create(hrm_ctx** out, const hrm_grid* grid, int32_t N, const doub
     if ((s = cuda_check(c, ctx_malloc(c, &c->F[d], sizeof(double) * nf * (M + N - 1)), "alloc faces"))) return bail(s);
     if ((int64_t)nf > c->defer_cap) c->defer_cap = (int64_t)nf;
   }
+  if ((s = cuda_check(c, ctx_malloc(c, &c->same, (size_t)c->nc), "alloc unchanged-cell flags"))) return bail(s);
   // worklist of the precision form's deferred midpoints (32-bit entries; none
   // beyond 2^32 - 1 midpoints, where the sweep keeps its fallbacks inline)
   if (c->defer_cap < (int64_t)0xffffffffll) {
@@ -783,6 +791,7 @@ void hrm_destroy(hrm_ctx* c) {
   drop_graph(c);
   ctx_free(c, c->Wn);
   ctx_free(c, c->Ws);
+  ctx_free(c, c->same);
   ctx_free(c, c->defer);
   ctx_free(c, c->V);
   ctx_free(c, c->AUX);
@@ -955,7 +964,7 @@ hrm_status hrm_dt(hrm_ctx* c, double cfl, double* dt_out, double* tau_out) {
   if (!c || !(cfl > 0.0)) return c ? fail(c, HRM_E_INVAL, "cfl must be positive") : HRM_E_INVAL;
   planes_stale(c);
   if (hrm_status s = check_boundaries(c)) return s;
-  c->ck->prim(c->Wn, c->V, c->AUX, nullptr, nullptr, c->dg, c->fl, c->st, tau_mode(c), c->stream);
+  c->ck->prim(c->Wn, c->V, c->AUX, nullptr, nullptr, c->dg, c->fl, c->st, tau_mode(c), nullptr, c->stream);
   launch_finalize(c->st, c->dg, c->D, cfl, 1, c->stream);
   c->launches += 2;
   StepState h;
@@ -1033,7 +1042,8 @@ hrm_status hrm_step_tau(hrm_ctx* c, double* tau) {
   if (c->params.precision == HRM_FP32)
     launch_prim32(c->N, c->D, c->Wn, c->P32, r32_target(c), c->dg, c->fl, c->st, tau_mode(c), c->stream);
   else
-    c->ck->prim(c->Wn, c->V, c->AUX, p32_target(c), r32_target(c), c->dg, c->fl, c->st, tau_mode(c), c->stream);
+    c->ck->prim(c->Wn, c->V, c->AUX, p32_target(c), r32_target(c), c->dg, c->fl, c->st, tau_mode(c), nullptr,
+                c->stream);
   ++c->launches;
   unsigned long long bits[3] = {0ull, 0ull, 0ull};
   if ((s = cuda_check(c, cudaMemcpyAsync(bits, c->st->tau_bits, sizeof bits, cudaMemcpyDeviceToHost, c->stream),
@@ -1162,7 +1172,7 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
   if (c->params.precision == HRM_FP32)
     launch_prim32(c->N, c->D, c->Wn, c->P32, r32_target(c), c->dg, c->fl, c->st, 0, c->stream);
   else
-    c->ck->prim(c->Wn, c->V, c->AUX, p32_target(c), r32_target(c), c->dg, c->fl, c->st, 0, c->stream);
+    c->ck->prim(c->Wn, c->V, c->AUX, p32_target(c), r32_target(c), c->dg, c->fl, c->st, 0, nullptr, c->stream);
   for (int d = 0; d < c->D; ++d) {
     if (separate_gate(c)) {
       launch_gate(c->N, c->D, d, c->P32, c->R32, c->dg, c->blob, gate_logit_threshold(c), c->gate[d],
@@ -1173,7 +1183,7 @@ hrm_status hrm_rhs(hrm_ctx* c, const double* lam, double* rhs) {
                    gate_of(c, d), c->stream);
   }
   c->fk->update(1, 0, c->Wn, c->Wn, out, c->F[0], c->F[1], c->F[2], c->dg, c->fl, c->st, 0.0, 1.0, 0, 0,
-                c->stream);
+                nullptr, c->stream);
   c->launches += 2 + c->D * sweep_kernels(c);
   if ((s = last_launch(c, "rhs"))) return s;
   // (the update writes interior cells only: the stage state's slices stay)

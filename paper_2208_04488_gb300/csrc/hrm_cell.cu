@@ -37,8 +37,9 @@ namespace {
 
 template <int N, int D>
 void prim_l(const double* W, double* V, double* AUX, float* P32, float* R32, const DevGrid& g, const DevFluid& f,
-            StepState* st, int tau, cudaStream_t s) {
-  k_prim<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, V, AUX, P32, R32, g, f, st, tau);
+            StepState* st, int tau, const uint8_t* same, cudaStream_t s) {
+  k_prim<N, D><<<grid_for(g.ncells, kCellThreads), kCellThreads, 0, s>>>(W, V, AUX, P32, R32, g, f, st, tau,
+                                                                          tau ? nullptr : same);
 }
 template <int N, int D>
 void ic_l(const double* prim, double* W, const DevGrid& g, const DevFluid& f, int64_t c0, int64_t c1,

@@ -177,15 +177,20 @@ __device__ __forceinline__ void block_tau_max(const double* s, unsigned long lon
   __syncthreads();  // red is reused by the next call in a persistent loop
 }
 
+// same (nullable, only without the CFL maxima): one byte per interior cell, set
+// where the last update left the cell's state bit for bit as it was in the
+// source whose primitives V, AUX (and P32, R32) already hold -- those are kept.
 template <int N, int D>
 __global__ void __launch_bounds__(kCellThreads)
     k_prim(const double* __restrict__ W, double* __restrict__ V, double* __restrict__ AUX,
-           float* __restrict__ P32, float* __restrict__ R32, DevGrid g, DevFluid f, StepState* st, int tau) {
+           float* __restrict__ P32, float* __restrict__ R32, DevGrid g, DevFluid f, StepState* st, int tau,
+           const uint8_t* __restrict__ same) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double s[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) s[d] = 0.0;
-  if (c < g.ncells) prim_body<N, D>(c, W, V, AUX, P32, R32, g, f, s, tau == 2);
+  const bool kept = same != nullptr && c < g.nint && same[c] != 0;
+  if (c < g.ncells && !kept) prim_body<N, D>(c, W, V, AUX, P32, R32, g, f, s, tau == 2);
   if (!tau) return;
   block_tau_max<D>(s, st->tau_bits);
 }

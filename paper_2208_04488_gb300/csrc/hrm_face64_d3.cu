@@ -26,7 +26,7 @@ void face_l(int precision, const double* W, const double* V, const double* AUX, 
 template <int N>
 void update_l(int mode, int fast, const double* Wn, const double* Wsrc, double* Wout, const double* F0,
               const double* F1, const double* F2, const DevGrid& g, const DevFluid& f, StepState* st, double a,
-              double b, int relax, int count, cudaStream_t s) {
+              double b, int relax, int count, uint8_t* same, cudaStream_t s) {
   if (fast && mode == 0) {
     update32_d3(N, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count, s);
     return;
@@ -35,7 +35,8 @@ void update_l(int mode, int fast, const double* Wn, const double* Wsrc, double* 
   if (mode == 1)
     k_update<N, kD, 1><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count);
   else
-    k_update<N, kD, 0><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count);
+    k_update<N, kD, 0><<<gr, kCellThreads, 0, s>>>(Wn, Wsrc, Wout, F0, F1, F2, g, f, st, a, b, relax, count,
+                                                   same);
 }
 
 template <int N>

@@ -903,7 +903,8 @@ template <int N, int D, int MODE, bool FAST = false>
 __device__ __forceinline__ void update_body(int64_t c, const double* Wn, const double* Wsrc, double* Wout,
                                             const double* __restrict__ F0, const double* __restrict__ F1,
                                             const double* __restrict__ F2, const DevGrid& g, const DevFluid& f,
-                                            StepState* st, double dt, double a, double b, int relax, int count) {
+                                            StepState* st, double dt, double a, double b, int relax, int count,
+                                            uint8_t* __restrict__ same = nullptr) {
   using L = Lay<N, D>;
   constexpr int M = L::M;
   const int64_t nc = g.ncells;
@@ -991,6 +992,13 @@ __device__ __forceinline__ void update_body(int64_t c, const double* Wn, const d
     relax_cell<N, D, FAST>(Wo, f);
   }
   if (count) count_bits(st, admissibility_bits<N, D>(Wo, f));
+  if (same) {
+    // the next stage's primitive pass keeps this cell's V and AUX where W_out is W_src
+    bool eq = true;
+#pragma unroll
+    for (int m = 0; m < M; ++m) eq = eq & (__double_as_longlong(Wo[m]) == __double_as_longlong(Ws[m]));
+    same[c] = eq ? 1 : 0;
+  }
 #pragma unroll
   for (int m = 0; m < M; ++m) Wout[m * nc + c] = Wo[m];
 }
@@ -999,11 +1007,11 @@ template <int N, int D, int MODE, bool FAST = false>
 __global__ void __launch_bounds__(kCellThreads)
     k_update(const double* Wn, const double* Wsrc, double* Wout, const double* __restrict__ F0,
              const double* __restrict__ F1, const double* __restrict__ F2, DevGrid g, DevFluid f,
-             StepState* st, double a, double b, int relax, int count) {
+             StepState* st, double a, double b, int relax, int count, uint8_t* __restrict__ same = nullptr) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.nint) return;
   update_body<N, D, MODE, FAST>(c, Wn, Wsrc, Wout, F0, F1, F2, g, f, st, MODE == 1 ? 0.0 : st->dt, a, b, relax,
-                                count);
+                                count, same);
 }
 
 }  // namespace hrm

@@ -14,8 +14,10 @@ namespace hrm {
 struct CellKernels {
   // P32 (nullable): FP32 planes for the precision form; R32 (nullable): FP32
   // rounding residues of rho, u_d, p for the learned gate
+  // same (nullable; ignored with tau): per interior cell, nonzero where W is bit
+  // for bit the state V, AUX, P32, R32 were computed from -- those cells are kept
   void (*prim)(const double* W, double* V, double* AUX, float* P32, float* R32, const DevGrid&, const DevFluid&,
-               StepState*, int tau, cudaStream_t);
+               StepState*, int tau, const uint8_t* same, cudaStream_t);
   void (*ic)(const double* prim, double* W, const DevGrid&, const DevFluid&, int64_t c0, int64_t c1, cudaStream_t);
   void (*relax)(double* W, const DevGrid&, const DevFluid&, cudaStream_t);
   void (*fields)(const double* W, double* out, int field, const DevGrid&, const DevFluid&, cudaStream_t);
@@ -69,10 +71,12 @@ struct FaceKernels {
   void (*face[3])(int precision, const double* W, const double* V, const double* AUX, const float* P32,
                   double* out, const DevGrid&, const DevFluid&, const DevParams&, const StepState*,
                   const GateArgs& gate, cudaStream_t);
-  // mode 0: RK combination, mode 1: write the RHS; fast: precision-form variant
+  // mode 0: RK combination, mode 1: write the RHS; fast: precision-form variant;
+  // same (nullable; FP64 RK combination): per interior cell, set to 1 where
+  // W_out equals W_src bit for bit, else 0
   void (*update)(int mode, int fast, const double* Wn, const double* Wsrc, double* Wout, const double* F0,
                  const double* F1, const double* F2, const DevGrid&, const DevFluid&, StepState*, double a,
-                 double b, int relax, int count, cudaStream_t);
+                 double b, int relax, int count, uint8_t* same, cudaStream_t);
 };
 
 const CellKernels* cell_kernels(int N, int D);

@@ -763,7 +763,7 @@ hrm_status hrm_detector_collect(hrm_detector* d, hrm_ctx* ctx, double delta, dou
   if ((s = ctx_view(ctx, &c))) return dfail(d, s, "context not usable");
   cudaStream_t st = c.stream;
   // primitives and FP32 planes of the context's current state
-  c.ck->prim(c.Wn, c.V, c.AUX, c.P32, c.R32, c.dg, c.fl, c.st, 0, st);
+  c.ck->prim(c.Wn, c.V, c.AUX, c.P32, c.R32, c.dg, c.fl, c.st, 0, nullptr, st);
   ctx_add_launches(ctx, 1);
   int64_t before = d->size;
   for (int dir = 0; dir < c.D; ++dir) {
