@@ -295,6 +295,53 @@ def test_grid_sweep_matches_the_full_face_evaluation(orc):
     assert sum(uni.values()) > 20 and mixed >= 2, (sum(uni.values()), mixed)
 
 
+def test_grid_sweep_matches_the_full_face_evaluation_2d(orc):
+    """As above in 2D, where each direction's flux takes that direction's velocity and
+    puts p in that direction's momentum slot: on the three-species shock-bubble after
+    one step (128 x 64), the grid right-hand side of every cell three cells from the sides equals
+    -sum_d (G^-_{d,+1/2} - G^+_{d,-1/2}) / dx_d assembled from fully evaluated faces of
+    both directions, with uniform and non-uniform stencils meeting in both."""
+    pr = P.shock_bubble_2d(128, 64)
+    f, g, W = orc.setup(pr)
+    p = orc.make_params()
+    dt, _ = orc.dt(f, g, W, pr.cfl)
+    W = orc.step(f, p, g, W, dt, 1)
+    lam = orc.lambdas(f, g, W, dt)
+    R = orc.rhs(f, p, g, W, lam)
+    nx, ny = pr.n
+    N, D = f.N, 2
+
+    faces = {}
+
+    def face(d, i, j):  # face between cells (i-1, j) and (i, j) for d = 0, (i, j-1) and (i, j) for d = 1
+        if (d, i, j) not in faces:
+            idx = [j * nx + (i + k) for k in range(-3, 3)] if d == 0 else [(j + k) * nx + i for k in range(-3, 3)]
+            W6 = np.ascontiguousarray(W[:, idx].T)
+            Gm, Gp, _ = orc.face(f, p, d, lam[d], W6)
+            faces[(d, i, j)] = (Gm, Gp, bool((W6 == W6[2]).all()))
+        return faces[(d, i, j)]
+
+    mixed = [0, 0]
+    uniform = [0, 0]
+    for j in range(3, ny - 3):
+        for i in range(3, nx - 3):
+            c = j * nx + i
+            Rf = np.zeros(W.shape[0])
+            for d in range(D):
+                lo = face(d, i, j)
+                hi = face(d, i + 1, j) if d == 0 else face(d, i, j + 1)
+                Rf = Rf - (hi[0] - lo[1]) / g.dx[d]
+                mixed[d] += lo[2] != hi[2]
+                uniform[d] += lo[2]
+            Vc, o = orc.prim_cell(f, W[:, c])
+            a = abs(Vc[N]) + abs(Vc[N + 1]) + o["c"]
+            pc, rho = Vc[N + D], W[:N, c].sum()
+            scale = np.concatenate([np.full(N, rho * a), np.full(D, rho * a * a + pc),
+                                    [(abs(W[N + D, c]) + pc) * a], np.full(N - 1, a)]) / min(g.dx[:D])
+            assert (np.abs(R[:, c] - Rf) <= 1e-12 * scale).all(), (i, j, (R[:, c] - Rf) / scale)
+    assert min(uniform) > 100 and min(mixed) >= 4, (uniform, mixed)
+
+
 def test_hllc_resolves_isolated_contact(orc):
     """Equal p and u, different composition: HLLC is exact for a contact, so
     s_* = u and the flux is the upwind (left) physical flux."""
