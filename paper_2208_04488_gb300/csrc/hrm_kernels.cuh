@@ -948,18 +948,22 @@ __device__ __forceinline__ void update_body(int64_t c, const double* Wn, const d
     const int64_t fl = HRM_IDX(g, (i2 * f1 + i1) * f0 + i0, nf);
     const int64_t fr = HRM_IDX(g, fl + (d == 0 ? 1 : (d == 1 ? f0 : f0 * f1)), nf);
     const double dx = g.dx[d], idx = g.inv_dx[d];
+    // where dx is a power of two (a significand field of zero), 1/dx is exact and
+    // df / dx and df * (1/dx) are the same correctly rounded number: the product
+    // then stands for the quotient at no change of any result
+    const bool scale = FAST || (__double_as_longlong(dx) & 0xFFFFFFFFFFFFFll) == 0;
     // G^-_{i+1/2} - G^+_{i-1/2}: the alpha slots of the right face use alpha_i
     // (planes AL..), those of the left face alpha_i as its right neighbour (planes M..)
 #pragma unroll
     for (int m = 0; m < L::NC; ++m) {
       const double df = F[m * nf + fr] - F[m * nf + fl];
-      rhs[m] = rhs[m] - (FAST ? df * idx : df / dx);
+      rhs[m] = rhs[m] - (scale ? df * idx : df / dx);
     }
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) {
       const int m = L::AL + k;
       const double df = F[m * nf + fr] - F[(M + k) * nf + fl];
-      rhs[m] = rhs[m] - (FAST ? df * idx : df / dx);
+      rhs[m] = rhs[m] - (scale ? df * idx : df / dx);
     }
   }
   if (MODE == 1) {
