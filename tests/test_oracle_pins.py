@@ -342,6 +342,55 @@ def test_grid_sweep_matches_the_full_face_evaluation_2d(orc):
     assert min(uniform) > 100 and min(mixed) >= 4, (uniform, mixed)
 
 
+def test_grid_sweep_matches_the_full_face_evaluation_3d(orc):
+    """As above in 3D: a water sphere in moving air (u = (40, -25, 15) m/s, uniform p
+    and T, 16^3 cells, the sphere's surface a jump), where every direction has
+    uniform and non-uniform stencils side by side; the grid right-hand side of every
+    cell three cells from the sides equals the one assembled from fully evaluated faces
+    of all three directions."""
+    n = 16
+    f = _fluid(orc, [P.PAPER_WATER, P.PAPER_AIR], D=3)
+    x = np.arange(n) + 0.5
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    inside = ((X - 8.2) ** 2 + (Y - 7.9) ** 2 + (Z - 8.1) ** 2 < 4.0 ** 2).ravel()
+    nc = n ** 3
+    prim = np.stack([np.where(inside, 1.0 - 1e-8, 1e-8), np.full(nc, 40.0), np.full(nc, -25.0),
+                     np.full(nc, 15.0), np.full(nc, 1.0e5), np.full(nc, 300.0)])
+    W = orc.ic_from_prim(f, prim)
+    g = orc.make_grid([n, n, n], [1e-3, 1e-3, 1e-3])
+    p = orc.make_params()
+    lam = [2e-4, 2e-4, 2e-4]
+    R = orc.rhs(f, p, g, W, lam)
+    N, D = f.N, 3
+    stride = [1, n, n * n]
+    faces = {}
+
+    def face(d, c):  # face of direction d between cell c - stride[d] and cell c
+        if (d, c) not in faces:
+            W6 = np.ascontiguousarray(W[:, [c + k * stride[d] for k in range(-3, 3)]].T)
+            Gm, Gp, _ = orc.face(f, p, d, lam[d], W6)
+            faces[(d, c)] = (Gm, Gp, bool((W6 == W6[2]).all()))
+        return faces[(d, c)]
+
+    mixed = [0, 0, 0]
+    for k in range(3, n - 3):
+        for j in range(3, n - 3):
+            for i in range(3, n - 3):
+                c = (k * n + j) * n + i
+                Rf = np.zeros(W.shape[0])
+                for d in range(D):
+                    lo, hi = face(d, c), face(d, c + stride[d])
+                    Rf = Rf - (hi[0] - lo[1]) / g.dx[d]
+                    mixed[d] += lo[2] != hi[2]
+                Vc, o = orc.prim_cell(f, W[:, c])
+                a = abs(Vc[N]) + abs(Vc[N + 1]) + abs(Vc[N + 2]) + o["c"]
+                pc, rho = Vc[N + D], W[:N, c].sum()
+                scale = np.concatenate([np.full(N, rho * a), np.full(D, rho * a * a + pc),
+                                        [(abs(W[N + D, c]) + pc) * a], np.full(N - 1, a)]) / g.dx[0]
+                assert (np.abs(R[:, c] - Rf) <= 1e-12 * scale).all(), (i, j, k, (R[:, c] - Rf) / scale)
+    assert min(mixed) >= 20, mixed
+
+
 def test_hllc_resolves_isolated_contact(orc):
     """Equal p and u, different composition: HLLC is exact for a contact, so
     s_* = u and the flux is the upwind (left) physical flux."""
