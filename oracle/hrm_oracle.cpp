@@ -22,7 +22,10 @@
 //   App. C           incremental-stencil WENO interpolation
 //   App. D           characteristic decomposition of the primitive variables
 // Where the paper is silent or ambiguous the reading taken is stated inline
-// (the same list is kept in the design notes).
+// (the same list is kept in the design notes). Where a step's exact-arithmetic
+// result is known in closed form it is taken directly, at the step itself: a
+// constant stencil interpolates to its value (App. C), and a midpoint of six
+// bit-identical node states gets the node's physical flux (face_flux).
 //
 // Built three times: normally (real == double); with -DOR_COUNT, where `real`
 // is a counting wrapper so that a run reports the algorithmic number of
