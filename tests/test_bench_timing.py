@@ -1,6 +1,7 @@
-"""Host logic of bench.py's kernel timing (no GPU): the concurrent sweeps of a
-stage are timed by their common bracket, shared among their launches, and the
-time shares leave out the sweeps' own (overlapping) brackets."""
+"""Host logic of bench.py (no GPU): the concurrent sweeps of a stage are timed
+by their common bracket, shared among their launches, and the time shares leave
+out the sweeps' own (overlapping) brackets; the method's flops per midpoint over
+a run are counted on its first and last state."""
 import os
 import sys
 
@@ -39,3 +40,28 @@ def test_without_a_sweeps_bracket_the_launches_add(mods):
     sh = bench.time_shares(hrm, per, 1)
     assert set(sh) == {"prim", "face_x", "update"}
     assert sum(sh.values()) == pytest.approx(1.0, abs=1e-3)
+
+
+def test_run_face_flops_means_the_first_and_last_state(mods):
+    """The method's flops per midpoint over a run are the mean of the oracle's
+    counts on the initial state and on the run's last state: a state with more
+    non-uniform stencils costs more (uniform stencils cost only the node flux)."""
+    bench, _ = mods
+    import oracle
+    from paper_2208_04488_gb300 import problems as P
+    pr = P.shock_bubble_2d(64, 32)
+    f, g, W0 = oracle.setup(pr)
+    same = bench.run_face_flops(pr, pr.cfl, W0)
+    first = bench.algorithmic_face_flops(pr, pr.cfl)
+    for d in range(pr.D):
+        assert same[d][0] == pytest.approx(first[d][0]) and same[d][1] == first[d][1]
+    p = oracle.make_params()
+    W = W0
+    for _ in range(3):
+        dt, _ = oracle.dt(f, g, W, pr.cfl)
+        W = oracle.step(f, p, g, W, dt, 1)
+    run = bench.run_face_flops(pr, pr.cfl, W)
+    last = bench.algorithmic_face_flops(pr, pr.cfl, W)
+    for d in range(pr.D):
+        assert run[d][0] == pytest.approx(0.5 * (first[d][0] + last[d][0]))
+        assert last[d][0] > first[d][0]
